@@ -1,0 +1,177 @@
+/*
+ * fmm_gb300.h -- C ABI of the GB300 (sm_103a) periodic fast multipole method
+ * for a net-charged cubic box neutralised by a uniform background charge
+ * (Urano, Shinoda, Yoshii & Okazaki, arXiv:2003.13218).
+ *
+ * Problem statement (Appendix A): N point charges q_i at r_i in a cubic unit
+ * cell of side b (volume V = b^3) under periodic boundary conditions, plus a
+ * uniform background charge of density -Q_C / V (Q_C = sum q_i), with the
+ * conducting boundary at infinity.  The energy evaluated is Eq. Velecfull:
+ *
+ *   V_elec = 1/2 sum_i q_i sum_{j in NF(i)} q_j / r_ij            (Eq. EqNF)
+ *          + 1/2 sum_i q_i sum_{n,m} L_n^m(l_max) R_n^m(r_i - r_L') (Eq. EqFF)
+ *          - pi Q_C^2 / (2 V kappa^2)                               (Eq. 6)
+ *          + (2 pi / 3V) Q_C sum_i q_i r_i^2                       (Eq. surfchargedend)
+ *          - (2 pi / 3V) mu . mu                                    (Appendix D)
+ *
+ * where the local coefficients L come from P2M (Eq. P2M), M2M, the level-0
+ * lattice sum over image cells (Eq. 12, with the self term 12c), M2L over each
+ * level's interaction list (Eq. Lcoeffdef) and L2L (Appendix B).
+ *
+ * Units: lengths in A, charges in e, energies in e^2/A (Gaussian units
+ * without 1/(4 pi eps0), Appendix A).  Multiply by 1389.35458 for kJ/mol.
+ *
+ * Conventions shared by every call
+ *  - All functions return fmm_status; nothing aborts, traps or exits.
+ *  - Position arrays are double[N][3] (x, y, z interleaved), charge arrays
+ *    double[N], membership arrays uint8_t[N] (1 = solute).  Pointers may be
+ *    device pointers (the fast path) or host pointers; host inputs are copied
+ *    to plan-owned device buffers inside the call and host outputs copied back.
+ *  - The caller owns every input and output buffer; the plan owns its scratch
+ *    memory, operator tables and stream binding.
+ *  - Work is enqueued on the plan's stream (default: the legacy default stream;
+ *    see FMM_OPT_STREAM).  Calls that return host scalars synchronise that
+ *    stream before returning.
+ *  - A plan is not thread-safe: use one plan per host thread or stream.
+ *  - Positions may lie outside [0, b); each atom is wrapped into the cell.
+ *  - Non-finite positions or charges yield FMM_ERR_NONFINITE (detected on the
+ *    device, reported after the call's kernels have finished).
+ */
+#ifndef FMM_GB300_H
+#define FMM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fmm_plan_s *fmm_plan;
+
+typedef enum {
+    FMM_OK = 0,
+    FMM_ERR_INVALID_ARG = 1, /* bad size, order, depth, pointer or option */
+    FMM_ERR_NONFINITE = 2,   /* NaN/Inf in positions or charges */
+    FMM_ERR_CUDA = 3,        /* a CUDA runtime call failed */
+    FMM_ERR_OOM = 4,         /* device or host allocation failed */
+    FMM_ERR_TIMEOUT = 5,     /* a bounded device wait ran out */
+    FMM_ERR_INTERNAL = 6,    /* a device-side consistency check failed */
+    FMM_ERR_UNSUPPORTED = 7  /* option value not built (e.g. ws != 1) */
+} fmm_status;
+
+/* Energy decomposition of Eq. Velecfull, e^2/A. */
+typedef struct {
+    double near;           /* first term: near-field pair sum (Eq. EqNF) */
+    double far;            /* second term: far field via local expansions (Eq. EqFF) */
+    double charged;        /* -pi Q_C^2 / (2 V kappa^2) (Eq. 6) */
+    double quad_surface;   /* +(2 pi / 3V) Q_C sum q_i r_i^2 (Eq. surfchargedend) */
+    double dipole_surface; /* -(2 pi / 3V) mu . mu (Appendix D) */
+    double total;          /* compensated sum of the five terms */
+} fmm_energy_terms;
+
+/* Parts of the reduced-far-field solute-solvent energy (Eq. FMMcalc). */
+typedef struct {
+    double e_uv;     /* NF_uv + W + bc_cross: interaction of (solute + its background)
+                        with (solvent + its background) */
+    double W;        /* far-field interaction, (A - B + C) / 2 */
+    double A;        /* sum_{i in u} q_i Phi_{u,v}^FF(r_i)  (full pass) */
+    double B;        /* sum_{i in u} q_i Phi_u^FF(r_i)      (solute-only pass) */
+    double C;        /* sum_{j in v} q_j Phi_u^FF(r_j)      (solute-only pass) */
+    double nf_uv;    /* near-field solute-solvent pair sum */
+    double bc_cross; /* -pi Q_u Q_v/(V kappa^2) + (2 pi/3V)(Q_u S2_v + Q_v S2_u)
+                        - (4 pi/3V) mu_u . mu_v */
+} fmm_uv_terms;
+
+/* Per-stage device times of the last call, milliseconds (CUDA events). */
+typedef struct {
+    float sort, upward, lattice, m2l, downward, l2p, p2p, reduce, total;
+} fmm_timings;
+
+/* Options for fmm_plan_set_option. */
+enum {
+    FMM_OPT_WS = 1,        /* well-separatedness; ival must be 1 (the only one built) */
+    FMM_OPT_PRECISION = 2, /* ival: FMM_PREC_FP64 (default) or FMM_PREC_MIXED */
+    FMM_OPT_KAPPA = 3,     /* dval: splitting parameter kappa of Eq. 12 and Eq. 6 in 1/A;
+                              <= 0 restores the default kappa = 2 / b */
+    FMM_OPT_M2L_SPLIT = 4, /* ival: mixed-precision M2L operand split, FMM_SPLIT_* */
+    FMM_OPT_STREAM = 5,    /* ival: cudaStream_t cast to int64 (0 = legacy default stream) */
+    FMM_OPT_TIMINGS = 6    /* ival: 1 records per-stage CUDA events (adds event overhead) */
+};
+enum { FMM_PREC_FP64 = 0, FMM_PREC_MIXED = 1 };
+enum {
+    FMM_SPLIT_BF16X3 = 0, /* tensor-core M2L: both operands as 3 bf16 terms, 6 products */
+    FMM_SPLIT_BF16X2 = 1, /* tensor-core M2L: 2 bf16 terms, 3 products */
+    FMM_SPLIT_FP32 = 2    /* FP32 CUDA-core M2L (no tensor cores) */
+};
+
+/*
+ * Create a plan for N charges in a cubic box of side `box` (A), with 2^depth
+ * leaf cells per side (depth = l_max of Appendix B) and expansion order
+ * p = n_max (0 <= n <= n_max, Eq. P2M).
+ * Errors: FMM_ERR_INVALID_ARG if box <= 0 or not finite, N < 1, p < 0 or
+ * p > 20, depth < 2 or depth > 8 (2^depth must exceed 2 ws + 1 so that the
+ * near field never holds a charge's own image); FMM_ERR_OOM; FMM_ERR_CUDA.
+ * On success *out owns device memory until fmm_plan_destroy.
+ */
+fmm_status fmm_plan_create(double box, int64_t N, int depth, int p, fmm_plan *out);
+
+/* Set an option (see FMM_OPT_*).  Changing WS, PRECISION, KAPPA or M2L_SPLIT
+ * rebuilds the plan's tables.  FMM_ERR_INVALID_ARG for unknown keys or bad
+ * values, FMM_ERR_UNSUPPORTED for values this build does not provide. */
+fmm_status fmm_plan_set_option(fmm_plan plan, int key, int64_t ival, double dval);
+
+/*
+ * Total energy (Eq. Velecfull).  pos: [N][3], q: [N] (device or host).
+ * energy: host out (required).  terms: host out, nullable.
+ * Synchronises the plan's stream.
+ */
+fmm_status fmm_energy(fmm_plan plan, const double *pos, const double *q, double *energy,
+                      fmm_energy_terms *terms);
+
+/*
+ * Energy and forces F_i = -dV_elec/dr_i: pair forces of the near field, minus
+ * q_i times the gradient of the far-field potential (L2P gradient; the FMM
+ * bilinear form is symmetric, so this is the exact gradient of Eq. EqFF), and
+ * -(4 pi / 3V) q_i (Q_C r_i - mu) from the two surface terms.  The charged
+ * term exerts no force.  The energy is piecewise smooth: it is not
+ * differentiable where a charge crosses a leaf face.
+ * forces: [N][3] out, same memory kind as pos.  energy: host out, nullable
+ * (non-null synchronises).
+ */
+fmm_status fmm_forces(fmm_plan plan, const double *pos, const double *q, double *forces, double *energy);
+
+/*
+ * Solute-solvent interaction energy with the reduced far field (Eq. FMMcalc):
+ * one full pass gives A; one pass over the solute charges alone gives B and C.
+ * is_solute: uint8 [N] (nonzero = solute).  e_uv: host out (required);
+ * terms: host out, nullable.  Synchronises.
+ */
+fmm_status fmm_solute_solvent_energy(fmm_plan plan, const double *pos, const double *q,
+                                     const uint8_t *is_solute, double *e_uv, fmm_uv_terms *terms);
+
+/*
+ * One call doing all of the above: energy terms, optional forces (nullable) and
+ * optional solute-solvent parts (is_solute and uv both non-null), sharing the
+ * full pass between them.  terms and uv are host outputs (nullable); forces has
+ * the memory kind of pos.  Synchronises when terms or uv is non-null.
+ */
+fmm_status fmm_evaluate(fmm_plan plan, const double *pos, const double *q, const uint8_t *is_solute,
+                        double *forces, fmm_energy_terms *terms, fmm_uv_terms *uv);
+
+/* Per-stage times of the last call (requires FMM_OPT_TIMINGS = 1). */
+fmm_status fmm_plan_get_timings(fmm_plan plan, fmm_timings *out);
+
+/* Number of kernel launches enqueued by the last call. */
+int64_t fmm_plan_last_launch_count(fmm_plan plan);
+
+/* Release the plan and its device memory.  Accepts NULL. */
+void fmm_plan_destroy(fmm_plan plan);
+
+/* Static string for a status code. */
+const char *fmm_status_string(fmm_status status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FMM_GB300_H */

@@ -1,0 +1,378 @@
+// fmm_api.cu -- the C ABI declared in include/fmm_gb300.h: plan lifecycle and
+// the order of the stages of one evaluation (Appendix B: sort, P2M, M2M,
+// level-0 lattice (Eq. 12), M2L + L2L per level, L2P, near field; then the
+// background-charge terms of Eq. Velecfull and, on request, the solute-only
+// pass of Eq. FMMcalc).
+#include <math.h>
+#include <string.h>
+
+#include <new>
+
+#include "fmm_internal.cuh"
+
+using namespace fmm;
+
+struct fmm_plan_s {
+    Plan P;
+};
+
+namespace {
+
+size_t reduction_scratch_bytes() { return sizeof(double) * 304 * 16 * 2; }
+
+void free_buffers(Plan &P)
+{
+    void *bufs[] = {P.in_pos, P.in_q,   P.out_forces, P.in_sol,   P.wpos,       P.key,    P.perm,   P.sleaf,
+                    P.cell_start, P.cell_fill, P.scan_tmp, P.sorted, P.sorted_u, P.sorted_sol, P.phi_nf, P.phi_ff,
+                    P.phi_u, P.f_nf, P.g_ff, P.red_partial, P.red_out, P.d_err};
+    for (void *b : bufs) cudaFree(b);
+    for (int l = 0; l <= 8; ++l) {
+        cudaFree(P.M[l]);
+        cudaFree(P.L[l]);
+        P.M[l] = P.L[l] = nullptr;
+    }
+    if (P.h_out) cudaFreeHost(P.h_out);
+    P.in_pos = P.in_q = P.out_forces = nullptr;
+    P.in_sol = nullptr;
+    P.wpos = nullptr;
+    P.key = P.perm = P.sleaf = P.cell_start = P.cell_fill = P.scan_tmp = nullptr;
+    P.sorted = P.sorted_u = nullptr;
+    P.sorted_sol = nullptr;
+    P.phi_nf = P.phi_ff = P.phi_u = P.f_nf = P.g_ff = nullptr;
+    P.red_partial = P.red_out = P.h_out = nullptr;
+    P.d_err = nullptr;
+}
+
+template <typename X>
+cudaError_t dalloc(X **p, size_t bytes)
+{
+    return cudaMalloc((void **)p, bytes < 16 ? 16 : bytes);
+}
+
+fmm_status alloc_buffers(Plan &P)
+{
+    int64_t N = P.N;
+    size_t nc = (size_t)P.nc;
+    // sized for FP64 so that the precision option can switch without reallocation
+    FMM_CUDA_TRY(dalloc(&P.wpos, sizeof(double) * 3 * N));
+    FMM_CUDA_TRY(dalloc(&P.key, sizeof(int) * N));
+    FMM_CUDA_TRY(dalloc(&P.perm, sizeof(int) * N));
+    FMM_CUDA_TRY(dalloc(&P.sleaf, sizeof(int) * N));
+    FMM_CUDA_TRY(dalloc(&P.cell_start, sizeof(int) * (P.nleaf + 1)));
+    FMM_CUDA_TRY(dalloc(&P.cell_fill, sizeof(int) * P.nleaf));
+    FMM_CUDA_TRY(dalloc(&P.scan_tmp, sizeof(int) * (P.nleaf / 4096 + 2)));
+    FMM_CUDA_TRY(dalloc(&P.sorted, sizeof(Particle<double>) * N));
+    FMM_CUDA_TRY(dalloc(&P.sorted_u, sizeof(Particle<double>) * N));
+    FMM_CUDA_TRY(dalloc(&P.sorted_sol, N));
+    FMM_CUDA_TRY(dalloc(&P.phi_nf, sizeof(double) * 2 * N));
+    FMM_CUDA_TRY(dalloc(&P.phi_ff, sizeof(double) * N));
+    FMM_CUDA_TRY(dalloc(&P.phi_u, sizeof(double) * N));
+    FMM_CUDA_TRY(dalloc(&P.f_nf, sizeof(double) * 3 * N));
+    FMM_CUDA_TRY(dalloc(&P.g_ff, sizeof(double) * 3 * N));
+    for (int l = 0; l <= P.d; ++l) {
+        size_t cells = (size_t)1 << (3 * l);
+        FMM_CUDA_TRY(dalloc(&P.M[l], sizeof(double) * cells * nc));
+        FMM_CUDA_TRY(dalloc(&P.L[l], sizeof(double) * cells * nc));
+    }
+    FMM_CUDA_TRY(dalloc(&P.red_partial, reduction_scratch_bytes()));
+    FMM_CUDA_TRY(dalloc(&P.red_out, sizeof(double) * 32));
+    FMM_CUDA_TRY(dalloc(&P.d_err, sizeof(int)));
+    FMM_CUDA_TRY(cudaMallocHost((void **)&P.h_out, sizeof(double) * 40));
+    return FMM_OK;
+}
+
+// 0 = device (or managed) memory, 1 = host memory, -1 = null
+int pointer_kind(const void *ptr)
+{
+    if (!ptr) return -1;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, ptr);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) ? 0 : 1;
+}
+
+fmm_status ensure_staging(Plan &P)
+{
+    if (!P.in_pos) FMM_CUDA_TRY(dalloc(&P.in_pos, sizeof(double) * 3 * P.N));
+    if (!P.in_q) FMM_CUDA_TRY(dalloc(&P.in_q, sizeof(double) * P.N));
+    if (!P.in_sol) FMM_CUDA_TRY(dalloc(&P.in_sol, P.N));
+    if (!P.out_forces) FMM_CUDA_TRY(dalloc(&P.out_forces, sizeof(double) * 3 * P.N));
+    return FMM_OK;
+}
+
+struct StageTimer {
+    Plan &P;
+    int k = 0;
+    explicit StageTimer(Plan &p) : P(p) {}
+    void mark()
+    {
+        if (P.timings_on && k < 12) cudaEventRecord(P.ev[k++], P.stream);
+    }
+};
+
+#define TRY(x)                               \
+    do {                                     \
+        fmm_status s_ = (x);                 \
+        if (s_ != FMM_OK) return s_;         \
+    } while (0)
+
+fmm_status far_field_pass(Plan &P, bool gradient, bool solute_only, StageTimer *tm)
+{
+    TRY(launch_upward(P, solute_only));
+    if (tm) tm->mark();
+    TRY(launch_lattice(P));
+    if (tm) tm->mark();
+    for (int l = 1; l <= P.d; ++l) {
+        if (tc_available(P, l)) TRY(launch_m2l_tc(P, l));
+        else TRY(launch_m2l_simt(P, l));
+        TRY(launch_l2l(P, l));
+    }
+    if (tm) tm->mark();
+    TRY(launch_l2p(P, gradient, solute_only));
+    if (tm) tm->mark();
+    return FMM_OK;
+}
+
+fmm_status evaluate(Plan &P, const double *pos, const double *q, const uint8_t *sol, double *forces,
+                    fmm_energy_terms *terms, fmm_uv_terms *uv)
+{
+    if (!pos || !q) return FMM_ERR_INVALID_ARG;
+    bool want_uv = sol && uv;
+    int kp = pointer_kind(pos), kq = pointer_kind(q);
+    int ks = want_uv ? pointer_kind(sol) : -1;
+    int kf = pointer_kind(forces);
+    bool host_any = kp == 1 || kq == 1 || ks == 1 || kf == 1;
+    if (host_any) TRY(ensure_staging(P));
+    P.launches = 0;
+    const double *dpos = pos, *dq = q;
+    const uint8_t *dsol = want_uv ? sol : nullptr;
+    double *dforces = forces;
+    if (kp == 1) {
+        FMM_CUDA_TRY(cudaMemcpyAsync(P.in_pos, pos, sizeof(double) * 3 * P.N, cudaMemcpyHostToDevice, P.stream));
+        dpos = P.in_pos;
+    }
+    if (kq == 1) {
+        FMM_CUDA_TRY(cudaMemcpyAsync(P.in_q, q, sizeof(double) * P.N, cudaMemcpyHostToDevice, P.stream));
+        dq = P.in_q;
+    }
+    if (ks == 1) {
+        FMM_CUDA_TRY(cudaMemcpyAsync(P.in_sol, sol, P.N, cudaMemcpyHostToDevice, P.stream));
+        dsol = P.in_sol;
+    }
+    if (kf == 1) dforces = P.out_forces;
+
+    StageTimer tm(P);
+    tm.mark();
+    FMM_CUDA_TRY(cudaMemsetAsync(P.d_err, 0, sizeof(int), P.stream));
+    TRY(launch_assign_sort(P, dpos, dq, dsol));
+    tm.mark();
+    TRY(launch_bc_moments(P, dq, dsol));
+    TRY(far_field_pass(P, forces != nullptr, false, &tm));
+    TRY(launch_p2p(P, forces != nullptr));
+    tm.mark();
+    if (want_uv) {
+        TRY(far_field_pass(P, false, true, nullptr));
+        TRY(launch_p2p_uv(P));
+    }
+    TRY(launch_energy_reduce(P, want_uv));
+    if (forces) TRY(launch_forces_out(P, dq, dforces));
+    tm.mark();
+    bool sync = terms || uv || kf == 1;
+    if (kf == 1)
+        FMM_CUDA_TRY(cudaMemcpyAsync(forces, P.out_forces, sizeof(double) * 3 * P.N, cudaMemcpyDeviceToHost, P.stream));
+    if (sync) {
+        FMM_CUDA_TRY(cudaMemcpyAsync(P.h_out, P.red_out, sizeof(double) * 29, cudaMemcpyDeviceToHost, P.stream));
+        FMM_CUDA_TRY(cudaMemcpyAsync(P.h_out + 32, P.d_err, sizeof(int), cudaMemcpyDeviceToHost, P.stream));
+        FMM_CUDA_TRY(cudaStreamSynchronize(P.stream));
+        int err;
+        memcpy(&err, P.h_out + 32, sizeof(int));
+        if (terms) {
+            terms->near = P.h_out[16];
+            terms->far = P.h_out[17];
+            terms->charged = P.h_out[18];
+            terms->quad_surface = P.h_out[19];
+            terms->dipole_surface = P.h_out[20];
+            terms->total = P.h_out[21];
+        }
+        if (uv) {
+            uv->e_uv = P.h_out[22];
+            uv->W = P.h_out[23];
+            uv->A = P.h_out[24];
+            uv->B = P.h_out[25];
+            uv->C = P.h_out[26];
+            uv->nf_uv = P.h_out[27];
+            uv->bc_cross = P.h_out[28];
+        }
+        if (P.timings_on && tm.k >= 8) {
+            float t[12];
+            for (int i = 0; i + 1 < tm.k; ++i) cudaEventElapsedTime(&t[i], P.ev[i], P.ev[i + 1]);
+            P.last.sort = t[0];
+            P.last.upward = t[1];
+            P.last.lattice = t[2];
+            P.last.m2l = t[3];
+            P.last.l2p = t[4];
+            P.last.p2p = t[5];
+            P.last.reduce = t[6];
+            P.last.downward = 0;
+            cudaEventElapsedTime(&P.last.total, P.ev[0], P.ev[tm.k - 1]);
+        }
+        if (err & ERRF_NONFINITE) return FMM_ERR_NONFINITE;
+        if (err & ERRF_TIMEOUT) return FMM_ERR_TIMEOUT;
+        if (err) return FMM_ERR_INTERNAL;
+    }
+    return FMM_OK;
+}
+
+fmm_status rebuild(Plan &P)
+{
+    tc_free(P);
+    TRY(build_tables(P));
+    if (P.precision == FMM_PREC_MIXED && P.split != FMM_SPLIT_FP32) TRY(tc_prepare(P));
+    return FMM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fmm_status fmm_plan_create(double box, int64_t N, int depth, int p, fmm_plan *out)
+{
+    if (!out) return FMM_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!(box > 0.0) || !isfinite(box) || N < 1 || N > ((int64_t)1 << 31) - 1 || p < 0 || p > P_MAX || depth < 2 ||
+        depth > 8)
+        return FMM_ERR_INVALID_ARG;
+    fmm_plan_s *h = new (std::nothrow) fmm_plan_s();
+    if (!h) return FMM_ERR_OOM;
+    Plan &P = h->P;
+    P.box = box;
+    P.N = N;
+    P.d = depth;
+    P.p = p;
+    P.nc = ncoef(p);
+    P.nleaf = (int64_t)1 << (3 * depth);
+    fmm_status s = alloc_buffers(P);
+    if (s == FMM_OK) {
+        for (int i = 0; i < 12; ++i) cudaEventCreate(&P.ev[i]);
+        s = rebuild(P);
+    }
+    if (s != FMM_OK) {
+        fmm_plan_destroy(h);
+        return s;
+    }
+    *out = h;
+    return FMM_OK;
+}
+
+fmm_status fmm_plan_set_option(fmm_plan plan, int key, int64_t ival, double dval)
+{
+    if (!plan) return FMM_ERR_INVALID_ARG;
+    Plan &P = plan->P;
+    switch (key) {
+    case FMM_OPT_WS:
+        if (ival == 1) return FMM_OK;
+        return ival >= 2 ? FMM_ERR_UNSUPPORTED : FMM_ERR_INVALID_ARG;
+    case FMM_OPT_PRECISION:
+        if (ival != FMM_PREC_FP64 && ival != FMM_PREC_MIXED) return FMM_ERR_INVALID_ARG;
+        P.precision = (int)ival;
+        return rebuild(P);
+    case FMM_OPT_KAPPA:
+        if (!isfinite(dval)) return FMM_ERR_INVALID_ARG;
+        P.kappa = dval > 0 ? dval : 0.0;
+        return rebuild(P);
+    case FMM_OPT_M2L_SPLIT:
+        if (ival != FMM_SPLIT_BF16X3 && ival != FMM_SPLIT_BF16X2 && ival != FMM_SPLIT_FP32) return FMM_ERR_INVALID_ARG;
+        P.split = (int)ival;
+        return rebuild(P);
+    case FMM_OPT_STREAM:
+        P.stream = (cudaStream_t)(intptr_t)ival;
+        return FMM_OK;
+    case FMM_OPT_TIMINGS:
+        P.timings_on = ival != 0;
+        return FMM_OK;
+    default:
+        return FMM_ERR_INVALID_ARG;
+    }
+}
+
+fmm_status fmm_energy(fmm_plan plan, const double *pos, const double *q, double *energy, fmm_energy_terms *terms)
+{
+    if (!plan || !energy) return FMM_ERR_INVALID_ARG;
+    fmm_energy_terms t;
+    fmm_status s = evaluate(plan->P, pos, q, nullptr, nullptr, &t, nullptr);
+    if (s != FMM_OK) return s;
+    *energy = t.total;
+    if (terms) *terms = t;
+    return FMM_OK;
+}
+
+fmm_status fmm_forces(fmm_plan plan, const double *pos, const double *q, double *forces, double *energy)
+{
+    if (!plan || !forces) return FMM_ERR_INVALID_ARG;
+    fmm_energy_terms t;
+    fmm_status s = evaluate(plan->P, pos, q, nullptr, forces, energy ? &t : nullptr, nullptr);
+    if (s != FMM_OK) return s;
+    if (energy) *energy = t.total;
+    return FMM_OK;
+}
+
+fmm_status fmm_solute_solvent_energy(fmm_plan plan, const double *pos, const double *q, const uint8_t *is_solute,
+                                     double *e_uv, fmm_uv_terms *terms)
+{
+    if (!plan || !e_uv || !is_solute) return FMM_ERR_INVALID_ARG;
+    fmm_uv_terms u;
+    fmm_status s = evaluate(plan->P, pos, q, is_solute, nullptr, nullptr, &u);
+    if (s != FMM_OK) return s;
+    *e_uv = u.e_uv;
+    if (terms) *terms = u;
+    return FMM_OK;
+}
+
+fmm_status fmm_evaluate(fmm_plan plan, const double *pos, const double *q, const uint8_t *is_solute, double *forces,
+                        fmm_energy_terms *terms, fmm_uv_terms *uv)
+{
+    if (!plan) return FMM_ERR_INVALID_ARG;
+    return evaluate(plan->P, pos, q, is_solute, forces, terms, uv);
+}
+
+fmm_status fmm_plan_get_timings(fmm_plan plan, fmm_timings *out)
+{
+    if (!plan || !out) return FMM_ERR_INVALID_ARG;
+    *out = plan->P.last;
+    return FMM_OK;
+}
+
+int64_t fmm_plan_last_launch_count(fmm_plan plan) { return plan ? plan->P.launches : -1; }
+
+void fmm_plan_destroy(fmm_plan plan)
+{
+    if (!plan) return;
+    Plan &P = plan->P;
+    cudaStreamSynchronize(P.stream);
+    tc_free(P);
+    free_tables(P);
+    free_buffers(P);
+    for (int i = 0; i < 12; ++i)
+        if (P.ev[i]) cudaEventDestroy(P.ev[i]);
+    delete plan;
+}
+
+const char *fmm_status_string(fmm_status s)
+{
+    switch (s) {
+    case FMM_OK: return "ok";
+    case FMM_ERR_INVALID_ARG: return "invalid argument";
+    case FMM_ERR_NONFINITE: return "non-finite position or charge";
+    case FMM_ERR_CUDA: return "CUDA runtime error";
+    case FMM_ERR_OOM: return "out of memory";
+    case FMM_ERR_TIMEOUT: return "device wait timed out";
+    case FMM_ERR_INTERNAL: return "internal consistency check failed";
+    case FMM_ERR_UNSUPPORTED: return "option value not supported by this build";
+    default: return "unknown status";
+    }
+}
+
+}  // extern "C"

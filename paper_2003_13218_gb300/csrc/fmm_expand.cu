@@ -1,0 +1,644 @@
+// fmm_expand.cu -- the expansion operators of Appendix B on the GPU:
+// P2M (Eq. P2M), M2M, the level-0 lattice operator (Eq. 12), M2L over the
+// interaction lists (Eq. Lcoeffdef, CUDA-core version), L2L and L2P with its
+// gradient (Eq. EqFF); plus the per-plan operator tables.
+//
+// Solid harmonics (normalisation that makes the printed equations hold with
+// no conjugates): R_n^m = r^n P_n^m e^{im phi}/(n+m)!,
+// I_n^m = (-1)^(n+m) (n-m)! P_n^m e^{im phi} / r^(n+1); both obey
+// C_n^{-m} = (-1)^m conj C_n^m, so only m >= 0 is stored.
+#include <math.h>
+
+#include <type_traits>
+
+#include "fmm_internal.cuh"
+
+namespace fmm {
+
+namespace {
+
+inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// ------------------------------------------------------------------ tables
+// R_n^m at the eight child-centre offsets w_c = ((c_x - 1/2)/2, ...) (in
+// units of the parent side): the M2M and L2L shift vectors.
+__global__ void k_octant_table(int p, double *__restrict__ R64, float *__restrict__ R32)
+{
+    int c = threadIdx.x;
+    if (c >= 8) return;
+    int nc = ncoef(p);
+    double w[3] = {((c & 1) - 0.5) * 0.5, (((c >> 1) & 1) - 0.5) * 0.5, (((c >> 2) & 1) - 0.5) * 0.5};
+    double tmp[NC_MAX];
+    regular_real<double>(p, w[0], w[1], w[2], tmp);
+    for (int i = 0; i < nc; ++i) {
+        R64[c * nc + i] = tmp[i];
+        R32[c * nc + i] = (float)tmp[i];
+    }
+}
+
+// complex I_j^k for any sign of k from the m >= 0 triangle
+__device__ inline Cx<double> tri_get(const Cx<double> *t, int j, int k)
+{
+    int ak = k < 0 ? -k : k;
+    Cx<double> v = t[tri(j, ak)];
+    if (k < 0) {
+        v.im = -v.im;
+        if (ak & 1) {
+            v.re = -v.re;
+            v.im = -v.im;
+        }
+    }
+    return v;
+}
+
+// Real form of Eq. Lcoeffdef: L_n^m = sum_{lambda, eta} M_lambda^eta O_{n+lambda}^{-(m+eta)}.
+// With M_lambda^{-eta} = (-1)^eta conj M_lambda^eta and M_lambda^eta = x + i y:
+//   eta = 0: L += x O(lambda, 0)
+//   eta > 0: L += x A + i y B,  A = O(lambda, eta) + (-1)^eta O(lambda, -eta),
+//                                B = O(lambda, eta) - (-1)^eta O(lambda, -eta),
+// where O(lambda, e) = O_{n+lambda}^{-(m+e)}.  Entry [k][j] maps input real k
+// to output real j.
+__device__ void build_real_operator(int p, const Cx<double> *O, double *__restrict__ Tout)
+{
+    int nc = ncoef(p);
+    for (int e = threadIdx.x; e < nc * nc; e += blockDim.x) {
+        int k = e / nc, j = e % nc;
+        // output (n, m, part)
+        int n = (int)sqrt((double)j);
+        while (n * n > j) --n;
+        while ((n + 1) * (n + 1) <= j) ++n;
+        int r = j - n * n;
+        int m = (r + 1) / 2;
+        bool out_im = (m > 0) && (r == 2 * m);
+        // input (lambda, eta, part)
+        int lam = (int)sqrt((double)k);
+        while (lam * lam > k) --lam;
+        while ((lam + 1) * (lam + 1) <= k) ++lam;
+        int ri = k - lam * lam;
+        int eta = (ri + 1) / 2;
+        bool in_im = (eta > 0) && (ri == 2 * eta);
+        double val;
+        Cx<double> o1 = tri_get(O, n + lam, -(m + eta));
+        if (eta == 0) {
+            val = out_im ? o1.im : o1.re;
+        } else {
+            Cx<double> o2 = tri_get(O, n + lam, eta - m);
+            double sg = (eta & 1) ? -1.0 : 1.0;
+            if (!in_im) {
+                Cx<double> A = {o1.re + sg * o2.re, o1.im + sg * o2.im};
+                val = out_im ? A.im : A.re;
+            } else {
+                Cx<double> B = {o1.re - sg * o2.re, o1.im - sg * o2.im};
+                val = out_im ? B.re : -B.im;
+            }
+        }
+        Tout[(size_t)k * nc + j] = val;
+    }
+}
+
+// one block per offset slot delta in [-3, 3]^3 (the 27 near slots stay zero)
+__global__ void k_m2l_operators(int p, double *__restrict__ T64, float *__restrict__ T32)
+{
+    extern __shared__ Cx<double> Ish[];
+    int slot = blockIdx.x;
+    int dx = slot % 7 - 3, dy = (slot / 7) % 7 - 3, dz = slot / 49 - 3;
+    int nc = ncoef(p);
+    double *T = T64 + (size_t)slot * nc * nc;
+    if (abs(dx) <= 1 && abs(dy) <= 1 && abs(dz) <= 1) {
+        for (int e = threadIdx.x; e < nc * nc; e += blockDim.x) {
+            T[e] = 0.0;
+            T32[(size_t)slot * nc * nc + e] = 0.0f;
+        }
+        return;
+    }
+    // I at r_L - r_M = -(delta) in cell units: target t, source t + delta
+    if (threadIdx.x == 0) irregular_tri<double>(2 * p, -(double)dx, -(double)dy, -(double)dz, Ish);
+    __syncthreads();
+    build_real_operator(p, Ish, T);
+    __syncthreads();
+    for (int e = threadIdx.x; e < nc * nc; e += blockDim.x) T32[(size_t)slot * nc * nc + e] = (float)T[e];
+}
+
+// single irregular harmonic I_j^k (k >= 0) by the column recurrence
+__device__ Cx<double> irregular_one(int j, int k, double x, double y, double z)
+{
+    double r2 = x * x + y * y + z * z, ir2 = 1.0 / r2;
+    Cx<double> dg = {1.0 / sqrt(r2), 0.0};
+    for (int m = 1; m <= k; ++m) {
+        double s = -(2.0 * m - 1.0) * ir2;
+        dg = {s * (x * dg.re - y * dg.im), s * (x * dg.im + y * dg.re)};
+    }
+    Cx<double> p2 = {0, 0}, p1 = dg;
+    for (int n = k + 1; n <= j; ++n) {
+        double a = -(2.0 * n - 1.0) * z, b = (double)((n + k - 1) * (n - k - 1));
+        Cx<double> c = {(a * p1.re - b * p2.re) * ir2, (a * p1.im - b * p2.im) * ir2};
+        p2 = p1;
+        p1 = c;
+    }
+    return p1;
+}
+
+struct KS {
+    double s = 0, c = 0;
+    __device__ void add(double x)
+    {
+        double t = s + x;
+        if (fabs(s) >= fabs(x)) c += (s - t) + x;
+        else c += (x - t) + s;
+        s = t;
+    }
+    __device__ double val() const { return s + c; }
+};
+
+// Eq. 12 on a unit box with splitting parameter kb = kappa * b:
+//   S_j^k = sum_{nu != 0} I_j^k(nu) Q(j + 1/2, kb^2 nu^2)                         (12a)
+//         + pi^{3/2} i^j / (2^{j-2} Gamma(j + 1/2)) sum_{k != 0} I_j^k(k) k^{2j-1} e^{-k^2/4kb^2}  (12b)
+//         - 2 kb / sqrt(pi) delta_{j0}                                           (12c)
+//         - sum_{nu in {-1,0,1}^3, nu != 0} I_j^k(nu)      (images covered by levels 1..l_max)
+// Q(a, x) = Gamma(a, x)/Gamma(a) by Q(1/2, x) = erfc(sqrt x) and
+// Q(a + 1, x) = Q(a, x) + x^a e^{-x} / Gamma(a + 1).  One thread per (j, k).
+__global__ void k_lattice_sum(int jmax, double kb, int nu_max, int nk_max, double *__restrict__ S)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    int ntri = (jmax + 1) * (jmax + 2) / 2;
+    if (t >= ntri) return;
+    int j = 0;
+    while (tri(j + 1, 0) <= t) ++j;
+    int k = t - tri(j, 0);
+    const double PI = 3.14159265358979323846;
+    KS re, im;
+    // real space (12a) and the near block
+    for (int nz = -nu_max; nz <= nu_max; ++nz)
+        for (int ny = -nu_max; ny <= nu_max; ++ny)
+            for (int nx = -nu_max; nx <= nu_max; ++nx) {
+                if (nx == 0 && ny == 0 && nz == 0) continue;
+                double r2 = (double)(nx * nx + ny * ny + nz * nz);
+                double x = kb * kb * r2;
+                double Q = erfc(sqrt(x));
+                double g = sqrt(PI);  // Gamma(1/2)
+                for (int i = 0; i < j; ++i) {
+                    double a = i + 0.5;
+                    g *= a;  // Gamma(i + 3/2)
+                    Q += exp(a * log(x) - x) / g;
+                }
+                bool near = abs(nx) <= 1 && abs(ny) <= 1 && abs(nz) <= 1;
+                double w = near ? Q - 1.0 : Q;
+                Cx<double> I = irregular_one(j, k, nx, ny, nz);
+                re.add(w * I.re);
+                im.add(w * I.im);
+            }
+    // reciprocal space (12b), k = 2 pi n
+    double gh = sqrt(PI);
+    for (int i = 0; i < j; ++i) gh *= (i + 0.5);  // Gamma(j + 1/2)
+    double pref = pow(PI, 1.5) / (ldexp(1.0, j - 2) * gh);
+    // i^j: j even -> (-1)^(j/2); odd degrees vanish by symmetry (kept exact)
+    KS rre, rim;
+    for (int nz = -nk_max; nz <= nk_max; ++nz)
+        for (int ny = -nk_max; ny <= nk_max; ++ny)
+            for (int nx = -nk_max; nx <= nk_max; ++nx) {
+                if (nx == 0 && ny == 0 && nz == 0) continue;
+                double kx = 2 * PI * nx, ky = 2 * PI * ny, kz = 2 * PI * nz;
+                double k2 = kx * kx + ky * ky + kz * kz;
+                double kk = sqrt(k2);
+                double w = pow(kk, 2 * j - 1) * exp(-k2 / (4 * kb * kb));
+                Cx<double> I = irregular_one(j, k, kx, ky, kz);
+                rre.add(w * I.re);
+                rim.add(w * I.im);
+            }
+    double cr = rre.val() * pref, ci = rim.val() * pref;
+    // multiply by i^j
+    double ore, oim;
+    switch (j & 3) {
+    case 0: ore = cr; oim = ci; break;
+    case 1: ore = -ci; oim = cr; break;
+    case 2: ore = -cr; oim = -ci; break;
+    default: ore = ci; oim = -cr; break;
+    }
+    re.add(ore);
+    im.add(oim);
+    if (j == 0) re.add(-2.0 * kb / sqrt(PI));
+    S[2 * t] = re.val();
+    S[2 * t + 1] = im.val();
+}
+
+__global__ void k_lattice_operator(int p, const double *__restrict__ S, double *__restrict__ T0)
+{
+    extern __shared__ Cx<double> Ssh[];
+    int ntri = (2 * p + 1) * (2 * p + 2) / 2;
+    for (int i = threadIdx.x; i < ntri; i += blockDim.x) Ssh[i] = {S[2 * i], S[2 * i + 1]};
+    __syncthreads();
+    build_real_operator(p, Ssh, T0);
+}
+
+// ------------------------------------------------------------------ P2M
+// Eq. P2M in level-scaled form: Mhat_n^m = sum_j q_j R_n^m((r_M - r_j)/h).
+// One thread per (leaf, m): the column n = m..p of every particle.
+template <typename T>
+__global__ void k_p2m(int p, int nside, const int *__restrict__ start, const Particle<T> *__restrict__ sp,
+                      T inv_h, int d, T *__restrict__ M)
+{
+    int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t nleaf = (int64_t)nside * nside * nside;
+    if (tid >= nleaf * (p + 1)) return;
+    int64_t leaf = tid / (p + 1);
+    int m = (int)(tid % (p + 1));
+    int x = (int)(leaf % nside), y = (int)((leaf / nside) % nside), z = (int)(leaf / ((int64_t)nside * nside));
+    T acc_re[P_MAX + 1], acc_im[P_MAX + 1];
+    for (int n = 0; n <= p; ++n) acc_re[n] = acc_im[n] = 0;
+    for (int s = start[leaf]; s < start[leaf + 1]; ++s) {
+        Particle<T> pt = sp[s];
+        T vx = -pt.x * inv_h, vy = -pt.y * inv_h, vz = -pt.z * inv_h;
+        T r2 = vx * vx + vy * vy + vz * vz;
+        T dre = 1, dim = 0;
+        for (int k = 1; k <= m; ++k) {
+            T sc = T(-0.5) / T(k);
+            T nre = sc * (vx * dre - vy * dim);
+            T nim = sc * (vx * dim + vy * dre);
+            dre = nre;
+            dim = nim;
+        }
+        T p2re = 0, p2im = 0, p1re = dre, p1im = dim;
+        acc_re[m] += pt.q * dre;
+        acc_im[m] += pt.q * dim;
+        for (int n = m + 1; n <= p; ++n) {
+            T a = T(2 * n - 1) * vz;
+            T inv = T(1) / T((n + m) * (n - m));
+            T cr = (a * p1re - r2 * p2re) * inv;
+            T ci = (a * p1im - r2 * p2im) * inv;
+            acc_re[n] += pt.q * cr;
+            acc_im[n] += pt.q * ci;
+            p2re = p1re;
+            p2im = p1im;
+            p1re = cr;
+            p1im = ci;
+        }
+    }
+    int nc = ncoef(p);
+    T *out = M + cell_index(d, x, y, z) * nc;
+    for (int n = m; n <= p; ++n) {
+        out[cre(n, m)] = acc_re[n];
+        if (m > 0) out[cim(n, m)] = acc_im[n];
+    }
+}
+
+// ------------------------------------------------------------------ M2M
+// Mhat_n^m(P) = sum_c sum_{k,l} R_{n-k}^{m-l}(u_c) Mhat_k^l(C_c) 2^{-k},
+// u_c = (r_P - r_C)/h_parent = -w_c,  R(-w) = (-1)^deg R(w).
+template <typename T>
+__global__ void k_m2m(int p, int lp, const T *__restrict__ Rw, const T *__restrict__ Mc, T *__restrict__ Mp)
+{
+    extern __shared__ unsigned char smem_raw[];
+    T *Rs = reinterpret_cast<T *>(smem_raw);
+    int nc = ncoef(p);
+    for (int i = threadIdx.x; i < 8 * nc; i += blockDim.x) Rs[i] = Rw[i];
+    __syncthreads();
+    int ntri = (p + 1) * (p + 2) / 2;
+    int64_t np = (int64_t)1 << lp;
+    int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (tid >= np * np * np * ntri) return;
+    int64_t par = tid / ntri;
+    int t = (int)(tid % ntri);
+    int n = 0;
+    while (tri(n + 1, 0) <= t) ++n;
+    int m = t - tri(n, 0);
+    int px = (int)(par % np), py = (int)((par / np) % np), pz = (int)(par / (np * np));
+    T accr = 0, acci = 0;
+    for (int c = 0; c < 8; ++c) {
+        const T *Mch = Mc + cell_index(lp + 1, 2 * px + (c & 1), 2 * py + ((c >> 1) & 1), 2 * pz + ((c >> 2) & 1)) * nc;
+        const T *R = Rs + c * nc;
+        T scale = 1;
+        for (int k = 0; k <= n; ++k) {
+            int dn = n - k;
+            T sgn = (dn & 1) ? T(-1) : T(1);
+            for (int l = -k; l <= k; ++l) {
+                int dm = m - l;
+                if (dm < -dn || dm > dn) continue;
+                Cx<T> r = coef(R, dn, dm);
+                Cx<T> mm = coef(Mch, k, l);
+                Cx<T> pr = cmul(r, mm);
+                accr += sgn * scale * pr.re;
+                acci += sgn * scale * pr.im;
+            }
+            scale *= T(0.5);
+        }
+    }
+    T *out = Mp + cell_index(lp, px, py, pz) * nc;
+    out[cre(n, m)] = accr;
+    if (m > 0) out[cim(n, m)] = acci;
+}
+
+// ------------------------------------------------------------------ lattice apply
+// Lbar(0) = T0 . Mhat(0) (Eq. 12 in place of I in Eq. Lcoeffdef), in FP64
+template <typename T>
+__global__ void k_lattice_apply(int p, const double *__restrict__ T0, const T *__restrict__ M0, T *__restrict__ L0)
+{
+    int nc = ncoef(p);
+    int j = threadIdx.x;
+    if (j >= nc) return;
+    double acc = 0;
+    for (int k = 0; k < nc; ++k) acc += T0[(size_t)k * nc + j] * (double)M0[k];
+    L0[j] = (T)acc;
+}
+
+// ------------------------------------------------------------------ M2L (CUDA cores)
+// Eq. Lcoeffdef over the 189-cell interaction list of each target, as dense
+// real operators per offset.  Block: TT targets of one parity class, one
+// thread per output coefficient.  Sources are read with periodic wrap.
+template <typename T, int TT>
+__global__ void k_m2l_simt(int p, int l, int cls, const T *__restrict__ Top, const T *__restrict__ M, T *__restrict__ L)
+{
+    extern __shared__ unsigned char smem_raw[];
+    T *S = reinterpret_cast<T *>(smem_raw);  // [TT][nc]
+    int nc = ncoef(p);
+    int np = 1 << (l - 1);
+    int64_t ncls = (int64_t)np * np * np;
+    int64_t t0 = (int64_t)blockIdx.x * TT;
+    int cx = cls & 1, cy = (cls >> 1) & 1, cz = (cls >> 2) & 1;
+    int j = threadIdx.x;
+    T acc[TT];
+#pragma unroll
+    for (int t = 0; t < TT; ++t) acc[t] = 0;
+    for (int dz = -2 - cz; dz <= 3 - cz; ++dz)
+        for (int dy = -2 - cy; dy <= 3 - cy; ++dy)
+            for (int dx = -2 - cx; dx <= 3 - cx; ++dx) {
+                if (abs(dx) <= 1 && abs(dy) <= 1 && abs(dz) <= 1) continue;
+                int sx = cx + dx, sy = cy + dy, sz = cz + dz;  // in [-2, 3]
+                int scls = (sx & 1) | ((sy & 1) << 1) | ((sz & 1) << 2);
+                int Dx = sx >> 1, Dy = sy >> 1, Dz = sz >> 1;  // floor division
+                __syncthreads();
+                for (int e = threadIdx.x; e < TT * nc; e += blockDim.x) {
+                    int t = e / nc, k = e % nc;
+                    int64_t tg = t0 + t;
+                    T v = 0;
+                    if (tg < ncls) {
+                        int Px = (int)(tg % np), Py = (int)((tg / np) % np), Pz = (int)(tg / ((int64_t)np * np));
+                        int Qx = (Px + Dx + np) % np, Qy = (Py + Dy + np) % np, Qz = (Pz + Dz + np) % np;
+                        int64_t src = scls * ncls + Qx + (int64_t)np * (Qy + (int64_t)np * Qz);
+                        v = M[src * nc + k];
+                    }
+                    S[t * nc + k] = v;
+                }
+                __syncthreads();
+                if (j < nc) {
+                    const T *Tp = Top + (size_t)off_slot(dx, dy, dz) * nc * nc + j;
+                    for (int k = 0; k < nc; ++k) {
+                        T w = Tp[(size_t)k * nc];
+#pragma unroll
+                        for (int t = 0; t < TT; ++t) acc[t] += w * S[t * nc + k];
+                    }
+                }
+            }
+    if (j < nc) {
+        for (int t = 0; t < TT; ++t) {
+            int64_t tg = t0 + t;
+            if (tg < ncls) L[(cls * ncls + tg) * nc + j] = acc[t];
+        }
+    }
+}
+
+// ------------------------------------------------------------------ L2L
+// Lhat_k^l(C) += sum_{n >= k, m} Lhat_n^m(P) R_{n-k}^{m-l}(w_c) 2^{-(k+1)}
+template <typename T>
+__global__ void k_l2l(int p, int l, const T *__restrict__ Rw, const T *__restrict__ Lp, T *__restrict__ Lc)
+{
+    extern __shared__ unsigned char smem_raw[];
+    T *Rs = reinterpret_cast<T *>(smem_raw);
+    int nc = ncoef(p);
+    for (int i = threadIdx.x; i < 8 * nc; i += blockDim.x) Rs[i] = Rw[i];
+    __syncthreads();
+    int ntri = (p + 1) * (p + 2) / 2;
+    int64_t n1 = (int64_t)1 << l;
+    int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (tid >= n1 * n1 * n1 * ntri) return;
+    int64_t ch = tid / ntri;
+    int t = (int)(tid % ntri);
+    int k = 0;
+    while (tri(k + 1, 0) <= t) ++k;
+    int lo = t - tri(k, 0);
+    int x = (int)(ch % n1), y = (int)((ch / n1) % n1), z = (int)(ch / (n1 * n1));
+    int c = (x & 1) | ((y & 1) << 1) | ((z & 1) << 2);
+    const T *Lpar = Lp + cell_index(l - 1, x >> 1, y >> 1, z >> 1) * nc;
+    const T *R = Rs + c * nc;
+    T accr = 0, acci = 0;
+    for (int n = k; n <= p; ++n) {
+        int dn = n - k;
+        for (int m = -n; m <= n; ++m) {
+            int dm = m - lo;
+            if (dm < -dn || dm > dn) continue;
+            Cx<T> pr = cmul(coef(Lpar, n, m), coef(R, dn, dm));
+            accr += pr.re;
+            acci += pr.im;
+        }
+    }
+    T scale = T(1);
+    for (int i = 0; i <= k; ++i) scale *= T(0.5);
+    T *out = Lc + cell_index(l, x, y, z) * nc;
+    out[cre(k, lo)] += scale * accr;
+    if (lo > 0) out[cim(k, lo)] += scale * acci;
+}
+
+// ------------------------------------------------------------------ L2P
+// Phi(r) = (1/h) sum L_n^m R_n^m(v), v = (r - r_L')/h, and
+// grad Phi = (1/h^2) sum_{n',m'} G_{n'}^{m'} R_{n'}^{m'}(v) with
+//   G^z = L_{n'+1}^{m'},  G^x = (L_{n'+1}^{m'-1} - L_{n'+1}^{m'+1})/2,
+//   G^y = -i (L_{n'+1}^{m'-1} + L_{n'+1}^{m'+1})/2.
+template <typename T>
+__global__ void k_l2p(int p, int d, int64_t N, const int *__restrict__ sleaf, const Particle<T> *__restrict__ sp,
+                      T inv_h, const T *__restrict__ L, T *__restrict__ phi, T *__restrict__ grad)
+{
+    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= N) return;
+    int nside = 1 << d;
+    int leaf = sleaf[s];
+    int x = leaf % nside, y = (leaf / nside) % nside, z = leaf / (nside * nside);
+    const T *Lc = L + cell_index(d, x, y, z) * ncoef(p);
+    Particle<T> pt = sp[s];
+    T vx = pt.x * inv_h, vy = pt.y * inv_h, vz = pt.z * inv_h;
+    T r2 = vx * vx + vy * vy + vz * vz;
+    T pot = 0, gx = 0, gy = 0, gz = 0;
+    T dre = 1, dim = 0;
+    for (int m = 0; m <= p; ++m) {
+        if (m > 0) {
+            T sc = T(-0.5) / T(m);
+            T nre = sc * (vx * dre - vy * dim);
+            T nim = sc * (vx * dim + vy * dre);
+            dre = nre;
+            dim = nim;
+        }
+        T w = m == 0 ? T(1) : T(2);
+        T p2re = 0, p2im = 0, rre = dre, rim = dim;
+        for (int n = m; n <= p; ++n) {
+            if (n > m) {
+                T a = T(2 * n - 1) * vz;
+                T inv = T(1) / T((n + m) * (n - m));
+                T cr = (a * rre - r2 * p2re) * inv;
+                T ci = (a * rim - r2 * p2im) * inv;
+                p2re = rre;
+                p2im = rim;
+                rre = cr;
+                rim = ci;
+            }
+            Cx<T> Lnm = coef(Lc, n, m);
+            pot += w * (Lnm.re * rre - Lnm.im * rim);
+            if (grad && n < p) {
+                Cx<T> a = coef(Lc, n + 1, m - 1), b = coef(Lc, n + 1, m + 1), c = coef(Lc, n + 1, m);
+                Cx<T> Gx = {T(0.5) * (a.re - b.re), T(0.5) * (a.im - b.im)};
+                Cx<T> Gy = {T(0.5) * (a.im + b.im), -T(0.5) * (a.re + b.re)};
+                gx += w * (Gx.re * rre - Gx.im * rim);
+                gy += w * (Gy.re * rre - Gy.im * rim);
+                gz += w * (c.re * rre - c.im * rim);
+            }
+        }
+    }
+    phi[s] = pot * inv_h;
+    if (grad) {
+        T s2 = inv_h * inv_h;
+        grad[3 * s] = gx * s2;
+        grad[3 * s + 1] = gy * s2;
+        grad[3 * s + 2] = gz * s2;
+    }
+}
+
+template <typename T>
+fmm_status upward_t(Plan &P, bool solute_only)
+{
+    int p = P.p, nc = P.nc, nside = 1 << P.d;
+    const Particle<T> *sp = (const Particle<T> *)(solute_only ? P.sorted_u : P.sorted);
+    T inv_h = (T)((double)nside / P.box);
+    int64_t nthr = P.nleaf * (p + 1);
+    k_p2m<T><<<blocks_for(nthr, 128), 128, 0, P.stream>>>(p, nside, P.cell_start, sp, inv_h, P.d, (T *)P.M[P.d]);
+    FMM_LAUNCH_CHECK(P);
+    const T *Rw = std::is_same<T, double>::value ? (const T *)P.tab.Rw64 : (const T *)P.tab.Rw32;
+    int ntri = (p + 1) * (p + 2) / 2;
+    for (int l = P.d - 1; l >= 0; --l) {
+        int64_t np = (int64_t)1 << l;
+        int64_t n = np * np * np * ntri;
+        k_m2m<T><<<blocks_for(n, 128), 128, 8 * nc * sizeof(T), P.stream>>>(p, l, Rw, (const T *)P.M[l + 1],
+                                                                            (T *)P.M[l]);
+        FMM_LAUNCH_CHECK(P);
+    }
+    return FMM_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ host side
+fmm_status build_tables(Plan &P)
+{
+    free_tables(P);
+    int p = P.p, nc = P.nc;
+    FMM_CUDA_TRY(cudaMalloc(&P.tab.Rw64, sizeof(double) * 8 * nc));
+    FMM_CUDA_TRY(cudaMalloc(&P.tab.Rw32, sizeof(float) * 8 * nc));
+    int ntri2 = (2 * p + 1) * (2 * p + 2) / 2;
+    FMM_CUDA_TRY(cudaMalloc(&P.tab.S, sizeof(double) * 2 * ntri2));
+    FMM_CUDA_TRY(cudaMalloc(&P.tab.T0, sizeof(double) * nc * nc));
+    FMM_CUDA_TRY(cudaMalloc(&P.tab.Top64, sizeof(double) * (size_t)NOFF * nc * nc));
+    FMM_CUDA_TRY(cudaMalloc(&P.tab.Top32, sizeof(float) * (size_t)NOFF * nc * nc));
+    k_octant_table<<<1, 32, 0, P.stream>>>(p, P.tab.Rw64, P.tab.Rw32);
+    FMM_LAUNCH_CHECK(P);
+    size_t shI = sizeof(Cx<double>) * ntri2;
+    k_m2l_operators<<<NOFF, 256, shI, P.stream>>>(p, P.tab.Top64, P.tab.Top32);
+    FMM_LAUNCH_CHECK(P);
+    double kappa = P.kappa > 0 ? P.kappa : 2.0 / P.box;
+    double kb = kappa * P.box;
+    int nu_max = (int)ceil(8.0 / kb) + 3;
+    int nk_max = (int)ceil(2.2 * kb) + 3;
+    k_lattice_sum<<<blocks_for(ntri2, 64), 64, 0, P.stream>>>(2 * p, kb, nu_max, nk_max, P.tab.S);
+    FMM_LAUNCH_CHECK(P);
+    k_lattice_operator<<<1, 256, shI, P.stream>>>(p, P.tab.S, P.tab.T0);
+    FMM_LAUNCH_CHECK(P);
+    FMM_CUDA_TRY(cudaStreamSynchronize(P.stream));
+    return FMM_OK;
+}
+
+void free_tables(Plan &P)
+{
+    cudaFree(P.tab.Rw64);
+    cudaFree(P.tab.Rw32);
+    cudaFree(P.tab.S);
+    cudaFree(P.tab.T0);
+    cudaFree(P.tab.Top64);
+    cudaFree(P.tab.Top32);
+    P.tab = Tables{};
+}
+
+fmm_status launch_upward(Plan &P, bool solute_only)
+{
+    return P.precision == FMM_PREC_FP64 ? upward_t<double>(P, solute_only) : upward_t<float>(P, solute_only);
+}
+
+fmm_status launch_lattice(Plan &P)
+{
+    if (P.precision == FMM_PREC_FP64)
+        k_lattice_apply<double><<<1, ((P.nc + 31) / 32) * 32, 0, P.stream>>>(P.p, P.tab.T0, (const double *)P.M[0],
+                                                                            (double *)P.L[0]);
+    else
+        k_lattice_apply<float><<<1, ((P.nc + 31) / 32) * 32, 0, P.stream>>>(P.p, P.tab.T0, (const float *)P.M[0],
+                                                                           (float *)P.L[0]);
+    FMM_LAUNCH_CHECK(P);
+    return FMM_OK;
+}
+
+fmm_status launch_m2l_simt(Plan &P, int l)
+{
+    int nc = P.nc;
+    int threads = ((nc + 31) / 32) * 32;
+    int64_t np = (int64_t)1 << (l - 1);
+    int64_t ncls = np * np * np;
+    static bool attr_set = false;
+    if (!attr_set) {
+        FMM_CUDA_TRY(cudaFuncSetAttribute(k_m2l_simt<double, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)(sizeof(double) * 16 * NC_MAX)));
+        FMM_CUDA_TRY(cudaFuncSetAttribute(k_m2l_simt<float, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)(sizeof(float) * 32 * NC_MAX)));
+        attr_set = true;
+    }
+    for (int cls = 0; cls < 8; ++cls) {
+        if (P.precision == FMM_PREC_FP64) {
+            constexpr int TT = 16;
+            size_t sh = sizeof(double) * TT * nc;
+            k_m2l_simt<double, TT><<<blocks_for(ncls, TT), threads, sh, P.stream>>>(
+                P.p, l, cls, P.tab.Top64, (const double *)P.M[l], (double *)P.L[l]);
+        } else {
+            constexpr int TT = 32;
+            size_t sh = sizeof(float) * TT * nc;
+            k_m2l_simt<float, TT><<<blocks_for(ncls, TT), threads, sh, P.stream>>>(
+                P.p, l, cls, P.tab.Top32, (const float *)P.M[l], (float *)P.L[l]);
+        }
+        FMM_LAUNCH_CHECK(P);
+    }
+    return FMM_OK;
+}
+
+fmm_status launch_l2l(Plan &P, int l)
+{
+    int ntri = (P.p + 1) * (P.p + 2) / 2;
+    int64_t n1 = (int64_t)1 << l;
+    int64_t n = n1 * n1 * n1 * ntri;
+    if (P.precision == FMM_PREC_FP64)
+        k_l2l<double><<<blocks_for(n, 128), 128, 8 * P.nc * sizeof(double), P.stream>>>(
+            P.p, l, P.tab.Rw64, (const double *)P.L[l - 1], (double *)P.L[l]);
+    else
+        k_l2l<float><<<blocks_for(n, 128), 128, 8 * P.nc * sizeof(float), P.stream>>>(
+            P.p, l, P.tab.Rw32, (const float *)P.L[l - 1], (float *)P.L[l]);
+    FMM_LAUNCH_CHECK(P);
+    return FMM_OK;
+}
+
+fmm_status launch_l2p(Plan &P, bool gradient, bool solute_only)
+{
+    int nside = 1 << P.d;
+    double inv_h = (double)nside / P.box;
+    if (P.precision == FMM_PREC_FP64)
+        k_l2p<double><<<blocks_for(P.N, 128), 128, 0, P.stream>>>(
+            P.p, P.d, P.N, P.sleaf, (const Particle<double> *)P.sorted, inv_h, (const double *)P.L[P.d],
+            (double *)(solute_only ? P.phi_u : P.phi_ff), gradient ? (double *)P.g_ff : nullptr);
+    else
+        k_l2p<float><<<blocks_for(P.N, 128), 128, 0, P.stream>>>(
+            P.p, P.d, P.N, P.sleaf, (const Particle<float> *)P.sorted, (float)inv_h, (const float *)P.L[P.d],
+            (float *)(solute_only ? P.phi_u : P.phi_ff), gradient ? (float *)P.g_ff : nullptr);
+    FMM_LAUNCH_CHECK(P);
+    return FMM_OK;
+}
+
+}  // namespace fmm

@@ -1,0 +1,237 @@
+// fmm_internal.cuh -- shared declarations of the GB300 periodic FMM library.
+//
+// Layouts (all device memory owned by the plan):
+//  * particles are sorted by leaf (linear leaf index x + n (y + n z), n = 2^d)
+//    with a CSR `cell_start[n^3 + 1]`; sorted records hold the coordinates
+//    relative to the leaf centre and the charge, in the path's real type;
+//  * expansion coefficients are real: for degree n, Re C_n^0 at n^2, and for
+//    m >= 1 Re C_n^m at n^2 + 2m - 1 and Im C_n^m at n^2 + 2m (the negative
+//    orders follow from C_n^{-m} = (-1)^m conj C_n^m);  (p+1)^2 reals per cell;
+//  * coefficients are level-scaled: Mhat_n = M_n / h_l^n and
+//    Lhat_n = L_n h_l^(n+1), h_l = b / 2^l, which makes the M2L operator of
+//    Eq. Lcoeffdef depend on the cell offset only;
+//  * cells of level l >= 1 are stored by parity class: cell (x, y, z) has class
+//    c = (x&1) | (y&1)<<1 | (z&1)<<2 and parent coordinates P = (x, y, z) >> 1;
+//    index = c * np^3 + P.x + np (P.y + np P.z), np = 2^(l-1).  Level 0 has one
+//    cell.  A target of class c and its interaction-list source t + delta then
+//    lie in class (c + delta) & 1 at parent offset (c + delta) >> 1, which is
+//    -1, 0 or +1 per axis.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/fmm_gb300.h"
+
+namespace fmm {
+
+constexpr int P_MAX = 20;
+constexpr int NC_MAX = (P_MAX + 1) * (P_MAX + 1);
+constexpr int NOFF = 343;  // 7^3 offset slots for delta in [-3, 3]^3 (316 used for ws = 1)
+
+enum : int { ERRF_NONFINITE = 1, ERRF_INTERNAL = 2, ERRF_TIMEOUT = 4 };
+
+__host__ __device__ inline int ncoef(int p) { return (p + 1) * (p + 1); }
+__host__ __device__ inline int cre(int n, int m) { return m == 0 ? n * n : n * n + 2 * m - 1; }
+__host__ __device__ inline int cim(int n, int m) { return n * n + 2 * m; }
+__host__ __device__ inline int off_slot(int dx, int dy, int dz) { return (dx + 3) + 7 * ((dy + 3) + 7 * (dz + 3)); }
+
+__host__ __device__ inline int64_t cell_index(int l, int x, int y, int z)
+{
+    if (l == 0) return 0;
+    int64_t np = (int64_t)1 << (l - 1);
+    int c = (x & 1) | ((y & 1) << 1) | ((z & 1) << 2);
+    return c * np * np * np + (x >> 1) + np * ((y >> 1) + np * (int64_t)(z >> 1));
+}
+
+template <typename T>
+struct Particle {  // sorted record: position relative to the leaf centre, charge
+    T x, y, z, q;
+};
+
+template <typename T>
+struct alignas(2 * sizeof(T)) Cx {
+    T re, im;
+};
+template <typename T>
+__host__ __device__ inline Cx<T> cmul(Cx<T> a, Cx<T> b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+
+// Level-independent tables built once per plan.
+struct Tables {
+    double *Rw64 = nullptr;   // [8][NC] real R_n^m(w_c), w_c = child-centre offset / parent side (+-1/4)
+    float *Rw32 = nullptr;
+    double *S = nullptr;      // [NC2] complex lattice sum S_j^k (j <= 2p, k >= 0), scaled to a unit box
+    double *T0 = nullptr;     // [NC][NC] real lattice operator (input-major: T0[k * NC + j])
+    double *Top64 = nullptr;  // [NOFF][NC][NC] real M2L operators (input-major), FP64 path
+    float *Top32 = nullptr;   // same in FP32 for the SIMT FP32 path
+};
+
+struct Plan {
+    // problem
+    double box = 0;
+    int64_t N = 0;
+    int d = 0, p = 0, ws = 1;
+    int precision = FMM_PREC_FP64;
+    int split = FMM_SPLIT_BF16X3;
+    double kappa = 0;  // 0 = default 2 / box
+    cudaStream_t stream = 0;
+    bool timings_on = false;
+    int nc = 0;
+    int64_t nleaf = 0;  // 8^d
+    int64_t launches = 0;
+
+    // particles
+    double *in_pos = nullptr, *in_q = nullptr, *out_forces = nullptr;  // staging for host pointers
+    uint8_t *in_sol = nullptr;
+    double *wpos = nullptr;        // [N][3] wrapped input positions (original order)
+    int *key = nullptr;            // [N] leaf of each particle
+    int *perm = nullptr;           // [N] sorted slot -> original index
+    int *sleaf = nullptr;          // [N] leaf of each sorted slot
+    int *cell_start = nullptr;     // [nleaf + 1]
+    int *cell_fill = nullptr;      // [nleaf]
+    int *scan_tmp = nullptr;
+    void *sorted = nullptr;        // Particle<T>[N]
+    void *sorted_u = nullptr;      // Particle<T>[N] with solvent charges zeroed (solute-only pass)
+    uint8_t *sorted_sol = nullptr; // [N]
+    void *phi_nf = nullptr, *phi_ff = nullptr;  // T[N] per-particle potentials (sorted order)
+    void *phi_u = nullptr;                      // T[N] solute-only far-field potential
+    void *f_nf = nullptr, *g_ff = nullptr;      // T[N][3] near-field field, far-field gradient
+    // expansions per level (T, class layout)
+    void *M[9] = {};
+    void *L[9] = {};
+    // tensor-core M2L planes (bf16, halo-padded), built by the TC path
+    void *tc_planes = nullptr;
+    size_t tc_plane_bytes = 0;
+    void *tc_ops = nullptr;
+    // reductions
+    double *red_partial = nullptr;  // partial sums
+    double *red_out = nullptr;      // [32] final FP64 scalars
+    double *h_out = nullptr;        // pinned host mirror
+    int *d_err = nullptr;
+    Tables tab;
+    cudaEvent_t ev[12] = {};
+    fmm_timings last{};
+};
+
+// ------------------------------------------------------------------ device helpers
+// Regular solid harmonics by their Cartesian recurrences:
+//   R_0^0 = 1,  R_m^m = -(x + i y) R_{m-1}^{m-1} / (2m),
+//   R_n^m = ((2n-1) z R_{n-1}^m - r^2 R_{n-2}^m) / ((n+m)(n-m)).
+// out must hold ncoef(p) reals (layout above).
+template <typename T>
+__host__ __device__ inline void regular_real(int p, T x, T y, T z, T *out)
+{
+    T r2 = x * x + y * y + z * z;
+    T dre = 1, dim = 0;  // R_m^m
+    for (int m = 0; m <= p; ++m) {
+        if (m > 0) {
+            T s = T(-0.5) / T(m);
+            T nre = s * (x * dre - y * dim);
+            T nim = s * (x * dim + y * dre);
+            dre = nre;
+            dim = nim;
+        }
+        T p2re = 0, p2im = 0, p1re = dre, p1im = dim;
+        out[cre(m, m)] = dre;
+        if (m > 0) out[cim(m, m)] = dim;
+        for (int n = m + 1; n <= p; ++n) {
+            T a = T(2 * n - 1) * z, b = r2;
+            T inv = T(1) / T((n + m) * (n - m));
+            T cr = (a * p1re - b * p2re) * inv;
+            T ci = (a * p1im - b * p2im) * inv;
+            out[cre(n, m)] = cr;
+            if (m > 0) out[cim(n, m)] = ci;
+            p2re = p1re;
+            p2im = p1im;
+            p1re = cr;
+            p1im = ci;
+        }
+    }
+}
+
+// Irregular solid harmonics I_n^m (sign (-1)^(n+m) folded in) up to degree pmax,
+// complex m >= 0 only: out[n*(n+1)/2 + m].
+//   I_0^0 = 1/r,  I_m^m = -(2m-1)(x + i y) I_{m-1}^{m-1} / r^2,
+//   I_n^m = (-(2n-1) z I_{n-1}^m - (n+m-1)(n-m-1) I_{n-2}^m) / r^2.
+__host__ __device__ inline int tri(int n, int m) { return n * (n + 1) / 2 + m; }
+
+template <typename T>
+__host__ __device__ inline void irregular_tri(int pmax, T x, T y, T z, Cx<T> *out)
+{
+    T r2 = x * x + y * y + z * z;
+    T ir2 = T(1) / r2;
+    Cx<T> dg = {T(1) / sqrt(r2), T(0)};
+    for (int m = 0; m <= pmax; ++m) {
+        if (m > 0) {
+            T s = -T(2 * m - 1) * ir2;
+            Cx<T> nd = {s * (x * dg.re - y * dg.im), s * (x * dg.im + y * dg.re)};
+            dg = nd;
+        }
+        out[tri(m, m)] = dg;
+        Cx<T> p2 = {0, 0}, p1 = dg;
+        for (int n = m + 1; n <= pmax; ++n) {
+            T a = -T(2 * n - 1) * z, b = T((n + m - 1) * (n - m - 1));
+            Cx<T> c = {(a * p1.re - b * p2.re) * ir2, (a * p1.im - b * p2.im) * ir2};
+            out[tri(n, m)] = c;
+            p2 = p1;
+            p1 = c;
+        }
+    }
+}
+
+// complex coefficient of order m (any sign) from the real layout
+template <typename T>
+__host__ __device__ inline Cx<T> coef(const T *a, int n, int m)
+{
+    if (m == 0) return {a[n * n], T(0)};
+    int am = m < 0 ? -m : m;
+    Cx<T> v = {a[n * n + 2 * am - 1], a[n * n + 2 * am]};
+    if (m < 0) {
+        v.im = -v.im;
+        if (am & 1) {
+            v.re = -v.re;
+            v.im = -v.im;
+        }
+    }
+    return v;
+}
+
+// ------------------------------------------------------------------ launchers
+// sort / reductions (fmm_sort.cu)
+fmm_status launch_assign_sort(Plan &P, const double *pos, const double *q, const uint8_t *sol);
+fmm_status launch_bc_moments(Plan &P, const double *q, const uint8_t *sol);
+fmm_status launch_energy_reduce(Plan &P, bool with_uv);
+fmm_status launch_forces_out(Plan &P, const double *q, double *forces);
+
+// expansions (fmm_expand.cu)
+fmm_status build_tables(Plan &P);
+void free_tables(Plan &P);
+fmm_status launch_upward(Plan &P, bool solute_only);
+fmm_status launch_lattice(Plan &P);
+fmm_status launch_m2l_simt(Plan &P, int level);
+fmm_status launch_l2l(Plan &P, int level);
+fmm_status launch_l2p(Plan &P, bool gradient, bool solute_only);
+
+// near field (fmm_p2p.cu)
+fmm_status launch_p2p(Plan &P, bool forces);
+fmm_status launch_p2p_uv(Plan &P);
+
+// tensor-core M2L (fmm_m2l_tc.cu)
+bool tc_available(const Plan &P, int level);
+fmm_status tc_prepare(Plan &P);
+fmm_status launch_m2l_tc(Plan &P, int level);
+void tc_free(Plan &P);
+
+#define FMM_CUDA_TRY(expr)                                        \
+    do {                                                          \
+        cudaError_t e_ = (expr);                                  \
+        if (e_ != cudaSuccess) return e_ == cudaErrorMemoryAllocation ? FMM_ERR_OOM : FMM_ERR_CUDA; \
+    } while (0)
+
+#define FMM_LAUNCH_CHECK(P)                                       \
+    do {                                                          \
+        (P).launches++;                                           \
+        cudaError_t e_ = cudaGetLastError();                      \
+        if (e_ != cudaSuccess) return FMM_ERR_CUDA;               \
+    } while (0)
+
+}  // namespace fmm

@@ -1,0 +1,219 @@
+"""Thin Python binding of the C ABI in include/fmm_gb300.h (argument marshalling only).
+
+Every step of an evaluation runs in the CUDA library ``libfmm_gb300.so``; this
+module only passes pointers, sizes and options.  If the library is missing the
+calls fail loudly -- there is no CPU fallback.
+
+Inputs may be CUDA tensors (float64 positions [N, 3], float64 charges [N],
+uint8 solute flags [N]) or host NumPy arrays / CPU tensors; host inputs go
+through the library's own host<->device copies.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfmm_gb300.so")
+
+FMM_OPT_WS, FMM_OPT_PRECISION, FMM_OPT_KAPPA, FMM_OPT_M2L_SPLIT, FMM_OPT_STREAM, FMM_OPT_TIMINGS = 1, 2, 3, 4, 5, 6
+PRECISION = {"fp64": 0, "mixed": 1}
+SPLIT = {"bf16x3": 0, "bf16x2": 1, "fp32": 2}
+STATUS = ["ok", "invalid argument", "non-finite input", "CUDA error", "out of memory", "timeout",
+          "internal error", "unsupported"]
+
+
+class FMMError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        msg = STATUS[code] if 0 <= code < len(STATUS) else "status %d" % code
+        super().__init__("%s: %s (status %d)" % (where, msg, code))
+
+
+class EnergyTerms(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in ("near", "far", "charged", "quad_surface", "dipole_surface", "total")]
+
+    def asdict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class UVTerms(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in ("e_uv", "W", "A", "B", "C", "nf_uv", "bc_cross")]
+
+    def asdict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Timings(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_float) for k in ("sort", "upward", "lattice", "m2l", "downward", "l2p", "p2p", "reduce",
+                                              "total")]
+
+    def asdict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_LIB = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libfmm_gb300.so (raises if it has not been built)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(path):
+        raise RuntimeError("libfmm_gb300.so not found at %s: run paper_2003_13218_gb300/build.py "
+                           "(or __graft_entry__.build()) first" % path)
+    L = ctypes.CDLL(path)
+    vp, i64, c_int, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    L.fmm_plan_create.argtypes = [dbl, i64, c_int, c_int, ctypes.POINTER(vp)]
+    L.fmm_plan_create.restype = c_int
+    L.fmm_plan_set_option.argtypes = [vp, c_int, i64, dbl]
+    L.fmm_plan_set_option.restype = c_int
+    L.fmm_energy.argtypes = [vp, vp, vp, ctypes.POINTER(dbl), ctypes.POINTER(EnergyTerms)]
+    L.fmm_energy.restype = c_int
+    L.fmm_forces.argtypes = [vp, vp, vp, vp, ctypes.POINTER(dbl)]
+    L.fmm_forces.restype = c_int
+    L.fmm_solute_solvent_energy.argtypes = [vp, vp, vp, vp, ctypes.POINTER(dbl), ctypes.POINTER(UVTerms)]
+    L.fmm_solute_solvent_energy.restype = c_int
+    L.fmm_evaluate.argtypes = [vp, vp, vp, vp, vp, ctypes.POINTER(EnergyTerms), ctypes.POINTER(UVTerms)]
+    L.fmm_evaluate.restype = c_int
+    L.fmm_plan_get_timings.argtypes = [vp, ctypes.POINTER(Timings)]
+    L.fmm_plan_get_timings.restype = c_int
+    L.fmm_plan_last_launch_count.argtypes = [vp]
+    L.fmm_plan_last_launch_count.restype = i64
+    L.fmm_plan_destroy.argtypes = [vp]
+    L.fmm_plan_destroy.restype = None
+    L.fmm_status_string.argtypes = [c_int]
+    L.fmm_status_string.restype = ctypes.c_char_p
+    _LIB = L
+    return L
+
+
+def _check(code, where):
+    if code != 0:
+        raise FMMError(code, where)
+
+
+def _ptr(x):
+    """(pointer, keepalive) for a CUDA/CPU tensor or NumPy array; None stays None."""
+    if x is None:
+        return None, None
+    if isinstance(x, torch.Tensor):
+        if not x.is_contiguous():
+            x = x.contiguous()
+        return ctypes.c_void_p(x.data_ptr()), x
+    a = np.ascontiguousarray(x)
+    return ctypes.c_void_p(a.ctypes.data), a
+
+
+class FMMPlan:
+    """A plan for N charges in a cubic box of side ``box`` (A), depth d, order p."""
+
+    def __init__(self, box: float, N: int, depth: int, p: int, precision: str = "fp64", kappa: float | None = None,
+                 split: str = "bf16x3", timings: bool = False):
+        self._lib = load_library()
+        h = ctypes.c_void_p()
+        _check(self._lib.fmm_plan_create(float(box), int(N), int(depth), int(p), ctypes.byref(h)), "fmm_plan_create")
+        self._h = h
+        self.box, self.N, self.depth, self.p = float(box), int(N), int(depth), int(p)
+        if split != "bf16x3":
+            self.set_option(FMM_OPT_M2L_SPLIT, SPLIT[split])
+        if precision != "fp64":
+            self.set_option(FMM_OPT_PRECISION, PRECISION[precision])
+        if kappa is not None:
+            self.set_option(FMM_OPT_KAPPA, 0, float(kappa))
+        if timings:
+            self.set_option(FMM_OPT_TIMINGS, 1)
+        self.precision = precision
+
+    def set_option(self, key: int, ival: int = 0, dval: float = 0.0):
+        _check(self._lib.fmm_plan_set_option(self._h, int(key), int(ival), float(dval)), "fmm_plan_set_option")
+
+    def _bind_stream(self, *tensors):
+        if any(isinstance(t, torch.Tensor) and t.is_cuda for t in tensors if t is not None):
+            s = torch.cuda.current_stream().cuda_stream
+            self._lib.fmm_plan_set_option(self._h, FMM_OPT_STREAM, int(s), 0.0)
+
+    def evaluate(self, pos, q, is_solute=None, forces=None, want_terms=True):
+        """fmm_evaluate: returns (terms dict or None, uv dict or None); fills ``forces`` if given."""
+        self._bind_stream(pos, q, is_solute, forces)
+        pp, kp = _ptr(pos)
+        pq, kq = _ptr(q)
+        ps, ks = _ptr(is_solute)
+        pf, kf = _ptr(forces)
+        t = EnergyTerms()
+        u = UVTerms()
+        _check(self._lib.fmm_evaluate(self._h, pp, pq, ps, pf, ctypes.byref(t) if want_terms else None,
+                                      ctypes.byref(u) if is_solute is not None else None), "fmm_evaluate")
+        return (t.asdict() if want_terms else None), (u.asdict() if is_solute is not None else None)
+
+    def energy(self, pos, q):
+        self._bind_stream(pos, q)
+        pp, kp = _ptr(pos)
+        pq, kq = _ptr(q)
+        e = ctypes.c_double()
+        t = EnergyTerms()
+        _check(self._lib.fmm_energy(self._h, pp, pq, ctypes.byref(e), ctypes.byref(t)), "fmm_energy")
+        return e.value, t.asdict()
+
+    def forces(self, pos, q, out=None, with_energy=True):
+        if out is None:
+            if isinstance(pos, torch.Tensor):
+                out = torch.empty((self.N, 3), dtype=torch.float64, device=pos.device)
+            else:
+                out = np.empty((self.N, 3), dtype=np.float64)
+        self._bind_stream(pos, q, out)
+        pp, kp = _ptr(pos)
+        pq, kq = _ptr(q)
+        pf, kf = _ptr(out)
+        e = ctypes.c_double()
+        _check(self._lib.fmm_forces(self._h, pp, pq, pf, ctypes.byref(e) if with_energy else None), "fmm_forces")
+        return out, (e.value if with_energy else None)
+
+    def solute_solvent_energy(self, pos, q, is_solute):
+        self._bind_stream(pos, q, is_solute)
+        pp, kp = _ptr(pos)
+        pq, kq = _ptr(q)
+        ps, ks = _ptr(is_solute)
+        e = ctypes.c_double()
+        u = UVTerms()
+        _check(self._lib.fmm_solute_solvent_energy(self._h, pp, pq, ps, ctypes.byref(e), ctypes.byref(u)),
+               "fmm_solute_solvent_energy")
+        return e.value, u.asdict()
+
+    def timings(self):
+        t = Timings()
+        _check(self._lib.fmm_plan_get_timings(self._h, ctypes.byref(t)), "fmm_plan_get_timings")
+        return t.asdict()
+
+    def last_launch_count(self) -> int:
+        return int(self._lib.fmm_plan_last_launch_count(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.fmm_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class FmmEnergy(torch.autograd.Function):
+    """E = V_elec(pos, q) with the hand-written adjoint: dE/dpos = -F (fmm_forces)."""
+
+    @staticmethod
+    def forward(ctx, pos, q, plan: FMMPlan):
+        F, e = plan.forces(pos.detach(), q.detach())
+        ctx.save_for_backward(F)
+        return torch.tensor(e, dtype=torch.float64, device=pos.device)
+
+    @staticmethod
+    def backward(ctx, grad_e):
+        (F,) = ctx.saved_tensors
+        return -F * grad_e, None, None

@@ -1,0 +1,197 @@
+"""GPU path vs the FP64 oracle, through the C ABI (marshalled by the thin binding).
+
+Tolerances:
+  * FP64 path: the same operators in the same precision, differing only in
+    summation order -> 1e-12 relative on energies, 1e-10 of the RMS force;
+  * mixed path (FP32 P2P/P2M/M2M/L2L/L2P, FP64 lattice and reductions):
+    1e-6 relative energy, 1e-5 relative RMS force (the stated error budget).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2003_13218_gb300 import boxes
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+def _plan(L, N, d, p, **kw):
+    from paper_2003_13218_gb300.fmm import FMMPlan
+    return FMMPlan(L, N, d, p, **kw)
+
+
+def _t(a, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a)).to(device=DEV, dtype=dtype)
+
+
+def _rms_rel(F, ref):
+    return np.sqrt(np.mean((F - ref) ** 2)) / np.sqrt(np.mean(ref ** 2))
+
+
+def _run(pos, q, L, d, p, precision="fp64", sol=None, **kw):
+    plan = _plan(L, len(q), d, p, precision=precision, **kw)
+    F = torch.empty((len(q), 3), dtype=torch.float64, device=DEV)
+    terms, uv = plan.evaluate(_t(pos), _t(q), None if sol is None else _t(sol, torch.uint8), forces=F)
+    torch.cuda.synchronize()
+    plan.close()
+    return terms, uv, F.cpu().numpy()
+
+
+CASES = [
+    # (name, N, L, d, p, seed) -- sizes span several tiles and a ragged tail
+    ("tiny", 37, 2.0, 2, 6, 1),
+    ("small", 700, 5.0, 3, 8, 2),
+    ("ragged", 1531, 7.0, 3, 10, 3),
+]
+
+
+@pytest.mark.parametrize("name,N,L,d,p,seed", CASES)
+def test_fp64_random_charged_boxes(name, N, L, d, p, seed):
+    pos, q = boxes.random_charges(N, L, seed=seed)
+    ref = oracle.fmm(pos, q, L, d, p)
+    terms, _, F = _run(pos, q, L, d, p)
+    for k in ("near", "far", "charged", "quad_surface", "dipole_surface"):
+        assert abs(terms[k] - ref[k]) <= 1e-12 * (abs(ref[k]) + abs(ref["total"])), k
+    assert abs(terms["total"] - ref["total"]) <= 1e-12 * abs(ref["total"])
+    assert _rms_rel(F, ref["forces"]) < 1e-10
+
+
+def test_fp64_ion_in_water_small_workload():
+    b, d, p = boxes.workload("mg_3k")
+    ref = oracle.fmm(b.pos, b.q, b.L, d, p)
+    terms, _, F = _run(b.pos, b.q, b.L, d, p)
+    assert abs(terms["total"] - ref["total"]) <= 1e-12 * abs(ref["total"])
+    assert abs(terms["far"] - ref["far"]) <= 1e-12 * abs(ref["total"])
+    assert _rms_rel(F, ref["forces"]) < 1e-10
+
+
+def test_mixed_ion_in_water_p12():
+    b, d, _ = boxes.workload("mg_3k")
+    p = 12
+    ref = oracle.fmm(b.pos, b.q, b.L, d, p)
+    terms, _, F = _run(b.pos, b.q, b.L, d, p, precision="mixed")
+    assert abs(terms["total"] - ref["total"]) <= 1e-6 * abs(ref["total"])
+    assert _rms_rel(F, ref["forces"]) < 1e-5
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("mixed", 1e-5)])
+def test_solute_solvent_against_oracle(precision, tol):
+    b, d, _ = boxes.workload("mg_3k")
+    p = 10
+    ref = oracle.solute_solvent(b.pos, b.q, b.is_solute, b.L, d, p)
+    _, uv, _ = _run(b.pos, b.q, b.L, d, p, precision=precision, sol=b.is_solute)
+    scale = abs(ref["A"]) + abs(ref["C"]) + abs(ref["e_uv"])
+    for k in ("e_uv", "W", "A", "B", "C", "nf_uv", "bc_cross"):
+        assert abs(uv[k] - ref[k]) <= tol * scale, (k, uv[k], ref[k])
+
+
+def test_single_charge_wigner_edge_case():
+    """N = 1: empty near field, all leaves but one empty; quad and dipole terms cancel."""
+    L = 3.0
+    pos = np.array([[0.4, 2.2, 1.3]])
+    q = np.array([1.5])
+    ref = oracle.fmm(pos, q, L, 2, 12)
+    terms, _, F = _run(pos, q, L, 2, 12)
+    assert abs(terms["total"] - ref["total"]) <= 1e-12 * abs(ref["total"])
+    assert terms["near"] == 0.0
+    assert np.max(np.abs(F - ref["forces"])) < 1e-10
+
+
+def test_wrapping_and_faces():
+    """Positions outside [0, L), on cell faces and on the box face x = L wrap as the oracle does."""
+    L, N = 4.0, 64
+    pos, q = boxes.random_charges(N, L, seed=9)
+    pos[0] = [L, 0.5 * L, 0.25 * L]        # x = L wraps to 0; y, z on faces of every level
+    pos[1] = [-0.3, 5.1, 11.7]            # outside the box
+    pos[2] = [0.0, 0.0, 0.0]
+    pos[3] = [L / 8, 3 * L / 8, 7 * L / 8]  # leaf corners at d = 3
+    ref = oracle.fmm(pos, q, L, 3, 8)
+    terms, _, F = _run(pos, q, L, 3, 8)
+    assert abs(terms["total"] - ref["total"]) <= 1e-12 * abs(ref["total"])
+    assert _rms_rel(F, ref["forces"]) < 1e-10
+
+
+def test_empty_leaves_deep_tree():
+    """Most leaves empty (N = 20, d = 4)."""
+    pos, q = boxes.random_charges(20, 3.0, seed=4)
+    ref = oracle.fmm(pos, q, 3.0, 4, 6)
+    terms, _, F = _run(pos, q, 3.0, 4, 6)
+    assert abs(terms["total"] - ref["total"]) <= 1e-12 * abs(ref["total"])
+    assert _rms_rel(F, ref["forces"]) < 1e-10
+
+
+def test_nonfinite_input_is_reported():
+    from paper_2003_13218_gb300.fmm import FMMError
+    pos, q = boxes.random_charges(50, 2.0, seed=5)
+    pos[7, 1] = np.nan
+    plan = _plan(2.0, 50, 2, 4)
+    with pytest.raises(FMMError) as e:
+        plan.energy(_t(pos), _t(q))
+    assert e.value.code == 2
+    plan.close()
+
+
+def test_invalid_arguments_are_rejected():
+    from paper_2003_13218_gb300.fmm import FMMError
+    for args in [(0.0, 10, 3, 4), (1.0, 0, 3, 4), (1.0, 10, 1, 4), (1.0, 10, 3, 21), (float("nan"), 10, 3, 4)]:
+        with pytest.raises(FMMError) as e:
+            _plan(*args)
+        assert e.value.code == 1
+    plan = _plan(2.0, 10, 2, 4)
+    with pytest.raises(FMMError) as e:
+        plan.set_option(1, 2)  # ws = 2 not built
+    assert e.value.code == 7
+    plan.close()
+
+
+def test_host_pointers_match_device_pointers():
+    pos, q = boxes.random_charges(300, 4.0, seed=6)
+    plan = _plan(4.0, 300, 3, 6)
+    Fd, ed = plan.forces(_t(pos), _t(q))
+    Fh, eh = plan.forces(pos, q)  # numpy host arrays: copies inside the call
+    assert ed == eh
+    assert np.array_equal(Fd.cpu().numpy(), Fh)
+    plan.close()
+
+
+def test_repeatable_bitwise():
+    pos, q = boxes.random_charges(500, 4.0, seed=7)
+    a = _run(pos, q, 4.0, 3, 8, precision="mixed")
+    b = _run(pos, q, 4.0, 3, 8, precision="mixed")
+    assert a[0]["total"] == b[0]["total"]
+    assert np.array_equal(a[2], b[2])
+
+
+def test_autograd_adjoint_matches_finite_differences():
+    """Forces are the exact gradient of the FP64 energy (away from leaf faces)."""
+    from paper_2003_13218_gb300.fmm import FmmEnergy
+    b = boxes.ion_in_water(200, "Mg", seed=8, L=18.0)
+    pos, q = b.pos, b.q
+    d, p = 3, 8
+    plan = _plan(b.L, b.N, d, p)
+    x = _t(pos).requires_grad_(True)
+    e = FmmEnergy.apply(x, _t(q), plan)
+    e.backward()
+    g = x.grad.cpu().numpy()
+    h = 1e-4  # A, central differences
+    leaf = b.L / 2 ** d
+    checked = 0
+    for i in range(64):
+        fr = pos[i] / leaf
+        if np.min(np.abs(fr - np.round(fr))) * leaf < 3 * h:
+            continue
+        for a in range(3):
+            pp = pos.copy()
+            pm = pos.copy()
+            pp[i, a] += h
+            pm[i, a] -= h
+            fd = (plan.energy(_t(pp), _t(q))[0] - plan.energy(_t(pm), _t(q))[0]) / (2 * h)
+            assert abs(fd - g[i, a]) < 1e-6 * (1 + abs(g[i, a]))
+        checked += 1
+    assert checked >= 10
+    plan.close()
