@@ -1,0 +1,362 @@
+#!/usr/bin/env python
+"""Throughput of the periodic FMM with a neutralising background charge.
+
+One step = one pass of the whole hot path on one batch: leaf sort, P2M, M2M,
+level-0 lattice (Eq. 12), M2L + L2L on every level, L2P with gradient, near
+field, background-charge terms (Eq. Velecfull), forces, and the reduced-far-
+field solute-solvent energy (Eq. FMMcalc) -- one fmm_evaluate call.
+
+Default workload: Na+ + 333,333 rigid TIP3P waters (N = 1,000,000, L = 215.3 A),
+depth 6, p = 12, ws = 1, mixed precision (FP32 near field and expansions,
+FP64 lattice operator, background terms and reductions).  The FP64 path on
+the same input is timed beside it and the mixed path's error against it is
+reported.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+For N > 1 launch with torch.distributed.run: every rank evaluates its own
+replica of the workload (the single-box path does not shard; weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-evals/s, FMM energy+forces @1M charges: mixed vs FP64 at ≤1e-6 rel err"
+UNIT = "particle-evals/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+# FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.070 GHz
+FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+# DRAM bytes of one M2L stage from an ncu capture; recorded with the sha256 of
+# the kernel source they were taken on (null once the kernel has changed).
+M2L_TRAFFIC = None  # {"src": "paper_2003_13218_gb300/csrc/...", "sha256": "...", "bytes_per_launch": ...}
+
+
+def m2l_flops(d: int, p: int) -> float:
+    """Algorithmic flops of the M2L stage: 2 C^2 per (target, source) pair, 189 pairs per target."""
+    C = (p + 1) ** 2
+    pairs = 189 * sum(8 ** l for l in range(1, d + 1))
+    return 2.0 * C * C * pairs
+
+
+def load_peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return FALLBACK_PEAKS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.lines = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def src_sha(rel):
+    try:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            return hashlib.sha256(f.read()).hexdigest()
+    except OSError:
+        return None
+
+
+# --------------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2003_13218_gb300 import boxes
+    from paper_2003_13218_gb300.fmm import FMMPlan
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    box, d, p = boxes.workload(args.workload, seed=rank)
+    N = box.N
+    pos = torch.from_numpy(box.pos).to(dev)
+    q = torch.from_numpy(box.q).to(dev)
+    sol = torch.from_numpy(box.is_solute).to(dev)
+    F = torch.empty((N, 3), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
+
+    plan = FMMPlan(box.L, N, d, p, precision="mixed", split=args.split, timings=True)
+    for _ in range(args.warmup):
+        plan.evaluate(pos, q, sol, forces=F)
+    torch.cuda.synchronize()
+    launches = plan.last_launch_count()
+    backend = plan.m2l_backend(d)
+
+    sampler = ClockSampler(local)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    stream = torch.cuda.current_stream()
+    ms_total = 0.0
+    m2l_ms = []
+    terms = uv = None
+    for _ in range(args.steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        terms, uv = plan.evaluate(pos, q, sol, forces=F)
+        e1.record(stream)
+        e1.synchronize()
+        ms_total += e0.elapsed_time(e1)
+        m2l_ms.append(plan.timings()["m2l_kernels"])
+        flush.zero_()  # L2 flush between timed steps (not timed)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    if ws > 1:
+        t = torch.tensor([ms_total], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+        dist.barrier()
+    stage = plan.timings()
+    F_mixed = F.cpu().numpy()
+
+    # end to end through the public API with host buffers (copies inside the call)
+    hpos, hq, hsol = box.pos, box.q, box.is_solute
+    hF = np.empty((N, 3))
+    plan.evaluate(hpos, hq, hsol, forces=hF)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        plan.evaluate(hpos, hq, hsol, forces=hF)
+    e2e_s = time.perf_counter() - t0
+    plan.close()
+
+    # the FP64 path on the same input
+    fp64 = None
+    if args.fp64_steps > 0:
+        p64 = FMMPlan(box.L, N, d, p, precision="fp64", timings=True)
+        F64 = torch.empty_like(F)
+        t64, uv64 = p64.evaluate(pos, q, sol, forces=F64)
+        torch.cuda.synchronize()
+        ms64 = 0.0
+        for _ in range(args.fp64_steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            t64, uv64 = p64.evaluate(pos, q, sol, forces=F64)
+            e1.record(stream)
+            e1.synchronize()
+            ms64 += e0.elapsed_time(e1)
+            flush.zero_()
+        F64h = F64.cpu().numpy()
+        p64.close()
+        fp64 = {
+            "value": N * args.fp64_steps / (ms64 / 1e3) * ws,
+            "ms_per_step": ms64 / args.fp64_steps,
+            "steps": args.fp64_steps,
+            "rel_err_energy_mixed_vs_fp64": abs(terms["total"] - t64["total"]) / abs(t64["total"]),
+            "rel_rms_force_err_mixed_vs_fp64": float(np.sqrt(np.mean((F_mixed - F64h) ** 2)) /
+                                                     np.sqrt(np.mean(F64h ** 2))),
+            "abs_err_e_uv_mixed_vs_fp64": abs(uv["e_uv"] - uv64["e_uv"]),
+        }
+
+    if rank != 0:
+        if ws > 1:
+            dist.destroy_process_group()
+        return
+    value = N * args.steps * ws / (ms_total / 1e3)
+    peaks, peak_kind = load_peaks()
+    flops = m2l_flops(d, p)
+    m2l_avg_ms = statistics.mean(m2l_ms)
+    achieved = flops / (m2l_avg_ms / 1e3) / 1e12
+    uses_tc = backend == "tcgen05"
+    if uses_tc:
+        peak = peaks.get("bf16_tflops", FALLBACK_PEAKS["bf16_tflops"])
+        roof = {"bound": "tensor", "peak_source": peak_kind + " bf16 dense burst"}
+    else:
+        peak = FP32_ALU_TFLOPS
+        roof = {"bound": "alu", "peak_source": "FP32 CUDA-core peak from unit counts and max clock"}
+    traffic = None
+    if M2L_TRAFFIC and src_sha(M2L_TRAFFIC["src"]) == M2L_TRAFFIC["sha256"]:
+        traffic = M2L_TRAFFIC["bytes_per_launch"]
+    roof.update({"kernel": "M2L (all levels, one call)", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                 "frac": achieved / peak, "traffic": traffic, "algorithmic_flops_per_launch": flops,
+                 "avg_launch_ms": m2l_avg_ms})
+    out = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_total / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32+bf16x3-tensor+f64" if uses_tc else "f32+f64",
+        "data": "synthetic (seeded ion-in-water boxes standing in for the paper's MD snapshots)",
+        "config": {"workload": "%s: %s+ + %d TIP3P waters, N=%d, L=%.2f A, depth %d, p %d, ws 1, mixed precision, "
+                               "energy+forces+solute-solvent per step" % (args.workload, box.ion, box.n_waters, N,
+                                                                          box.L, d, p),
+                   "l2": "flushed between timed steps (256 MB write)", "parallelism": "replicas" if ws > 1 else "1 GPU",
+                   "m2l_split": args.split},
+        "roofline": roof,
+        "e2e": {"value": N * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": N * (24 + 8 + 1),
+                "d2h_bytes_per_step": N * 24 + 29 * 8 + 4},
+        "gpu_launches": launches * args.steps,
+        "clocks": clocks,
+        "stage_ms": stage,
+        "fp64_path": fp64,
+    }
+    if ws == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args.workload)
+    print(json.dumps(out), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+# --------------------------------------------------------------------- the oracle
+def sample_box(workload: str, shrink: int):
+    """A sub-box of the workload with the same density, leaf occupancy and order p:
+    1/shrink^3 of the waters in a box 1/shrink the side, depth reduced by log2(shrink)."""
+    from paper_2003_13218_gb300 import boxes
+    w = boxes.WORKLOADS[workload]
+    L = w["L"] if w["L"] is not None else (w["n_waters"] / boxes.WATER_DENSITY) ** (1 / 3)
+    k = int(round(math.log2(shrink)))
+    b = boxes.ion_in_water(w["n_waters"] // shrink ** 3, w["ion"], seed=0, L=L / shrink)
+    return b, w["depth"] - k, w["p"]
+
+
+def oracle_step(b, d, p):
+    import oracle
+    oracle.fmm(b.pos, b.q, b.L, d, p, forces=True)
+    oracle.solute_solvent(b.pos, b.q, b.is_solute, b.L, d, p)
+
+
+def cpu_baseline(workload: str):
+    import oracle
+    b, d, p = sample_box(workload, 4)
+    t0 = time.perf_counter()
+    oracle_step(b, d, p)
+    dt = time.perf_counter() - t0
+    return {"value": b.N / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": "one energy+forces+solute-solvent evaluation of a 1/64 sub-box of the workload "
+                      "(N=%d, L=%.2f A, depth %d, p %d: same density, leaf occupancy and order), %.1f s" %
+                      (b.N, b.L, d, p, dt)}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    b, d, p = sample_box(args.workload, 8)
+    for _ in range(args.warmup):
+        oracle_step(b, d, p)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_step(b, d, p)
+    dt = time.perf_counter() - t0
+    value = b.N * args.steps / dt
+    sample = ("per step one energy+forces+solute-solvent evaluation of a 1/512 sub-box of the workload "
+              "(N=%d, L=%.2f A, depth %d, p %d: same density, leaf occupancy and order)" % (b.N, b.L, d, p))
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload + " (bounded CPU sample, see cpu_baseline.sample)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="na_1m")
+    ap.add_argument("--split", default="bf16x3", choices=["bf16x3", "bf16x2", "fp32"])
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -83,9 +83,12 @@ typedef struct {
                         - (4 pi/3V) mu_u . mu_v */
 } fmm_uv_terms;
 
-/* Per-stage device times of the last call, milliseconds (CUDA events). */
+/* Per-stage device times of the last call, milliseconds (CUDA events on the
+ * plan's stream).  m2l_l2l covers M2L and L2L of levels 1..l_max of the full
+ * pass; m2l_kernels the M2L launches alone; solute_pass the solute-only pass
+ * of Eq. FMMcalc (0 when not requested). */
 typedef struct {
-    float sort, upward, lattice, m2l, downward, l2p, p2p, reduce, total;
+    float sort, upward, lattice, m2l_l2l, l2p, p2p, solute_pass, reduce, total, m2l_kernels;
 } fmm_timings;
 
 /* Options for fmm_plan_set_option. */
@@ -164,6 +167,11 @@ fmm_status fmm_plan_get_timings(fmm_plan plan, fmm_timings *out);
 
 /* Number of kernel launches enqueued by the last call. */
 int64_t fmm_plan_last_launch_count(fmm_plan plan);
+
+/* Which M2L implementation the plan runs at `level` (1..depth):
+ * 0 = FP64 CUDA cores, 1 = FP32 CUDA cores, 2 = tcgen05 tensor cores;
+ * -1 for a NULL plan or a level out of range. */
+int fmm_plan_m2l_backend(fmm_plan plan, int level);
 
 /* Release the plan and its device memory.  Accepts NULL. */
 void fmm_plan_destroy(fmm_plan plan);

@@ -125,9 +125,12 @@ fmm_status far_field_pass(Plan &P, bool gradient, bool solute_only, StageTimer *
     if (tm) tm->mark();
     TRY(launch_lattice(P));
     if (tm) tm->mark();
+    bool ev = tm && P.timings_on;
     for (int l = 1; l <= P.d; ++l) {
+        if (ev) cudaEventRecord(P.ev_m2l[2 * (l - 1)], P.stream);
         if (tc_available(P, l)) TRY(launch_m2l_tc(P, l));
         else TRY(launch_m2l_simt(P, l));
+        if (ev) cudaEventRecord(P.ev_m2l[2 * (l - 1) + 1], P.stream);
         TRY(launch_l2l(P, l));
     }
     if (tm) tm->mark();
@@ -177,6 +180,7 @@ fmm_status evaluate(Plan &P, const double *pos, const double *q, const uint8_t *
         TRY(far_field_pass(P, false, true, nullptr));
         TRY(launch_p2p_uv(P));
     }
+    tm.mark();
     TRY(launch_energy_reduce(P, want_uv));
     if (forces) TRY(launch_forces_out(P, dq, dforces));
     tm.mark();
@@ -206,18 +210,25 @@ fmm_status evaluate(Plan &P, const double *pos, const double *q, const uint8_t *
             uv->nf_uv = P.h_out[27];
             uv->bc_cross = P.h_out[28];
         }
-        if (P.timings_on && tm.k >= 8) {
+        if (P.timings_on && tm.k >= 9) {
             float t[12];
             for (int i = 0; i + 1 < tm.k; ++i) cudaEventElapsedTime(&t[i], P.ev[i], P.ev[i + 1]);
             P.last.sort = t[0];
             P.last.upward = t[1];
             P.last.lattice = t[2];
-            P.last.m2l = t[3];
+            P.last.m2l_l2l = t[3];
             P.last.l2p = t[4];
             P.last.p2p = t[5];
-            P.last.reduce = t[6];
-            P.last.downward = 0;
+            P.last.solute_pass = t[6];
+            P.last.reduce = t[7];
             cudaEventElapsedTime(&P.last.total, P.ev[0], P.ev[tm.k - 1]);
+            float m = 0;
+            for (int l = 1; l <= P.d; ++l) {
+                float x = 0;
+                cudaEventElapsedTime(&x, P.ev_m2l[2 * (l - 1)], P.ev_m2l[2 * (l - 1) + 1]);
+                m += x;
+            }
+            P.last.m2l_kernels = m;
         }
         if (err & ERRF_NONFINITE) return FMM_ERR_NONFINITE;
         if (err & ERRF_TIMEOUT) return FMM_ERR_TIMEOUT;
@@ -257,6 +268,7 @@ fmm_status fmm_plan_create(double box, int64_t N, int depth, int p, fmm_plan *ou
     fmm_status s = alloc_buffers(P);
     if (s == FMM_OK) {
         for (int i = 0; i < 12; ++i) cudaEventCreate(&P.ev[i]);
+        for (int i = 0; i < 18; ++i) cudaEventCreate(&P.ev_m2l[i]);
         s = rebuild(P);
     }
     if (s != FMM_OK) {
@@ -347,6 +359,13 @@ fmm_status fmm_plan_get_timings(fmm_plan plan, fmm_timings *out)
 
 int64_t fmm_plan_last_launch_count(fmm_plan plan) { return plan ? plan->P.launches : -1; }
 
+int fmm_plan_m2l_backend(fmm_plan plan, int level)
+{
+    if (!plan || level < 1 || level > plan->P.d) return -1;
+    if (tc_available(plan->P, level)) return 2;
+    return plan->P.precision == FMM_PREC_FP64 ? 0 : 1;
+}
+
 void fmm_plan_destroy(fmm_plan plan)
 {
     if (!plan) return;
@@ -357,6 +376,8 @@ void fmm_plan_destroy(fmm_plan plan)
     free_buffers(P);
     for (int i = 0; i < 12; ++i)
         if (P.ev[i]) cudaEventDestroy(P.ev[i]);
+    for (int i = 0; i < 18; ++i)
+        if (P.ev_m2l[i]) cudaEventDestroy(P.ev_m2l[i]);
     delete plan;
 }
 

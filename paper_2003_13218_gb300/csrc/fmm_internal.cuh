@@ -98,10 +98,8 @@ struct Plan {
     // expansions per level (T, class layout)
     void *M[9] = {};
     void *L[9] = {};
-    // tensor-core M2L planes (bf16, halo-padded), built by the TC path
-    void *tc_planes = nullptr;
-    size_t tc_plane_bytes = 0;
-    void *tc_ops = nullptr;
+    // tensor-core M2L state (bf16 operand planes, operator tables, TMA maps)
+    void *tc = nullptr;
     // reductions
     double *red_partial = nullptr;  // partial sums
     double *red_out = nullptr;      // [32] final FP64 scalars
@@ -109,6 +107,7 @@ struct Plan {
     int *d_err = nullptr;
     Tables tab;
     cudaEvent_t ev[12] = {};
+    cudaEvent_t ev_m2l[18] = {};  // around each level's M2L launch (full pass)
     fmm_timings last{};
 };
 

@@ -1,11 +1,610 @@
-// fmm_m2l_tc.cu -- tensor-core (tcgen05) M2L for the mixed-precision path.
+// fmm_m2l_tc.cu -- M2L of Eq. Lcoeffdef on the 5th-generation tensor cores
+// (tcgen05) for the mixed-precision path.
+//
+// For one level and one parity class c, the local coefficients of 128 target
+// cells (a brick of parent coordinates) are
+//     L[t][j] = sum_{delta in IL(c)} sum_k M[t + delta][k] T_delta[k][j]
+// i.e. 189 dense products (128 x K) . (K x N):
+//   M dimension = 128 targets, N = (p+1)^2 output coefficients padded to 16,
+//   K = (p+1)^2 input coefficients padded to 32.
+// The A operand of offset delta is the same brick shifted to class
+// (c + delta) & 1 and parent offset (c + delta) >> 1 in {-1, 0, 1}^3; the
+// source planes carry a one-cell periodic halo so that every TMA box lies
+// inside the array.  Operands are split into bf16 terms, x = x0 + x1 (+ x2),
+// and the products x_i y_j with i + j below the split order are summed
+// (bf16x3: 6 products, ~2^-24 relative; bf16x2: 3 products, ~2^-16).
+//
+// Accumulation.  The tensor core's FP32 accumulation rounds with a bias, which
+// over thousands of MMAs into one accumulator shows up at the 1e-5 level.  So
+// each offset's products go into a fresh TMEM accumulator (two, alternating),
+// and the epilogue warps drain it and add it to the row held in FP32 registers
+// (round to nearest) while the tensor core works on the next offset.
+//
+// Roles (6 warps): warp 0 lane 0 issues TMA loads into a 3-stage ring, warp 1
+// lane 0 issues tcgen05.mma, warps 2..5 drain TMEM (warp w reads TMEM lanes
+// 32 (w mod 4) .. +31, one target row per thread) and write the FP32 level
+// array.  Every mbarrier wait is bounded (globaltimer); on a timeout the
+// kernel records FMM_ERR_TIMEOUT, waits (bounded) for its copies and MMAs in
+// flight, frees TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <string.h>
+
+#include <new>
+
 #include "fmm_internal.cuh"
 
 namespace fmm {
 
-bool tc_available(const Plan &, int) { return false; }
-fmm_status tc_prepare(Plan &) { return FMM_OK; }
-fmm_status launch_m2l_tc(Plan &, int) { return FMM_ERR_UNSUPPORTED; }
-void tc_free(Plan &) {}
+namespace {
+
+constexpr int TC_THREADS = 192;
+constexpr int TC_STAGES = 3;
+constexpr int TC_ROWS = 128;          // MMA M
+constexpr int KCHUNK = 32;            // bf16 elements per 64-byte swizzled row
+constexpr int ROW_BYTES = 64;
+constexpr uint32_t TMEM_COLS = 512;   // two accumulators of up to 256 columns
+constexpr int TC_PMAX = 15;           // N = (p+1)^2 rounded to 16 must not exceed 256
+constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // 2 s
+constexpr int NUM_IL = 189;
+
+struct TcState {
+    int pa = 0, pb = 0;
+    int npad = 0, kp = 0;
+    __nv_bfloat16 *planes[9] = {};
+    size_t part_elems[9] = {};
+    __nv_bfloat16 *ops = nullptr;
+    size_t ops_part_elems = 0;
+    CUtensorMap mapA[9][3];
+    CUtensorMap mapB[3];
+    int bx[9], by[9], bz[9];
+};
+
+struct TcArgs {
+    int np, bx, by, bz, rows, tiles_x, tiles_y, tiles_per_class;
+    int nc, npad, kchunks;
+    uint32_t idesc;
+    float *L;
+    int *err;
+};
+
+// ------------------------------------------------------------------ PTX wrappers
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait on phase `parity`; false on timeout or when the CTA aborts
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag)
+{
+    uint64_t t0 = global_ns();
+    for (uint32_t i = 0;; ++i) {
+        if (mbar_try(bar, parity)) return true;
+        if ((i & 63) == 63) {
+            if (*abort_flag) return false;
+            if (global_ns() - t0 > WAIT_LIMIT_NS) return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, uint32_t bar, int c0, int c1, int c2,
+                                            int c3)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, uint32_t bar, int c0, int c1, int c2)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+            "r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+        : "memory");
+}
+
+// tcgen05 shared-memory matrix descriptor: K-major, 64-byte swizzle,
+// 8-row groups 512 bytes apart (stride byte offset), version field 1.
+__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1 << 16;                       // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)((512u >> 4) & 0x3FFFu) << 32; // stride byte offset
+    d |= (uint64_t)1 << 46;                       // descriptor version
+    d |= (uint64_t)4 << 61;                       // 64-byte swizzle
+    return d;
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
+        "[%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// ------------------------------------------------------------------ the kernel
+template <int PA, int PB>
+struct Products;
+template <>
+struct Products<3, 3> {  // x_i y_j with i + j <= 2
+    static constexpr int n = 6;
+    __device__ static constexpr int a(int k) { return k == 0 ? 0 : k == 1 ? 0 : k == 2 ? 1 : k == 3 ? 0 : k == 4 ? 1 : 2; }
+    __device__ static constexpr int b(int k) { return k == 0 ? 0 : k == 1 ? 1 : k == 2 ? 0 : k == 3 ? 2 : k == 4 ? 1 : 0; }
+};
+template <>
+struct Products<2, 2> {  // i + j <= 1
+    static constexpr int n = 3;
+    __device__ static constexpr int a(int k) { return k == 2 ? 1 : 0; }
+    __device__ static constexpr int b(int k) { return k == 1 ? 1 : 0; }
+};
+
+// PA, PB: bf16 terms of the A (moments) and B (operator) operands;
+// NCH: output coefficients / 16 (the accumulator width held in registers).
+template <int PA, int PB, int NCH>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_m2l_tc(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
+             const __grid_constant__ CUtensorMap mA2, const __grid_constant__ CUtensorMap mB0,
+             const __grid_constant__ CUtensorMap mB1, const __grid_constant__ CUtensorMap mB2, TcArgs a)
+{
+    extern __shared__ uint8_t smem_dyn[];
+    __shared__ __align__(8) uint64_t bar_full[TC_STAGES];
+    __shared__ __align__(8) uint64_t bar_empty[TC_STAGES];
+    __shared__ __align__(8) uint64_t bar_tfull[2];
+    __shared__ __align__(8) uint64_t bar_tempty[2];
+    __shared__ __align__(8) uint64_t bar_done;
+    __shared__ uint32_t tmem_sh;
+    __shared__ int abort_sh;
+    __shared__ int produced_sh, consumed_sh;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t smem0 = (smem_u32(smem_dyn) + 1023u) & ~1023u;
+    const uint32_t stageA = TC_ROWS * ROW_BYTES;
+    const uint32_t stageB = (uint32_t)a.npad * ROW_BYTES;
+    const uint32_t stage_bytes = PA * stageA + PB * stageB;
+    const uint32_t tx_bytes = (uint32_t)(PA * a.rows * ROW_BYTES) + PB * stageB;
+
+    const int cls = blockIdx.x / a.tiles_per_class;
+    const int tile = blockIdx.x % a.tiles_per_class;
+    const int x0 = (tile % a.tiles_x) * a.bx;
+    const int y0 = ((tile / a.tiles_x) % a.tiles_y) * a.by;
+    const int z0 = (tile / (a.tiles_x * a.tiles_y)) * a.bz;
+    const int cx = cls & 1, cy = (cls >> 1) & 1, cz = (cls >> 2) & 1;
+    const int np2 = a.np + 2;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < TC_STAGES; ++s) {
+            mbar_init(smem_u32(&bar_full[s]), 1);
+            mbar_init(smem_u32(&bar_empty[s]), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&bar_tfull[b]), 1);
+            mbar_init(smem_u32(&bar_tempty[b]), 4);  // one arrival per epilogue warp
+        }
+        mbar_init(smem_u32(&bar_done), 1);
+        abort_sh = 0;
+        produced_sh = 0;
+        consumed_sh = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_sh)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = tmem_sh;
+    volatile int *abort_flag = &abort_sh;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- producer: TMA loads of the A brick and the B operator
+            const CUtensorMap *mA[3] = {&mA0, &mA1, &mA2};
+            const CUtensorMap *mB[3] = {&mB0, &mB1, &mB2};
+            int it = 0;
+            bool ok = true;
+            for (int dz = -2 - cz; dz <= 3 - cz && ok; ++dz)
+                for (int dy = -2 - cy; dy <= 3 - cy && ok; ++dy)
+                    for (int dx = -2 - cx; dx <= 3 - cx && ok; ++dx) {
+                        if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1 && dz >= -1 && dz <= 1) continue;
+                        const int sx = cx + dx, sy = cy + dy, sz = cz + dz;
+                        const int scls = (sx & 1) | ((sy & 1) << 1) | ((sz & 1) << 2);
+                        const int hx = x0 + (sx >> 1) + 1, hy = y0 + (sy >> 1) + 1;
+                        const int hz = scls * np2 + z0 + (sz >> 1) + 1;
+                        const int slot = off_slot(dx, dy, dz);
+                        for (int kc = 0; kc < a.kchunks; ++kc) {
+                            const int s = it % TC_STAGES;
+                            const uint32_t round = (uint32_t)(it / TC_STAGES);
+                            if (it >= TC_STAGES &&
+                                !mbar_wait(smem_u32(&bar_empty[s]), (round & 1u) ^ 1u, abort_flag)) {
+                                ok = false;
+                                break;
+                            }
+                            const uint32_t full = smem_u32(&bar_full[s]);
+                            mbar_expect_tx(full, tx_bytes);
+                            const uint32_t base = smem0 + (uint32_t)s * stage_bytes;
+#pragma unroll
+                            for (int i = 0; i < PA; ++i)
+                                tma_load_4d(base + i * stageA, mA[i], full, kc * KCHUNK, hx, hy, hz);
+#pragma unroll
+                            for (int j = 0; j < PB; ++j)
+                                tma_load_3d(base + PA * stageA + j * stageB, mB[j], full, kc * KCHUNK, 0, slot);
+                            ++it;
+                        }
+                    }
+            produced_sh = it;
+            if (!ok) {
+                abort_sh = 1;
+                atomicOr(a.err, ERRF_TIMEOUT);
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------- MMA issuer: one fresh accumulator per offset
+            using PR = Products<PA, PB>;
+            int it = 0;
+            bool ok = true;
+            for (int o = 0; o < NUM_IL && ok; ++o) {
+                const int acc = o & 1;
+                const uint32_t use = (uint32_t)(o >> 1);
+                if (o >= 2 && !mbar_wait(smem_u32(&bar_tempty[acc]), (use - 1u) & 1u, abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                fence_after();
+                const uint32_t tmem_d = tmem + (uint32_t)(acc * 256);
+                for (int kc = 0; kc < a.kchunks; ++kc) {
+                    const int s = it % TC_STAGES;
+                    const uint32_t round = (uint32_t)(it / TC_STAGES);
+                    if (!mbar_wait(smem_u32(&bar_full[s]), round & 1u, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    fence_after();
+                    const uint32_t base = smem0 + (uint32_t)s * stage_bytes;
+#pragma unroll
+                    for (int pr = 0; pr < PR::n; ++pr) {
+#pragma unroll
+                        for (int k16 = 0; k16 < 2; ++k16) {
+                            const uint64_t ad = sdesc_sw64(base + PR::a(pr) * stageA + k16 * 32);
+                            const uint64_t bd = sdesc_sw64(base + PA * stageA + PR::b(pr) * stageB + k16 * 32);
+                            mma_bf16(tmem_d, ad, bd, a.idesc, (kc | pr | k16) != 0 ? 1u : 0u);
+                        }
+                    }
+                    mma_commit(smem_u32(&bar_empty[s]));
+                    ++it;
+                }
+                if (ok) mma_commit(smem_u32(&bar_tfull[acc]));
+            }
+            consumed_sh = it;
+            if (!ok) {
+                abort_sh = 1;
+                atomicOr(a.err, ERRF_TIMEOUT);
+            }
+            mma_commit(smem_u32(&bar_done));  // arrives once every issued MMA has completed
+        }
+        __syncwarp();
+    } else {
+        // ---------------- epilogue warps: drain each offset's accumulator into FP32 registers
+        const int quad = warp & 3;
+        const int row = quad * 32 + lane;
+        float Lr[NCH * 16];
+#pragma unroll
+        for (int i = 0; i < NCH * 16; ++i) Lr[i] = 0.f;
+        bool ok = true;
+        for (int o = 0; o < NUM_IL; ++o) {
+            const int acc = o & 1;
+            const uint32_t use = (uint32_t)(o >> 1);
+            if (!mbar_wait(smem_u32(&bar_tfull[acc]), use & 1u, abort_flag)) {
+                ok = false;
+                break;
+            }
+            fence_after();
+            const uint32_t taddr = tmem + (uint32_t)(acc * 256) + ((uint32_t)(quad * 32) << 16);
+#pragma unroll
+            for (int c = 0; c < NCH; ++c) {
+                uint32_t r[16];
+                tmem_ld16(taddr + (uint32_t)(c * 16), r);
+                tmem_wait_ld();
+#pragma unroll
+                for (int j = 0; j < 16; ++j) Lr[c * 16 + j] += __uint_as_float(r[j]);
+            }
+            fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&bar_tempty[acc]));
+        }
+        if (!ok) {
+            abort_sh = 1;
+            if (lane == 0) atomicOr(a.err, ERRF_TIMEOUT);
+        } else if (row < a.rows) {
+            const int tx = row % a.bx, ty = (row / a.bx) % a.by, tz = row / (a.bx * a.by);
+            const int64_t np = a.np;
+            const int64_t lin = (x0 + tx) + np * ((y0 + ty) + np * (int64_t)(z0 + tz));
+            float *dst = a.L + ((int64_t)cls * np * np * np + lin) * a.nc;
+#pragma unroll
+            for (int i = 0; i < NCH * 16; ++i)
+                if (i < a.nc) dst[i] = Lr[i];
+        }
+    }
+
+    // ---------------- teardown: wait (bounded) for MMAs and copies in flight, free TMEM
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile int no_abort = 0;
+        if (!mbar_wait(smem_u32(&bar_done), 0, &no_abort)) atomicOr(a.err, ERRF_TIMEOUT);
+        if (abort_sh)
+            for (int it = consumed_sh; it < produced_sh; ++it)
+                mbar_wait(smem_u32(&bar_full[it % TC_STAGES]), (uint32_t)(it / TC_STAGES) & 1u, &no_abort);
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+}
+
+// ------------------------------------------------------------------ operand preparation
+__device__ __forceinline__ void split_bf16(float v, int parts, __nv_bfloat16 *o, size_t stride)
+{
+    __nv_bfloat16 b0 = __float2bfloat16_rn(v);
+    float r = v - __bfloat162float(b0);
+    o[0] = b0;
+    __nv_bfloat16 b1 = __float2bfloat16_rn(r);
+    o[stride] = b1;
+    if (parts > 2) o[2 * stride] = __float2bfloat16_rn(r - __bfloat162float(b1));
+}
+
+// FP32 class-layout moments -> bf16 split planes [part][class][hz][hy][hx][k] with a periodic halo
+__global__ void k_split_halo(const float *__restrict__ M, int np, int nc, int kp, int parts,
+                             __nv_bfloat16 *__restrict__ planes, size_t part_elems)
+{
+    const int64_t np2 = np + 2;
+    const int64_t total = 8 * np2 * np2 * np2 * kp;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int k = (int)(e % kp);
+        int64_t cell = e / kp;
+        const int hx = (int)(cell % np2);
+        const int hy = (int)((cell / np2) % np2);
+        const int64_t hzc = cell / (np2 * np2);
+        const int c = (int)(hzc / np2), hz = (int)(hzc % np2);
+        const int px = (hx - 1 + np) % np, py = (hy - 1 + np) % np, pz = (hz - 1 + np) % np;
+        float v = 0.f;
+        if (k < nc) v = M[((int64_t)c * np * np * np + px + (int64_t)np * (py + (int64_t)np * pz)) * nc + k];
+        split_bf16(v, parts, planes + e, part_elems);
+    }
+}
+
+// FP64 input-major operators T[slot][k][j] -> bf16 split B tables [part][slot][j][k] (K-major)
+__global__ void k_split_ops(const double *__restrict__ T, int nc, int npad, int kp, int parts,
+                            __nv_bfloat16 *__restrict__ ops, size_t part_elems)
+{
+    const int64_t total = (int64_t)NOFF * npad * kp;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int k = (int)(e % kp);
+        const int j = (int)((e / kp) % npad);
+        const int slot = (int)(e / ((int64_t)kp * npad));
+        double v = (j < nc && k < nc) ? T[((int64_t)slot * nc + k) * nc + j] : 0.0;
+        __nv_bfloat16 b0 = __float2bfloat16_rn((float)v);
+        double r = v - (double)__bfloat162float(b0);
+        __nv_bfloat16 b1 = __float2bfloat16_rn((float)r);
+        double r2 = r - (double)__bfloat162float(b1);
+        ops[e] = b0;
+        ops[e + part_elems] = b1;
+        if (parts > 2) ops[e + 2 * part_elems] = __float2bfloat16_rn((float)r2);
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+int tile_dim(int np, int cap) { return np < cap ? np : cap; }
+
+size_t tc_smem_bytes(int pa, int pb, int npad)
+{
+    // at least 120 KB so that a second CTA (and its 512 TMEM columns) never shares the SM
+    size_t need = TC_STAGES * (size_t)(pa * TC_ROWS * ROW_BYTES + pb * npad * ROW_BYTES) + 1024;
+    return need < 120 * 1024 ? 120 * 1024 : need;
+}
+
+typedef void (*TcKernel)(CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap, TcArgs);
+
+template <int PA>
+TcKernel pick_kernel(int nch)
+{
+    switch (nch) {
+#define FMM_TC_CASE(n) \
+    case n: return (TcKernel)k_m2l_tc<PA, PA, n>;
+        FMM_TC_CASE(1) FMM_TC_CASE(2) FMM_TC_CASE(3) FMM_TC_CASE(4) FMM_TC_CASE(5) FMM_TC_CASE(6) FMM_TC_CASE(7)
+        FMM_TC_CASE(8) FMM_TC_CASE(9) FMM_TC_CASE(10) FMM_TC_CASE(11) FMM_TC_CASE(12) FMM_TC_CASE(13)
+        FMM_TC_CASE(14) FMM_TC_CASE(15) FMM_TC_CASE(16)
+#undef FMM_TC_CASE
+    default: return nullptr;
+    }
+}
+
+}  // namespace
+
+bool tc_available(const Plan &P, int level)
+{
+    return P.tc != nullptr && level >= 1 && level <= P.d;
+}
+
+fmm_status tc_prepare(Plan &P)
+{
+    tc_free(P);
+    if (P.precision != FMM_PREC_MIXED || P.p > TC_PMAX) return FMM_OK;  // CUDA-core M2L
+    int pa = P.split == FMM_SPLIT_BF16X3 ? 3 : 2;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+    if (!enc) return FMM_OK;
+    TcState *S = new (std::nothrow) TcState();
+    if (!S) return FMM_ERR_OOM;
+    S->pa = S->pb = pa;
+    S->npad = (P.nc + 15) / 16 * 16;
+    S->kp = (P.nc + KCHUNK - 1) / KCHUNK * KCHUNK;
+    P.tc = S;
+    // operator tables
+    S->ops_part_elems = (size_t)NOFF * S->npad * S->kp;
+    FMM_CUDA_TRY(cudaMalloc(&S->ops, sizeof(__nv_bfloat16) * S->ops_part_elems * S->pb));
+    k_split_ops<<<1216, 256, 0, P.stream>>>(P.tab.Top64, P.nc, S->npad, S->kp, S->pb, S->ops, S->ops_part_elems);
+    FMM_LAUNCH_CHECK(P);
+    for (int j = 0; j < S->pb; ++j) {
+        cuuint64_t dims[3] = {(cuuint64_t)S->kp, (cuuint64_t)S->npad, (cuuint64_t)NOFF};
+        cuuint64_t strides[2] = {(cuuint64_t)S->kp * 2, (cuuint64_t)S->kp * 2 * S->npad};
+        cuuint32_t box[3] = {KCHUNK, (cuuint32_t)S->npad, 1};
+        cuuint32_t es[3] = {1, 1, 1};
+        if (enc(&S->mapB[j], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, S->ops + j * S->ops_part_elems, dims, strides, box,
+                es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return FMM_ERR_INTERNAL;
+    }
+    for (int j = S->pb; j < 3; ++j) S->mapB[j] = S->mapB[0];
+    // source planes per level
+    for (int l = 1; l <= P.d; ++l) {
+        int np = 1 << (l - 1);
+        int64_t np2 = np + 2;
+        S->bx[l] = tile_dim(np, TC_ROWS);
+        S->by[l] = tile_dim(np, TC_ROWS / S->bx[l]);
+        S->bz[l] = tile_dim(np, TC_ROWS / (S->bx[l] * S->by[l]));
+        S->part_elems[l] = (size_t)8 * np2 * np2 * np2 * S->kp;
+        FMM_CUDA_TRY(cudaMalloc(&S->planes[l], sizeof(__nv_bfloat16) * S->part_elems[l] * S->pa));
+        for (int i = 0; i < S->pa; ++i) {
+            cuuint64_t dims[4] = {(cuuint64_t)S->kp, (cuuint64_t)np2, (cuuint64_t)np2, (cuuint64_t)(8 * np2)};
+            cuuint64_t strides[3] = {(cuuint64_t)S->kp * 2, (cuuint64_t)S->kp * 2 * np2,
+                                     (cuuint64_t)S->kp * 2 * np2 * np2};
+            cuuint32_t box[4] = {KCHUNK, (cuuint32_t)S->bx[l], (cuuint32_t)S->by[l], (cuuint32_t)S->bz[l]};
+            cuuint32_t es[4] = {1, 1, 1, 1};
+            if (enc(&S->mapA[l][i], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, S->planes[l] + i * S->part_elems[l], dims,
+                    strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+                return FMM_ERR_INTERNAL;
+        }
+        for (int i = S->pa; i < 3; ++i) S->mapA[l][i] = S->mapA[l][0];
+    }
+    TcKernel k = pa == 3 ? pick_kernel<3>(S->npad / 16) : pick_kernel<2>(S->npad / 16);
+    if (!k) return FMM_ERR_INTERNAL;
+    FMM_CUDA_TRY(cudaFuncSetAttribute((const void *)k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)tc_smem_bytes(S->pa, S->pb, S->npad)));
+    FMM_CUDA_TRY(cudaStreamSynchronize(P.stream));
+    return FMM_OK;
+}
+
+fmm_status launch_m2l_tc(Plan &P, int l)
+{
+    TcState *S = (TcState *)P.tc;
+    if (!S) return FMM_ERR_INTERNAL;
+    int np = 1 << (l - 1);
+    int64_t np2 = np + 2;
+    int64_t n = 8 * np2 * np2 * np2 * S->kp;
+    unsigned blocks = (unsigned)((n + 255) / 256 < 4864 ? (n + 255) / 256 : 4864);
+    k_split_halo<<<blocks, 256, 0, P.stream>>>((const float *)P.M[l], np, P.nc, S->kp, S->pa, S->planes[l],
+                                               S->part_elems[l]);
+    FMM_LAUNCH_CHECK(P);
+    TcArgs a;
+    a.np = np;
+    a.bx = S->bx[l];
+    a.by = S->by[l];
+    a.bz = S->bz[l];
+    a.rows = a.bx * a.by * a.bz;
+    a.tiles_x = np / a.bx;
+    a.tiles_y = np / a.by;
+    a.tiles_per_class = a.tiles_x * a.tiles_y * (np / a.bz);
+    a.nc = P.nc;
+    a.npad = S->npad;
+    a.kchunks = S->kp / KCHUNK;
+    a.idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(S->npad >> 3) << 17) | ((uint32_t)(TC_ROWS >> 4) << 24);
+    a.L = (float *)P.L[l];
+    a.err = P.d_err;
+    unsigned grid = 8u * (unsigned)a.tiles_per_class;
+    TcKernel k = S->pa == 3 ? pick_kernel<3>(S->npad / 16) : pick_kernel<2>(S->npad / 16);
+    if (!k) return FMM_ERR_INTERNAL;
+    k<<<grid, TC_THREADS, tc_smem_bytes(S->pa, S->pb, S->npad), P.stream>>>(
+        S->mapA[l][0], S->mapA[l][1], S->mapA[l][2], S->mapB[0], S->mapB[1], S->mapB[2], a);
+    FMM_LAUNCH_CHECK(P);
+    return FMM_OK;
+}
+
+void tc_free(Plan &P)
+{
+    TcState *S = (TcState *)P.tc;
+    if (!S) return;
+    for (int l = 0; l < 9; ++l) cudaFree(S->planes[l]);
+    cudaFree(S->ops);
+    delete S;
+    P.tc = nullptr;
+}
 
 }  // namespace fmm

@@ -48,8 +48,8 @@ class UVTerms(ctypes.Structure):
 
 
 class Timings(ctypes.Structure):
-    _fields_ = [(k, ctypes.c_float) for k in ("sort", "upward", "lattice", "m2l", "downward", "l2p", "p2p", "reduce",
-                                              "total")]
+    _fields_ = [(k, ctypes.c_float) for k in ("sort", "upward", "lattice", "m2l_l2l", "l2p", "p2p", "solute_pass",
+                                              "reduce", "total", "m2l_kernels")]
 
     def asdict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -84,6 +84,8 @@ def load_library(path: str = LIB_PATH):
     L.fmm_plan_get_timings.restype = c_int
     L.fmm_plan_last_launch_count.argtypes = [vp]
     L.fmm_plan_last_launch_count.restype = i64
+    L.fmm_plan_m2l_backend.argtypes = [vp, c_int]
+    L.fmm_plan_m2l_backend.restype = c_int
     L.fmm_plan_destroy.argtypes = [vp]
     L.fmm_plan_destroy.restype = None
     L.fmm_status_string.argtypes = [c_int]
@@ -191,6 +193,10 @@ class FMMPlan:
 
     def last_launch_count(self) -> int:
         return int(self._lib.fmm_plan_last_launch_count(self._h))
+
+    def m2l_backend(self, level: int) -> str:
+        code = int(self._lib.fmm_plan_m2l_backend(self._h, int(level)))
+        return {0: "fp64-simt", 1: "fp32-simt", 2: "tcgen05"}.get(code, "invalid")
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

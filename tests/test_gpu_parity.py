@@ -195,3 +195,51 @@ def test_autograd_adjoint_matches_finite_differences():
         checked += 1
     assert checked >= 10
     plan.close()
+
+
+# ----------------------------------------------------------------------------- tensor-core M2L
+def _sub_box(nw, L, seed=0):
+    return boxes.ion_in_water(nw, "Na", seed=seed, L=L)
+
+
+@pytest.mark.parametrize("split,tol_e,tol_f", [("bf16x3", 2e-7, 2e-6), ("bf16x2", 2e-6, 5e-5)])
+def test_tensor_core_m2l_matches_cuda_core_m2l(split, tol_e, tol_f):
+    """Mixed path with tcgen05 M2L (full 128-target tiles at levels 4, 5) against the same path
+    with the FP32 CUDA-core M2L, and both against the FP64 GPU path."""
+    b = _sub_box(333333 // 64, 215.3 / 4)  # N = 15,625, d = 4
+    d, p = 4, 12
+    t_tc, _, F_tc = _run(b.pos, b.q, b.L, d, p, precision="mixed", split=split)
+    t_cc, _, F_cc = _run(b.pos, b.q, b.L, d, p, precision="mixed", split="fp32")
+    t_64, _, F_64 = _run(b.pos, b.q, b.L, d, p)
+    assert abs(t_tc["far"] - t_cc["far"]) <= tol_e * abs(t_64["total"])
+    assert abs(t_tc["total"] - t_64["total"]) <= 1e-6 * abs(t_64["total"])
+    assert _rms_rel(F_tc, F_cc) < tol_f
+    assert _rms_rel(F_tc, F_64) < 1e-5
+
+
+def test_tensor_core_backend_is_used():
+    b = _sub_box(1000, 30.0)
+    plan = _plan(b.L, b.N, 4, 12, precision="mixed")
+    assert all(plan.m2l_backend(l) == "tcgen05" for l in range(1, 5))
+    plan.close()
+    plan = _plan(b.L, b.N, 4, 12)
+    assert plan.m2l_backend(4) == "fp64-simt"
+    plan.close()
+
+
+def test_100k_workload_sampled_against_oracle():
+    """Cl- + 33,333 waters (N = 100,000, d = 5, p = 12) in the configuration the benchmark runs:
+    per-particle forces on 48 sampled charges against the oracle computed one by one, and the
+    mixed energy against the FP64 GPU path."""
+    b, d, p = boxes.workload("cl_100k")
+    rng = np.random.default_rng(0)
+    idx = np.sort(rng.choice(b.N, 48, replace=False))
+    idx[0] = 0  # the ion
+    ref = oracle.fmm_sampled(b.pos, b.q, b.L, d, p, idx)
+    t_m, uv_m, F_m = _run(b.pos, b.q, b.L, d, p, precision="mixed", sol=b.is_solute)
+    t_64, uv_64, F_64 = _run(b.pos, b.q, b.L, d, p, sol=b.is_solute)
+    scale = np.sqrt(np.mean(ref["forces"] ** 2))
+    assert np.max(np.abs(F_64[idx] - ref["forces"])) < 1e-10 * scale
+    assert np.sqrt(np.mean((F_m[idx] - ref["forces"]) ** 2)) < 1e-5 * scale
+    assert abs(t_m["total"] - t_64["total"]) <= 1e-6 * abs(t_64["total"])
+    assert abs(uv_m["e_uv"] - uv_64["e_uv"]) <= 1e-5 * (abs(uv_64["A"]) + abs(uv_64["C"]))
