@@ -40,16 +40,32 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 # FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.070 GHz
 FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
-# DRAM bytes of one M2L stage from an ncu capture; recorded with the sha256 of
-# the kernel source they were taken on (null once the kernel has changed).
-M2L_TRAFFIC = None  # {"src": "paper_2003_13218_gb300/csrc/...", "sha256": "...", "bytes_per_launch": ...}
+# DRAM bytes (read + write) of one level-6 tensor-core M2L launch of the na_1m
+# workload, from the ncu capture summarised in profiles/k_m2l_tc_na_1m_level6.md,
+# with the sha256 of the kernel's device code it was taken on: the value is
+# reported only while that code is unchanged.
+M2L_TRAFFIC = {"src": "paper_2003_13218_gb300/csrc/fmm_m2l_tc.cu",
+               "sha256": "cd50ff008fde69b58629c4c3b3c7a3c8f98194a1e965a69a44b687ddfe6d6e2c",
+               "workload": "na_1m", "level": 6, "bytes_per_launch": 13.593296e9 + 0.175873792e9}
+KERNEL_BEGIN = "// ------------------------------------------------------------------ the kernel"
+KERNEL_END = "// ------------------------------------------------------------------ operand preparation"
 
 
-def m2l_flops(d: int, p: int) -> float:
-    """Algorithmic flops of the M2L stage: 2 C^2 per (target, source) pair, 189 pairs per target."""
+def m2l_flops(d: int, p: int, levels=None) -> float:
+    """Algorithmic flops of M2L: 2 C^2 per (target, source) pair, 189 sources per target."""
     C = (p + 1) ** 2
-    pairs = 189 * sum(8 ** l for l in range(1, d + 1))
+    levels = range(1, d + 1) if levels is None else levels
+    pairs = 189 * sum(8 ** l for l in levels)
     return 2.0 * C * C * pairs
+
+
+def kernel_sha(rel):
+    try:
+        with open(os.path.join(ROOT, rel)) as f:
+            s = f.read()
+        return hashlib.sha256(s[s.index(KERNEL_BEGIN):s.index(KERNEL_END)].encode()).hexdigest()
+    except (OSError, ValueError):
+        return None
 
 
 def load_peaks():
@@ -176,7 +192,8 @@ def run_ours(args):
         e1.record(stream)
         e1.synchronize()
         ms_total += e0.elapsed_time(e1)
-        m2l_ms.append(plan.timings()["m2l_kernels"])
+        tm = plan.timings()
+        m2l_ms.append((tm["m2l_top"], tm["m2l_kernels"]))
         flush.zero_()  # L2 flush between timed steps (not timed)
     torch.cuda.synchronize()
     clocks = sampler.stop()
@@ -233,22 +250,30 @@ def run_ours(args):
         return
     value = N * args.steps * ws / (ms_total / 1e3)
     peaks, peak_kind = load_peaks()
-    flops = m2l_flops(d, p)
-    m2l_avg_ms = statistics.mean(m2l_ms)
-    achieved = flops / (m2l_avg_ms / 1e3) / 1e12
     uses_tc = backend == "tcgen05"
+    stage_flops = m2l_flops(d, p)
+    stage_ms = statistics.mean(x[1] for x in m2l_ms)
     if uses_tc:
+        # the dominant launch: the tensor-core M2L of the finest level
+        flops = m2l_flops(d, p, levels=[d])
+        launch_ms = statistics.mean(x[0] for x in m2l_ms)
         peak = peaks.get("bf16_tflops", FALLBACK_PEAKS["bf16_tflops"])
-        roof = {"bound": "tensor", "peak_source": peak_kind + " bf16 dense burst"}
+        roof = {"bound": "tensor", "peak_source": peak_kind + " bf16 dense burst (MEASURED_PEAKS.json)",
+                "kernel": "k_m2l_tc, level %d (one launch)" % d}
+        traffic = None
+        if (M2L_TRAFFIC and M2L_TRAFFIC["workload"] == args.workload and M2L_TRAFFIC["level"] == d
+                and kernel_sha(M2L_TRAFFIC["src"]) == M2L_TRAFFIC["sha256"]):
+            traffic = M2L_TRAFFIC["bytes_per_launch"]
     else:
+        flops, launch_ms = stage_flops, stage_ms
         peak = FP32_ALU_TFLOPS
-        roof = {"bound": "alu", "peak_source": "FP32 CUDA-core peak from unit counts and max clock"}
-    traffic = None
-    if M2L_TRAFFIC and src_sha(M2L_TRAFFIC["src"]) == M2L_TRAFFIC["sha256"]:
-        traffic = M2L_TRAFFIC["bytes_per_launch"]
-    roof.update({"kernel": "M2L (all levels, one call)", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                 "frac": achieved / peak, "traffic": traffic, "algorithmic_flops_per_launch": flops,
-                 "avg_launch_ms": m2l_avg_ms})
+        roof = {"bound": "alu", "peak_source": "FP32 CUDA-core peak from unit counts and max clock",
+                "kernel": "k_m2l_simt<float> (all levels, one evaluation)"}
+        traffic = None
+    achieved = flops / (launch_ms / 1e3) / 1e12
+    roof.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+                 "algorithmic_flops_per_launch": flops, "avg_launch_ms": launch_ms,
+                 "m2l_all_levels": {"ms": stage_ms, "tflops": stage_flops / (stage_ms / 1e3) / 1e12}})
     out = {
         "metric": METRIC,
         "value": value,

@@ -150,6 +150,7 @@ fmm_status evaluate(Plan &P, const double *pos, const double *q, const uint8_t *
     bool host_any = kp == 1 || kq == 1 || ks == 1 || kf == 1;
     if (host_any) TRY(ensure_staging(P));
     P.launches = 0;
+    P.top_recorded = false;
     const double *dpos = pos, *dq = q;
     const uint8_t *dsol = want_uv ? sol : nullptr;
     double *dforces = forces;
@@ -229,6 +230,8 @@ fmm_status evaluate(Plan &P, const double *pos, const double *q, const uint8_t *
                 m += x;
             }
             P.last.m2l_kernels = m;
+            P.last.m2l_top = 0;
+            if (P.top_recorded) cudaEventElapsedTime(&P.last.m2l_top, P.ev_top[0], P.ev_top[1]);
         }
         if (err & ERRF_NONFINITE) return FMM_ERR_NONFINITE;
         if (err & ERRF_TIMEOUT) return FMM_ERR_TIMEOUT;
@@ -269,6 +272,7 @@ fmm_status fmm_plan_create(double box, int64_t N, int depth, int p, fmm_plan *ou
     if (s == FMM_OK) {
         for (int i = 0; i < 12; ++i) cudaEventCreate(&P.ev[i]);
         for (int i = 0; i < 18; ++i) cudaEventCreate(&P.ev_m2l[i]);
+        for (int i = 0; i < 2; ++i) cudaEventCreate(&P.ev_top[i]);
         s = rebuild(P);
     }
     if (s != FMM_OK) {
@@ -378,6 +382,8 @@ void fmm_plan_destroy(fmm_plan plan)
         if (P.ev[i]) cudaEventDestroy(P.ev[i]);
     for (int i = 0; i < 18; ++i)
         if (P.ev_m2l[i]) cudaEventDestroy(P.ev_m2l[i]);
+    for (int i = 0; i < 2; ++i)
+        if (P.ev_top[i]) cudaEventDestroy(P.ev_top[i]);
     delete plan;
 }
 

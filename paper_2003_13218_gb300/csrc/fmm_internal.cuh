@@ -108,6 +108,8 @@ struct Plan {
     Tables tab;
     cudaEvent_t ev[12] = {};
     cudaEvent_t ev_m2l[18] = {};  // around each level's M2L launch (full pass)
+    cudaEvent_t ev_top[2] = {};   // around the tensor-core M2L launch of level d
+    bool top_recorded = false;
     fmm_timings last{};
 };
 

@@ -591,9 +591,15 @@ fmm_status launch_m2l_tc(Plan &P, int l)
     unsigned grid = 8u * (unsigned)a.tiles_per_class;
     TcKernel k = S->pa == 3 ? pick_kernel<3>(S->npad / 16) : pick_kernel<2>(S->npad / 16);
     if (!k) return FMM_ERR_INTERNAL;
+    const bool time_it = P.timings_on && l == P.d && P.ev_top[0];
+    if (time_it) cudaEventRecord(P.ev_top[0], P.stream);
     k<<<grid, TC_THREADS, tc_smem_bytes(S->pa, S->pb, S->npad), P.stream>>>(
         S->mapA[l][0], S->mapA[l][1], S->mapA[l][2], S->mapB[0], S->mapB[1], S->mapB[2], a);
     FMM_LAUNCH_CHECK(P);
+    if (time_it) {
+        cudaEventRecord(P.ev_top[1], P.stream);
+        P.top_recorded = true;
+    }
     return FMM_OK;
 }
 

@@ -49,7 +49,7 @@ class UVTerms(ctypes.Structure):
 
 class Timings(ctypes.Structure):
     _fields_ = [(k, ctypes.c_float) for k in ("sort", "upward", "lattice", "m2l_l2l", "l2p", "p2p", "solute_pass",
-                                              "reduce", "total", "m2l_kernels")]
+                                              "reduce", "total", "m2l_kernels", "m2l_top")]
 
     def asdict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
