@@ -178,7 +178,9 @@ fmm_status evaluate(Plan &P, const double *pos, const double *q, const uint8_t *
     TRY(launch_p2p(P, forces != nullptr));
     tm.mark();
     if (want_uv) {
-        TRY(far_field_pass(P, false, true, nullptr));
+        bool sparse_done = false;
+        TRY(launch_solute_pass(P, &sparse_done));
+        if (!sparse_done) TRY(far_field_pass(P, false, true, nullptr));
         TRY(launch_p2p_uv(P));
     }
     tm.mark();
@@ -240,12 +242,18 @@ fmm_status evaluate(Plan &P, const double *pos, const double *q, const uint8_t *
     return FMM_OK;
 }
 
-fmm_status rebuild(Plan &P)
+// tensor-core operands follow the precision and split options
+fmm_status retc(Plan &P)
 {
     tc_free(P);
-    TRY(build_tables(P));
     if (P.precision == FMM_PREC_MIXED && P.split != FMM_SPLIT_FP32) TRY(tc_prepare(P));
     return FMM_OK;
+}
+
+fmm_status rebuild(Plan &P)
+{
+    TRY(build_tables(P));
+    return retc(P);
 }
 
 }  // namespace
@@ -273,7 +281,8 @@ fmm_status fmm_plan_create(double box, int64_t N, int depth, int p, fmm_plan *ou
         for (int i = 0; i < 12; ++i) cudaEventCreate(&P.ev[i]);
         for (int i = 0; i < 18; ++i) cudaEventCreate(&P.ev_m2l[i]);
         for (int i = 0; i < 2; ++i) cudaEventCreate(&P.ev_top[i]);
-        s = rebuild(P);
+        s = solute_prepare(P);
+        if (s == FMM_OK) s = rebuild(P);
     }
     if (s != FMM_OK) {
         fmm_plan_destroy(h);
@@ -293,16 +302,18 @@ fmm_status fmm_plan_set_option(fmm_plan plan, int key, int64_t ival, double dval
         return ival >= 2 ? FMM_ERR_UNSUPPORTED : FMM_ERR_INVALID_ARG;
     case FMM_OPT_PRECISION:
         if (ival != FMM_PREC_FP64 && ival != FMM_PREC_MIXED) return FMM_ERR_INVALID_ARG;
+        if (P.precision == (int)ival) return FMM_OK;
         P.precision = (int)ival;
-        return rebuild(P);
+        return retc(P);
     case FMM_OPT_KAPPA:
         if (!isfinite(dval)) return FMM_ERR_INVALID_ARG;
         P.kappa = dval > 0 ? dval : 0.0;
-        return rebuild(P);
+        return build_lattice(P);
     case FMM_OPT_M2L_SPLIT:
         if (ival != FMM_SPLIT_BF16X3 && ival != FMM_SPLIT_BF16X2 && ival != FMM_SPLIT_FP32) return FMM_ERR_INVALID_ARG;
+        if (P.split == (int)ival) return FMM_OK;
         P.split = (int)ival;
-        return rebuild(P);
+        return retc(P);
     case FMM_OPT_STREAM:
         P.stream = (cudaStream_t)(intptr_t)ival;
         return FMM_OK;
@@ -376,6 +387,7 @@ void fmm_plan_destroy(fmm_plan plan)
     Plan &P = plan->P;
     cudaStreamSynchronize(P.stream);
     tc_free(P);
+    solute_free(P);
     free_tables(P);
     free_buffers(P);
     for (int i = 0; i < 12; ++i)

@@ -156,55 +156,87 @@ struct KS {
 //         - 2 kb / sqrt(pi) delta_{j0}                                           (12c)
 //         - sum_{nu in {-1,0,1}^3, nu != 0} I_j^k(nu)      (images covered by levels 1..l_max)
 // Q(a, x) = Gamma(a, x)/Gamma(a) by Q(1/2, x) = erfc(sqrt x) and
-// Q(a + 1, x) = Q(a, x) + x^a e^{-x} / Gamma(a + 1).  One thread per (j, k).
-__global__ void k_lattice_sum(int jmax, double kb, int nu_max, int nk_max, double *__restrict__ S)
+// Q(a + 1, x) = Q(a, x) + x^a e^{-x} / Gamma(a + 1).  One block per (j, k):
+// threads stride over the lattice vectors, then a fixed-order reduction.
+constexpr int LAT_THREADS = 256;
+
+__device__ void block_merge(KS &v, double (*sh)[2])
 {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    int ntri = (jmax + 1) * (jmax + 2) / 2;
-    if (t >= ntri) return;
+    sh[threadIdx.x][0] = v.s;
+    sh[threadIdx.x][1] = v.c;
+    __syncthreads();
+    for (int o = LAT_THREADS / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            KS a;
+            a.s = sh[threadIdx.x][0];
+            a.c = sh[threadIdx.x][1];
+            a.add(sh[threadIdx.x + o][0]);
+            a.add(sh[threadIdx.x + o][1]);
+            sh[threadIdx.x][0] = a.s;
+            sh[threadIdx.x][1] = a.c;
+        }
+        __syncthreads();
+    }
+    v.s = sh[0][0];
+    v.c = sh[0][1];
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(LAT_THREADS) k_lattice_sum(int jmax, double kb, int nu_max, int nk_max,
+                                                              double *__restrict__ S)
+{
+    __shared__ double sh[LAT_THREADS][2];
+    int t = blockIdx.x;
     int j = 0;
     while (tri(j + 1, 0) <= t) ++j;
     int k = t - tri(j, 0);
     const double PI = 3.14159265358979323846;
     KS re, im;
     // real space (12a) and the near block
-    for (int nz = -nu_max; nz <= nu_max; ++nz)
-        for (int ny = -nu_max; ny <= nu_max; ++ny)
-            for (int nx = -nu_max; nx <= nu_max; ++nx) {
-                if (nx == 0 && ny == 0 && nz == 0) continue;
-                double r2 = (double)(nx * nx + ny * ny + nz * nz);
-                double x = kb * kb * r2;
-                double Q = erfc(sqrt(x));
-                double g = sqrt(PI);  // Gamma(1/2)
-                for (int i = 0; i < j; ++i) {
-                    double a = i + 0.5;
-                    g *= a;  // Gamma(i + 3/2)
-                    Q += exp(a * log(x) - x) / g;
-                }
-                bool near = abs(nx) <= 1 && abs(ny) <= 1 && abs(nz) <= 1;
-                double w = near ? Q - 1.0 : Q;
-                Cx<double> I = irregular_one(j, k, nx, ny, nz);
-                re.add(w * I.re);
-                im.add(w * I.im);
-            }
+    const int side = 2 * nu_max + 1;
+    const int nvec = side * side * side;
+    for (int v = threadIdx.x; v < nvec; v += LAT_THREADS) {
+        int nx = v % side - nu_max, ny = (v / side) % side - nu_max, nz = v / (side * side) - nu_max;
+        if (nx == 0 && ny == 0 && nz == 0) continue;
+        double r2 = (double)(nx * nx + ny * ny + nz * nz);
+        double x = kb * kb * r2;
+        double Q = erfc(sqrt(x));
+        double g = sqrt(PI);  // Gamma(1/2)
+        for (int i = 0; i < j; ++i) {
+            double a = i + 0.5;
+            g *= a;  // Gamma(i + 3/2)
+            Q += exp(a * log(x) - x) / g;
+        }
+        bool near = abs(nx) <= 1 && abs(ny) <= 1 && abs(nz) <= 1;
+        double w = near ? Q - 1.0 : Q;
+        Cx<double> I = irregular_one(j, k, nx, ny, nz);
+        re.add(w * I.re);
+        im.add(w * I.im);
+    }
     // reciprocal space (12b), k = 2 pi n
     double gh = sqrt(PI);
     for (int i = 0; i < j; ++i) gh *= (i + 0.5);  // Gamma(j + 1/2)
     double pref = pow(PI, 1.5) / (ldexp(1.0, j - 2) * gh);
     // i^j: j even -> (-1)^(j/2); odd degrees vanish by symmetry (kept exact)
     KS rre, rim;
-    for (int nz = -nk_max; nz <= nk_max; ++nz)
-        for (int ny = -nk_max; ny <= nk_max; ++ny)
-            for (int nx = -nk_max; nx <= nk_max; ++nx) {
-                if (nx == 0 && ny == 0 && nz == 0) continue;
-                double kx = 2 * PI * nx, ky = 2 * PI * ny, kz = 2 * PI * nz;
-                double k2 = kx * kx + ky * ky + kz * kz;
-                double kk = sqrt(k2);
-                double w = pow(kk, 2 * j - 1) * exp(-k2 / (4 * kb * kb));
-                Cx<double> I = irregular_one(j, k, kx, ky, kz);
-                rre.add(w * I.re);
-                rim.add(w * I.im);
-            }
+    const int kside = 2 * nk_max + 1;
+    const int nk = kside * kside * kside;
+    for (int v = threadIdx.x; v < nk; v += LAT_THREADS) {
+        int nx = v % kside - nk_max, ny = (v / kside) % kside - nk_max, nz = v / (kside * kside) - nk_max;
+        if (nx == 0 && ny == 0 && nz == 0) continue;
+        double kx = 2 * PI * nx, ky = 2 * PI * ny, kz = 2 * PI * nz;
+        double k2 = kx * kx + ky * ky + kz * kz;
+        double kk = sqrt(k2);
+        double w = pow(kk, 2 * j - 1) * exp(-k2 / (4 * kb * kb));
+        Cx<double> I = irregular_one(j, k, kx, ky, kz);
+        rre.add(w * I.re);
+        rim.add(w * I.im);
+    }
+    block_merge(re, sh);
+    block_merge(im, sh);
+    block_merge(rre, sh);
+    block_merge(rim, sh);
+    if (threadIdx.x != 0) return;
     double cr = rre.val() * pref, ci = rim.val() * pref;
     // multiply by i^j
     double ore, oim;
@@ -543,9 +575,26 @@ fmm_status build_tables(Plan &P)
     double kb = kappa * P.box;
     int nu_max = (int)ceil(8.0 / kb) + 3;
     int nk_max = (int)ceil(2.2 * kb) + 3;
-    k_lattice_sum<<<blocks_for(ntri2, 64), 64, 0, P.stream>>>(2 * p, kb, nu_max, nk_max, P.tab.S);
+    k_lattice_sum<<<ntri2, LAT_THREADS, 0, P.stream>>>(2 * p, kb, nu_max, nk_max, P.tab.S);
     FMM_LAUNCH_CHECK(P);
     k_lattice_operator<<<1, 256, shI, P.stream>>>(p, P.tab.S, P.tab.T0);
+    FMM_LAUNCH_CHECK(P);
+    FMM_CUDA_TRY(cudaStreamSynchronize(P.stream));
+    return FMM_OK;
+}
+
+fmm_status build_lattice(Plan &P)
+{
+    if (!P.tab.S || !P.tab.T0) return build_tables(P);
+    int p = P.p;
+    int ntri2 = (2 * p + 1) * (2 * p + 2) / 2;
+    double kappa = P.kappa > 0 ? P.kappa : 2.0 / P.box;
+    double kb = kappa * P.box;
+    int nu_max = (int)ceil(8.0 / kb) + 3;
+    int nk_max = (int)ceil(2.2 * kb) + 3;
+    k_lattice_sum<<<ntri2, LAT_THREADS, 0, P.stream>>>(2 * p, kb, nu_max, nk_max, P.tab.S);
+    FMM_LAUNCH_CHECK(P);
+    k_lattice_operator<<<1, 256, sizeof(Cx<double>) * ntri2, P.stream>>>(p, P.tab.S, P.tab.T0);
     FMM_LAUNCH_CHECK(P);
     FMM_CUDA_TRY(cudaStreamSynchronize(P.stream));
     return FMM_OK;

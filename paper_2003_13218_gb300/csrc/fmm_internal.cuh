@@ -100,6 +100,8 @@ struct Plan {
     void *L[9] = {};
     // tensor-core M2L state (bf16 operand planes, operator tables, TMA maps)
     void *tc = nullptr;
+    // scratch of the sparse solute-only pass
+    void *sol = nullptr;
     // reductions
     double *red_partial = nullptr;  // partial sums
     double *red_out = nullptr;      // [32] final FP64 scalars
@@ -205,6 +207,7 @@ fmm_status launch_forces_out(Plan &P, const double *q, double *forces);
 
 // expansions (fmm_expand.cu)
 fmm_status build_tables(Plan &P);
+fmm_status build_lattice(Plan &P);  // the kappa-dependent lattice table only
 void free_tables(Plan &P);
 fmm_status launch_upward(Plan &P, bool solute_only);
 fmm_status launch_lattice(Plan &P);
@@ -215,6 +218,11 @@ fmm_status launch_l2p(Plan &P, bool gradient, bool solute_only);
 // near field (fmm_p2p.cu)
 fmm_status launch_p2p(Plan &P, bool forces);
 fmm_status launch_p2p_uv(Plan &P);
+
+// sparse solute-only pass of Eq. FMMcalc (fmm_solute.cu)
+fmm_status solute_prepare(Plan &P);
+void solute_free(Plan &P);
+fmm_status launch_solute_pass(Plan &P, bool *done);
 
 // tensor-core M2L (fmm_m2l_tc.cu)
 bool tc_available(const Plan &P, int level);

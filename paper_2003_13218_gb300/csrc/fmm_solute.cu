@@ -1,0 +1,541 @@
+// fmm_solute.cu -- the solute-only far-field pass of the reduced scheme for the
+// solute-solvent energy (Eq. FMMcalc): Phi_u^FF at every charge, from the
+// solute charges alone.
+//
+// With a handful of solute charges only the leaves holding them and their
+// ancestors carry solute moments.  The pass therefore
+//  * builds the list of active cells per level (at most NU_MAX per level),
+//    P2M at the active leaves and M2M along the active ancestors;
+//  * runs the ordinary dense M2L + L2L on the coarse levels 1..LD (few cells)
+//    after the level-0 lattice operator, giving the full local expansion at
+//    level LD;
+//  * on the finer levels evaluates M2L only onto the targets whose interaction
+//    list contains an active source (at most 189 per source), kept as a
+//    sorted list per level;
+//  * evaluates Phi_u at every charge as the level-LD expansion plus the sparse
+//    contributions found at its finer ancestors.  A local expansion is a
+//    polynomial of degree p, so evaluating it at a charge directly equals
+//    shifting it to the leaf with L2L first (Appendix B) up to rounding.
+// When more than NU_MAX charges are solute, or the tree has no finer levels,
+// the caller runs the dense pass instead.
+#include <math.h>
+
+#include <new>
+#include <type_traits>
+
+#include "fmm_internal.cuh"
+
+namespace fmm {
+
+namespace {
+
+constexpr int NU_MAX = 32;      // solute charges handled by the sparse pass
+constexpr int LD = 3;           // levels 0..LD treated densely
+constexpr int MAX_TGT = NU_MAX * 189;
+
+struct SoluteScratch {
+    int *list = nullptr;     // [NU_MAX] sorted slots of solute charges; [NU_MAX] = count
+    int *cells = nullptr;    // [9][NU_MAX] active cell (linear index) per level
+    int *ncells = nullptr;   // [9]
+    void *MU = nullptr;      // [9][NU_MAX][nc] solute moments of the active cells
+    int *flags = nullptr;    // [8^d] target marks of one level
+    int *pos = nullptr;      // [8^d + 1] exclusive scan of the marks
+    int *scan_tmp = nullptr;
+    int *tlist = nullptr;    // [9][MAX_TGT] sorted targets per fine level
+    void *contrib = nullptr; // [9][MAX_TGT][nc] M2L sums at those targets
+    int *h_count = nullptr;  // pinned
+};
+
+inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+__device__ inline void cell_xyz(int64_t lin, int n, int &x, int &y, int &z)
+{
+    x = (int)(lin % n);
+    y = (int)((lin / n) % n);
+    z = (int)(lin / ((int64_t)n * n));
+}
+
+// collect the sorted slots of the solute charges (list order is irrelevant:
+// the active cells are sorted afterwards); list[NU_MAX] counts all of them
+__global__ void k_sol_list(int64_t N, const uint8_t *__restrict__ sol, int *__restrict__ list)
+{
+    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= N || !sol[s]) return;
+    int idx = atomicAdd(&list[NU_MAX], 1);
+    if (idx < NU_MAX) list[idx] = (int)s;
+}
+
+// active cells per level: leaves of the solute charges and their ancestors,
+// each list sorted by linear index and without repeats (one thread)
+__global__ void k_sol_cells(int d, const int *__restrict__ list, const int *__restrict__ sleaf, int *__restrict__ cells,
+                            int *__restrict__ ncells)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int n = list[NU_MAX];
+    if (n > NU_MAX) n = NU_MAX;
+    int cur[NU_MAX], cnt = 0;
+    for (int i = 0; i < n; ++i) cur[cnt++] = sleaf[list[i]];
+    for (int l = d; l >= 0; --l) {
+        // sort + unique
+        for (int i = 1; i < cnt; ++i) {
+            int v = cur[i], j = i - 1;
+            while (j >= 0 && cur[j] > v) {
+                cur[j + 1] = cur[j];
+                --j;
+            }
+            cur[j + 1] = v;
+        }
+        int u = 0;
+        for (int i = 0; i < cnt; ++i)
+            if (u == 0 || cur[i] != cur[u - 1]) cur[u++] = cur[i];
+        cnt = u;
+        for (int i = 0; i < cnt; ++i) cells[l * NU_MAX + i] = cur[i];
+        ncells[l] = cnt;
+        if (l == 0) break;
+        int nl = 1 << l;
+        for (int i = 0; i < cnt; ++i) {
+            int x, y, z;
+            cell_xyz(cur[i], nl, x, y, z);
+            cur[i] = (x >> 1) + (nl >> 1) * ((y >> 1) + (nl >> 1) * (z >> 1));
+        }
+    }
+}
+
+// P2M of the solute charges of active leaf blockIdx.x; thread m = column m
+template <typename T>
+__global__ void k_sol_p2m(int p, int d, const int *__restrict__ cells, const int *__restrict__ ncells,
+                          const int *__restrict__ start, const Particle<T> *__restrict__ spu, T inv_h, T *__restrict__ MU)
+{
+    int i = blockIdx.x;
+    if (i >= ncells[d]) return;
+    int m = threadIdx.x;
+    if (m > p) return;
+    int nc = ncoef(p);
+    int leaf = cells[d * NU_MAX + i];
+    T accr[P_MAX + 1], acci[P_MAX + 1];
+    for (int n = 0; n <= p; ++n) accr[n] = acci[n] = 0;
+    for (int s = start[leaf]; s < start[leaf + 1]; ++s) {
+        Particle<T> pt = spu[s];
+        if (pt.q == T(0)) continue;
+        T vx = -pt.x * inv_h, vy = -pt.y * inv_h, vz = -pt.z * inv_h;
+        T r2 = vx * vx + vy * vy + vz * vz;
+        T dre = 1, dim = 0;
+        for (int k = 1; k <= m; ++k) {
+            T sc = T(-0.5) / T(k);
+            T nre = sc * (vx * dre - vy * dim), nim = sc * (vx * dim + vy * dre);
+            dre = nre;
+            dim = nim;
+        }
+        T p2re = 0, p2im = 0, p1re = dre, p1im = dim;
+        accr[m] += pt.q * dre;
+        acci[m] += pt.q * dim;
+        for (int n = m + 1; n <= p; ++n) {
+            T a = T(2 * n - 1) * vz, inv = T(1) / T((n + m) * (n - m));
+            T cr = (a * p1re - r2 * p2re) * inv, ci = (a * p1im - r2 * p2im) * inv;
+            accr[n] += pt.q * cr;
+            acci[n] += pt.q * ci;
+            p2re = p1re;
+            p2im = p1im;
+            p1re = cr;
+            p1im = ci;
+        }
+    }
+    T *out = MU + ((size_t)d * NU_MAX + i) * nc;
+    for (int n = m; n <= p; ++n) {
+        out[cre(n, m)] = accr[n];
+        if (m > 0) out[cim(n, m)] = acci[n];
+    }
+}
+
+// M2M from the active children at level l+1 into active cell blockIdx.x of level l
+template <typename T>
+__global__ void k_sol_m2m(int p, int l, const int *__restrict__ cells, const int *__restrict__ ncells,
+                          const T *__restrict__ Rw, T *__restrict__ MU)
+{
+    int i = blockIdx.x;
+    if (i >= ncells[l]) return;
+    int nc = ncoef(p);
+    int ntri = (p + 1) * (p + 2) / 2;
+    int nl = 1 << l;
+    int px, py, pz;
+    cell_xyz(cells[l * NU_MAX + i], nl, px, py, pz);
+    for (int t = threadIdx.x; t < ntri; t += blockDim.x) {
+        int n = 0;
+        while (tri(n + 1, 0) <= t) ++n;
+        int m = t - tri(n, 0);
+        T accr = 0, acci = 0;
+        for (int k = 0; k < ncells[l + 1]; ++k) {
+            int cx, cy, cz;
+            cell_xyz(cells[(l + 1) * NU_MAX + k], 2 * nl, cx, cy, cz);
+            if ((cx >> 1) != px || (cy >> 1) != py || (cz >> 1) != pz) continue;
+            int oct = (cx & 1) | ((cy & 1) << 1) | ((cz & 1) << 2);
+            const T *Mch = MU + ((size_t)(l + 1) * NU_MAX + k) * nc;
+            const T *R = Rw + oct * nc;
+            T scale = 1;
+            for (int kk = 0; kk <= n; ++kk) {
+                int dn = n - kk;
+                T sgn = (dn & 1) ? T(-1) : T(1);
+                for (int ll = -kk; ll <= kk; ++ll) {
+                    int dm = m - ll;
+                    if (dm < -dn || dm > dn) continue;
+                    Cx<T> pr = cmul(coef(R, dn, dm), coef(Mch, kk, ll));
+                    accr += sgn * scale * pr.re;
+                    acci += sgn * scale * pr.im;
+                }
+                scale *= T(0.5);
+            }
+        }
+        T *out = MU + ((size_t)l * NU_MAX + i) * nc;
+        out[cre(n, m)] = accr;
+        if (m > 0) out[cim(n, m)] = acci;
+    }
+}
+
+// copy the active cells' moments of the coarse levels into the zeroed dense arrays
+template <typename T>
+__global__ void k_sol_scatter(int p, int lmax, const int *__restrict__ cells, const int *__restrict__ ncells,
+                              const T *__restrict__ MU, T *M0, T *M1, T *M2, T *M3)
+{
+    int l = blockIdx.y;
+    if (l > lmax) return;
+    int i = blockIdx.x;
+    if (i >= ncells[l]) return;
+    int nc = ncoef(p);
+    int nl = 1 << l;
+    int x, y, z;
+    cell_xyz(cells[l * NU_MAX + i], nl, x, y, z);
+    T *M = l == 0 ? M0 : l == 1 ? M1 : l == 2 ? M2 : M3;
+    T *dst = M + cell_index(l, x, y, z) * nc;
+    const T *src = MU + ((size_t)l * NU_MAX + i) * nc;
+    for (int k = threadIdx.x; k < nc; k += blockDim.x) dst[k] = src[k];
+}
+
+// interaction-list test: is s = t + delta in IL(t)?  (per axis delta in
+// [-2 - c, 3 - c] for target parity c, and not all |delta| <= 1)
+__device__ inline bool in_il(int dx, int dy, int dz, int tx, int ty, int tz)
+{
+    if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1 && dz >= -1 && dz <= 1) return false;
+    int cx = tx & 1, cy = ty & 1, cz = tz & 1;
+    return dx >= -2 - cx && dx <= 3 - cx && dy >= -2 - cy && dy <= 3 - cy && dz >= -2 - cz && dz <= 3 - cz;
+}
+
+__device__ inline int wrap_delta(int d, int n)  // representative of d mod n in [-n/2, n/2)
+{
+    d %= n;
+    if (d < -n / 2) d += n;
+    if (d >= n / 2) d -= n;
+    return d;
+}
+
+// mark the targets of active source blockIdx.x at level l (one thread per candidate offset)
+__global__ void k_sol_mark(int l, const int *__restrict__ cells, const int *__restrict__ ncells, int *__restrict__ flags)
+{
+    int i = blockIdx.x;
+    if (i >= ncells[l]) return;
+    int o = threadIdx.x;
+    if (o >= 343) return;
+    int dx = o % 7 - 3, dy = (o / 7) % 7 - 3, dz = o / 49 - 3;
+    int n = 1 << l;
+    int sx, sy, sz;
+    cell_xyz(cells[l * NU_MAX + i], n, sx, sy, sz);
+    int tx = (sx - dx + n) & (n - 1), ty = (sy - dy + n) & (n - 1), tz = (sz - dz + n) & (n - 1);
+    if (!in_il(dx, dy, dz, tx, ty, tz)) return;
+    flags[tx + n * (ty + n * tz)] = 1;
+}
+
+__global__ void k_sol_compact(int64_t n, const int *__restrict__ flags, const int *__restrict__ pos,
+                              int *__restrict__ tlist)
+{
+    int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c < n && flags[c]) {
+        int k = pos[c];
+        if (k < MAX_TGT) tlist[k] = (int)c;
+    }
+}
+
+// contribution of every active source to target tlist[blockIdx.x] (Eq. Lcoeffdef)
+template <typename T>
+__global__ void k_sol_m2l(int p, int l, const int *__restrict__ cells, const int *__restrict__ ncells,
+                          const int *__restrict__ tlist, const int *__restrict__ tcount, const T *__restrict__ Top,
+                          const T *__restrict__ MU, T *__restrict__ contrib)
+{
+    int b = blockIdx.x;
+    int cnt = *tcount;
+    if (cnt > MAX_TGT) cnt = MAX_TGT;
+    if (b >= cnt) return;
+    int nc = ncoef(p);
+    int n = 1 << l;
+    int tx, ty, tz;
+    cell_xyz(tlist[b], n, tx, ty, tz);
+    for (int j = threadIdx.x; j < nc; j += blockDim.x) {
+        T acc = 0;
+        for (int s = 0; s < ncells[l]; ++s) {
+            int sx, sy, sz;
+            cell_xyz(cells[l * NU_MAX + s], n, sx, sy, sz);
+            int dx = wrap_delta(sx - tx, n), dy = wrap_delta(sy - ty, n), dz = wrap_delta(sz - tz, n);
+            if (!in_il(dx, dy, dz, tx, ty, tz)) continue;
+            const T *Tp = Top + (size_t)off_slot(dx, dy, dz) * nc * nc + j;
+            const T *Ms = MU + ((size_t)l * NU_MAX + s) * nc;
+            for (int k = 0; k < nc; ++k) acc += Tp[(size_t)k * nc] * Ms[k];
+        }
+        contrib[((size_t)l * MAX_TGT + b) * nc + j] = acc;
+    }
+}
+
+// Phi at (v) from the real-layout local coefficients Lc (scaled), v in cell units
+template <typename T>
+__device__ T l2p_value(int p, const T *__restrict__ Lc, T vx, T vy, T vz)
+{
+    T r2 = vx * vx + vy * vy + vz * vz;
+    T pot = 0, dre = 1, dim = 0;
+    for (int m = 0; m <= p; ++m) {
+        if (m > 0) {
+            T sc = T(-0.5) / T(m);
+            T nre = sc * (vx * dre - vy * dim), nim = sc * (vx * dim + vy * dre);
+            dre = nre;
+            dim = nim;
+        }
+        T w = m == 0 ? T(1) : T(2);
+        T p2re = 0, p2im = 0, rre = dre, rim = dim;
+        for (int n = m; n <= p; ++n) {
+            if (n > m) {
+                T a = T(2 * n - 1) * vz, inv = T(1) / T((n + m) * (n - m));
+                T cr = (a * rre - r2 * p2re) * inv, ci = (a * rim - r2 * p2im) * inv;
+                p2re = rre;
+                p2im = rim;
+                rre = cr;
+                rim = ci;
+            }
+            Cx<T> L = coef(Lc, n, m);
+            pot += w * (L.re * rre - L.im * rim);
+        }
+    }
+    return pot;
+}
+
+// Phi_u at every charge: level-LD expansion plus the sparse finer-level sums
+template <typename T>
+__global__ void k_sol_eval(int p, int d, int64_t N, T h_leaf, const int *__restrict__ sleaf,
+                           const Particle<T> *__restrict__ sp, const T *__restrict__ Lld, const int *__restrict__ tlist,
+                           const int *__restrict__ tcounts, const T *__restrict__ contrib, T *__restrict__ phi)
+{
+    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= N) return;
+    int nc = ncoef(p);
+    int nside = 1 << d;
+    int leaf = sleaf[s];
+    int x, y, z;
+    cell_xyz(leaf, nside, x, y, z);
+    Particle<T> pt = sp[s];
+    T total = 0;
+    for (int l = LD; l <= d; ++l) {
+        int sh = d - l;
+        int ax = x >> sh, ay = y >> sh, az = z >> sh;
+        // centre of the leaf relative to the centre of its level-l ancestor, in leaf units
+        T ox = T((x - (ax << sh)) + 0.5) - T(0.5) * T(1 << sh);
+        T oy = T((y - (ay << sh)) + 0.5) - T(0.5) * T(1 << sh);
+        T oz = T((z - (az << sh)) + 0.5) - T(0.5) * T(1 << sh);
+        T inv = T(1) / (h_leaf * T(1 << sh));
+        T vx = (pt.x + ox * h_leaf) * inv, vy = (pt.y + oy * h_leaf) * inv, vz = (pt.z + oz * h_leaf) * inv;
+        if (l == LD) {
+            total += l2p_value<T>(p, Lld + cell_index(l, ax, ay, az) * nc, vx, vy, vz) * inv;
+            continue;
+        }
+        int cnt = tcounts[l];
+        if (cnt > MAX_TGT) cnt = MAX_TGT;
+        int key = ax + (1 << l) * (ay + (1 << l) * az);
+        const int *tl = tlist + (size_t)l * MAX_TGT;
+        int lo = 0, hi = cnt;
+        while (lo < hi) {
+            int mid = (lo + hi) >> 1;
+            if (tl[mid] < key) lo = mid + 1;
+            else hi = mid;
+        }
+        if (lo < cnt && tl[lo] == key)
+            total += l2p_value<T>(p, contrib + ((size_t)l * MAX_TGT + lo) * nc, vx, vy, vz) * inv;
+    }
+    phi[s] = total;
+}
+
+// exclusive scan (one block per 4096 flags), reusing the layout of the sort's scan
+__global__ void k_flag_scan_blocks(int64_t n, const int *__restrict__ in, int *__restrict__ out, int *__restrict__ sums)
+{
+    __shared__ int ws[32];
+    int64_t base = (int64_t)blockIdx.x * 4096 + threadIdx.x * 16;
+    int v[16], local = 0;
+    for (int k = 0; k < 16; ++k) {
+        int64_t idx = base + k;
+        v[k] = idx < n ? in[idx] : 0;
+        local += v[k];
+    }
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int x = local;
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int t = lane < (int)(blockDim.x >> 5) ? ws[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        ws[lane] = t;
+    }
+    __syncthreads();
+    int excl = x - local + (wid > 0 ? ws[wid - 1] : 0);
+    for (int k = 0; k < 16; ++k) {
+        int64_t idx = base + k;
+        if (idx < n) out[idx] = excl;
+        excl += v[k];
+    }
+    if (threadIdx.x == blockDim.x - 1) sums[blockIdx.x] = excl;
+}
+
+__global__ void k_flag_scan_sums(int nb, int *__restrict__ sums, int *__restrict__ total)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        int acc = 0;
+        for (int b = 0; b < nb; ++b) {
+            int t = sums[b];
+            sums[b] = acc;
+            acc += t;
+        }
+        *total = acc;
+    }
+}
+
+__global__ void k_flag_scan_add(int64_t n, int *__restrict__ out, const int *__restrict__ sums)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] += sums[i / 4096];
+}
+
+template <typename T>
+fmm_status solute_sparse_t(Plan &P, SoluteScratch &S)
+{
+    const int p = P.p, d = P.d, nc = P.nc;
+    const int nside = 1 << d;
+    const double h = P.box / nside;
+    const T *Rw = std::is_same<T, double>::value ? (const T *)P.tab.Rw64 : (const T *)P.tab.Rw32;
+    const T *Top = std::is_same<T, double>::value ? (const T *)P.tab.Top64 : (const T *)P.tab.Top32;
+    T *MU = (T *)S.MU;
+    // moments of the active cells
+    k_sol_cells<<<1, 32, 0, P.stream>>>(d, S.list, P.sleaf, S.cells, S.ncells);
+    FMM_LAUNCH_CHECK(P);
+    k_sol_p2m<T><<<NU_MAX, 32, 0, P.stream>>>(p, d, S.cells, S.ncells, P.cell_start, (const Particle<T> *)P.sorted_u,
+                                             (T)(1.0 / h), MU);
+    FMM_LAUNCH_CHECK(P);
+    for (int l = d - 1; l >= 0; --l) {
+        k_sol_m2m<T><<<NU_MAX, 128, 0, P.stream>>>(p, l, S.cells, S.ncells, Rw, MU);
+        FMM_LAUNCH_CHECK(P);
+    }
+    // dense coarse levels 0..LD
+    for (int l = 0; l <= LD; ++l)
+        FMM_CUDA_TRY(cudaMemsetAsync(P.M[l], 0, sizeof(T) * ((size_t)1 << (3 * l)) * nc, P.stream));
+    k_sol_scatter<T><<<dim3(NU_MAX, LD + 1), 128, 0, P.stream>>>(p, LD, S.cells, S.ncells, MU, (T *)P.M[0],
+                                                                 (T *)P.M[1], (T *)P.M[2], (T *)P.M[3]);
+    FMM_LAUNCH_CHECK(P);
+    fmm_status st = launch_lattice(P);
+    if (st != FMM_OK) return st;
+    for (int l = 1; l <= LD; ++l) {
+        st = tc_available(P, l) ? launch_m2l_tc(P, l) : launch_m2l_simt(P, l);
+        if (st != FMM_OK) return st;
+        st = launch_l2l(P, l);
+        if (st != FMM_OK) return st;
+    }
+    // sparse finer levels
+    for (int l = LD + 1; l <= d; ++l) {
+        int64_t n = (int64_t)1 << (3 * l);
+        FMM_CUDA_TRY(cudaMemsetAsync(S.flags, 0, sizeof(int) * n, P.stream));
+        k_sol_mark<<<NU_MAX, 352, 0, P.stream>>>(l, S.cells, S.ncells, S.flags);
+        FMM_LAUNCH_CHECK(P);
+        int nb = (int)((n + 4095) / 4096);
+        k_flag_scan_blocks<<<nb, 256, 0, P.stream>>>(n, S.flags, S.pos, S.scan_tmp);
+        FMM_LAUNCH_CHECK(P);
+        k_flag_scan_sums<<<1, 32, 0, P.stream>>>(nb, S.scan_tmp, S.ncells + 16 + l);
+        FMM_LAUNCH_CHECK(P);
+        k_flag_scan_add<<<blocks_for(n, 256), 256, 0, P.stream>>>(n, S.pos, S.scan_tmp);
+        FMM_LAUNCH_CHECK(P);
+        k_sol_compact<<<blocks_for(n, 256), 256, 0, P.stream>>>(n, S.flags, S.pos, S.tlist + (size_t)l * MAX_TGT);
+        FMM_LAUNCH_CHECK(P);
+        k_sol_m2l<T><<<MAX_TGT, ((nc + 31) / 32) * 32, 0, P.stream>>>(p, l, S.cells, S.ncells,
+                                                                       S.tlist + (size_t)l * MAX_TGT,
+                                                                       S.ncells + 16 + l, Top, MU, (T *)S.contrib);
+        FMM_LAUNCH_CHECK(P);
+    }
+    k_sol_eval<T><<<blocks_for(P.N, 128), 128, 0, P.stream>>>(p, d, P.N, (T)h, P.sleaf, (const Particle<T> *)P.sorted,
+                                                              (const T *)P.L[LD], S.tlist, S.ncells + 16,
+                                                              (const T *)S.contrib, (T *)P.phi_u);
+    FMM_LAUNCH_CHECK(P);
+    return FMM_OK;
+}
+
+}  // namespace
+
+fmm_status solute_prepare(Plan &P)
+{
+    solute_free(P);
+    if (P.d <= LD) return FMM_OK;
+    SoluteScratch *S = new (std::nothrow) SoluteScratch();
+    if (!S) return FMM_ERR_OOM;
+    P.sol = S;
+    int64_t nleaf = (int64_t)1 << (3 * P.d);
+    FMM_CUDA_TRY(cudaMalloc(&S->list, sizeof(int) * (NU_MAX + 4)));
+    FMM_CUDA_TRY(cudaMalloc(&S->cells, sizeof(int) * 9 * NU_MAX));
+    FMM_CUDA_TRY(cudaMalloc(&S->ncells, sizeof(int) * 32));
+    FMM_CUDA_TRY(cudaMalloc(&S->MU, sizeof(double) * 9 * NU_MAX * P.nc));
+    FMM_CUDA_TRY(cudaMalloc(&S->flags, sizeof(int) * nleaf));
+    FMM_CUDA_TRY(cudaMalloc(&S->pos, sizeof(int) * (nleaf + 1)));
+    FMM_CUDA_TRY(cudaMalloc(&S->scan_tmp, sizeof(int) * (nleaf / 4096 + 2)));
+    FMM_CUDA_TRY(cudaMalloc(&S->tlist, sizeof(int) * 9 * MAX_TGT));
+    FMM_CUDA_TRY(cudaMalloc(&S->contrib, sizeof(double) * (size_t)(P.d + 1) * MAX_TGT * P.nc));
+    FMM_CUDA_TRY(cudaMallocHost((void **)&S->h_count, sizeof(int)));
+    return FMM_OK;
+}
+
+void solute_free(Plan &P)
+{
+    SoluteScratch *S = (SoluteScratch *)P.sol;
+    if (!S) return;
+    cudaFree(S->list);
+    cudaFree(S->cells);
+    cudaFree(S->ncells);
+    cudaFree(S->MU);
+    cudaFree(S->flags);
+    cudaFree(S->pos);
+    cudaFree(S->scan_tmp);
+    cudaFree(S->tlist);
+    cudaFree(S->contrib);
+    if (S->h_count) cudaFreeHost(S->h_count);
+    delete S;
+    P.sol = nullptr;
+}
+
+// Phi_u into P.phi_u by the sparse pass; *done = false asks for the dense pass
+fmm_status launch_solute_pass(Plan &P, bool *done)
+{
+    *done = false;
+    SoluteScratch *S = (SoluteScratch *)P.sol;
+    if (!S) return FMM_OK;
+    FMM_CUDA_TRY(cudaMemsetAsync(S->list + NU_MAX, 0, sizeof(int), P.stream));
+    k_sol_list<<<blocks_for(P.N, 256), 256, 0, P.stream>>>(P.N, P.sorted_sol, S->list);
+    FMM_LAUNCH_CHECK(P);
+    FMM_CUDA_TRY(cudaMemcpyAsync(S->h_count, S->list + NU_MAX, sizeof(int), cudaMemcpyDeviceToHost, P.stream));
+    FMM_CUDA_TRY(cudaStreamSynchronize(P.stream));
+    int n = *S->h_count;
+    if (n > NU_MAX) return FMM_OK;
+    if (n == 0) {
+        size_t bytes = (P.precision == FMM_PREC_FP64 ? sizeof(double) : sizeof(float)) * P.N;
+        FMM_CUDA_TRY(cudaMemsetAsync(P.phi_u, 0, bytes, P.stream));
+        *done = true;
+        return FMM_OK;
+    }
+    fmm_status s = P.precision == FMM_PREC_FP64 ? solute_sparse_t<double>(P, *S) : solute_sparse_t<float>(P, *S);
+    if (s == FMM_OK) *done = true;
+    return s;
+}
+
+}  // namespace fmm

@@ -1,0 +1,44 @@
+"""Solute-solvent energy of the reduced far-field scheme (Eq. FMMcalc) on trees
+deep enough for the sparse solute-only pass (depth >= 4), against the oracle's
+two dense passes.  Cases: one ion (one active cell per level), a 16-atom solute
+spread over several cells (shared targets, merged ancestors), and a 40-atom
+solute (beyond the sparse pass's 32 charges: the dense pass runs instead)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2003_13218_gb300 import boxes
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+KEYS = ("e_uv", "W", "A", "B", "C", "nf_uv", "bc_cross")
+
+
+def _box():
+    return boxes.ion_in_water(333333 // 64, "Na", seed=5, L=215.3 / 4)  # N = 15,625
+
+
+def _gpu_uv(b, sol, d, p, precision):
+    from paper_2003_13218_gb300.fmm import FMMPlan
+    plan = FMMPlan(b.L, b.N, d, p, precision=precision)
+    dev = "cuda:0"
+    _, uv = plan.evaluate(torch.from_numpy(b.pos).to(dev), torch.from_numpy(b.q).to(dev),
+                          torch.from_numpy(sol).to(dev), forces=None)
+    plan.close()
+    return uv
+
+
+@pytest.mark.parametrize("n_solute", [1, 16, 40])
+def test_sparse_solute_pass_against_oracle(n_solute):
+    b = _box()
+    sol = np.zeros(b.N, np.uint8)
+    sol[:n_solute] = 1  # the ion and the first waters' atoms
+    d, p = 4, 8
+    ref = oracle.solute_solvent(b.pos, b.q, sol, b.L, d, p)
+    scale = abs(ref["A"]) + abs(ref["C"]) + abs(ref["e_uv"])
+    for precision, tol in (("fp64", 1e-11), ("mixed", 1e-5)):
+        uv = _gpu_uv(b, sol, d, p, precision)
+        for k in KEYS:
+            assert abs(uv[k] - ref[k]) <= tol * scale, (precision, k, uv[k], ref[k])
+        assert abs((uv["A"] - uv["B"]) - uv["C"]) <= 10 * tol * scale  # reciprocity (P10)
