@@ -313,52 +313,6 @@ __global__ void k_p2m(int p, int nside, const int *__restrict__ start, const Par
     }
 }
 
-// ------------------------------------------------------------------ M2M
-// Mhat_n^m(P) = sum_c sum_{k,l} R_{n-k}^{m-l}(u_c) Mhat_k^l(C_c) 2^{-k},
-// u_c = (r_P - r_C)/h_parent = -w_c,  R(-w) = (-1)^deg R(w).
-template <typename T>
-__global__ void k_m2m(int p, int lp, const T *__restrict__ Rw, const T *__restrict__ Mc, T *__restrict__ Mp)
-{
-    extern __shared__ unsigned char smem_raw[];
-    T *Rs = reinterpret_cast<T *>(smem_raw);
-    int nc = ncoef(p);
-    for (int i = threadIdx.x; i < 8 * nc; i += blockDim.x) Rs[i] = Rw[i];
-    __syncthreads();
-    int ntri = (p + 1) * (p + 2) / 2;
-    int64_t np = (int64_t)1 << lp;
-    int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (tid >= np * np * np * ntri) return;
-    int64_t par = tid / ntri;
-    int t = (int)(tid % ntri);
-    int n = 0;
-    while (tri(n + 1, 0) <= t) ++n;
-    int m = t - tri(n, 0);
-    int px = (int)(par % np), py = (int)((par / np) % np), pz = (int)(par / (np * np));
-    T accr = 0, acci = 0;
-    for (int c = 0; c < 8; ++c) {
-        const T *Mch = Mc + cell_index(lp + 1, 2 * px + (c & 1), 2 * py + ((c >> 1) & 1), 2 * pz + ((c >> 2) & 1)) * nc;
-        const T *R = Rs + c * nc;
-        T scale = 1;
-        for (int k = 0; k <= n; ++k) {
-            int dn = n - k;
-            T sgn = (dn & 1) ? T(-1) : T(1);
-            for (int l = -k; l <= k; ++l) {
-                int dm = m - l;
-                if (dm < -dn || dm > dn) continue;
-                Cx<T> r = coef(R, dn, dm);
-                Cx<T> mm = coef(Mch, k, l);
-                Cx<T> pr = cmul(r, mm);
-                accr += sgn * scale * pr.re;
-                acci += sgn * scale * pr.im;
-            }
-            scale *= T(0.5);
-        }
-    }
-    T *out = Mp + cell_index(lp, px, py, pz) * nc;
-    out[cre(n, m)] = accr;
-    if (m > 0) out[cim(n, m)] = acci;
-}
-
 // ------------------------------------------------------------------ lattice apply
 // Lbar(0) = T0 . Mhat(0) (Eq. 12 in place of I in Eq. Lcoeffdef), in FP64
 template <typename T>
@@ -426,47 +380,6 @@ __global__ void k_m2l_simt(int p, int l, int cls, const T *__restrict__ Top, con
             if (tg < ncls) L[(cls * ncls + tg) * nc + j] = acc[t];
         }
     }
-}
-
-// ------------------------------------------------------------------ L2L
-// Lhat_k^l(C) += sum_{n >= k, m} Lhat_n^m(P) R_{n-k}^{m-l}(w_c) 2^{-(k+1)}
-template <typename T>
-__global__ void k_l2l(int p, int l, const T *__restrict__ Rw, const T *__restrict__ Lp, T *__restrict__ Lc)
-{
-    extern __shared__ unsigned char smem_raw[];
-    T *Rs = reinterpret_cast<T *>(smem_raw);
-    int nc = ncoef(p);
-    for (int i = threadIdx.x; i < 8 * nc; i += blockDim.x) Rs[i] = Rw[i];
-    __syncthreads();
-    int ntri = (p + 1) * (p + 2) / 2;
-    int64_t n1 = (int64_t)1 << l;
-    int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (tid >= n1 * n1 * n1 * ntri) return;
-    int64_t ch = tid / ntri;
-    int t = (int)(tid % ntri);
-    int k = 0;
-    while (tri(k + 1, 0) <= t) ++k;
-    int lo = t - tri(k, 0);
-    int x = (int)(ch % n1), y = (int)((ch / n1) % n1), z = (int)(ch / (n1 * n1));
-    int c = (x & 1) | ((y & 1) << 1) | ((z & 1) << 2);
-    const T *Lpar = Lp + cell_index(l - 1, x >> 1, y >> 1, z >> 1) * nc;
-    const T *R = Rs + c * nc;
-    T accr = 0, acci = 0;
-    for (int n = k; n <= p; ++n) {
-        int dn = n - k;
-        for (int m = -n; m <= n; ++m) {
-            int dm = m - lo;
-            if (dm < -dn || dm > dn) continue;
-            Cx<T> pr = cmul(coef(Lpar, n, m), coef(R, dn, dm));
-            accr += pr.re;
-            acci += pr.im;
-        }
-    }
-    T scale = T(1);
-    for (int i = 0; i <= k; ++i) scale *= T(0.5);
-    T *out = Lc + cell_index(l, x, y, z) * nc;
-    out[cre(k, lo)] += scale * accr;
-    if (lo > 0) out[cim(k, lo)] += scale * acci;
 }
 
 // ------------------------------------------------------------------ L2P
@@ -540,14 +453,9 @@ fmm_status upward_t(Plan &P, bool solute_only)
     int64_t nthr = P.nleaf * (p + 1);
     k_p2m<T><<<blocks_for(nthr, 128), 128, 0, P.stream>>>(p, nside, P.cell_start, sp, inv_h, P.d, (T *)P.M[P.d]);
     FMM_LAUNCH_CHECK(P);
-    const T *Rw = std::is_same<T, double>::value ? (const T *)P.tab.Rw64 : (const T *)P.tab.Rw32;
-    int ntri = (p + 1) * (p + 2) / 2;
     for (int l = P.d - 1; l >= 0; --l) {
-        int64_t np = (int64_t)1 << l;
-        int64_t n = np * np * np * ntri;
-        k_m2m<T><<<blocks_for(n, 128), 128, 8 * nc * sizeof(T), P.stream>>>(p, l, Rw, (const T *)P.M[l + 1],
-                                                                            (T *)P.M[l]);
-        FMM_LAUNCH_CHECK(P);
+        fmm_status st = launch_m2m(P, l);
+        if (st != FMM_OK) return st;
     }
     return FMM_OK;
 }
@@ -568,6 +476,10 @@ fmm_status build_tables(Plan &P)
     FMM_CUDA_TRY(cudaMalloc(&P.tab.Top32, sizeof(float) * (size_t)NOFF * nc * nc));
     k_octant_table<<<1, 32, 0, P.stream>>>(p, P.tab.Rw64, P.tab.Rw32);
     FMM_LAUNCH_CHECK(P);
+    {
+        fmm_status st = build_translation_ops(P);
+        if (st != FMM_OK) return st;
+    }
     size_t shI = sizeof(Cx<double>) * ntri2;
     k_m2l_operators<<<NOFF, 256, shI, P.stream>>>(p, P.tab.Top64, P.tab.Top32);
     FMM_LAUNCH_CHECK(P);
@@ -608,6 +520,10 @@ void free_tables(Plan &P)
     cudaFree(P.tab.T0);
     cudaFree(P.tab.Top64);
     cudaFree(P.tab.Top32);
+    cudaFree(P.tab.l2l64);
+    cudaFree(P.tab.l2l32);
+    cudaFree(P.tab.m2m64);
+    cudaFree(P.tab.m2m32);
     P.tab = Tables{};
 }
 
@@ -656,21 +572,6 @@ fmm_status launch_m2l_simt(Plan &P, int l)
         }
         FMM_LAUNCH_CHECK(P);
     }
-    return FMM_OK;
-}
-
-fmm_status launch_l2l(Plan &P, int l)
-{
-    int ntri = (P.p + 1) * (P.p + 2) / 2;
-    int64_t n1 = (int64_t)1 << l;
-    int64_t n = n1 * n1 * n1 * ntri;
-    if (P.precision == FMM_PREC_FP64)
-        k_l2l<double><<<blocks_for(n, 128), 128, 8 * P.nc * sizeof(double), P.stream>>>(
-            P.p, l, P.tab.Rw64, (const double *)P.L[l - 1], (double *)P.L[l]);
-    else
-        k_l2l<float><<<blocks_for(n, 128), 128, 8 * P.nc * sizeof(float), P.stream>>>(
-            P.p, l, P.tab.Rw32, (const float *)P.L[l - 1], (float *)P.L[l]);
-    FMM_LAUNCH_CHECK(P);
     return FMM_OK;
 }
 

@@ -63,6 +63,10 @@ struct Tables {
     double *T0 = nullptr;     // [NC][NC] real lattice operator (input-major: T0[k * NC + j])
     double *Top64 = nullptr;  // [NOFF][NC][NC] real M2L operators (input-major), FP64 path
     float *Top32 = nullptr;   // same in FP32 for the SIMT FP32 path
+    double *l2l64 = nullptr;  // [8 NC][NC] L2L operators of the 8 child octants (row-major)
+    float *l2l32 = nullptr;
+    double *m2m64 = nullptr;  // [NC][8 NC] M2M operators (row-major)
+    float *m2m32 = nullptr;
 };
 
 struct Plan {
@@ -212,7 +216,11 @@ void free_tables(Plan &P);
 fmm_status launch_upward(Plan &P, bool solute_only);
 fmm_status launch_lattice(Plan &P);
 fmm_status launch_m2l_simt(Plan &P, int level);
-fmm_status launch_l2l(Plan &P, int level);
+
+// M2M / L2L as dense products (fmm_translate.cu)
+fmm_status build_translation_ops(Plan &P);
+fmm_status launch_m2m(Plan &P, int level);  // level + 1 -> level
+fmm_status launch_l2l(Plan &P, int level);  // level - 1 -> level (accumulates)
 fmm_status launch_l2p(Plan &P, bool gradient, bool solute_only);
 
 // near field (fmm_p2p.cu)

@@ -1,0 +1,262 @@
+// fmm_translate.cu -- M2M and L2L (Appendix B) as dense products.
+//
+// In level-scaled coefficients both translations are fixed linear maps per
+// child octant c (w_c = child-centre offset / parent side = (+-1/4)^3):
+//   L2L: Lhat_k^l(child) = sum_{n >= k, m} Lhat_n^m(parent) R_{n-k}^{m-l}(w_c) 2^{-(k+1)}
+//   M2M: Mhat_n^m(parent) = sum_c sum_{k <= n, l} R_{n-k}^{m-l}(-w_c) Mhat_k^l(child_c) 2^{-k}
+// so a whole level is one product with gathered columns:
+//   L2L: [8 C x C] (all octants stacked) . [C x parents]   -> added to the children
+//   M2M: [C x 8 C] . [8 C x parents] (the 8 children of each parent) -> parents
+// The real operator matrices are built once per plan from the complex forms.
+#include <math.h>
+
+#include <type_traits>
+
+#include "fmm_internal.cuh"
+
+namespace fmm {
+
+namespace {
+
+inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+__device__ inline void split_index(int j, int &n, int &m, bool &im)
+{
+    n = (int)sqrt((double)j);
+    while (n * n > j) --n;
+    while ((n + 1) * (n + 1) <= j) ++n;
+    int r = j - n * n;
+    m = (r + 1) / 2;
+    im = (m > 0) && (r == 2 * m);
+}
+
+// unit input coefficient: C_n^m = u (u = 1 or i), C_n^{-m} = (-1)^m conj(u)
+__device__ inline Cx<double> unit_pos(bool im) { return im ? Cx<double>{0, 1} : Cx<double>{1, 0}; }
+__device__ inline Cx<double> unit_neg(bool im, int m)
+{
+    Cx<double> u = unit_pos(im);
+    u.im = -u.im;
+    if (m & 1) {
+        u.re = -u.re;
+        u.im = -u.im;
+    }
+    return u;
+}
+
+// L2L operators, row-major [8 nc][nc]: row c nc + j (child output j), column e (parent input)
+__global__ void k_l2l_ops(int p, const double *__restrict__ Rw, double *__restrict__ A64, float *__restrict__ A32)
+{
+    int nc = ncoef(p);
+    int64_t total = (int64_t)8 * nc * nc;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        int e = (int)(t % nc);
+        int row = (int)(t / nc);
+        int c = row / nc, j = row % nc;
+        int k, l, n, m;
+        bool oim, iim;
+        split_index(j, k, l, oim);
+        split_index(e, n, m, iim);
+        double v = 0;
+        if (n >= k) {
+            const double *R = Rw + c * nc;
+            Cx<double> acc = {0, 0};
+            int dn = n - k;
+            if (m - l >= -dn && m - l <= dn) acc = cmul(unit_pos(iim), coef(R, dn, m - l));
+            if (m > 0 && -m - l >= -dn && -m - l <= dn) {
+                Cx<double> t2 = cmul(unit_neg(iim, m), coef(R, dn, -m - l));
+                acc.re += t2.re;
+                acc.im += t2.im;
+            }
+            double s = ldexp(1.0, -(k + 1));
+            v = s * (oim ? acc.im : acc.re);
+        }
+        A64[t] = v;
+        A32[t] = (float)v;
+    }
+}
+
+// M2M operators, row-major [nc][8 nc]: row j (parent output), column c nc + e (child input)
+__global__ void k_m2m_ops(int p, const double *__restrict__ Rw, double *__restrict__ B64, float *__restrict__ B32)
+{
+    int nc = ncoef(p);
+    int64_t total = (int64_t)8 * nc * nc;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        int col = (int)(t % (8 * nc));
+        int j = (int)(t / (8 * nc));
+        int c = col / nc, e = col % nc;
+        int n, m, k, l;
+        bool oim, iim;
+        split_index(j, n, m, oim);
+        split_index(e, k, l, iim);
+        double v = 0;
+        if (k <= n) {
+            const double *R = Rw + c * nc;
+            int dn = n - k;
+            double sg = (dn & 1) ? -1.0 : 1.0;  // R(-w) = (-1)^deg R(w)
+            Cx<double> acc = {0, 0};
+            if (m - l >= -dn && m - l <= dn) acc = cmul(coef(R, dn, m - l), unit_pos(iim));
+            if (l > 0 && m + l >= -dn && m + l <= dn) {
+                Cx<double> t2 = cmul(coef(R, dn, m + l), unit_neg(iim, l));
+                acc.re += t2.re;
+                acc.im += t2.im;
+            }
+            double s = sg * ldexp(1.0, -k);
+            v = s * (oim ? acc.im : acc.re);
+        }
+        B64[t] = v;
+        B32[t] = (float)v;
+    }
+}
+
+// Dense product with gathered columns:
+//   C[coff(n) + moff(m)] (+)= sum_k A[m][k] B[boff(n) + koff(k)]
+// MODE 0 (M2M, parents at level l): boff = n nc, koff(k) = (k / nc) 8^l nc + k % nc,
+//         coff = cell_index(l, P(n)) nc, moff(m) = m, overwrite;
+// MODE 1 (L2L, children at level l): boff = cell_index(l - 1, P(n)) nc, koff(k) = k,
+//         coff = n nc, moff(m) = (m / nc) 8^(l-1) nc + m % nc, accumulate.
+// n runs over the parent coordinates P in x-fastest order.
+template <typename T, int MODE, int BM, int BN, int BK, int TM, int TN>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+    k_translate(int M, int64_t N, int K, int nc, int l, const T *__restrict__ A, const T *__restrict__ B,
+                T *__restrict__ C)
+{
+    constexpr int NT = (BM / TM) * (BN / TN);
+    __shared__ T As[BK][BM];
+    __shared__ T Bs[BK][BN];
+    __shared__ int64_t bcol[BN];
+    __shared__ int64_t ccol[BN];
+    const int tid = threadIdx.x;
+    const int m0 = blockIdx.y * BM;
+    const int64_t n0 = (int64_t)blockIdx.x * BN;
+    const int np = MODE == 0 ? (1 << l) : (1 << (l - 1));  // parents per side
+    const int64_t np3 = (int64_t)np * np * np;
+    for (int i = tid; i < BN; i += NT) {
+        int64_t n = n0 + i;
+        int64_t b = 0, c = 0;
+        if (n < N) {
+            int px = (int)(n % np), py = (int)((n / np) % np), pz = (int)(n / ((int64_t)np * np));
+            if (MODE == 0) {
+                b = n * nc;
+                c = cell_index(l, px, py, pz) * nc;
+            } else {
+                b = cell_index(l - 1, px, py, pz) * nc;
+                c = n * nc;
+            }
+        }
+        bcol[i] = b;
+        ccol[i] = c;
+    }
+    const int tm = tid % (BM / TM), tn = tid / (BM / TM);
+    T acc[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = 0;
+    __syncthreads();
+    for (int k0 = 0; k0 < K; k0 += BK) {
+        for (int e = tid; e < BM * BK; e += NT) {
+            int kk = e % BK, mm = e / BK;
+            int m = m0 + mm, k = k0 + kk;
+            As[kk][mm] = (m < M && k < K) ? A[(size_t)m * K + k] : T(0);
+        }
+        for (int e = tid; e < BN * BK; e += NT) {
+            int kk = e % BK, nn = e / BK;
+            int k = k0 + kk;
+            T v = 0;
+            if (n0 + nn < N && k < K) {
+                int64_t ko = MODE == 0 ? (int64_t)(k / nc) * np3 * nc + (k % nc) : k;
+                v = B[bcol[nn] + ko];
+            }
+            Bs[kk][nn] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            T a[TM], b[TN];
+#pragma unroll
+            for (int i = 0; i < TM; ++i) a[i] = As[kk][tm + i * (BM / TM)];
+#pragma unroll
+            for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tn + j * (BN / TN)];
+#pragma unroll
+            for (int i = 0; i < TM; ++i)
+#pragma unroll
+                for (int j = 0; j < TN; ++j) acc[i][j] += a[i] * b[j];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+        int nn = tn + j * (BN / TN);
+        if (n0 + nn >= N) continue;
+#pragma unroll
+        for (int i = 0; i < TM; ++i) {
+            int m = m0 + tm + i * (BM / TM);
+            if (m >= M) continue;
+            if (MODE == 0) {
+                C[ccol[nn] + m] = acc[i][j];
+            } else {
+                int64_t mo = (int64_t)(m / nc) * np3 * nc + (m % nc);
+                C[ccol[nn] + mo] += acc[i][j];
+            }
+        }
+    }
+}
+
+template <typename T, int MODE>
+fmm_status launch_translate(Plan &P, int l, const T *A, const T *B, T *C)
+{
+    const int nc = P.nc;
+    const int M = MODE == 0 ? nc : 8 * nc;
+    const int K = MODE == 0 ? 8 * nc : nc;
+    const int64_t N = MODE == 0 ? ((int64_t)1 << (3 * l)) : ((int64_t)1 << (3 * (l - 1)));
+    if (std::is_same<T, float>::value) {
+        constexpr int BM = 64, BN = 128, BK = 8, TM = 4, TN = 8;
+        dim3 grid(blocks_for(N, BN), (M + BM - 1) / BM);
+        k_translate<T, MODE, BM, BN, BK, TM, TN><<<grid, (BM / TM) * (BN / TN), 0, P.stream>>>(M, N, K, nc, l, A, B,
+                                                                                               C);
+    } else {
+        constexpr int BM = 64, BN = 64, BK = 8, TM = 4, TN = 4;
+        dim3 grid(blocks_for(N, BN), (M + BM - 1) / BM);
+        k_translate<T, MODE, BM, BN, BK, TM, TN><<<grid, (BM / TM) * (BN / TN), 0, P.stream>>>(M, N, K, nc, l, A, B,
+                                                                                               C);
+    }
+    FMM_LAUNCH_CHECK(P);
+    return FMM_OK;
+}
+
+}  // namespace
+
+fmm_status build_translation_ops(Plan &P)
+{
+    const int nc = P.nc;
+    const size_t n = (size_t)8 * nc * nc;
+    if (!P.tab.l2l64) {
+        FMM_CUDA_TRY(cudaMalloc(&P.tab.l2l64, sizeof(double) * n));
+        FMM_CUDA_TRY(cudaMalloc(&P.tab.l2l32, sizeof(float) * n));
+        FMM_CUDA_TRY(cudaMalloc(&P.tab.m2m64, sizeof(double) * n));
+        FMM_CUDA_TRY(cudaMalloc(&P.tab.m2m32, sizeof(float) * n));
+    }
+    k_l2l_ops<<<blocks_for(n, 256), 256, 0, P.stream>>>(P.p, P.tab.Rw64, P.tab.l2l64, P.tab.l2l32);
+    FMM_LAUNCH_CHECK(P);
+    k_m2m_ops<<<blocks_for(n, 256), 256, 0, P.stream>>>(P.p, P.tab.Rw64, P.tab.m2m64, P.tab.m2m32);
+    FMM_LAUNCH_CHECK(P);
+    return FMM_OK;
+}
+
+// M2M into level l (parents) from level l + 1
+fmm_status launch_m2m(Plan &P, int l)
+{
+    if (P.precision == FMM_PREC_FP64)
+        return launch_translate<double, 0>(P, l, P.tab.m2m64, (const double *)P.M[l + 1], (double *)P.M[l]);
+    return launch_translate<float, 0>(P, l, P.tab.m2m32, (const float *)P.M[l + 1], (float *)P.M[l]);
+}
+
+// L2L from level l - 1 into level l (added to the M2L result)
+fmm_status launch_l2l(Plan &P, int l)
+{
+    if (P.precision == FMM_PREC_FP64)
+        return launch_translate<double, 1>(P, l, P.tab.l2l64, (const double *)P.L[l - 1], (double *)P.L[l]);
+    return launch_translate<float, 1>(P, l, P.tab.l2l32, (const float *)P.L[l - 1], (float *)P.L[l]);
+}
+
+}  // namespace fmm
