@@ -59,13 +59,17 @@ struct TcState {
     CUtensorMap mapA[9][3];
     CUtensorMap mapB[3];
     int bx[9], by[9], bz[9];
+    int groups[9], per_group[9];  // offset groups per tile (small levels run more CTAs)
+    float *Lpart = nullptr;       // partial sums of the offset groups
 };
 
 struct TcArgs {
     int np, bx, by, bz, rows, tiles_x, tiles_y, tiles_per_class;
     int nc, npad, kchunks;
+    int groups, per_group;  // the 189 offsets split over `groups` CTAs per tile (small levels)
     uint32_t idesc;
     float *L;
+    float *Lpart;           // [groups][8 np^3][nc] partial sums when groups > 1
     int *err;
 };
 
@@ -223,8 +227,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const uint32_t stage_bytes = PA * stageA + PB * stageB;
     const uint32_t tx_bytes = (uint32_t)(PA * a.rows * ROW_BYTES) + PB * stageB;
 
-    const int cls = blockIdx.x / a.tiles_per_class;
-    const int tile = blockIdx.x % a.tiles_per_class;
+    // the 8 parity classes of one brick run side by side: CTAs resident at the
+    // same time then read overlapping shifted bricks, which stay in L2
+    const int grp = blockIdx.x % a.groups;
+    const int cls = (blockIdx.x / a.groups) & 7;
+    const int tile = (blockIdx.x / a.groups) >> 3;
+    const int o_begin = grp * a.per_group;
+    const int o_end = o_begin + a.per_group < NUM_IL ? o_begin + a.per_group : NUM_IL;
+    const int nloc = o_end > o_begin ? o_end - o_begin : 0;
     const int x0 = (tile % a.tiles_x) * a.bx;
     const int y0 = ((tile / a.tiles_x) % a.tiles_y) * a.by;
     const int z0 = (tile / (a.tiles_x * a.tiles_y)) * a.bz;
@@ -264,11 +274,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const CUtensorMap *mA[3] = {&mA0, &mA1, &mA2};
             const CUtensorMap *mB[3] = {&mB0, &mB1, &mB2};
             int it = 0;
+            int oi = -1;  // position of the offset in the interaction-list order
             bool ok = true;
             for (int dz = -2 - cz; dz <= 3 - cz && ok; ++dz)
                 for (int dy = -2 - cy; dy <= 3 - cy && ok; ++dy)
                     for (int dx = -2 - cx; dx <= 3 - cx && ok; ++dx) {
                         if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1 && dz >= -1 && dz <= 1) continue;
+                        ++oi;
+                        if (oi < o_begin || oi >= o_end) continue;
                         const int sx = cx + dx, sy = cy + dy, sz = cz + dz;
                         const int scls = (sx & 1) | ((sy & 1) << 1) | ((sz & 1) << 2);
                         const int hx = x0 + (sx >> 1) + 1, hy = y0 + (sy >> 1) + 1;
@@ -307,7 +320,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             using PR = Products<PA, PB>;
             int it = 0;
             bool ok = true;
-            for (int o = 0; o < NUM_IL && ok; ++o) {
+            for (int o = 0; o < nloc && ok; ++o) {
                 const int acc = o & 1;
                 const uint32_t use = (uint32_t)(o >> 1);
                 if (o >= 2 && !mbar_wait(smem_u32(&bar_tempty[acc]), (use - 1u) & 1u, abort_flag)) {
@@ -355,7 +368,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
         for (int i = 0; i < NCH * 16; ++i) Lr[i] = 0.f;
         bool ok = true;
-        for (int o = 0; o < NUM_IL; ++o) {
+        for (int o = 0; o < nloc; ++o) {
             const int acc = o & 1;
             const uint32_t use = (uint32_t)(o >> 1);
             if (!mbar_wait(smem_u32(&bar_tfull[acc]), use & 1u, abort_flag)) {
@@ -383,7 +396,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const int tx = row % a.bx, ty = (row / a.bx) % a.by, tz = row / (a.bx * a.by);
             const int64_t np = a.np;
             const int64_t lin = (x0 + tx) + np * ((y0 + ty) + np * (int64_t)(z0 + tz));
-            float *dst = a.L + ((int64_t)cls * np * np * np + lin) * a.nc;
+            float *dst = a.groups == 1 ? a.L + ((int64_t)cls * np * np * np + lin) * a.nc
+                                       : a.Lpart + (((int64_t)grp * 8 + cls) * np * np * np + lin) * a.nc;
 #pragma unroll
             for (int i = 0; i < NCH * 16; ++i)
                 if (i < a.nc) dst[i] = Lr[i];
@@ -454,6 +468,16 @@ __global__ void k_split_ops(const double *__restrict__ T, int nc, int npad, int 
         ops[e] = b0;
         ops[e + part_elems] = b1;
         if (parts > 2) ops[e + 2 * part_elems] = __float2bfloat16_rn((float)r2);
+    }
+}
+
+// L = sum over the offset groups, in group order
+__global__ void k_group_sum(int64_t n, int groups, const float *__restrict__ part, float *__restrict__ L)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        float s = 0.f;
+        for (int g = 0; g < groups; ++g) s += part[(int64_t)g * n + e];
+        L[e] = s;
     }
 }
 
@@ -533,6 +557,7 @@ fmm_status tc_prepare(Plan &P)
     }
     for (int j = S->pb; j < 3; ++j) S->mapB[j] = S->mapB[0];
     // source planes per level
+    size_t lpart_elems = 0;
     for (int l = 1; l <= P.d; ++l) {
         int np = 1 << (l - 1);
         int64_t np2 = np + 2;
@@ -553,7 +578,19 @@ fmm_status tc_prepare(Plan &P)
                 return FMM_ERR_INTERNAL;
         }
         for (int i = S->pa; i < 3; ++i) S->mapA[l][i] = S->mapA[l][0];
+        // enough CTAs to fill the GPU twice: split the 189 offsets when tiles are few
+        int tiles = 8 * (np / S->bx[l]) * (np / S->by[l]) * (np / S->bz[l]);
+        int want = (2 * 152 + tiles - 1) / tiles;
+        if (want < 1) want = 1;
+        if (want > 27) want = 27;
+        S->per_group[l] = (NUM_IL + want - 1) / want;
+        S->groups[l] = (NUM_IL + S->per_group[l] - 1) / S->per_group[l];
+        if (S->groups[l] > 1) {
+            size_t need = (size_t)S->groups[l] * 8 * np * np * np * P.nc;
+            if (need > lpart_elems) lpart_elems = need;
+        }
     }
+    if (lpart_elems) FMM_CUDA_TRY(cudaMalloc(&S->Lpart, sizeof(float) * lpart_elems));
     TcKernel k = pa == 3 ? pick_kernel<3>(S->npad / 16) : pick_kernel<2>(S->npad / 16);
     if (!k) return FMM_ERR_INTERNAL;
     FMM_CUDA_TRY(cudaFuncSetAttribute((const void *)k, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -587,8 +624,11 @@ fmm_status launch_m2l_tc(Plan &P, int l)
     a.kchunks = S->kp / KCHUNK;
     a.idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(S->npad >> 3) << 17) | ((uint32_t)(TC_ROWS >> 4) << 24);
     a.L = (float *)P.L[l];
+    a.Lpart = S->Lpart;
+    a.groups = S->groups[l];
+    a.per_group = S->per_group[l];
     a.err = P.d_err;
-    unsigned grid = 8u * (unsigned)a.tiles_per_class;
+    unsigned grid = 8u * (unsigned)a.tiles_per_class * (unsigned)a.groups;
     TcKernel k = S->pa == 3 ? pick_kernel<3>(S->npad / 16) : pick_kernel<2>(S->npad / 16);
     if (!k) return FMM_ERR_INTERNAL;
     const bool time_it = P.timings_on && l == P.d && P.ev_top[0];
@@ -600,6 +640,12 @@ fmm_status launch_m2l_tc(Plan &P, int l)
         cudaEventRecord(P.ev_top[1], P.stream);
         P.top_recorded = true;
     }
+    if (a.groups > 1) {
+        int64_t n = (int64_t)8 * np * np * np * P.nc;
+        k_group_sum<<<(unsigned)((n + 255) / 256 < 2048 ? (n + 255) / 256 : 2048), 256, 0, P.stream>>>(
+            n, a.groups, S->Lpart, a.L);
+        FMM_LAUNCH_CHECK(P);
+    }
     return FMM_OK;
 }
 
@@ -609,6 +655,7 @@ void tc_free(Plan &P)
     if (!S) return;
     for (int l = 0; l < 9; ++l) cudaFree(S->planes[l]);
     cudaFree(S->ops);
+    cudaFree(S->Lpart);
     delete S;
     P.tc = nullptr;
 }

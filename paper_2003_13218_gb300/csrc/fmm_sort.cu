@@ -249,18 +249,32 @@ __global__ void k_energy_partial(int64_t N, const Particle<T> *__restrict__ sp, 
     block_reduce_store<6>(acc, partial);
 }
 
+// block partials -> totals; blockDim.x == RED_THREADS, fixed-order tree per quantity
 template <int NQ>
 __device__ void final_sum(const double *__restrict__ partial, int nb, double *out)
 {
-    // one thread per quantity, blocks summed in order
-    int q = threadIdx.x;
-    if (q < NQ) {
+    __shared__ double sh[RED_THREADS][2];
+    for (int q = 0; q < NQ; ++q) {
         KSum k{0, 0};
-        for (int b = 0; b < nb; ++b) {
+        for (int b = threadIdx.x; b < nb; b += RED_THREADS) {
             k.add(partial[(b * NQ + q) * 2]);
             k.add(partial[(b * NQ + q) * 2 + 1]);
         }
-        out[q] = k.val();
+        sh[threadIdx.x][0] = k.s;
+        sh[threadIdx.x][1] = k.c;
+        __syncthreads();
+        for (int o = RED_THREADS / 2; o > 0; o >>= 1) {
+            if ((int)threadIdx.x < o) {
+                KSum a{sh[threadIdx.x][0], sh[threadIdx.x][1]};
+                a.add(sh[threadIdx.x + o][0]);
+                a.add(sh[threadIdx.x + o][1]);
+                sh[threadIdx.x][0] = a.s;
+                sh[threadIdx.x][1] = a.c;
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) out[q] = sh[0][0] + sh[0][1];
+        __syncthreads();
     }
 }
 
@@ -386,7 +400,7 @@ fmm_status launch_bc_moments(Plan &P, const double *q, const uint8_t *sol)
 {
     k_bc_partial<<<RED_BLOCKS, RED_THREADS, 0, P.stream>>>(P.N, P.wpos, q, sol, P.red_partial);
     FMM_LAUNCH_CHECK(P);
-    k_bc_final<<<1, 32, 0, P.stream>>>(P.red_partial, RED_BLOCKS, P.red_out);
+    k_bc_final<<<1, RED_THREADS, 0, P.stream>>>(P.red_partial, RED_BLOCKS, P.red_out);
     FMM_LAUNCH_CHECK(P);
     return FMM_OK;
 }
@@ -408,7 +422,7 @@ fmm_status launch_energy_reduce(Plan &P, bool with_uv)
     }
     FMM_LAUNCH_CHECK(P);
     double kappa = P.kappa > 0 ? P.kappa : 2.0 / P.box;
-    k_energy_final<<<1, 32, 0, P.stream>>>(part, RED_BLOCKS, P.red_out, P.box, kappa, with_uv ? 1 : 0);
+    k_energy_final<<<1, RED_THREADS, 0, P.stream>>>(part, RED_BLOCKS, P.red_out, P.box, kappa, with_uv ? 1 : 0);
     FMM_LAUNCH_CHECK(P);
     return FMM_OK;
 }

@@ -72,6 +72,9 @@ __global__ void k_l2l_ops(int p, const double *__restrict__ Rw, double *__restri
         }
         A64[t] = v;
         A32[t] = (float)v;
+        const size_t tt = (size_t)total + (size_t)e * (8 * nc) + row;  // transposed copy [nc][8 nc]
+        A64[tt] = v;
+        A32[tt] = (float)v;
     }
 }
 
@@ -105,6 +108,9 @@ __global__ void k_m2m_ops(int p, const double *__restrict__ Rw, double *__restri
         }
         B64[t] = v;
         B32[t] = (float)v;
+        const size_t tt = (size_t)total + (size_t)col * nc + j;  // transposed copy [8 nc][nc]
+        B64[tt] = v;
+        B32[tt] = (float)v;
     }
 }
 
@@ -202,13 +208,56 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
     }
 }
 
+// The same products for coarse levels (few columns): one block per
+// (column, 32 outputs), the 8 warps split K, partial sums added in warp order.
+// AT is the operator transposed, [K][M].
 template <typename T, int MODE>
-fmm_status launch_translate(Plan &P, int l, const T *A, const T *B, T *C)
+__global__ void __launch_bounds__(256)
+    k_translate_small(int M, int K, int nc, int l, const T *__restrict__ AT, const T *__restrict__ B, T *__restrict__ C)
+{
+    __shared__ T part[8][32];
+    const int64_t n = blockIdx.x;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int m = blockIdx.y * 32 + lane;
+    const int np = MODE == 0 ? (1 << l) : (1 << (l - 1));
+    const int64_t np3 = (int64_t)np * np * np;
+    const int px = (int)(n % np), py = (int)((n / np) % np), pz = (int)(n / ((int64_t)np * np));
+    const int64_t bcol = MODE == 0 ? n * nc : cell_index(l - 1, px, py, pz) * nc;
+    const int k0 = (int)((int64_t)K * w / 8), k1 = (int)((int64_t)K * (w + 1) / 8);
+    T acc = 0;
+    if (m < M) {
+        for (int k = k0; k < k1; ++k) {
+            int64_t ko = MODE == 0 ? (int64_t)(k / nc) * np3 * nc + (k % nc) : k;
+            acc += AT[(size_t)k * M + m] * B[bcol + ko];
+        }
+    }
+    part[w][lane] = acc;
+    __syncthreads();
+    if (w == 0 && m < M) {
+        T s = 0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) s += part[i][lane];
+        if (MODE == 0) {
+            C[cell_index(l, px, py, pz) * nc + m] = s;
+        } else {
+            C[((int64_t)(m / nc) * np3 + n) * nc + (m % nc)] += s;
+        }
+    }
+}
+
+template <typename T, int MODE>
+fmm_status launch_translate(Plan &P, int l, const T *A, const T *AT, const T *B, T *C)
 {
     const int nc = P.nc;
     const int M = MODE == 0 ? nc : 8 * nc;
     const int K = MODE == 0 ? 8 * nc : nc;
     const int64_t N = MODE == 0 ? ((int64_t)1 << (3 * l)) : ((int64_t)1 << (3 * (l - 1)));
+    if (N <= 4096) {
+        dim3 grid((unsigned)N, (M + 31) / 32);
+        k_translate_small<T, MODE><<<grid, 256, 0, P.stream>>>(M, K, nc, l, AT, B, C);
+        FMM_LAUNCH_CHECK(P);
+        return FMM_OK;
+    }
     if (std::is_same<T, float>::value) {
         constexpr int BM = 64, BN = 128, BK = 8, TM = 4, TN = 8;
         dim3 grid(blocks_for(N, BN), (M + BM - 1) / BM);
@@ -230,11 +279,11 @@ fmm_status build_translation_ops(Plan &P)
 {
     const int nc = P.nc;
     const size_t n = (size_t)8 * nc * nc;
-    if (!P.tab.l2l64) {
-        FMM_CUDA_TRY(cudaMalloc(&P.tab.l2l64, sizeof(double) * n));
-        FMM_CUDA_TRY(cudaMalloc(&P.tab.l2l32, sizeof(float) * n));
-        FMM_CUDA_TRY(cudaMalloc(&P.tab.m2m64, sizeof(double) * n));
-        FMM_CUDA_TRY(cudaMalloc(&P.tab.m2m32, sizeof(float) * n));
+    if (!P.tab.l2l64) {  // each table followed by its transpose
+        FMM_CUDA_TRY(cudaMalloc(&P.tab.l2l64, sizeof(double) * 2 * n));
+        FMM_CUDA_TRY(cudaMalloc(&P.tab.l2l32, sizeof(float) * 2 * n));
+        FMM_CUDA_TRY(cudaMalloc(&P.tab.m2m64, sizeof(double) * 2 * n));
+        FMM_CUDA_TRY(cudaMalloc(&P.tab.m2m32, sizeof(float) * 2 * n));
     }
     k_l2l_ops<<<blocks_for(n, 256), 256, 0, P.stream>>>(P.p, P.tab.Rw64, P.tab.l2l64, P.tab.l2l32);
     FMM_LAUNCH_CHECK(P);
@@ -246,17 +295,23 @@ fmm_status build_translation_ops(Plan &P)
 // M2M into level l (parents) from level l + 1
 fmm_status launch_m2m(Plan &P, int l)
 {
+    const size_t n = (size_t)8 * P.nc * P.nc;
     if (P.precision == FMM_PREC_FP64)
-        return launch_translate<double, 0>(P, l, P.tab.m2m64, (const double *)P.M[l + 1], (double *)P.M[l]);
-    return launch_translate<float, 0>(P, l, P.tab.m2m32, (const float *)P.M[l + 1], (float *)P.M[l]);
+        return launch_translate<double, 0>(P, l, P.tab.m2m64, P.tab.m2m64 + n, (const double *)P.M[l + 1],
+                                           (double *)P.M[l]);
+    return launch_translate<float, 0>(P, l, P.tab.m2m32, P.tab.m2m32 + n, (const float *)P.M[l + 1],
+                                      (float *)P.M[l]);
 }
 
 // L2L from level l - 1 into level l (added to the M2L result)
 fmm_status launch_l2l(Plan &P, int l)
 {
+    const size_t n = (size_t)8 * P.nc * P.nc;
     if (P.precision == FMM_PREC_FP64)
-        return launch_translate<double, 1>(P, l, P.tab.l2l64, (const double *)P.L[l - 1], (double *)P.L[l]);
-    return launch_translate<float, 1>(P, l, P.tab.l2l32, (const float *)P.L[l - 1], (float *)P.L[l]);
+        return launch_translate<double, 1>(P, l, P.tab.l2l64, P.tab.l2l64 + n, (const double *)P.L[l - 1],
+                                           (double *)P.L[l]);
+    return launch_translate<float, 1>(P, l, P.tab.l2l32, P.tab.l2l32 + n, (const float *)P.L[l - 1],
+                                      (float *)P.L[l]);
 }
 
 }  // namespace fmm
