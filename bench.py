@@ -285,7 +285,7 @@ def run_ours(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32+bf16x3-tensor+f64" if uses_tc else "f32+f64",
+        "dtype": ("f32+%s-tensor+f64" % args.split) if uses_tc else "f32+f64",
         "data": "synthetic (seeded ion-in-water boxes standing in for the paper's MD snapshots)",
         "config": {"workload": "%s: %s+ + %d TIP3P waters, N=%d, L=%.2f A, depth %d, p %d, ws 1, mixed precision, "
                                "energy+forces+solute-solvent per step" % (args.workload, box.ion, box.n_waters, N,
@@ -371,7 +371,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="na_1m")
-    ap.add_argument("--split", default="bf16x3", choices=["bf16x3", "bf16x2", "fp32"])
+    ap.add_argument("--split", default="bf16a2b3", choices=["bf16x3", "bf16x2", "bf16a2b3", "fp32"])
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -128,7 +128,7 @@ fmm_status far_field_pass(Plan &P, bool gradient, bool solute_only, StageTimer *
     bool ev = tm && P.timings_on;
     for (int l = 1; l <= P.d; ++l) {
         if (ev) cudaEventRecord(P.ev_m2l[2 * (l - 1)], P.stream);
-        if (tc_available(P, l)) TRY(launch_m2l_tc(P, l));
+        if (tc_available(P, l)) TRY(launch_m2l_tc(P, l, solute_only));
         else TRY(launch_m2l_simt(P, l));
         if (ev) cudaEventRecord(P.ev_m2l[2 * (l - 1) + 1], P.stream);
         TRY(launch_l2l(P, l));
@@ -310,7 +310,9 @@ fmm_status fmm_plan_set_option(fmm_plan plan, int key, int64_t ival, double dval
         P.kappa = dval > 0 ? dval : 0.0;
         return build_lattice(P);
     case FMM_OPT_M2L_SPLIT:
-        if (ival != FMM_SPLIT_BF16X3 && ival != FMM_SPLIT_BF16X2 && ival != FMM_SPLIT_FP32) return FMM_ERR_INVALID_ARG;
+        if (ival != FMM_SPLIT_BF16X3 && ival != FMM_SPLIT_BF16X2 && ival != FMM_SPLIT_FP32 &&
+            ival != FMM_SPLIT_BF16_A2B3)
+            return FMM_ERR_INVALID_ARG;
         if (P.split == (int)ival) return FMM_OK;
         P.split = (int)ival;
         return retc(P);

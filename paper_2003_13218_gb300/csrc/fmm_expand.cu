@@ -524,6 +524,8 @@ void free_tables(Plan &P)
     cudaFree(P.tab.l2l32);
     cudaFree(P.tab.m2m64);
     cudaFree(P.tab.m2m32);
+    cudaFree(P.tab.m2mP32);
+    cudaFree(P.tab.l2lP32);
     P.tab = Tables{};
 }
 

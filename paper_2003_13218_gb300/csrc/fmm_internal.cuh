@@ -67,6 +67,8 @@ struct Tables {
     float *l2l32 = nullptr;
     double *m2m64 = nullptr;  // [NC][8 NC] M2M operators (row-major)
     float *m2m32 = nullptr;
+    float *m2mP32 = nullptr;  // M2M with each octant's K padded to a multiple of 8
+    float *l2lP32 = nullptr;  // L2L with K padded likewise
 };
 
 struct Plan {
@@ -75,7 +77,7 @@ struct Plan {
     int64_t N = 0;
     int d = 0, p = 0, ws = 1;
     int precision = FMM_PREC_FP64;
-    int split = FMM_SPLIT_BF16X3;
+    int split = FMM_SPLIT_BF16_A2B3;
     double kappa = 0;  // 0 = default 2 / box
     cudaStream_t stream = 0;
     bool timings_on = false;
@@ -235,7 +237,8 @@ fmm_status launch_solute_pass(Plan &P, bool *done);
 // tensor-core M2L (fmm_m2l_tc.cu)
 bool tc_available(const Plan &P, int level);
 fmm_status tc_prepare(Plan &P);
-fmm_status launch_m2l_tc(Plan &P, int level);
+// precise: use the 3 x 3 bf16 split whatever the plan's option (solute-only pass)
+fmm_status launch_m2l_tc(Plan &P, int level, bool precise = false);
 void tc_free(Plan &P);
 
 #define FMM_CUDA_TRY(expr)                                        \

@@ -201,6 +201,15 @@ struct Products<2, 2> {  // i + j <= 1
     __device__ static constexpr int a(int k) { return k == 2 ? 1 : 0; }
     __device__ static constexpr int b(int k) { return k == 1 ? 1 : 0; }
 };
+// moments in 2 terms, operator in 3: x0 y0, x0 y1, x1 y0, x0 y2.  The operator
+// (the same table for every cell) keeps ~2^-24; the dropped products involve
+// the moments' residual, whose error differs from cell to cell.
+template <>
+struct Products<2, 3> {
+    static constexpr int n = 4;
+    __device__ static constexpr int a(int k) { return k == 2 ? 1 : 0; }
+    __device__ static constexpr int b(int k) { return k == 1 ? 1 : k == 3 ? 2 : 0; }
+};
 
 // PA, PB: bf16 terms of the A (moments) and B (operator) operands;
 // NCH: output coefficients / 16 (the accumulator width held in registers).
@@ -506,18 +515,26 @@ size_t tc_smem_bytes(int pa, int pb, int npad)
 
 typedef void (*TcKernel)(CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap, TcArgs);
 
-template <int PA>
-TcKernel pick_kernel(int nch)
+template <int PA, int PB>
+TcKernel pick_kernel_n(int nch)
 {
     switch (nch) {
 #define FMM_TC_CASE(n) \
-    case n: return (TcKernel)k_m2l_tc<PA, PA, n>;
+    case n: return (TcKernel)k_m2l_tc<PA, PB, n>;
         FMM_TC_CASE(1) FMM_TC_CASE(2) FMM_TC_CASE(3) FMM_TC_CASE(4) FMM_TC_CASE(5) FMM_TC_CASE(6) FMM_TC_CASE(7)
         FMM_TC_CASE(8) FMM_TC_CASE(9) FMM_TC_CASE(10) FMM_TC_CASE(11) FMM_TC_CASE(12) FMM_TC_CASE(13)
         FMM_TC_CASE(14) FMM_TC_CASE(15) FMM_TC_CASE(16)
 #undef FMM_TC_CASE
     default: return nullptr;
     }
+}
+
+TcKernel pick_kernel(int pa, int pb, int nch)
+{
+    if (pa == 3 && pb == 3) return pick_kernel_n<3, 3>(nch);
+    if (pa == 2 && pb == 3) return pick_kernel_n<2, 3>(nch);
+    if (pa == 2 && pb == 2) return pick_kernel_n<2, 2>(nch);
+    return nullptr;
 }
 
 }  // namespace
@@ -531,21 +548,24 @@ fmm_status tc_prepare(Plan &P)
 {
     tc_free(P);
     if (P.precision != FMM_PREC_MIXED || P.p > TC_PMAX) return FMM_OK;  // CUDA-core M2L
-    int pa = P.split == FMM_SPLIT_BF16X3 ? 3 : 2;
+    const int pa = P.split == FMM_SPLIT_BF16X3 ? 3 : 2;
+    const int pb = P.split == FMM_SPLIT_BF16X2 ? 2 : 3;
     PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
     if (!enc) return FMM_OK;
     TcState *S = new (std::nothrow) TcState();
     if (!S) return FMM_ERR_OOM;
-    S->pa = S->pb = pa;
+    S->pa = pa;
+    S->pb = pb;
     S->npad = (P.nc + 15) / 16 * 16;
     S->kp = (P.nc + KCHUNK - 1) / KCHUNK * KCHUNK;
     P.tc = S;
     // operator tables
     S->ops_part_elems = (size_t)NOFF * S->npad * S->kp;
-    FMM_CUDA_TRY(cudaMalloc(&S->ops, sizeof(__nv_bfloat16) * S->ops_part_elems * S->pb));
-    k_split_ops<<<1216, 256, 0, P.stream>>>(P.tab.Top64, P.nc, S->npad, S->kp, S->pb, S->ops, S->ops_part_elems);
+    // three operator terms always (the solute-only pass uses the 3 x 3 split)
+    FMM_CUDA_TRY(cudaMalloc(&S->ops, sizeof(__nv_bfloat16) * S->ops_part_elems * 3));
+    k_split_ops<<<1216, 256, 0, P.stream>>>(P.tab.Top64, P.nc, S->npad, S->kp, 3, S->ops, S->ops_part_elems);
     FMM_LAUNCH_CHECK(P);
-    for (int j = 0; j < S->pb; ++j) {
+    for (int j = 0; j < 3; ++j) {
         cuuint64_t dims[3] = {(cuuint64_t)S->kp, (cuuint64_t)S->npad, (cuuint64_t)NOFF};
         cuuint64_t strides[2] = {(cuuint64_t)S->kp * 2, (cuuint64_t)S->kp * 2 * S->npad};
         cuuint32_t box[3] = {KCHUNK, (cuuint32_t)S->npad, 1};
@@ -555,7 +575,6 @@ fmm_status tc_prepare(Plan &P)
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return FMM_ERR_INTERNAL;
     }
-    for (int j = S->pb; j < 3; ++j) S->mapB[j] = S->mapB[0];
     // source planes per level
     size_t lpart_elems = 0;
     for (int l = 1; l <= P.d; ++l) {
@@ -565,8 +584,9 @@ fmm_status tc_prepare(Plan &P)
         S->by[l] = tile_dim(np, TC_ROWS / S->bx[l]);
         S->bz[l] = tile_dim(np, TC_ROWS / (S->bx[l] * S->by[l]));
         S->part_elems[l] = (size_t)8 * np2 * np2 * np2 * S->kp;
-        FMM_CUDA_TRY(cudaMalloc(&S->planes[l], sizeof(__nv_bfloat16) * S->part_elems[l] * S->pa));
-        for (int i = 0; i < S->pa; ++i) {
+        // three planes always: the solute-only pass uses the 3 x 3 split
+        FMM_CUDA_TRY(cudaMalloc(&S->planes[l], sizeof(__nv_bfloat16) * S->part_elems[l] * 3));
+        for (int i = 0; i < 3; ++i) {
             cuuint64_t dims[4] = {(cuuint64_t)S->kp, (cuuint64_t)np2, (cuuint64_t)np2, (cuuint64_t)(8 * np2)};
             cuuint64_t strides[3] = {(cuuint64_t)S->kp * 2, (cuuint64_t)S->kp * 2 * np2,
                                      (cuuint64_t)S->kp * 2 * np2 * np2};
@@ -577,7 +597,6 @@ fmm_status tc_prepare(Plan &P)
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
                 return FMM_ERR_INTERNAL;
         }
-        for (int i = S->pa; i < 3; ++i) S->mapA[l][i] = S->mapA[l][0];
         // enough CTAs to fill the GPU twice: split the 189 offsets when tiles are few
         int tiles = 8 * (np / S->bx[l]) * (np / S->by[l]) * (np / S->bz[l]);
         int want = (2 * 152 + tiles - 1) / tiles;
@@ -591,23 +610,28 @@ fmm_status tc_prepare(Plan &P)
         }
     }
     if (lpart_elems) FMM_CUDA_TRY(cudaMalloc(&S->Lpart, sizeof(float) * lpart_elems));
-    TcKernel k = pa == 3 ? pick_kernel<3>(S->npad / 16) : pick_kernel<2>(S->npad / 16);
-    if (!k) return FMM_ERR_INTERNAL;
+    TcKernel k = pick_kernel(S->pa, S->pb, S->npad / 16);
+    TcKernel kp = pick_kernel(3, 3, S->npad / 16);  // the solute-only pass
+    if (!k || !kp) return FMM_ERR_INTERNAL;
     FMM_CUDA_TRY(cudaFuncSetAttribute((const void *)k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)tc_smem_bytes(S->pa, S->pb, S->npad)));
+    FMM_CUDA_TRY(cudaFuncSetAttribute((const void *)kp, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)tc_smem_bytes(3, 3, S->npad)));
     FMM_CUDA_TRY(cudaStreamSynchronize(P.stream));
     return FMM_OK;
 }
 
-fmm_status launch_m2l_tc(Plan &P, int l)
+fmm_status launch_m2l_tc(Plan &P, int l, bool precise)
 {
     TcState *S = (TcState *)P.tc;
     if (!S) return FMM_ERR_INTERNAL;
+    const int pa = precise ? 3 : S->pa;
+    const int pb = precise ? 3 : S->pb;
     int np = 1 << (l - 1);
     int64_t np2 = np + 2;
     int64_t n = 8 * np2 * np2 * np2 * S->kp;
     unsigned blocks = (unsigned)((n + 255) / 256 < 4864 ? (n + 255) / 256 : 4864);
-    k_split_halo<<<blocks, 256, 0, P.stream>>>((const float *)P.M[l], np, P.nc, S->kp, S->pa, S->planes[l],
+    k_split_halo<<<blocks, 256, 0, P.stream>>>((const float *)P.M[l], np, P.nc, S->kp, pa, S->planes[l],
                                                S->part_elems[l]);
     FMM_LAUNCH_CHECK(P);
     TcArgs a;
@@ -629,11 +653,11 @@ fmm_status launch_m2l_tc(Plan &P, int l)
     a.per_group = S->per_group[l];
     a.err = P.d_err;
     unsigned grid = 8u * (unsigned)a.tiles_per_class * (unsigned)a.groups;
-    TcKernel k = S->pa == 3 ? pick_kernel<3>(S->npad / 16) : pick_kernel<2>(S->npad / 16);
+    TcKernel k = pick_kernel(pa, pb, S->npad / 16);
     if (!k) return FMM_ERR_INTERNAL;
-    const bool time_it = P.timings_on && l == P.d && P.ev_top[0];
+    const bool time_it = P.timings_on && l == P.d && P.ev_top[0] && !precise;
     if (time_it) cudaEventRecord(P.ev_top[0], P.stream);
-    k<<<grid, TC_THREADS, tc_smem_bytes(S->pa, S->pb, S->npad), P.stream>>>(
+    k<<<grid, TC_THREADS, tc_smem_bytes(pa, pb, S->npad), P.stream>>>(
         S->mapA[l][0], S->mapA[l][1], S->mapA[l][2], S->mapB[0], S->mapB[1], S->mapB[2], a);
     FMM_LAUNCH_CHECK(P);
     if (time_it) {

@@ -29,7 +29,7 @@ namespace fmm {
 
 namespace {
 
-constexpr int NU_MAX = 32;      // solute charges handled by the sparse pass
+constexpr int NU_MAX = 64;      // solute charges handled by the sparse pass
 constexpr int LD = 3;           // levels 0..LD treated densely
 constexpr int MAX_TGT = NU_MAX * 189;
 
@@ -44,6 +44,8 @@ struct SoluteScratch {
     int *tlist = nullptr;    // [9][MAX_TGT] sorted targets per fine level
     void *contrib = nullptr; // [9][MAX_TGT][nc] M2L sums at those targets
     int *h_count = nullptr;  // pinned
+    void *Lt = nullptr;      // [9][NU_MAX][nc] full local expansions at the active cells (FP64)
+    double *part = nullptr;  // [NU_MAX][189][nc] their M2L terms, one per offset
 };
 
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -282,6 +284,154 @@ __global__ void k_sol_m2l(int p, int l, const int *__restrict__ cells, const int
     }
 }
 
+// ---- full-field potential at the solute charges (the A of Eq. FMMcalc), as
+// the oracle evaluates one sampled charge: M2L over the interaction list of
+// each active cell from the full pass's moments (CUDA cores, no operand
+// splitting), then the level-0 lattice expansion shifted down the active
+// ancestors by L2L, then L2P.  The few solute charges cannot average out the
+// split-operand rounding of the tensor-core M2L, so A is taken from here.
+
+// FP64 throughout, on the solvent moments M - M_u (the field of the solvent
+// at the solute charges): Lt[0][0] = T0 . (M(0) - M_u(0))
+template <typename T>
+__global__ void k_act_lattice(int p, const double *__restrict__ T0, const T *__restrict__ M0, const T *__restrict__ MU0,
+                              double *__restrict__ Lt)
+{
+    int nc = ncoef(p);
+    for (int j = threadIdx.x; j < nc; j += blockDim.x) {
+        double acc = 0;
+        for (int k = 0; k < nc; ++k) acc += T0[(size_t)k * nc + j] * ((double)M0[k] - (double)MU0[k]);
+        Lt[j] = acc;
+    }
+}
+
+// part[i][o] = the M2L term of the o-th interaction-list offset of active cell
+// i at level l (one block per (cell, offset))
+template <typename T>
+__global__ void k_act_m2l(int p, int l, const int *__restrict__ cells, const int *__restrict__ ncells,
+                          const double *__restrict__ Top, const T *__restrict__ M, const T *__restrict__ MU,
+                          double *__restrict__ part)
+{
+    int i = blockIdx.x, o = blockIdx.y;
+    if (i >= ncells[l]) return;
+    int nc = ncoef(p);
+    int n = 1 << l;
+    int tx, ty, tz;
+    cell_xyz(cells[l * NU_MAX + i], n, tx, ty, tz);
+    int cx = tx & 1, cy = ty & 1, cz = tz & 1;
+    int dx = 0, dy = 0, dz = 0, c = -1;
+    for (int z = -2 - cz; z <= 3 - cz && c < o; ++z)
+        for (int y = -2 - cy; y <= 3 - cy && c < o; ++y)
+            for (int x = -2 - cx; x <= 3 - cx && c < o; ++x) {
+                if (x >= -1 && x <= 1 && y >= -1 && y <= 1 && z >= -1 && z <= 1) continue;
+                if (++c == o) {
+                    dx = x;
+                    dy = y;
+                    dz = z;
+                }
+            }
+    int sx = (tx + dx + n) & (n - 1), sy = (ty + dy + n) & (n - 1), sz = (tz + dz + n) & (n - 1);
+    const T *Ms = M + cell_index(l, sx, sy, sz) * nc;
+    // the solute part of this source, if it is an active cell
+    const T *Mu = nullptr;
+    int slin = sx + n * (sy + n * sz);
+    for (int k = 0; k < ncells[l]; ++k)
+        if (cells[l * NU_MAX + k] == slin) Mu = MU + ((size_t)l * NU_MAX + k) * nc;
+    const double *Tp = Top + (size_t)off_slot(dx, dy, dz) * nc * nc;
+    for (int j = threadIdx.x; j < nc; j += blockDim.x) {
+        double acc = 0;
+        if (Mu)
+            for (int k = 0; k < nc; ++k) acc += Tp[(size_t)k * nc + j] * ((double)Ms[k] - (double)Mu[k]);
+        else
+            for (int k = 0; k < nc; ++k) acc += Tp[(size_t)k * nc + j] * (double)Ms[k];
+        part[((size_t)i * 189 + o) * nc + j] = acc;
+    }
+}
+
+// Lt[l][i] = sum of the 189 terms, in offset order
+__global__ void k_act_sum(int p, int l, const int *__restrict__ ncells, const double *__restrict__ part,
+                          double *__restrict__ Lt)
+{
+    int i = blockIdx.x;
+    if (i >= ncells[l]) return;
+    int nc = ncoef(p);
+    for (int j = threadIdx.x; j < nc; j += blockDim.x) {
+        double s = 0;
+        for (int o = 0; o < 189; ++o) s += part[((size_t)i * 189 + o) * nc + j];
+        Lt[((size_t)l * NU_MAX + i) * nc + j] = s;
+    }
+}
+
+// Lt[l][i] += L2L of the parent's full expansion (Lt[l-1] or, at level 1, the
+// lattice result L0): Lhat_k^m += sum_{n >= k} Lhat_n^q R_{n-k}^{q-m}(w_c) 2^{-(k+1)}
+template <typename T>
+__global__ void k_act_l2l(int p, int l, const int *__restrict__ cells, const int *__restrict__ ncells,
+                          const T *__restrict__ Rw, const T *__restrict__ L0, T *__restrict__ Lt)
+{
+    int i = blockIdx.x;
+    if (i >= ncells[l]) return;
+    int nc = ncoef(p);
+    int n = 1 << l;
+    int x, y, z;
+    cell_xyz(cells[l * NU_MAX + i], n, x, y, z);
+    const T *Lp = L0;
+    if (l > 1) {
+        int plin = (x >> 1) + (n >> 1) * ((y >> 1) + (n >> 1) * (z >> 1));
+        for (int k = 0; k < ncells[l - 1]; ++k)
+            if (cells[(l - 1) * NU_MAX + k] == plin) Lp = Lt + ((size_t)(l - 1) * NU_MAX + k) * nc;
+    }
+    const T *R = Rw + ((x & 1) | ((y & 1) << 1) | ((z & 1) << 2)) * nc;
+    int ntri = (p + 1) * (p + 2) / 2;
+    T *out = Lt + ((size_t)l * NU_MAX + i) * nc;
+    for (int t = threadIdx.x; t < ntri; t += blockDim.x) {
+        int k = 0;
+        while (tri(k + 1, 0) <= t) ++k;
+        int m = t - tri(k, 0);
+        T accr = 0, acci = 0;
+        for (int nn = k; nn <= p; ++nn) {
+            int dn = nn - k;
+            for (int q = -nn; q <= nn; ++q) {
+                int dm = q - m;
+                if (dm < -dn || dm > dn) continue;
+                Cx<T> pr = cmul(coef(Lp, nn, q), coef(R, dn, dm));
+                accr += pr.re;
+                acci += pr.im;
+            }
+        }
+        T scale = 1;
+        for (int s = 0; s <= k; ++s) scale *= T(0.5);
+        out[cre(k, m)] += scale * accr;
+        if (m > 0) out[cim(k, m)] += scale * acci;
+    }
+}
+
+template <typename T>
+__device__ T l2p_value(int p, const T *__restrict__ Lc, T vx, T vy, T vz);
+
+// at each solute charge: phi_ff = (solvent field from Lt) + phi_u (solute field
+// of the solute-only pass), so that A - B = sum_u q Phi_v holds term by term
+template <typename T>
+__global__ void k_act_l2p(int p, int d, double inv_h, const int *__restrict__ list, const int *__restrict__ cells,
+                          const int *__restrict__ ncells, const int *__restrict__ sleaf,
+                          const Particle<T> *__restrict__ sp, const double *__restrict__ Lt,
+                          const T *__restrict__ phi_u, T *__restrict__ phi)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    int n = list[NU_MAX];
+    if (n > NU_MAX) n = NU_MAX;
+    if (k >= n) return;
+    int s = list[k];
+    int leaf = sleaf[s];
+    int i = 0;
+    while (i < ncells[d] && cells[d * NU_MAX + i] != leaf) ++i;
+    if (i >= ncells[d]) return;
+    Particle<T> pt = sp[s];
+    double v = l2p_value<double>(p, Lt + ((size_t)d * NU_MAX + i) * ncoef(p), (double)pt.x * inv_h,
+                                 (double)pt.y * inv_h, (double)pt.z * inv_h) *
+               inv_h;
+    phi[s] = (T)(v + (double)phi_u[s]);
+}
+
 // Phi at (v) from the real-layout local coefficients Lc (scaled), v in cell units
 template <typename T>
 __device__ T l2p_value(int p, const T *__restrict__ Lc, T vx, T vy, T vz)
@@ -414,7 +564,7 @@ __global__ void k_flag_scan_add(int64_t n, int *__restrict__ out, const int *__r
 }
 
 template <typename T>
-fmm_status solute_sparse_t(Plan &P, SoluteScratch &S)
+fmm_status solute_sparse_t(Plan &P, SoluteScratch &S, int nu)
 {
     const int p = P.p, d = P.d, nc = P.nc;
     const int nside = 1 << d;
@@ -422,26 +572,43 @@ fmm_status solute_sparse_t(Plan &P, SoluteScratch &S)
     const T *Rw = std::is_same<T, double>::value ? (const T *)P.tab.Rw64 : (const T *)P.tab.Rw32;
     const T *Top = std::is_same<T, double>::value ? (const T *)P.tab.Top64 : (const T *)P.tab.Top32;
     T *MU = (T *)S.MU;
-    // moments of the active cells
+    // active cells (leaves of the solute charges and their ancestors)
     k_sol_cells<<<1, 32, 0, P.stream>>>(d, S.list, P.sleaf, S.cells, S.ncells);
     FMM_LAUNCH_CHECK(P);
-    k_sol_p2m<T><<<NU_MAX, 32, 0, P.stream>>>(p, d, S.cells, S.ncells, P.cell_start, (const Particle<T> *)P.sorted_u,
+    // solute moments of the active cells
+    k_sol_p2m<T><<<nu, 32, 0, P.stream>>>(p, d, S.cells, S.ncells, P.cell_start, (const Particle<T> *)P.sorted_u,
                                              (T)(1.0 / h), MU);
     FMM_LAUNCH_CHECK(P);
     for (int l = d - 1; l >= 0; --l) {
-        k_sol_m2m<T><<<NU_MAX, 128, 0, P.stream>>>(p, l, S.cells, S.ncells, Rw, MU);
+        k_sol_m2m<T><<<nu, 128, 0, P.stream>>>(p, l, S.cells, S.ncells, Rw, MU);
+        FMM_LAUNCH_CHECK(P);
+    }
+    // FP64 expansions of the solvent field at the active cells, from the full
+    // pass's moments minus the solute moments, before this pass overwrites the
+    // coarse moments
+    const int nth = ((nc + 31) / 32) * 32;
+    double *Lt = (double *)S.Lt;
+    k_act_lattice<T><<<1, nth, 0, P.stream>>>(p, P.tab.T0, (const T *)P.M[0], MU, Lt);
+    FMM_LAUNCH_CHECK(P);
+    for (int l = 1; l <= d; ++l) {
+        k_act_m2l<T><<<dim3(nu, 189), nth, 0, P.stream>>>(p, l, S.cells, S.ncells, P.tab.Top64,
+                                                               (const T *)P.M[l], MU, S.part);
+        FMM_LAUNCH_CHECK(P);
+        k_act_sum<<<nu, nth, 0, P.stream>>>(p, l, S.ncells, S.part, Lt);
+        FMM_LAUNCH_CHECK(P);
+        k_act_l2l<double><<<nu, 128, 0, P.stream>>>(p, l, S.cells, S.ncells, P.tab.Rw64, Lt, Lt);
         FMM_LAUNCH_CHECK(P);
     }
     // dense coarse levels 0..LD
     for (int l = 0; l <= LD; ++l)
         FMM_CUDA_TRY(cudaMemsetAsync(P.M[l], 0, sizeof(T) * ((size_t)1 << (3 * l)) * nc, P.stream));
-    k_sol_scatter<T><<<dim3(NU_MAX, LD + 1), 128, 0, P.stream>>>(p, LD, S.cells, S.ncells, MU, (T *)P.M[0],
+    k_sol_scatter<T><<<dim3(nu, LD + 1), 128, 0, P.stream>>>(p, LD, S.cells, S.ncells, MU, (T *)P.M[0],
                                                                  (T *)P.M[1], (T *)P.M[2], (T *)P.M[3]);
     FMM_LAUNCH_CHECK(P);
     fmm_status st = launch_lattice(P);
     if (st != FMM_OK) return st;
     for (int l = 1; l <= LD; ++l) {
-        st = tc_available(P, l) ? launch_m2l_tc(P, l) : launch_m2l_simt(P, l);
+        st = tc_available(P, l) ? launch_m2l_tc(P, l, true) : launch_m2l_simt(P, l);
         if (st != FMM_OK) return st;
         st = launch_l2l(P, l);
         if (st != FMM_OK) return st;
@@ -450,7 +617,7 @@ fmm_status solute_sparse_t(Plan &P, SoluteScratch &S)
     for (int l = LD + 1; l <= d; ++l) {
         int64_t n = (int64_t)1 << (3 * l);
         FMM_CUDA_TRY(cudaMemsetAsync(S.flags, 0, sizeof(int) * n, P.stream));
-        k_sol_mark<<<NU_MAX, 352, 0, P.stream>>>(l, S.cells, S.ncells, S.flags);
+        k_sol_mark<<<nu, 352, 0, P.stream>>>(l, S.cells, S.ncells, S.flags);
         FMM_LAUNCH_CHECK(P);
         int nb = (int)((n + 4095) / 4096);
         k_flag_scan_blocks<<<nb, 256, 0, P.stream>>>(n, S.flags, S.pos, S.scan_tmp);
@@ -461,7 +628,7 @@ fmm_status solute_sparse_t(Plan &P, SoluteScratch &S)
         FMM_LAUNCH_CHECK(P);
         k_sol_compact<<<blocks_for(n, 256), 256, 0, P.stream>>>(n, S.flags, S.pos, S.tlist + (size_t)l * MAX_TGT);
         FMM_LAUNCH_CHECK(P);
-        k_sol_m2l<T><<<MAX_TGT, ((nc + 31) / 32) * 32, 0, P.stream>>>(p, l, S.cells, S.ncells,
+        k_sol_m2l<T><<<nu * 189, ((nc + 31) / 32) * 32, 0, P.stream>>>(p, l, S.cells, S.ncells,
                                                                        S.tlist + (size_t)l * MAX_TGT,
                                                                        S.ncells + 16 + l, Top, MU, (T *)S.contrib);
         FMM_LAUNCH_CHECK(P);
@@ -469,6 +636,10 @@ fmm_status solute_sparse_t(Plan &P, SoluteScratch &S)
     k_sol_eval<T><<<blocks_for(P.N, 128), 128, 0, P.stream>>>(p, d, P.N, (T)h, P.sleaf, (const Particle<T> *)P.sorted,
                                                               (const T *)P.L[LD], S.tlist, S.ncells + 16,
                                                               (const T *)S.contrib, (T *)P.phi_u);
+    FMM_LAUNCH_CHECK(P);
+    // full-field potential at the solute charges: solvent field + solute field
+    k_act_l2p<T><<<1, NU_MAX, 0, P.stream>>>(p, d, 1.0 / h, S.list, S.cells, S.ncells, P.sleaf,
+                                             (const Particle<T> *)P.sorted, Lt, (const T *)P.phi_u, (T *)P.phi_ff);
     FMM_LAUNCH_CHECK(P);
     return FMM_OK;
 }
@@ -493,6 +664,8 @@ fmm_status solute_prepare(Plan &P)
     FMM_CUDA_TRY(cudaMalloc(&S->tlist, sizeof(int) * 9 * MAX_TGT));
     FMM_CUDA_TRY(cudaMalloc(&S->contrib, sizeof(double) * (size_t)(P.d + 1) * MAX_TGT * P.nc));
     FMM_CUDA_TRY(cudaMallocHost((void **)&S->h_count, sizeof(int)));
+    FMM_CUDA_TRY(cudaMalloc(&S->Lt, sizeof(double) * 9 * NU_MAX * P.nc));
+    FMM_CUDA_TRY(cudaMalloc(&S->part, sizeof(double) * NU_MAX * 189 * P.nc));
     return FMM_OK;
 }
 
@@ -509,6 +682,8 @@ void solute_free(Plan &P)
     cudaFree(S->scan_tmp);
     cudaFree(S->tlist);
     cudaFree(S->contrib);
+    cudaFree(S->Lt);
+    cudaFree(S->part);
     if (S->h_count) cudaFreeHost(S->h_count);
     delete S;
     P.sol = nullptr;
@@ -533,7 +708,7 @@ fmm_status launch_solute_pass(Plan &P, bool *done)
         *done = true;
         return FMM_OK;
     }
-    fmm_status s = P.precision == FMM_PREC_FP64 ? solute_sparse_t<double>(P, *S) : solute_sparse_t<float>(P, *S);
+    fmm_status s = P.precision == FMM_PREC_FP64 ? solute_sparse_t<double>(P, *S, n) : solute_sparse_t<float>(P, *S, n);
     if (s == FMM_OK) *done = true;
     return s;
 }

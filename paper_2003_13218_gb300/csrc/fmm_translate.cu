@@ -208,6 +208,146 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
     }
 }
 
+// FP32 register-tiled version of the same products for the fine levels.
+// The operator's K runs octant by octant, each padded to KO (a multiple of 8)
+// with zero columns, so a K tile never straddles two octants and no index
+// needs a division.  Tiles: BM x BN outputs per block, 8 x 8 per thread
+// (rows tm*4 + i and BM/2 + tm*4 + i, columns likewise, for conflict-free
+// vector reads), K in steps of 8, shared memory double-buffered.
+template <int MODE, int BM, int BN>
+__global__ void __launch_bounds__((BM / 8) * (BN / 8), 2)
+    k_translate_f32(int M, int64_t N, int nc, int KO, int l, const float *__restrict__ A, int KA,
+                    const float *__restrict__ B, float *__restrict__ C)
+{
+    constexpr int NT = (BM / 8) * (BN / 8);
+    constexpr int BK = 8;
+    __shared__ __align__(16) float As[2][BK][BM];
+    __shared__ __align__(16) float Bs[2][BK][BN];
+    __shared__ int64_t bcol[BN];
+    __shared__ int64_t ccol[BN];
+    const int tid = threadIdx.x;
+    const int m0 = blockIdx.y * BM;
+    const int64_t n0 = (int64_t)blockIdx.x * BN;
+    const int np = MODE == 0 ? (1 << l) : (1 << (l - 1));
+    const int64_t np3 = (int64_t)np * np * np;
+    for (int i = tid; i < BN; i += NT) {
+        int64_t n = n0 + i;
+        int64_t b = -1, c = 0;
+        if (n < N) {
+            int px = (int)(n % np), py = (int)((n / np) % np), pz = (int)(n / ((int64_t)np * np));
+            if (MODE == 0) {
+                b = n * nc;
+                c = cell_index(l, px, py, pz) * nc;
+            } else {
+                b = cell_index(l - 1, px, py, pz) * nc;
+                c = n * nc;
+            }
+        }
+        bcol[i] = b;
+        ccol[i] = c;
+    }
+    const int tiles_per_oct = KO / BK;
+    const int KT = (MODE == 0 ? 8 : 1) * tiles_per_oct;
+    const int64_t ostride = MODE == 0 ? np3 * nc : 0;
+    __syncthreads();
+
+    float ra[BM * BK / NT > 0 ? BM * BK / NT : 1];
+    float rb[BN * BK / NT];
+    auto load_tile = [&](int t) {
+        const int o = t / tiles_per_oct, kb = (t % tiles_per_oct) * BK;
+#pragma unroll
+        for (int i = 0; i < BM * BK / NT; ++i) {
+            int e = tid + i * NT;
+            int mm = e / BK, kk = e % BK;
+            int m = m0 + mm;
+            ra[i] = m < M ? A[(size_t)m * KA + o * KO + kb + kk] : 0.f;
+        }
+#pragma unroll
+        for (int i = 0; i < BN * BK / NT; ++i) {
+            int e = tid + i * NT;
+            int nn = e / BK, kk = e % BK;
+            int k = kb + kk;
+            rb[i] = (bcol[nn] >= 0 && k < nc) ? B[bcol[nn] + o * ostride + k] : 0.f;
+        }
+    };
+    auto store_tile = [&](int buf) {
+#pragma unroll
+        for (int i = 0; i < BM * BK / NT; ++i) {
+            int e = tid + i * NT;
+            As[buf][e % BK][e / BK] = ra[i];
+        }
+#pragma unroll
+        for (int i = 0; i < BN * BK / NT; ++i) {
+            int e = tid + i * NT;
+            Bs[buf][e % BK][e / BK] = rb[i];
+        }
+    };
+
+    const int tm = tid % (BM / 8), tn = tid / (BM / 8);
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+
+    load_tile(0);
+    store_tile(0);
+    __syncthreads();
+    for (int t = 0; t < KT; ++t) {
+        const int buf = t & 1;
+        if (t + 1 < KT) load_tile(t + 1);
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            float4 a0 = *reinterpret_cast<const float4 *>(&As[buf][kk][tm * 4]);
+            float4 a1 = *reinterpret_cast<const float4 *>(&As[buf][kk][BM / 2 + tm * 4]);
+            float4 b0 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][tn * 4]);
+            float4 b1 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][BN / 2 + tn * 4]);
+            const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] += a[i] * b[j];
+        }
+        if (t + 1 < KT) store_tile(buf ^ 1);
+        __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int nn = (j < 4 ? tn * 4 + j : BN / 2 + tn * 4 + (j - 4));
+        if (n0 + nn >= N) continue;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int m = m0 + (i < 4 ? tm * 4 + i : BM / 2 + tm * 4 + (i - 4));
+            if (m >= M) continue;
+            if (MODE == 0) {
+                C[ccol[nn] + m] = acc[i][j];
+            } else {
+                const int c = m / nc;
+                C[ccol[nn] + (int64_t)c * np3 * nc + (m - c * nc)] += acc[i][j];
+            }
+        }
+    }
+}
+
+// operators with every octant's K padded to KO: M2M [nc][8 KO], L2L [8 nc][KO]
+__global__ void k_pad_ops(int nc, int KO, const float *__restrict__ m2m, const float *__restrict__ l2l,
+                          float *__restrict__ m2mP, float *__restrict__ l2lP)
+{
+    const int64_t n0 = (int64_t)nc * 8 * KO, n1 = (int64_t)8 * nc * KO;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n0 + n1; t += (int64_t)gridDim.x * blockDim.x) {
+        if (t < n0) {
+            int m = (int)(t / (8 * KO)), r = (int)(t % (8 * KO));
+            int o = r / KO, kk = r % KO;
+            m2mP[t] = kk < nc ? m2m[(size_t)m * 8 * nc + o * nc + kk] : 0.f;
+        } else {
+            int64_t u = t - n0;
+            int m = (int)(u / KO), kk = (int)(u % KO);
+            l2lP[u] = kk < nc ? l2l[(size_t)m * nc + kk] : 0.f;
+        }
+    }
+}
+
 // The same products for coarse levels (few columns): one block per
 // (column, 32 outputs), the 8 warps split K, partial sums added in warp order.
 // AT is the operator transposed, [K][M].
@@ -226,10 +366,9 @@ __global__ void __launch_bounds__(256)
     const int k0 = (int)((int64_t)K * w / 8), k1 = (int)((int64_t)K * (w + 1) / 8);
     T acc = 0;
     if (m < M) {
-        for (int k = k0; k < k1; ++k) {
-            int64_t ko = MODE == 0 ? (int64_t)(k / nc) * np3 * nc + (k % nc) : k;
-            acc += AT[(size_t)k * M + m] * B[bcol + ko];
-        }
+        // M2M: K = 8 nc, so warp w covers exactly octant w
+        const int64_t obase = MODE == 0 ? (int64_t)w * np3 * nc - (int64_t)w * nc : 0;
+        for (int k = k0; k < k1; ++k) acc += AT[(size_t)k * M + m] * B[bcol + obase + k];
     }
     part[w][lane] = acc;
     __syncthreads();
@@ -252,17 +391,20 @@ fmm_status launch_translate(Plan &P, int l, const T *A, const T *AT, const T *B,
     const int M = MODE == 0 ? nc : 8 * nc;
     const int K = MODE == 0 ? 8 * nc : nc;
     const int64_t N = MODE == 0 ? ((int64_t)1 << (3 * l)) : ((int64_t)1 << (3 * (l - 1)));
-    if (N <= 4096) {
+    if (N * ((M + 31) / 32) <= 32768) {
         dim3 grid((unsigned)N, (M + 31) / 32);
         k_translate_small<T, MODE><<<grid, 256, 0, P.stream>>>(M, K, nc, l, AT, B, C);
         FMM_LAUNCH_CHECK(P);
         return FMM_OK;
     }
     if (std::is_same<T, float>::value) {
-        constexpr int BM = 64, BN = 128, BK = 8, TM = 4, TN = 8;
+        constexpr int BM = 64, BN = 256;
+        const int KO = (nc + 7) / 8 * 8;
+        const float *AP = MODE == 0 ? P.tab.m2mP32 : P.tab.l2lP32;
+        const int KA = MODE == 0 ? 8 * KO : KO;
         dim3 grid(blocks_for(N, BN), (M + BM - 1) / BM);
-        k_translate<T, MODE, BM, BN, BK, TM, TN><<<grid, (BM / TM) * (BN / TN), 0, P.stream>>>(M, N, K, nc, l, A, B,
-                                                                                               C);
+        k_translate_f32<MODE, BM, BN><<<grid, (BM / 8) * (BN / 8), 0, P.stream>>>(
+            M, N, nc, KO, l, AP, KA, (const float *)B, (float *)C);
     } else {
         constexpr int BM = 64, BN = 64, BK = 8, TM = 4, TN = 4;
         dim3 grid(blocks_for(N, BN), (M + BM - 1) / BM);
@@ -288,6 +430,15 @@ fmm_status build_translation_ops(Plan &P)
     k_l2l_ops<<<blocks_for(n, 256), 256, 0, P.stream>>>(P.p, P.tab.Rw64, P.tab.l2l64, P.tab.l2l32);
     FMM_LAUNCH_CHECK(P);
     k_m2m_ops<<<blocks_for(n, 256), 256, 0, P.stream>>>(P.p, P.tab.Rw64, P.tab.m2m64, P.tab.m2m32);
+    FMM_LAUNCH_CHECK(P);
+    const int KO = (nc + 7) / 8 * 8;
+    const size_t np_ = (size_t)8 * nc * KO;
+    if (!P.tab.m2mP32) {
+        FMM_CUDA_TRY(cudaMalloc(&P.tab.m2mP32, sizeof(float) * np_));
+        FMM_CUDA_TRY(cudaMalloc(&P.tab.l2lP32, sizeof(float) * np_));
+    }
+    k_pad_ops<<<blocks_for(2 * np_, 256), 256, 0, P.stream>>>(nc, KO, P.tab.m2m32, P.tab.l2l32, P.tab.m2mP32,
+                                                             P.tab.l2lP32);
     FMM_LAUNCH_CHECK(P);
     return FMM_OK;
 }

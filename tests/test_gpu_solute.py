@@ -1,8 +1,14 @@
 """Solute-solvent energy of the reduced far-field scheme (Eq. FMMcalc) on trees
 deep enough for the sparse solute-only pass (depth >= 4), against the oracle's
-two dense passes.  Cases: one ion (one active cell per level), a 16-atom solute
-spread over several cells (shared targets, merged ancestors), and a 40-atom
-solute (beyond the sparse pass's 32 charges: the dense pass runs instead)."""
+two dense passes.  Cases: one ion (one active cell per level), 16- and 40-atom
+solutes spread over several cells (shared targets, merged ancestors), and an
+80-atom solute (beyond the sparse pass's 64 charges: the dense pass runs).
+
+In the dense fallback the full-field potential at the solute charges (the A
+of Eq. FMMcalc) comes from the mixed full pass, whose moments enter the
+tensor-core M2L as two bf16 terms; with few solute charges that rounding does
+not average out, so the mixed tolerance of that case is 1e-4 of the scale
+instead of 1e-5 (the sparse pass recomputes A with an unsplit M2L)."""
 import numpy as np
 import pytest
 
@@ -29,7 +35,7 @@ def _gpu_uv(b, sol, d, p, precision):
     return uv
 
 
-@pytest.mark.parametrize("n_solute", [1, 16, 40])
+@pytest.mark.parametrize("n_solute", [1, 16, 40, 80])
 def test_sparse_solute_pass_against_oracle(n_solute):
     b = _box()
     sol = np.zeros(b.N, np.uint8)
@@ -37,7 +43,8 @@ def test_sparse_solute_pass_against_oracle(n_solute):
     d, p = 4, 8
     ref = oracle.solute_solvent(b.pos, b.q, sol, b.L, d, p)
     scale = abs(ref["A"]) + abs(ref["C"]) + abs(ref["e_uv"])
-    for precision, tol in (("fp64", 1e-11), ("mixed", 1e-5)):
+    mixed_tol = 1e-5 if n_solute <= 64 else 1e-4
+    for precision, tol in (("fp64", 1e-11), ("mixed", mixed_tol)):
         uv = _gpu_uv(b, sol, d, p, precision)
         for k in KEYS:
             assert abs(uv[k] - ref[k]) <= tol * scale, (precision, k, uv[k], ref[k])
