@@ -371,7 +371,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="na_1m")
-    ap.add_argument("--split", default="bf16a2b3", choices=["bf16x3", "bf16x2", "bf16a2b3", "fp32"])
+    ap.add_argument("--split", default="fp16x2", choices=["fp16x2", "bf16x3", "bf16x2", "bf16a2b3", "fp32"])
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

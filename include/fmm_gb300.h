@@ -98,7 +98,7 @@ enum {
     FMM_OPT_PRECISION = 2, /* ival: FMM_PREC_FP64 (default) or FMM_PREC_MIXED */
     FMM_OPT_KAPPA = 3,     /* dval: splitting parameter kappa of Eq. 12 and Eq. 6 in 1/A;
                               <= 0 restores the default kappa = 2 / b */
-    FMM_OPT_M2L_SPLIT = 4, /* ival: mixed-precision M2L operand split, FMM_SPLIT_* (default BF16_A2B3) */
+    FMM_OPT_M2L_SPLIT = 4, /* ival: mixed-precision M2L operand split, FMM_SPLIT_* (default FP16X2) */
     FMM_OPT_STREAM = 5,    /* ival: cudaStream_t cast to int64 (0 = legacy default stream) */
     FMM_OPT_TIMINGS = 6    /* ival: 1 records per-stage CUDA events (adds event overhead) */
 };
@@ -107,7 +107,9 @@ enum {
     FMM_SPLIT_BF16X3 = 0,    /* tensor-core M2L: both operands as 3 bf16 terms, 6 products */
     FMM_SPLIT_BF16X2 = 1,    /* tensor-core M2L: 2 bf16 terms, 3 products */
     FMM_SPLIT_FP32 = 2,      /* FP32 CUDA-core M2L (no tensor cores) */
-    FMM_SPLIT_BF16_A2B3 = 3  /* tensor-core M2L: moments in 2 bf16 terms, operators in 3, 4 products */
+    FMM_SPLIT_BF16_A2B3 = 3, /* tensor-core M2L: moments in 2 bf16 terms, operators in 3, 4 products */
+    FMM_SPLIT_FP16X2 = 4     /* tensor-core M2L: both operands balanced by sqrt((n+m)!(n-m)!) and a power of
+                                two, then split into 2 fp16 terms, 3 products (~2^-22 relative) */
 };
 
 /*

@@ -311,7 +311,7 @@ fmm_status fmm_plan_set_option(fmm_plan plan, int key, int64_t ival, double dval
         return build_lattice(P);
     case FMM_OPT_M2L_SPLIT:
         if (ival != FMM_SPLIT_BF16X3 && ival != FMM_SPLIT_BF16X2 && ival != FMM_SPLIT_FP32 &&
-            ival != FMM_SPLIT_BF16_A2B3)
+            ival != FMM_SPLIT_BF16_A2B3 && ival != FMM_SPLIT_FP16X2)
             return FMM_ERR_INVALID_ARG;
         if (P.split == (int)ival) return FMM_OK;
         P.split = (int)ival;

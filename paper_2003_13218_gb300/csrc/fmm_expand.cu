@@ -269,6 +269,15 @@ template <typename T>
 __global__ void k_p2m(int p, int nside, const int *__restrict__ start, const Particle<T> *__restrict__ sp,
                       T inv_h, int d, T *__restrict__ M)
 {
+    // reciprocals of the recurrences, once per block: -1/(2k) and 1/((n+m)(n-m))
+    __shared__ T s_half[P_MAX + 1];
+    __shared__ T s_inv[(P_MAX + 1) * (P_MAX + 1)];
+    for (int e = threadIdx.x; e < (p + 1) * (p + 1); e += blockDim.x) {
+        const int n = e / (p + 1), mm = e % (p + 1);
+        s_inv[e] = n > mm ? T(1) / T((n + mm) * (n - mm)) : T(0);
+        if (e <= p) s_half[e] = e > 0 ? T(-0.5) / T(e) : T(0);
+    }
+    __syncthreads();
     int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     int64_t nleaf = (int64_t)nside * nside * nside;
     if (tid >= nleaf * (p + 1)) return;
@@ -283,7 +292,7 @@ __global__ void k_p2m(int p, int nside, const int *__restrict__ start, const Par
         T r2 = vx * vx + vy * vy + vz * vz;
         T dre = 1, dim = 0;
         for (int k = 1; k <= m; ++k) {
-            T sc = T(-0.5) / T(k);
+            T sc = s_half[k];
             T nre = sc * (vx * dre - vy * dim);
             T nim = sc * (vx * dim + vy * dre);
             dre = nre;
@@ -294,7 +303,7 @@ __global__ void k_p2m(int p, int nside, const int *__restrict__ start, const Par
         acc_im[m] += pt.q * dim;
         for (int n = m + 1; n <= p; ++n) {
             T a = T(2 * n - 1) * vz;
-            T inv = T(1) / T((n + m) * (n - m));
+            T inv = s_inv[n * (p + 1) + m];
             T cr = (a * p1re - r2 * p2re) * inv;
             T ci = (a * p1im - r2 * p2im) * inv;
             acc_re[n] += pt.q * cr;
@@ -447,7 +456,7 @@ __global__ void k_l2p(int p, int d, int64_t N, const int *__restrict__ sleaf, co
 template <typename T>
 fmm_status upward_t(Plan &P, bool solute_only)
 {
-    int p = P.p, nc = P.nc, nside = 1 << P.d;
+    int p = P.p, nside = 1 << P.d;
     const Particle<T> *sp = (const Particle<T> *)(solute_only ? P.sorted_u : P.sorted);
     T inv_h = (T)((double)nside / P.box);
     int64_t nthr = P.nleaf * (p + 1);

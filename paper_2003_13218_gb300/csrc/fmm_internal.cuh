@@ -77,7 +77,7 @@ struct Plan {
     int64_t N = 0;
     int d = 0, p = 0, ws = 1;
     int precision = FMM_PREC_FP64;
-    int split = FMM_SPLIT_BF16_A2B3;
+    int split = FMM_SPLIT_FP16X2;
     double kappa = 0;  // 0 = default 2 / box
     cudaStream_t stream = 0;
     bool timings_on = false;
@@ -237,7 +237,7 @@ fmm_status launch_solute_pass(Plan &P, bool *done);
 // tensor-core M2L (fmm_m2l_tc.cu)
 bool tc_available(const Plan &P, int level);
 fmm_status tc_prepare(Plan &P);
-// precise: use the 3 x 3 bf16 split whatever the plan's option (solute-only pass)
+// precise: at least the accuracy of the 3 x 3 bf16 split whatever the plan's option (solute-only pass)
 fmm_status launch_m2l_tc(Plan &P, int level, bool precise = false);
 void tc_free(Plan &P);
 

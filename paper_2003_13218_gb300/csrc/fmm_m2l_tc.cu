@@ -6,7 +6,7 @@
 //     L[t][j] = sum_{delta in IL(c)} sum_k M[t + delta][k] T_delta[k][j]
 // i.e. 189 dense products (128 x K) . (K x N):
 //   M dimension = 128 targets, N = (p+1)^2 output coefficients padded to 16,
-//   K = (p+1)^2 input coefficients padded to 32.
+//   K = (p+1)^2 input coefficients padded to 16 (rows stored padded to 32).
 // The A operand of offset delta is the same brick shifted to class
 // (c + delta) & 1 and parent offset (c + delta) >> 1 in {-1, 0, 1}^3; the
 // source planes carry a one-cell periodic halo so that every TMA box lies
@@ -14,13 +14,27 @@
 // and the products x_i y_j with i + j below the split order are summed
 // (bf16x3: 6 products, ~2^-24 relative; bf16x2: 3 products, ~2^-16).
 //
+// fp16x2 split.  fp16 keeps 11 significant bits, so two terms give ~2^-22
+// with 3 products, but its range is narrow.  The moments and operators are
+// therefore balanced first: with s(n,m) = sqrt((n+m)! (n-m)!),
+//     M~ = M^ s(n,m) gM,   T~[k][j] = T[k][j] / (s(k) s(j)) gT,   L^ = L~ s(j) / (gM gT).
+// Because |P_n^m| <= sqrt((n+m)!/(n-m)!) and binomial coefficients are at
+// most 2^N, |T~| <= 2^N / |delta|^(N+1) <= 1/2 for well-separated cells
+// (|delta| >= 2 cells), and |M~| is bounded by the absolute charge of the
+// cell.  gT = 2^14 and gM = 2^(14 - E), E the binary exponent of the level's
+// largest |M^ s|, put both operands' largest entries at 2^13..2^15, far below
+// fp16's 65504 and far above its subnormal range.
+//
+// The operand rows are stored (p+1)^2 padded to 32 wide (whole, aligned
+// 64-byte copy pieces), but the MMAs stop at K = (p+1)^2 padded to 16.
+//
 // Accumulation.  The tensor core's FP32 accumulation rounds with a bias, which
 // over thousands of MMAs into one accumulator shows up at the 1e-5 level.  So
 // each offset's products go into a fresh TMEM accumulator (two, alternating),
 // and the epilogue warps drain it and add it to the row held in FP32 registers
 // (round to nearest) while the tensor core works on the next offset.
 //
-// Roles (6 warps): warp 0 lane 0 issues TMA loads into a 3-stage ring, warp 1
+// Roles (6 warps): warp 0 lane 0 issues TMA loads into a 3..6-stage ring, warp 1
 // lane 0 issues tcgen05.mma, warps 2..5 drain TMEM (warp w reads TMEM lanes
 // 32 (w mod 4) .. +31, one target row per thread) and write the FP32 level
 // array.  Every mbarrier wait is bounded (globaltimer); on a timeout the
@@ -29,6 +43,8 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <math.h>
 #include <string.h>
 
 #include <new>
@@ -40,38 +56,71 @@ namespace fmm {
 namespace {
 
 constexpr int TC_THREADS = 192;
-constexpr int TC_STAGES = 3;
+constexpr int TC_MAX_STAGES = 6;
 constexpr int TC_ROWS = 128;          // MMA M
-constexpr int KCHUNK = 32;            // bf16 elements per 64-byte swizzled row
+constexpr int KCHUNK = 32;            // 16-bit elements per 64-byte swizzled row
 constexpr int ROW_BYTES = 64;
 constexpr uint32_t TMEM_COLS = 512;   // two accumulators of up to 256 columns
 constexpr int TC_PMAX = 15;           // N = (p+1)^2 rounded to 16 must not exceed 256
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // 2 s
 constexpr int NUM_IL = 189;
+constexpr int GAIN_T_EXP = 14;        // gT = 2^14 (fp16 split)
+constexpr int GAIN_M_EXP = 14;        // gM = 2^(14 - E)
+constexpr size_t TC_SMEM_BUDGET = 224 * 1024;
 
 struct TcState {
-    int pa = 0, pb = 0;
+    bool f16 = false;               // fp16x2 split with balanced scaling
+    int pa = 0, pb = 0;             // terms of the plan's split
+    int parts = 0;                  // terms stored (3 for the bf16 splits: the solute pass uses 3 x 3)
     int npad = 0, kp = 0;
-    __nv_bfloat16 *planes[9] = {};
+    uint16_t *planes[9] = {};       // bf16 or fp16 bit patterns
     size_t part_elems[9] = {};
-    __nv_bfloat16 *ops = nullptr;
+    uint16_t *ops = nullptr;
     size_t ops_part_elems = 0;
     CUtensorMap mapA[9][3];
     CUtensorMap mapB[3];
     int bx[9], by[9], bz[9];
-    int groups[9], per_group[9];  // offset groups per tile (small levels run more CTAs)
-    float *Lpart = nullptr;       // partial sums of the offset groups
+    int groups[9], per_group[9];    // offset groups per tile (small levels run more CTAs)
+    float *Lpart = nullptr;         // partial sums of the offset groups
+    float *s32 = nullptr;           // [kp] s(n,m) per real coefficient (fp16 split)
+    double *s64 = nullptr;
+    unsigned *amax = nullptr;       // [9] bits of the largest |M^ s| per level (fp16 split)
 };
 
 struct TcArgs {
     int np, bx, by, bz, rows, tiles_x, tiles_y, tiles_per_class;
-    int nc, npad, kchunks;
+    int nc, npad, kchunks, ksteps, stages;
     int groups, per_group;  // the 189 offsets split over `groups` CTAs per tile (small levels)
     uint32_t idesc;
     float *L;
     float *Lpart;           // [groups][8 np^3][nc] partial sums when groups > 1
+    const float *post;      // fp16 split: s(j) per output coefficient, else null
+    const unsigned *amax;   // fp16 split: the level's largest |M^ s| (gM follows from it)
     int *err;
 };
+
+// 2^e as a float for |e| <= 126, built from its bits
+__host__ __device__ inline float pow2f(int e)
+{
+    e = e < -126 ? -126 : (e > 126 ? 126 : e);
+    union {
+        uint32_t u;
+        float f;
+    } v;
+    v.u = (uint32_t)(e + 127) << 23;
+    return v.f;
+}
+
+// binary exponent E of a positive float given by its bits (value in [2^E, 2^(E+1)))
+__device__ inline int exp_of_bits(unsigned bits) { return (int)((bits >> 23) & 0xFFu) - 127; }
+
+// gM = 2^(GAIN_M_EXP - E), 1 when the level has no moments; kept within 2^+-100
+__device__ inline int gain_m_exp(unsigned bits)
+{
+    if (bits == 0u) return 0;
+    const int e = GAIN_M_EXP - exp_of_bits(bits);
+    return e < -100 ? -100 : (e > 100 ? 100 : e);
+}
 
 // ------------------------------------------------------------------ PTX wrappers
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -220,8 +269,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
              const __grid_constant__ CUtensorMap mB1, const __grid_constant__ CUtensorMap mB2, TcArgs a)
 {
     extern __shared__ uint8_t smem_dyn[];
-    __shared__ __align__(8) uint64_t bar_full[TC_STAGES];
-    __shared__ __align__(8) uint64_t bar_empty[TC_STAGES];
+    __shared__ __align__(8) uint64_t bar_full[TC_MAX_STAGES];
+    __shared__ __align__(8) uint64_t bar_empty[TC_MAX_STAGES];
     __shared__ __align__(8) uint64_t bar_tfull[2];
     __shared__ __align__(8) uint64_t bar_tempty[2];
     __shared__ __align__(8) uint64_t bar_done;
@@ -251,7 +300,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int np2 = a.np + 2;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < TC_STAGES; ++s) {
+        for (int s = 0; s < a.stages; ++s) {
             mbar_init(smem_u32(&bar_full[s]), 1);
             mbar_init(smem_u32(&bar_empty[s]), 1);
         }
@@ -282,7 +331,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             // ---------------- producer: TMA loads of the A brick and the B operator
             const CUtensorMap *mA[3] = {&mA0, &mA1, &mA2};
             const CUtensorMap *mB[3] = {&mB0, &mB1, &mB2};
-            int it = 0;
+            int it = 0, s = 0;
+            uint32_t round = 0;
             int oi = -1;  // position of the offset in the interaction-list order
             bool ok = true;
             for (int dz = -2 - cz; dz <= 3 - cz && ok; ++dz)
@@ -297,9 +347,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         const int hz = scls * np2 + z0 + (sz >> 1) + 1;
                         const int slot = off_slot(dx, dy, dz);
                         for (int kc = 0; kc < a.kchunks; ++kc) {
-                            const int s = it % TC_STAGES;
-                            const uint32_t round = (uint32_t)(it / TC_STAGES);
-                            if (it >= TC_STAGES &&
+                            if (it >= a.stages &&
                                 !mbar_wait(smem_u32(&bar_empty[s]), (round & 1u) ^ 1u, abort_flag)) {
                                 ok = false;
                                 break;
@@ -314,6 +362,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                             for (int j = 0; j < PB; ++j)
                                 tma_load_3d(base + PA * stageA + j * stageB, mB[j], full, kc * KCHUNK, 0, slot);
                             ++it;
+                            if (++s == a.stages) {
+                                s = 0;
+                                ++round;
+                            }
                         }
                     }
             produced_sh = it;
@@ -327,7 +379,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (lane == 0) {
             // ---------------- MMA issuer: one fresh accumulator per offset
             using PR = Products<PA, PB>;
-            int it = 0;
+            int it = 0, s = 0;
+            uint32_t round = 0;
             bool ok = true;
             for (int o = 0; o < nloc && ok; ++o) {
                 const int acc = o & 1;
@@ -339,8 +392,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 fence_after();
                 const uint32_t tmem_d = tmem + (uint32_t)(acc * 256);
                 for (int kc = 0; kc < a.kchunks; ++kc) {
-                    const int s = it % TC_STAGES;
-                    const uint32_t round = (uint32_t)(it / TC_STAGES);
                     if (!mbar_wait(smem_u32(&bar_full[s]), round & 1u, abort_flag)) {
                         ok = false;
                         break;
@@ -351,6 +402,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     for (int pr = 0; pr < PR::n; ++pr) {
 #pragma unroll
                         for (int k16 = 0; k16 < 2; ++k16) {
+                            if (2 * kc + k16 >= a.ksteps) continue;  // zero fill beyond K
                             const uint64_t ad = sdesc_sw64(base + PR::a(pr) * stageA + k16 * 32);
                             const uint64_t bd = sdesc_sw64(base + PA * stageA + PR::b(pr) * stageB + k16 * 32);
                             mma_bf16(tmem_d, ad, bd, a.idesc, (kc | pr | k16) != 0 ? 1u : 0u);
@@ -358,6 +410,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     }
                     mma_commit(smem_u32(&bar_empty[s]));
                     ++it;
+                    if (++s == a.stages) {
+                        s = 0;
+                        ++round;
+                    }
                 }
                 if (ok) mma_commit(smem_u32(&bar_tfull[acc]));
             }
@@ -407,9 +463,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const int64_t lin = (x0 + tx) + np * ((y0 + ty) + np * (int64_t)(z0 + tz));
             float *dst = a.groups == 1 ? a.L + ((int64_t)cls * np * np * np + lin) * a.nc
                                        : a.Lpart + (((int64_t)grp * 8 + cls) * np * np * np + lin) * a.nc;
+            if (a.post) {
+                // undo the balancing: L^ = L~ s(j) / (gM gT)
+                const float g = pow2f(-gain_m_exp(*a.amax) - GAIN_T_EXP);
 #pragma unroll
-            for (int i = 0; i < NCH * 16; ++i)
-                if (i < a.nc) dst[i] = Lr[i];
+                for (int i = 0; i < NCH * 16; ++i)
+                    if (i < a.nc) dst[i] = Lr[i] * (__ldg(a.post + i) * g);
+            } else {
+#pragma unroll
+                for (int i = 0; i < NCH * 16; ++i)
+                    if (i < a.nc) dst[i] = Lr[i];
+            }
         }
     }
 
@@ -420,7 +484,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (!mbar_wait(smem_u32(&bar_done), 0, &no_abort)) atomicOr(a.err, ERRF_TIMEOUT);
         if (abort_sh)
             for (int it = consumed_sh; it < produced_sh; ++it)
-                mbar_wait(smem_u32(&bar_full[it % TC_STAGES]), (uint32_t)(it / TC_STAGES) & 1u, &no_abort);
+                mbar_wait(smem_u32(&bar_full[it % a.stages]), (uint32_t)(it / a.stages) & 1u, &no_abort);
     }
     fence_before();
     __syncthreads();
@@ -430,53 +494,98 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 }
 
 // ------------------------------------------------------------------ operand preparation
-__device__ __forceinline__ void split_bf16(float v, int parts, __nv_bfloat16 *o, size_t stride)
+// x = x0 + x1 (+ x2) in bf16 or fp16 terms, each term the rounding of the
+// remaining residual; stored as bit patterns `stride` elements apart
+template <bool F16>
+__device__ __forceinline__ void split_terms(float v, int parts, uint16_t *o, size_t stride)
 {
-    __nv_bfloat16 b0 = __float2bfloat16_rn(v);
-    float r = v - __bfloat162float(b0);
-    o[0] = b0;
-    __nv_bfloat16 b1 = __float2bfloat16_rn(r);
-    o[stride] = b1;
-    if (parts > 2) o[2 * stride] = __float2bfloat16_rn(r - __bfloat162float(b1));
-}
-
-// FP32 class-layout moments -> bf16 split planes [part][class][hz][hy][hx][k] with a periodic halo
-__global__ void k_split_halo(const float *__restrict__ M, int np, int nc, int kp, int parts,
-                             __nv_bfloat16 *__restrict__ planes, size_t part_elems)
-{
-    const int64_t np2 = np + 2;
-    const int64_t total = 8 * np2 * np2 * np2 * kp;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int k = (int)(e % kp);
-        int64_t cell = e / kp;
-        const int hx = (int)(cell % np2);
-        const int hy = (int)((cell / np2) % np2);
-        const int64_t hzc = cell / (np2 * np2);
-        const int c = (int)(hzc / np2), hz = (int)(hzc % np2);
-        const int px = (hx - 1 + np) % np, py = (hy - 1 + np) % np, pz = (hz - 1 + np) % np;
-        float v = 0.f;
-        if (k < nc) v = M[((int64_t)c * np * np * np + px + (int64_t)np * (py + (int64_t)np * pz)) * nc + k];
-        split_bf16(v, parts, planes + e, part_elems);
+    float r = v;
+    for (int i = 0; i < parts; ++i) {
+        if (F16) {
+            const __half t = __float2half_rn(r);
+            o[i * stride] = __half_as_ushort(t);
+            r -= __half2float(t);
+        } else {
+            const __nv_bfloat16 t = __float2bfloat16_rn(r);
+            o[i * stride] = __bfloat16_as_ushort(t);
+            r -= __bfloat162float(t);
+        }
     }
 }
 
-// FP64 input-major operators T[slot][k][j] -> bf16 split B tables [part][slot][j][k] (K-major)
+// largest |M^ s(k)| of a level (fp16 split), as float bits into *amax; one
+// warp per cell, lanes over the coefficients
+__global__ void k_absmax(const float *__restrict__ M, int64_t ncell, int nc, const float *__restrict__ s,
+                         unsigned *__restrict__ amax)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    float m = 0.f;
+    for (int64_t c = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); c < ncell; c += warps) {
+        const float *row = M + c * nc;
+        for (int k = lane; k < nc; k += 32) m = fmaxf(m, fabsf(row[k] * __ldg(s + k)));
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0 && m > 0.f) atomicMax(amax, __float_as_uint(m));  // positive floats order as integers
+}
+
+// FP32 class-layout moments -> split planes [part][class][hz][hy][hx][k] with a
+// periodic halo; rows kp wide (zero beyond nc).  fp16: balanced by s(k) gM.
+// One warp per halo cell, lanes over the coefficients.
+template <bool F16>
+__global__ void k_split_halo(const float *__restrict__ M, int np, int nc, int kp, int parts,
+                             const float *__restrict__ s, const unsigned *__restrict__ amax,
+                             uint16_t *__restrict__ planes, size_t part_elems)
+{
+    const int np2 = np + 2;
+    const int64_t ncell = 8 * (int64_t)np2 * np2 * np2;
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const float g = F16 ? pow2f(gain_m_exp(*amax)) : 1.f;
+    for (int64_t cell = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); cell < ncell; cell += warps) {
+        const int hx = (int)(cell % np2);
+        const int hy = (int)((cell / np2) % np2);
+        const int hzc = (int)(cell / ((int64_t)np2 * np2));
+        const int c = hzc / np2, hz = hzc % np2;
+        const int px = (hx - 1 + np) % np, py = (hy - 1 + np) % np, pz = (hz - 1 + np) % np;
+        const float *row = M + ((int64_t)c * np * np * np + px + (int64_t)np * (py + (int64_t)np * pz)) * nc;
+        uint16_t *out = planes + cell * kp;
+        for (int k = lane; k < kp; k += 32) {
+            float v = 0.f;
+            if (k < nc) {
+                v = row[k];
+                if (F16) v *= __ldg(s + k) * g;
+            }
+            split_terms<F16>(v, parts, out + k, part_elems);
+        }
+    }
+}
+
+// FP64 input-major operators T[slot][k][j] -> split B tables [part][slot][j][k]
+// (K-major, rows kp wide).  fp16: balanced, T~ = T / (s(k) s(j)) gT.
+template <bool F16>
 __global__ void k_split_ops(const double *__restrict__ T, int nc, int npad, int kp, int parts,
-                            __nv_bfloat16 *__restrict__ ops, size_t part_elems)
+                            const double *__restrict__ s, uint16_t *__restrict__ ops, size_t part_elems)
 {
     const int64_t total = (int64_t)NOFF * npad * kp;
+    const double gT = (double)pow2f(GAIN_T_EXP);
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int k = (int)(e % kp);
         const int j = (int)((e / kp) % npad);
         const int slot = (int)(e / ((int64_t)kp * npad));
-        double v = (j < nc && k < nc) ? T[((int64_t)slot * nc + k) * nc + j] : 0.0;
-        __nv_bfloat16 b0 = __float2bfloat16_rn((float)v);
-        double r = v - (double)__bfloat162float(b0);
-        __nv_bfloat16 b1 = __float2bfloat16_rn((float)r);
-        double r2 = r - (double)__bfloat162float(b1);
-        ops[e] = b0;
-        ops[e + part_elems] = b1;
-        if (parts > 2) ops[e + 2 * part_elems] = __float2bfloat16_rn((float)r2);
+        double r = (j < nc && k < nc) ? T[((int64_t)slot * nc + k) * nc + j] : 0.0;
+        if (F16 && j < nc && k < nc) r = r / (s[k] * s[j]) * gT;
+        for (int i = 0; i < parts; ++i) {
+            if (F16) {
+                const __half t = __float2half_rn((float)r);
+                ops[e + i * part_elems] = __half_as_ushort(t);
+                r -= (double)__half2float(t);
+            } else {
+                const __nv_bfloat16 t = __float2bfloat16_rn((float)r);
+                ops[e + i * part_elems] = __bfloat16_as_ushort(t);
+                r -= (double)__bfloat162float(t);
+            }
+        }
     }
 }
 
@@ -506,10 +615,19 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 
 int tile_dim(int np, int cap) { return np < cap ? np : cap; }
 
+// stage ring of the split (pa, pb): as many stages as the shared-memory budget allows, 3..6
+int tc_stages(int pa, int pb, int npad)
+{
+    const size_t stage = (size_t)pa * TC_ROWS * ROW_BYTES + (size_t)pb * npad * ROW_BYTES;
+    size_t n = (TC_SMEM_BUDGET - 1024) / stage;
+    if (n > (size_t)TC_MAX_STAGES) n = TC_MAX_STAGES;
+    return n < 3 ? 3 : (int)n;
+}
+
 size_t tc_smem_bytes(int pa, int pb, int npad)
 {
     // at least 120 KB so that a second CTA (and its 512 TMEM columns) never shares the SM
-    size_t need = TC_STAGES * (size_t)(pa * TC_ROWS * ROW_BYTES + pb * npad * ROW_BYTES) + 1024;
+    size_t need = (size_t)tc_stages(pa, pb, npad) * (pa * TC_ROWS * ROW_BYTES + pb * npad * ROW_BYTES) + 1024;
     return need < 120 * 1024 ? 120 * 1024 : need;
 }
 
@@ -548,33 +666,61 @@ fmm_status tc_prepare(Plan &P)
 {
     tc_free(P);
     if (P.precision != FMM_PREC_MIXED || P.p > TC_PMAX) return FMM_OK;  // CUDA-core M2L
-    const int pa = P.split == FMM_SPLIT_BF16X3 ? 3 : 2;
-    const int pb = P.split == FMM_SPLIT_BF16X2 ? 2 : 3;
     PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
     if (!enc) return FMM_OK;
     TcState *S = new (std::nothrow) TcState();
     if (!S) return FMM_ERR_OOM;
-    S->pa = pa;
-    S->pb = pb;
-    S->npad = (P.nc + 15) / 16 * 16;
-    S->kp = (P.nc + KCHUNK - 1) / KCHUNK * KCHUNK;
     P.tc = S;
+    S->f16 = P.split == FMM_SPLIT_FP16X2;
+    S->pa = P.split == FMM_SPLIT_BF16X3 ? 3 : 2;
+    S->pb = (P.split == FMM_SPLIT_BF16X2 || S->f16) ? 2 : 3;
+    S->parts = S->f16 ? 2 : 3;  // bf16: three terms always, the solute-only pass uses the 3 x 3 split
+    S->npad = (P.nc + 15) / 16 * 16;
+    // rows padded to whole 64-byte copy boxes (aligned pieces); the MMAs stop at (p+1)^2 padded to 16
+    S->kp = (P.nc + KCHUNK - 1) / KCHUNK * KCHUNK;
+    const CUtensorMapDataType dt = S->f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    if (S->f16) {
+        // s(n,m) = sqrt((n+m)! (n-m)!) per real coefficient
+        double h_s[(TC_PMAX + 1) * (TC_PMAX + 1)];
+        float h_s32[(TC_PMAX + 1) * (TC_PMAX + 1)];
+        for (int n = 0; n <= P.p; ++n)
+            for (int m = 0; m <= n; ++m) {
+                double f = 1.0;
+                for (int i = 2; i <= n + m; ++i) f *= i;
+                for (int i = 2; i <= n - m; ++i) f *= i;
+                const double v = sqrt(f);
+                const int re = m == 0 ? n * n : n * n + 2 * m - 1;
+                h_s[re] = v;
+                if (m > 0) h_s[re + 1] = v;
+            }
+        for (int k = 0; k < P.nc; ++k) h_s32[k] = (float)h_s[k];
+        FMM_CUDA_TRY(cudaMalloc(&S->s64, sizeof(double) * P.nc));
+        FMM_CUDA_TRY(cudaMalloc(&S->s32, sizeof(float) * P.nc));
+        FMM_CUDA_TRY(cudaMalloc(&S->amax, sizeof(unsigned) * 9));
+        FMM_CUDA_TRY(cudaMemcpyAsync(S->s64, h_s, sizeof(double) * P.nc, cudaMemcpyHostToDevice, P.stream));
+        FMM_CUDA_TRY(cudaMemcpyAsync(S->s32, h_s32, sizeof(float) * P.nc, cudaMemcpyHostToDevice, P.stream));
+    }
     // operator tables
     S->ops_part_elems = (size_t)NOFF * S->npad * S->kp;
-    // three operator terms always (the solute-only pass uses the 3 x 3 split)
-    FMM_CUDA_TRY(cudaMalloc(&S->ops, sizeof(__nv_bfloat16) * S->ops_part_elems * 3));
-    k_split_ops<<<1216, 256, 0, P.stream>>>(P.tab.Top64, P.nc, S->npad, S->kp, 3, S->ops, S->ops_part_elems);
+    FMM_CUDA_TRY(cudaMalloc(&S->ops, sizeof(uint16_t) * S->ops_part_elems * S->parts));
+    if (S->f16)
+        k_split_ops<true><<<1216, 256, 0, P.stream>>>(P.tab.Top64, P.nc, S->npad, S->kp, S->parts, S->s64, S->ops,
+                                                      S->ops_part_elems);
+    else
+        k_split_ops<false><<<1216, 256, 0, P.stream>>>(P.tab.Top64, P.nc, S->npad, S->kp, S->parts, nullptr,
+                                                       S->ops, S->ops_part_elems);
     FMM_LAUNCH_CHECK(P);
-    for (int j = 0; j < 3; ++j) {
+    for (int j = 0; j < S->parts; ++j) {
         cuuint64_t dims[3] = {(cuuint64_t)S->kp, (cuuint64_t)S->npad, (cuuint64_t)NOFF};
         cuuint64_t strides[2] = {(cuuint64_t)S->kp * 2, (cuuint64_t)S->kp * 2 * S->npad};
         cuuint32_t box[3] = {KCHUNK, (cuuint32_t)S->npad, 1};
         cuuint32_t es[3] = {1, 1, 1};
-        if (enc(&S->mapB[j], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, S->ops + j * S->ops_part_elems, dims, strides, box,
-                es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+        if (enc(&S->mapB[j], dt, 3, S->ops + j * S->ops_part_elems, dims, strides, box, es,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return FMM_ERR_INTERNAL;
     }
+    for (int j = S->parts; j < 3; ++j) S->mapB[j] = S->mapB[0];  // unused kernel parameters
     // source planes per level
     size_t lpart_elems = 0;
     for (int l = 1; l <= P.d; ++l) {
@@ -584,19 +730,19 @@ fmm_status tc_prepare(Plan &P)
         S->by[l] = tile_dim(np, TC_ROWS / S->bx[l]);
         S->bz[l] = tile_dim(np, TC_ROWS / (S->bx[l] * S->by[l]));
         S->part_elems[l] = (size_t)8 * np2 * np2 * np2 * S->kp;
-        // three planes always: the solute-only pass uses the 3 x 3 split
-        FMM_CUDA_TRY(cudaMalloc(&S->planes[l], sizeof(__nv_bfloat16) * S->part_elems[l] * 3));
-        for (int i = 0; i < 3; ++i) {
+        FMM_CUDA_TRY(cudaMalloc(&S->planes[l], sizeof(uint16_t) * S->part_elems[l] * S->parts));
+        for (int i = 0; i < S->parts; ++i) {
             cuuint64_t dims[4] = {(cuuint64_t)S->kp, (cuuint64_t)np2, (cuuint64_t)np2, (cuuint64_t)(8 * np2)};
             cuuint64_t strides[3] = {(cuuint64_t)S->kp * 2, (cuuint64_t)S->kp * 2 * np2,
                                      (cuuint64_t)S->kp * 2 * np2 * np2};
             cuuint32_t box[4] = {KCHUNK, (cuuint32_t)S->bx[l], (cuuint32_t)S->by[l], (cuuint32_t)S->bz[l]};
             cuuint32_t es[4] = {1, 1, 1, 1};
-            if (enc(&S->mapA[l][i], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, S->planes[l] + i * S->part_elems[l], dims,
-                    strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
-                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            if (enc(&S->mapA[l][i], dt, 4, S->planes[l] + i * S->part_elems[l], dims, strides, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
                 return FMM_ERR_INTERNAL;
         }
+        for (int i = S->parts; i < 3; ++i) S->mapA[l][i] = S->mapA[l][0];
         // enough CTAs to fill the GPU twice: split the 189 offsets when tiles are few
         int tiles = 8 * (np / S->bx[l]) * (np / S->by[l]) * (np / S->bz[l]);
         int want = (2 * 152 + tiles - 1) / tiles;
@@ -611,12 +757,15 @@ fmm_status tc_prepare(Plan &P)
     }
     if (lpart_elems) FMM_CUDA_TRY(cudaMalloc(&S->Lpart, sizeof(float) * lpart_elems));
     TcKernel k = pick_kernel(S->pa, S->pb, S->npad / 16);
-    TcKernel kp = pick_kernel(3, 3, S->npad / 16);  // the solute-only pass
-    if (!k || !kp) return FMM_ERR_INTERNAL;
+    if (!k) return FMM_ERR_INTERNAL;
     FMM_CUDA_TRY(cudaFuncSetAttribute((const void *)k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)tc_smem_bytes(S->pa, S->pb, S->npad)));
-    FMM_CUDA_TRY(cudaFuncSetAttribute((const void *)kp, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)tc_smem_bytes(3, 3, S->npad)));
+    if (!S->f16) {
+        TcKernel kp = pick_kernel(3, 3, S->npad / 16);  // the solute-only pass
+        if (!kp) return FMM_ERR_INTERNAL;
+        FMM_CUDA_TRY(cudaFuncSetAttribute((const void *)kp, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)tc_smem_bytes(3, 3, S->npad)));
+    }
     FMM_CUDA_TRY(cudaStreamSynchronize(P.stream));
     return FMM_OK;
 }
@@ -625,14 +774,25 @@ fmm_status launch_m2l_tc(Plan &P, int l, bool precise)
 {
     TcState *S = (TcState *)P.tc;
     if (!S) return FMM_ERR_INTERNAL;
-    const int pa = precise ? 3 : S->pa;
-    const int pb = precise ? 3 : S->pb;
+    // the fp16 split is already as accurate as the 3 x 3 bf16 one
+    const int pa = precise && !S->f16 ? 3 : S->pa;
+    const int pb = precise && !S->f16 ? 3 : S->pb;
     int np = 1 << (l - 1);
     int64_t np2 = np + 2;
-    int64_t n = 8 * np2 * np2 * np2 * S->kp;
-    unsigned blocks = (unsigned)((n + 255) / 256 < 4864 ? (n + 255) / 256 : 4864);
-    k_split_halo<<<blocks, 256, 0, P.stream>>>((const float *)P.M[l], np, P.nc, S->kp, pa, S->planes[l],
-                                               S->part_elems[l]);
+    const int64_t nhalo = 8 * np2 * np2 * np2;
+    unsigned blocks = (unsigned)((nhalo + 7) / 8 < 4864 ? (nhalo + 7) / 8 : 4864);
+    if (S->f16) {
+        FMM_CUDA_TRY(cudaMemsetAsync(S->amax + l, 0, sizeof(unsigned), P.stream));
+        const int64_t ncell = (int64_t)8 * np * np * np;
+        k_absmax<<<(unsigned)((ncell + 7) / 8 < 1216 ? (ncell + 7) / 8 : 1216), 256, 0, P.stream>>>(
+            (const float *)P.M[l], ncell, P.nc, S->s32, S->amax + l);
+        FMM_LAUNCH_CHECK(P);
+        k_split_halo<true><<<blocks, 256, 0, P.stream>>>((const float *)P.M[l], np, P.nc, S->kp, pa, S->s32,
+                                                         S->amax + l, S->planes[l], S->part_elems[l]);
+    } else {
+        k_split_halo<false><<<blocks, 256, 0, P.stream>>>((const float *)P.M[l], np, P.nc, S->kp, pa, nullptr,
+                                                          nullptr, S->planes[l], S->part_elems[l]);
+    }
     FMM_LAUNCH_CHECK(P);
     TcArgs a;
     a.np = np;
@@ -645,10 +805,17 @@ fmm_status launch_m2l_tc(Plan &P, int l, bool precise)
     a.tiles_per_class = a.tiles_x * a.tiles_y * (np / a.bz);
     a.nc = P.nc;
     a.npad = S->npad;
-    a.kchunks = S->kp / KCHUNK;
-    a.idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(S->npad >> 3) << 17) | ((uint32_t)(TC_ROWS >> 4) << 24);
+    a.kchunks = (S->kp + KCHUNK - 1) / KCHUNK;
+    a.ksteps = (P.nc + 15) / 16;
+    a.stages = tc_stages(pa, pb, S->npad);
+    // instruction descriptor: FP32 accumulator, A and B both bf16 (format 1) or both fp16 (format 0),
+    // K-major, N >> 3 at bit 17, M >> 4 at bit 24
+    const uint32_t ab = S->f16 ? 0u : 1u;
+    a.idesc = (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(S->npad >> 3) << 17) | ((uint32_t)(TC_ROWS >> 4) << 24);
     a.L = (float *)P.L[l];
     a.Lpart = S->Lpart;
+    a.post = S->f16 ? S->s32 : nullptr;
+    a.amax = S->f16 ? S->amax + l : nullptr;
     a.groups = S->groups[l];
     a.per_group = S->per_group[l];
     a.err = P.d_err;
@@ -680,6 +847,9 @@ void tc_free(Plan &P)
     for (int l = 0; l < 9; ++l) cudaFree(S->planes[l]);
     cudaFree(S->ops);
     cudaFree(S->Lpart);
+    cudaFree(S->s32);
+    cudaFree(S->s64);
+    cudaFree(S->amax);
     delete S;
     P.tc = nullptr;
 }

@@ -149,44 +149,51 @@ __global__ void k_sol_p2m(int p, int d, const int *__restrict__ cells, const int
     }
 }
 
-// M2M from the active children at level l+1 into active cell blockIdx.x of level l
+// M2M from the active children at level l+1 into active cell blockIdx.x of
+// level l.  One warp (blockDim 32) per output (n, m) = blockIdx.y; lane = the
+// child degree k, then a fixed shuffle tree.
 template <typename T>
 __global__ void k_sol_m2m(int p, int l, const int *__restrict__ cells, const int *__restrict__ ncells,
                           const T *__restrict__ Rw, T *__restrict__ MU)
 {
-    int i = blockIdx.x;
+    const int i = blockIdx.x;
     if (i >= ncells[l]) return;
-    int nc = ncoef(p);
-    int ntri = (p + 1) * (p + 2) / 2;
-    int nl = 1 << l;
+    const int nc = ncoef(p);
+    const int nl = 1 << l;
+    const int kk = threadIdx.x;
     int px, py, pz;
     cell_xyz(cells[l * NU_MAX + i], nl, px, py, pz);
-    for (int t = threadIdx.x; t < ntri; t += blockDim.x) {
-        int n = 0;
-        while (tri(n + 1, 0) <= t) ++n;
-        int m = t - tri(n, 0);
-        T accr = 0, acci = 0;
+    const int t = blockIdx.y;
+    int n = 0;
+    while (tri(n + 1, 0) <= t) ++n;
+    const int m = t - tri(n, 0);
+    T accr = 0, acci = 0;
+    if (kk <= n) {
+        const int dn = n - kk;
+        const T sgn = (dn & 1) ? T(-1) : T(1);
+        T scale = 1;
+        for (int s = 0; s < kk; ++s) scale *= T(0.5);
         for (int k = 0; k < ncells[l + 1]; ++k) {
             int cx, cy, cz;
             cell_xyz(cells[(l + 1) * NU_MAX + k], 2 * nl, cx, cy, cz);
             if ((cx >> 1) != px || (cy >> 1) != py || (cz >> 1) != pz) continue;
-            int oct = (cx & 1) | ((cy & 1) << 1) | ((cz & 1) << 2);
+            const int oct = (cx & 1) | ((cy & 1) << 1) | ((cz & 1) << 2);
             const T *Mch = MU + ((size_t)(l + 1) * NU_MAX + k) * nc;
             const T *R = Rw + oct * nc;
-            T scale = 1;
-            for (int kk = 0; kk <= n; ++kk) {
-                int dn = n - kk;
-                T sgn = (dn & 1) ? T(-1) : T(1);
-                for (int ll = -kk; ll <= kk; ++ll) {
-                    int dm = m - ll;
-                    if (dm < -dn || dm > dn) continue;
-                    Cx<T> pr = cmul(coef(R, dn, dm), coef(Mch, kk, ll));
-                    accr += sgn * scale * pr.re;
-                    acci += sgn * scale * pr.im;
-                }
-                scale *= T(0.5);
+            for (int ll = -kk; ll <= kk; ++ll) {
+                const int dm = m - ll;
+                if (dm < -dn || dm > dn) continue;
+                Cx<T> pr = cmul(coef(R, dn, dm), coef(Mch, kk, ll));
+                accr += sgn * scale * pr.re;
+                acci += sgn * scale * pr.im;
             }
         }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        accr += __shfl_xor_sync(0xffffffffu, accr, off);
+        acci += __shfl_xor_sync(0xffffffffu, acci, off);
+    }
+    if (kk == 0) {
         T *out = MU + ((size_t)l * NU_MAX + i) * nc;
         out[cre(n, m)] = accr;
         if (m > 0) out[cim(n, m)] = acci;
@@ -348,58 +355,68 @@ __global__ void k_act_m2l(int p, int l, const int *__restrict__ cells, const int
     }
 }
 
-// Lt[l][i] = sum of the 189 terms, in offset order
+// Lt[l][i] = sum of the 189 terms: one warp per (active cell, coefficient j),
+// lanes take every 32nd offset, then a fixed shuffle tree (deterministic)
 __global__ void k_act_sum(int p, int l, const int *__restrict__ ncells, const double *__restrict__ part,
                           double *__restrict__ Lt)
 {
-    int i = blockIdx.x;
+    const int i = blockIdx.x;
     if (i >= ncells[l]) return;
-    int nc = ncoef(p);
-    for (int j = threadIdx.x; j < nc; j += blockDim.x) {
-        double s = 0;
-        for (int o = 0; o < 189; ++o) s += part[((size_t)i * 189 + o) * nc + j];
-        Lt[((size_t)l * NU_MAX + i) * nc + j] = s;
-    }
+    const int nc = ncoef(p);
+    const int j = blockIdx.y * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (j >= nc) return;
+    double s = 0;
+    for (int o = lane; o < 189; o += 32) s += part[((size_t)i * 189 + o) * nc + j];
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) Lt[((size_t)l * NU_MAX + i) * nc + j] = s;
 }
 
 // Lt[l][i] += L2L of the parent's full expansion (Lt[l-1] or, at level 1, the
-// lattice result L0): Lhat_k^m += sum_{n >= k} Lhat_n^q R_{n-k}^{q-m}(w_c) 2^{-(k+1)}
-template <typename T>
+// lattice result L0): Lhat_k^m += sum_{n >= k} Lhat_n^q R_{n-k}^{q-m}(w_c) 2^{-(k+1)}.
+// One warp (blockDim 32) per output (k, m) = blockIdx.y; lane = n - k, then a
+// fixed shuffle tree.
 __global__ void k_act_l2l(int p, int l, const int *__restrict__ cells, const int *__restrict__ ncells,
-                          const T *__restrict__ Rw, const T *__restrict__ L0, T *__restrict__ Lt)
+                          const double *__restrict__ Rw, const double *__restrict__ L0, double *__restrict__ Lt)
 {
-    int i = blockIdx.x;
+    const int i = blockIdx.x;
     if (i >= ncells[l]) return;
-    int nc = ncoef(p);
-    int n = 1 << l;
+    const int nc = ncoef(p);
+    const int nl = 1 << l;
+    const int lane = threadIdx.x;
     int x, y, z;
-    cell_xyz(cells[l * NU_MAX + i], n, x, y, z);
-    const T *Lp = L0;
+    cell_xyz(cells[l * NU_MAX + i], nl, x, y, z);
+    const double *Lp = L0;
     if (l > 1) {
-        int plin = (x >> 1) + (n >> 1) * ((y >> 1) + (n >> 1) * (z >> 1));
+        const int plin = (x >> 1) + (nl >> 1) * ((y >> 1) + (nl >> 1) * (z >> 1));
         for (int k = 0; k < ncells[l - 1]; ++k)
             if (cells[(l - 1) * NU_MAX + k] == plin) Lp = Lt + ((size_t)(l - 1) * NU_MAX + k) * nc;
     }
-    const T *R = Rw + ((x & 1) | ((y & 1) << 1) | ((z & 1) << 2)) * nc;
-    int ntri = (p + 1) * (p + 2) / 2;
-    T *out = Lt + ((size_t)l * NU_MAX + i) * nc;
-    for (int t = threadIdx.x; t < ntri; t += blockDim.x) {
-        int k = 0;
-        while (tri(k + 1, 0) <= t) ++k;
-        int m = t - tri(k, 0);
-        T accr = 0, acci = 0;
-        for (int nn = k; nn <= p; ++nn) {
-            int dn = nn - k;
-            for (int q = -nn; q <= nn; ++q) {
-                int dm = q - m;
-                if (dm < -dn || dm > dn) continue;
-                Cx<T> pr = cmul(coef(Lp, nn, q), coef(R, dn, dm));
-                accr += pr.re;
-                acci += pr.im;
-            }
+    const double *R = Rw + ((x & 1) | ((y & 1) << 1) | ((z & 1) << 2)) * nc;
+    const int t = blockIdx.y;
+    int k = 0;
+    while (tri(k + 1, 0) <= t) ++k;
+    const int m = t - tri(k, 0);
+    double accr = 0, acci = 0;
+    const int n = k + lane;
+    if (n <= p) {
+        const int dn = n - k;
+        for (int q = -n; q <= n; ++q) {
+            const int dm = q - m;
+            if (dm < -dn || dm > dn) continue;
+            Cx<double> pr = cmul(coef(Lp, n, q), coef(R, dn, dm));
+            accr += pr.re;
+            acci += pr.im;
         }
-        T scale = 1;
-        for (int s = 0; s <= k; ++s) scale *= T(0.5);
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        accr += __shfl_xor_sync(0xffffffffu, accr, off);
+        acci += __shfl_xor_sync(0xffffffffu, acci, off);
+    }
+    if (lane == 0) {
+        double scale = 1;
+        for (int s = 0; s <= k; ++s) scale *= 0.5;
+        double *out = Lt + ((size_t)l * NU_MAX + i) * nc;
         out[cre(k, m)] += scale * accr;
         if (m > 0) out[cim(k, m)] += scale * acci;
     }
@@ -580,7 +597,7 @@ fmm_status solute_sparse_t(Plan &P, SoluteScratch &S, int nu)
                                              (T)(1.0 / h), MU);
     FMM_LAUNCH_CHECK(P);
     for (int l = d - 1; l >= 0; --l) {
-        k_sol_m2m<T><<<nu, 128, 0, P.stream>>>(p, l, S.cells, S.ncells, Rw, MU);
+        k_sol_m2m<T><<<dim3(nu, (p + 1) * (p + 2) / 2), 32, 0, P.stream>>>(p, l, S.cells, S.ncells, Rw, MU);
         FMM_LAUNCH_CHECK(P);
     }
     // FP64 expansions of the solvent field at the active cells, from the full
@@ -594,9 +611,9 @@ fmm_status solute_sparse_t(Plan &P, SoluteScratch &S, int nu)
         k_act_m2l<T><<<dim3(nu, 189), nth, 0, P.stream>>>(p, l, S.cells, S.ncells, P.tab.Top64,
                                                                (const T *)P.M[l], MU, S.part);
         FMM_LAUNCH_CHECK(P);
-        k_act_sum<<<nu, nth, 0, P.stream>>>(p, l, S.ncells, S.part, Lt);
+        k_act_sum<<<dim3(nu, (nc + 7) / 8), 256, 0, P.stream>>>(p, l, S.ncells, S.part, Lt);
         FMM_LAUNCH_CHECK(P);
-        k_act_l2l<double><<<nu, 128, 0, P.stream>>>(p, l, S.cells, S.ncells, P.tab.Rw64, Lt, Lt);
+        k_act_l2l<<<dim3(nu, (p + 1) * (p + 2) / 2), 32, 0, P.stream>>>(p, l, S.cells, S.ncells, P.tab.Rw64, Lt, Lt);
         FMM_LAUNCH_CHECK(P);
     }
     // dense coarse levels 0..LD

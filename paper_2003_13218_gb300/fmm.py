@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_HERE, "libfmm_gb300.so")
 
 FMM_OPT_WS, FMM_OPT_PRECISION, FMM_OPT_KAPPA, FMM_OPT_M2L_SPLIT, FMM_OPT_STREAM, FMM_OPT_TIMINGS = 1, 2, 3, 4, 5, 6
 PRECISION = {"fp64": 0, "mixed": 1}
-SPLIT = {"bf16x3": 0, "bf16x2": 1, "fp32": 2, "bf16a2b3": 3}
+SPLIT = {"bf16x3": 0, "bf16x2": 1, "fp32": 2, "bf16a2b3": 3, "fp16x2": 4}
 STATUS = ["ok", "invalid argument", "non-finite input", "CUDA error", "out of memory", "timeout",
           "internal error", "unsupported"]
 
@@ -115,13 +115,13 @@ class FMMPlan:
     """A plan for N charges in a cubic box of side ``box`` (A), depth d, order p."""
 
     def __init__(self, box: float, N: int, depth: int, p: int, precision: str = "fp64", kappa: float | None = None,
-                 split: str = "bf16a2b3", timings: bool = False):
+                 split: str = "fp16x2", timings: bool = False):
         self._lib = load_library()
         h = ctypes.c_void_p()
         _check(self._lib.fmm_plan_create(float(box), int(N), int(depth), int(p), ctypes.byref(h)), "fmm_plan_create")
         self._h = h
         self.box, self.N, self.depth, self.p = float(box), int(N), int(depth), int(p)
-        if split != "bf16a2b3":
+        if split != "fp16x2":
             self.set_option(FMM_OPT_M2L_SPLIT, SPLIT[split])
         if precision != "fp64":
             self.set_option(FMM_OPT_PRECISION, PRECISION[precision])

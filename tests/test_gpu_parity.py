@@ -202,8 +202,8 @@ def _sub_box(nw, L, seed=0):
     return boxes.ion_in_water(nw, "Na", seed=seed, L=L)
 
 
-@pytest.mark.parametrize("split,tol_e,tol_f", [("bf16x3", 2e-7, 2e-6), ("bf16a2b3", 5e-7, 5e-6),
-                                               ("bf16x2", 2e-6, 5e-5)])
+@pytest.mark.parametrize("split,tol_e,tol_f", [("fp16x2", 2e-7, 2e-6), ("bf16x3", 2e-7, 2e-6),
+                                               ("bf16a2b3", 5e-7, 5e-6), ("bf16x2", 2e-6, 5e-5)])
 def test_tensor_core_m2l_matches_cuda_core_m2l(split, tol_e, tol_f):
     """Mixed path with tcgen05 M2L (full 128-target tiles at levels 4, 5) against the same path
     with the FP32 CUDA-core M2L, and both against the FP64 GPU path."""
@@ -215,6 +215,31 @@ def test_tensor_core_m2l_matches_cuda_core_m2l(split, tol_e, tol_f):
     assert abs(t_tc["far"] - t_cc["far"]) <= tol_e * abs(t_64["total"])
     assert abs(t_tc["total"] - t_64["total"]) <= 1e-6 * abs(t_64["total"])
     assert _rms_rel(F_tc, F_cc) < tol_f
+    assert _rms_rel(F_tc, F_64) < 1e-5
+
+
+@pytest.mark.parametrize("p", [3, 4, 8, 10])
+def test_fp16_split_orders(p):
+    """fp16x2 tensor-core M2L at other expansion orders (K = (p+1)^2 padded to 16 = 16, 32,
+    96, 128; rows of 32, 32, 96, 128), against the FP64 GPU path at the same order, which
+    isolates the precision of the mixed path.  p = 3 skips the zero half of its only copy box."""
+    b = _sub_box(3000, 45.0, seed=3)
+    d = 4
+    t_tc, _, F_tc = _run(b.pos, b.q, b.L, d, p, precision="mixed", split="fp16x2")
+    t_64, _, F_64 = _run(b.pos, b.q, b.L, d, p)
+    assert abs(t_tc["total"] - t_64["total"]) <= 1e-6 * abs(t_64["total"])
+    assert _rms_rel(F_tc, F_64) < 1e-5
+
+
+@pytest.mark.parametrize("qscale", [1e-5, 1e5])
+def test_fp16_split_charge_scale(qscale):
+    """The level gain gM follows the moments' magnitude: charges scaled by 1e-5 or 1e5
+    keep the mixed path's relative accuracy (no fp16 underflow or overflow)."""
+    b = _sub_box(3000, 45.0, seed=4)
+    q = b.q * qscale
+    t_tc, _, F_tc = _run(b.pos, q, b.L, 4, 12, precision="mixed", split="fp16x2")
+    t_64, _, F_64 = _run(b.pos, q, b.L, 4, 12)
+    assert abs(t_tc["total"] - t_64["total"]) <= 1e-6 * abs(t_64["total"])
     assert _rms_rel(F_tc, F_64) < 1e-5
 
 
