@@ -51,11 +51,12 @@ KERNEL_BEGIN = "// -------------------------------------------------------------
 KERNEL_END = "// ------------------------------------------------------------------ operand preparation"
 
 
-def m2l_flops(d: int, p: int, levels=None) -> float:
-    """Algorithmic flops of M2L: 2 C^2 per (target, source) pair, 189 sources per target."""
+def m2l_flops(d: int, p: int, levels=None, fused_l2l=False) -> float:
+    """Algorithmic flops of M2L: 2 C^2 per (target, source) pair, 189 sources per target,
+    plus one dense C x C product per target when the L2L is fused into the same launch."""
     C = (p + 1) ** 2
     levels = range(1, d + 1) if levels is None else levels
-    pairs = 189 * sum(8 ** l for l in levels)
+    pairs = (189 + (1 if fused_l2l else 0)) * sum(8 ** l for l in levels)
     return 2.0 * C * C * pairs
 
 
@@ -251,15 +252,16 @@ def run_ours(args):
     value = N * args.steps * ws / (ms_total / 1e3)
     peaks, peak_kind = load_peaks()
     uses_tc = backend == "tcgen05"
-    stage_flops = m2l_flops(d, p)
+    fused = uses_tc and args.split == "fp16x2"  # the fp16 split fuses the L2L into each level's launch
+    stage_flops = m2l_flops(d, p, fused_l2l=fused)
     stage_ms = statistics.mean(x[1] for x in m2l_ms)
     if uses_tc:
         # the dominant launch: the tensor-core M2L of the finest level
-        flops = m2l_flops(d, p, levels=[d])
+        flops = m2l_flops(d, p, levels=[d], fused_l2l=fused)
         launch_ms = statistics.mean(x[0] for x in m2l_ms)
         peak = peaks.get("bf16_tflops", FALLBACK_PEAKS["bf16_tflops"])
         roof = {"bound": "tensor", "peak_source": peak_kind + " bf16 dense burst (MEASURED_PEAKS.json)",
-                "kernel": "k_m2l_tc, level %d (one launch)" % d}
+                "kernel": "k_m2l_tc, level %d (one launch%s)" % (d, ", M2L + fused L2L" if fused else "")}
         traffic = None
         if (M2L_TRAFFIC and M2L_TRAFFIC["workload"] == args.workload and M2L_TRAFFIC["level"] == d
                 and kernel_sha(M2L_TRAFFIC["src"]) == M2L_TRAFFIC["sha256"]):

@@ -128,10 +128,12 @@ fmm_status far_field_pass(Plan &P, bool gradient, bool solute_only, StageTimer *
     bool ev = tm && P.timings_on;
     for (int l = 1; l <= P.d; ++l) {
         if (ev) cudaEventRecord(P.ev_m2l[2 * (l - 1)], P.stream);
-        if (tc_available(P, l)) TRY(launch_m2l_tc(P, l, solute_only));
+        // with the fp16 split the upward pass left the planes split and the L2L is fused
+        const bool fused = tc_available(P, l) && tc_translations(P);
+        if (tc_available(P, l)) TRY(launch_m2l_tc(P, l, solute_only, !fused));
         else TRY(launch_m2l_simt(P, l));
         if (ev) cudaEventRecord(P.ev_m2l[2 * (l - 1) + 1], P.stream);
-        TRY(launch_l2l(P, l));
+        if (!fused) TRY(launch_l2l(P, l));
     }
     if (tm) tm->mark();
     TRY(launch_l2p(P, gradient, solute_only));

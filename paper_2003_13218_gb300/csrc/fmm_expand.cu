@@ -462,8 +462,10 @@ fmm_status upward_t(Plan &P, bool solute_only)
     int64_t nthr = P.nleaf * (p + 1);
     k_p2m<T><<<blocks_for(nthr, 128), 128, 0, P.stream>>>(p, nside, P.cell_start, sp, inv_h, P.d, (T *)P.M[P.d]);
     FMM_LAUNCH_CHECK(P);
+    const bool tc = tc_translations(P);
     for (int l = P.d - 1; l >= 0; --l) {
-        fmm_status st = launch_m2m(P, l);
+        fmm_status st = tc ? tc_split_moments(P, l + 1) : FMM_OK;
+        if (st == FMM_OK) st = tc ? launch_m2m_tc(P, l) : launch_m2m(P, l);
         if (st != FMM_OK) return st;
     }
     return FMM_OK;

@@ -234,11 +234,19 @@ fmm_status solute_prepare(Plan &P);
 void solute_free(Plan &P);
 fmm_status launch_solute_pass(Plan &P, bool *done);
 
-// tensor-core M2L (fmm_m2l_tc.cu)
+// tensor-core M2L, and with the fp16 split also M2M and L2L (fmm_m2l_tc.cu)
 bool tc_available(const Plan &P, int level);
+// fp16 split: M2M on the tensor cores and L2L fused into each level's M2L
+bool tc_translations(const Plan &P);
 fmm_status tc_prepare(Plan &P);
-// precise: at least the accuracy of the 3 x 3 bf16 split whatever the plan's option (solute-only pass)
-fmm_status launch_m2l_tc(Plan &P, int level, bool precise = false);
+// fp16 split: balanced halo planes of M[level] (done by the upward pass before the M2M into level - 1)
+fmm_status tc_split_moments(Plan &P, int level);
+// fp16 split: M2M into level (< d) from the planes of level + 1
+fmm_status launch_m2m_tc(Plan &P, int level);
+// precise: at least the accuracy of the 3 x 3 bf16 split whatever the plan's option (solute-only pass);
+// split: (re)build the planes of M[level] first (always done for the bf16 splits).  With the fp16
+// split the L2L from level - 1 is included: L[level] = M2L + L2L.
+fmm_status launch_m2l_tc(Plan &P, int level, bool precise = false, bool split = true);
 void tc_free(Plan &P);
 
 #define FMM_CUDA_TRY(expr)                                        \

@@ -68,8 +68,13 @@ constexpr int GAIN_T_EXP = 14;        // gT = 2^14 (fp16 split)
 constexpr int GAIN_M_EXP = 14;        // gM = 2^(14 - E)
 constexpr size_t TC_SMEM_BUDGET = 224 * 1024;
 
+// operator slots of the B tables: the M2L offsets (NOFF), then M2M and L2L per child octant
+constexpr int SLOT_M2M = NOFF;
+constexpr int SLOT_L2L = NOFF + 8;
+constexpr int NSLOT = NOFF + 16;
+
 struct TcState {
-    bool f16 = false;               // fp16x2 split with balanced scaling
+    bool f16 = false;               // fp16x2 split with balanced scaling (and tensor-core translations)
     int pa = 0, pb = 0;             // terms of the plan's split
     int parts = 0;                  // terms stored (3 for the bf16 splits: the solute pass uses 3 x 3)
     int npad = 0, kp = 0;
@@ -79,23 +84,34 @@ struct TcState {
     size_t ops_part_elems = 0;
     CUtensorMap mapA[9][3];
     CUtensorMap mapB[3];
+    CUtensorMap mapL[9][2];         // fp16: parent-level local expansions for the fused L2L of level l
+    uint16_t *planesL = nullptr;    // natural order [part][z][y][x][kp], sized for level d - 1
+    size_t partL_elems = 0;
     int bx[9], by[9], bz[9];
     int groups[9], per_group[9];    // offset groups per tile (small levels run more CTAs)
+    int mgroups[9], mper_group[9];  // the same for the M2M into level l
     float *Lpart = nullptr;         // partial sums of the offset groups
-    float *s32 = nullptr;           // [kp] s(n,m) per real coefficient (fp16 split)
+    float *s32 = nullptr;           // [nc] s(n,m) per real coefficient (fp16 split)
+    float *s32inv = nullptr;        // [nc] 1 / s(n,m)
     double *s64 = nullptr;
     unsigned *amax = nullptr;       // [9] bits of the largest |M^ s| per level (fp16 split)
+    unsigned *amaxL = nullptr;      // [9] bits of the largest |L^ / s| per level
 };
 
 struct TcArgs {
+    int mode;               // 0: M2L (+ fused L2L), 1: M2M
     int np, bx, by, bz, rows, tiles_x, tiles_y, tiles_per_class;
     int nc, npad, kchunks, ksteps, stages;
-    int groups, per_group;  // the 189 offsets split over `groups` CTAs per tile (small levels)
+    int groups, per_group;  // the offsets split over `groups` CTAs per tile (small levels)
+    int n_off;              // offsets: 189 (+1 with the fused L2L) or 8 (M2M)
+    int src_np2;            // M2M: halo'd side of the child level's planes
+    int out_np;             // M2M: class-layout side of the parent level (0 at level 0)
     uint32_t idesc;
-    float *L;
-    float *Lpart;           // [groups][8 np^3][nc] partial sums when groups > 1
-    const float *post;      // fp16 split: s(j) per output coefficient, else null
-    const unsigned *amax;   // fp16 split: the level's largest |M^ s| (gM follows from it)
+    float *L;               // output level array (L of the level, or M of the parent level)
+    float *Lpart;           // [groups][level cells][nc] partial sums when groups > 1
+    const float *post;      // fp16 split: s(j) (M2L) or 1 / s(j) (M2M) per output coefficient, else null
+    const unsigned *amax;   // fp16 split: largest |M^ s| of the A planes (gM follows from it)
+    const unsigned *amaxL;  // fused L2L: largest |L^ / s| of the parent planes (gL), else null
     int *err;
 };
 
@@ -260,13 +276,24 @@ struct Products<2, 3> {
     __device__ static constexpr int b(int k) { return k == 1 ? 1 : k == 3 ? 2 : 0; }
 };
 
-// PA, PB: bf16 terms of the A (moments) and B (operator) operands;
-// NCH: output coefficients / 16 (the accumulator width held in registers).
+// One CTA sums, for 128 target rows, the products of a list of offsets:
+//   mode 0 (M2L): the 189 interaction-list offsets of parity class `cls`, A
+//     from the halo'd source planes of the level; with fused L2L (fp16 split)
+//     a 190th offset whose A is the parent level's local expansion at the
+//     targets' parents (natural-order planes) and whose B is the L2L operator
+//     of child octant `cls`; its accumulator is scaled by gM / gL.
+//   mode 1 (M2M): the 8 child octants o, A from class plane o of the child
+//     level's planes at the targets' own coordinates, B the M2M operator of o;
+//     targets are a brick of the parent level in natural order, written to its
+//     class layout.
+// PA, PB: terms of the A and B operands; NCH: output coefficients / 16 (the
+// accumulator width held in registers).
 template <int PA, int PB, int NCH>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_m2l_tc(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
              const __grid_constant__ CUtensorMap mA2, const __grid_constant__ CUtensorMap mB0,
-             const __grid_constant__ CUtensorMap mB1, const __grid_constant__ CUtensorMap mB2, TcArgs a)
+             const __grid_constant__ CUtensorMap mB1, const __grid_constant__ CUtensorMap mB2,
+             const __grid_constant__ CUtensorMap mL0, const __grid_constant__ CUtensorMap mL1, TcArgs a)
 {
     extern __shared__ uint8_t smem_dyn[];
     __shared__ __align__(8) uint64_t bar_full[TC_MAX_STAGES];
@@ -285,13 +312,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const uint32_t stage_bytes = PA * stageA + PB * stageB;
     const uint32_t tx_bytes = (uint32_t)(PA * a.rows * ROW_BYTES) + PB * stageB;
 
-    // the 8 parity classes of one brick run side by side: CTAs resident at the
-    // same time then read overlapping shifted bricks, which stay in L2
+    // M2L: the 8 parity classes of one brick run side by side, so CTAs resident
+    // at the same time read overlapping shifted bricks, which stay in L2
     const int grp = blockIdx.x % a.groups;
-    const int cls = (blockIdx.x / a.groups) & 7;
-    const int tile = (blockIdx.x / a.groups) >> 3;
+    const int cls = a.mode == 0 ? (blockIdx.x / a.groups) & 7 : 0;
+    const int tile = a.mode == 0 ? (blockIdx.x / a.groups) >> 3 : blockIdx.x / a.groups;
     const int o_begin = grp * a.per_group;
-    const int o_end = o_begin + a.per_group < NUM_IL ? o_begin + a.per_group : NUM_IL;
+    const int o_end = o_begin + a.per_group < a.n_off ? o_begin + a.per_group : a.n_off;
     const int nloc = o_end > o_begin ? o_end - o_begin : 0;
     const int x0 = (tile % a.tiles_x) * a.bx;
     const int y0 = ((tile / a.tiles_x) % a.tiles_y) * a.by;
@@ -330,44 +357,53 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (lane == 0) {
             // ---------------- producer: TMA loads of the A brick and the B operator
             const CUtensorMap *mA[3] = {&mA0, &mA1, &mA2};
+            const CUtensorMap *mL[3] = {&mL0, &mL1, &mL1};
             const CUtensorMap *mB[3] = {&mB0, &mB1, &mB2};
             int it = 0, s = 0;
             uint32_t round = 0;
-            int oi = -1;  // position of the offset in the interaction-list order
             bool ok = true;
-            for (int dz = -2 - cz; dz <= 3 - cz && ok; ++dz)
-                for (int dy = -2 - cy; dy <= 3 - cy && ok; ++dy)
-                    for (int dx = -2 - cx; dx <= 3 - cx && ok; ++dx) {
-                        if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1 && dz >= -1 && dz <= 1) continue;
-                        ++oi;
-                        if (oi < o_begin || oi >= o_end) continue;
-                        const int sx = cx + dx, sy = cy + dy, sz = cz + dz;
-                        const int scls = (sx & 1) | ((sy & 1) << 1) | ((sz & 1) << 2);
-                        const int hx = x0 + (sx >> 1) + 1, hy = y0 + (sy >> 1) + 1;
-                        const int hz = scls * np2 + z0 + (sz >> 1) + 1;
-                        const int slot = off_slot(dx, dy, dz);
-                        for (int kc = 0; kc < a.kchunks; ++kc) {
-                            if (it >= a.stages &&
-                                !mbar_wait(smem_u32(&bar_empty[s]), (round & 1u) ^ 1u, abort_flag)) {
-                                ok = false;
-                                break;
-                            }
-                            const uint32_t full = smem_u32(&bar_full[s]);
-                            mbar_expect_tx(full, tx_bytes);
-                            const uint32_t base = smem0 + (uint32_t)s * stage_bytes;
-#pragma unroll
-                            for (int i = 0; i < PA; ++i)
-                                tma_load_4d(base + i * stageA, mA[i], full, kc * KCHUNK, hx, hy, hz);
-#pragma unroll
-                            for (int j = 0; j < PB; ++j)
-                                tma_load_3d(base + PA * stageA + j * stageB, mB[j], full, kc * KCHUNK, 0, slot);
-                            ++it;
-                            if (++s == a.stages) {
-                                s = 0;
-                                ++round;
-                            }
-                        }
+            // all K chunks of one offset: A from maps `src` at (c1, c2, c3), B at `slot`
+            auto load_offset = [&](const CUtensorMap *const *src, int c1, int c2, int c3, int slot) {
+                for (int kc = 0; kc < a.kchunks && ok; ++kc) {
+                    if (it >= a.stages && !mbar_wait(smem_u32(&bar_empty[s]), (round & 1u) ^ 1u, abort_flag)) {
+                        ok = false;
+                        break;
                     }
+                    const uint32_t full = smem_u32(&bar_full[s]);
+                    mbar_expect_tx(full, tx_bytes);
+                    const uint32_t base = smem0 + (uint32_t)s * stage_bytes;
+#pragma unroll
+                    for (int i = 0; i < PA; ++i) tma_load_4d(base + i * stageA, src[i], full, kc * KCHUNK, c1, c2, c3);
+#pragma unroll
+                    for (int j = 0; j < PB; ++j)
+                        tma_load_3d(base + PA * stageA + j * stageB, mB[j], full, kc * KCHUNK, 0, slot);
+                    ++it;
+                    if (++s == a.stages) {
+                        s = 0;
+                        ++round;
+                    }
+                }
+            };
+            if (a.mode == 0) {
+                int oi = -1;  // position of the offset in the interaction-list order
+                for (int dz = -2 - cz; dz <= 3 - cz && ok; ++dz)
+                    for (int dy = -2 - cy; dy <= 3 - cy && ok; ++dy)
+                        for (int dx = -2 - cx; dx <= 3 - cx && ok; ++dx) {
+                            if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1 && dz >= -1 && dz <= 1) continue;
+                            ++oi;
+                            if (oi < o_begin || oi >= o_end) continue;
+                            const int sx = cx + dx, sy = cy + dy, sz = cz + dz;
+                            const int scls = (sx & 1) | ((sy & 1) << 1) | ((sz & 1) << 2);
+                            load_offset(mA, x0 + (sx >> 1) + 1, y0 + (sy >> 1) + 1, scls * np2 + z0 + (sz >> 1) + 1,
+                                        off_slot(dx, dy, dz));
+                        }
+                // fused L2L: the parents' local expansions (natural order, no halo)
+                if (ok && a.n_off > NUM_IL && NUM_IL >= o_begin && NUM_IL < o_end)
+                    load_offset(mL, x0, y0, z0, NOFF + 8 + cls);
+            } else {
+                for (int o = o_begin; o < o_end && ok; ++o)
+                    load_offset(mA, x0 + 1, y0 + 1, o * a.src_np2 + z0 + 1, NOFF + o);
+            }
             produced_sh = it;
             if (!ok) {
                 abort_sh = 1;
@@ -429,6 +465,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         // ---------------- epilogue warps: drain each offset's accumulator into FP32 registers
         const int quad = warp & 3;
         const int row = quad * 32 + lane;
+        // fused L2L offset: its A planes carry the gain gL instead of gM
+        const float l2l_fac =
+            a.amaxL ? pow2f(gain_m_exp(*a.amax) - gain_m_exp(*a.amaxL)) : 1.f;
         float Lr[NCH * 16];
 #pragma unroll
         for (int i = 0; i < NCH * 16; ++i) Lr[i] = 0.f;
@@ -441,6 +480,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 break;
             }
             fence_after();
+            const float fac = (a.mode == 0 && o_begin + o == NUM_IL) ? l2l_fac : 1.f;
             const uint32_t taddr = tmem + (uint32_t)(acc * 256) + ((uint32_t)(quad * 32) << 16);
 #pragma unroll
             for (int c = 0; c < NCH; ++c) {
@@ -448,7 +488,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 tmem_ld16(taddr + (uint32_t)(c * 16), r);
                 tmem_wait_ld();
 #pragma unroll
-                for (int j = 0; j < 16; ++j) Lr[c * 16 + j] += __uint_as_float(r[j]);
+                for (int j = 0; j < 16; ++j) Lr[c * 16 + j] = fmaf(__uint_as_float(r[j]), fac, Lr[c * 16 + j]);
             }
             fence_before();
             __syncwarp();
@@ -460,11 +500,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         } else if (row < a.rows) {
             const int tx = row % a.bx, ty = (row / a.bx) % a.by, tz = row / (a.bx * a.by);
             const int64_t np = a.np;
-            const int64_t lin = (x0 + tx) + np * ((y0 + ty) + np * (int64_t)(z0 + tz));
-            float *dst = a.groups == 1 ? a.L + ((int64_t)cls * np * np * np + lin) * a.nc
-                                       : a.Lpart + (((int64_t)grp * 8 + cls) * np * np * np + lin) * a.nc;
+            int64_t idx, level_cells;
+            if (a.mode == 0) {
+                idx = (int64_t)cls * np * np * np + (x0 + tx) + np * ((y0 + ty) + np * (int64_t)(z0 + tz));
+                level_cells = 8 * np * np * np;
+            } else {
+                // natural coordinates of the parent level -> its class layout
+                const int px = x0 + tx, py = y0 + ty, pz = z0 + tz;
+                const int64_t on = a.out_np;
+                idx = on == 0 ? 0
+                              : (int64_t)((px & 1) | ((py & 1) << 1) | ((pz & 1) << 2)) * on * on * on + (px >> 1) +
+                                    on * ((py >> 1) + on * (int64_t)(pz >> 1));
+                level_cells = np * np * np;
+            }
+            float *dst = (a.groups == 1 ? a.L : a.Lpart + (int64_t)grp * level_cells * a.nc) + idx * a.nc;
             if (a.post) {
-                // undo the balancing: L^ = L~ s(j) / (gM gT)
+                // undo the balancing: x^ = x~ post(j) / (gM gT)
                 const float g = pow2f(-gain_m_exp(*a.amax) - GAIN_T_EXP);
 #pragma unroll
                 for (int i = 0; i < NCH * 16; ++i)
@@ -561,20 +612,61 @@ __global__ void k_split_halo(const float *__restrict__ M, int np, int nc, int kp
     }
 }
 
-// FP64 input-major operators T[slot][k][j] -> split B tables [part][slot][j][k]
-// (K-major, rows kp wide).  fp16: balanced, T~ = T / (s(k) s(j)) gT.
+// FP32 class-layout local expansion of level `lev` (side n = 2^lev) -> fp16
+// split planes in natural order [part][z][y][x][k], balanced L~ = L^ / s(k) gL
+// (the A operand of the fused L2L).  One warp per cell.
+__global__ void k_split_L(const float *__restrict__ L, int lev, int nc, int kp, const float *__restrict__ sinv,
+                          const unsigned *__restrict__ amaxL, uint16_t *__restrict__ planes, size_t part_elems)
+{
+    const int n = 1 << lev, h = n >> 1;
+    const int64_t ncell = (int64_t)n * n * n;
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const float g = pow2f(gain_m_exp(*amaxL));
+    for (int64_t cell = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); cell < ncell; cell += warps) {
+        const int x = (int)(cell % n), y = (int)((cell / n) % n), z = (int)(cell / ((int64_t)n * n));
+        const int64_t src = lev == 0 ? 0
+                                     : (int64_t)((x & 1) | ((y & 1) << 1) | ((z & 1) << 2)) * h * h * h + (x >> 1) +
+                                           (int64_t)h * ((y >> 1) + (int64_t)h * (z >> 1));
+        const float *row = L + src * nc;
+        uint16_t *out = planes + cell * kp;
+        for (int k = lane; k < kp; k += 32) {
+            const float v = k < nc ? row[k] * (__ldg(sinv + k) * g) : 0.f;
+            split_terms<true>(v, 2, out + k, part_elems);
+        }
+    }
+}
+
+// FP64 operators -> split B tables [part][slot][j][k] (K-major, rows kp wide):
+// slots < NOFF the M2L operators T[slot][k][j] (input-major), then per child
+// octant o the M2M operator (M2M[j][o nc + k], parent output j) and the L2L
+// operator (L2L[o nc + j][k], child output j).  fp16: balanced with gT,
+//   M2L  T~ = T / (s(k) s(j)),  M2M  S~ = S s(j) / s(k),  L2L  U~ = U s(k) / s(j);
+// bf16: the translation slots stay zero (unused).
 template <bool F16>
-__global__ void k_split_ops(const double *__restrict__ T, int nc, int npad, int kp, int parts,
+__global__ void k_split_ops(const double *__restrict__ T, const double *__restrict__ m2m,
+                            const double *__restrict__ l2l, int nc, int npad, int kp, int parts,
                             const double *__restrict__ s, uint16_t *__restrict__ ops, size_t part_elems)
 {
-    const int64_t total = (int64_t)NOFF * npad * kp;
+    const int64_t total = (int64_t)NSLOT * npad * kp;
     const double gT = (double)pow2f(GAIN_T_EXP);
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int k = (int)(e % kp);
         const int j = (int)((e / kp) % npad);
         const int slot = (int)(e / ((int64_t)kp * npad));
-        double r = (j < nc && k < nc) ? T[((int64_t)slot * nc + k) * nc + j] : 0.0;
-        if (F16 && j < nc && k < nc) r = r / (s[k] * s[j]) * gT;
+        double r = 0.0;
+        if (j < nc && k < nc) {
+            if (slot < NOFF) {
+                r = T[((int64_t)slot * nc + k) * nc + j];
+                if (F16) r = r / (s[k] * s[j]) * gT;
+            } else if (F16 && slot < SLOT_L2L) {
+                const int o = slot - SLOT_M2M;
+                r = m2m[(int64_t)j * 8 * nc + o * nc + k] * s[j] / s[k] * gT;
+            } else if (F16) {
+                const int o = slot - SLOT_L2L;
+                r = l2l[((int64_t)o * nc + j) * nc + k] * s[k] / s[j] * gT;
+            }
+        }
         for (int i = 0; i < parts; ++i) {
             if (F16) {
                 const __half t = __float2half_rn((float)r);
@@ -631,7 +723,8 @@ size_t tc_smem_bytes(int pa, int pb, int npad)
     return need < 120 * 1024 ? 120 * 1024 : need;
 }
 
-typedef void (*TcKernel)(CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap, TcArgs);
+typedef void (*TcKernel)(CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap,
+                         CUtensorMap, TcArgs);
 
 template <int PA, int PB>
 TcKernel pick_kernel_n(int nch)
@@ -655,11 +748,63 @@ TcKernel pick_kernel(int pa, int pb, int nch)
     return nullptr;
 }
 
+#define TRY_TC(x)                          \
+    do {                                   \
+        fmm_status st_ = (x);              \
+        if (st_ != FMM_OK) return st_;     \
+    } while (0)
+
+// offsets split over `want` CTAs per tile: per_group offsets each
+void split_offsets(int n_off, int tiles, int max_groups, int &groups, int &per_group)
+{
+    int want = (2 * 152 + tiles - 1) / tiles;  // enough CTAs to fill the GPU twice
+    if (want < 1) want = 1;
+    if (want > max_groups) want = max_groups;
+    per_group = (n_off + want - 1) / want;
+    groups = (n_off + per_group - 1) / per_group;
+}
+
+fmm_status encode_planes(PFN_cuTensorMapEncodeTiled_v12000 enc, CUtensorMap *map, CUtensorMapDataType dt, void *base,
+                         int kp, int64_t d1, int64_t d2, int64_t d3, int b1, int b2, int b3)
+{
+    cuuint64_t dims[4] = {(cuuint64_t)kp, (cuuint64_t)d1, (cuuint64_t)d2, (cuuint64_t)d3};
+    cuuint64_t strides[3] = {(cuuint64_t)kp * 2, (cuuint64_t)kp * 2 * d1, (cuuint64_t)kp * 2 * d1 * d2};
+    cuuint32_t box[4] = {KCHUNK, (cuuint32_t)b1, (cuuint32_t)b2, (cuuint32_t)b3};
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    return enc(map, dt, 4, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS
+               ? FMM_OK
+               : FMM_ERR_INTERNAL;
+}
+
+void fill_common(const Plan &P, const TcState *S, int pa, int pb, TcArgs &a)
+{
+    a.nc = P.nc;
+    a.npad = S->npad;
+    a.kchunks = (S->kp + KCHUNK - 1) / KCHUNK;
+    a.ksteps = (P.nc + 15) / 16;
+    a.stages = tc_stages(pa, pb, S->npad);
+    // instruction descriptor: FP32 accumulator, A and B both bf16 (format 1) or both fp16 (format 0),
+    // K-major, N >> 3 at bit 17, M >> 4 at bit 24
+    const uint32_t ab = S->f16 ? 0u : 1u;
+    a.idesc = (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(S->npad >> 3) << 17) | ((uint32_t)(TC_ROWS >> 4) << 24);
+    a.Lpart = S->Lpart;
+    a.err = P.d_err;
+    a.src_np2 = 0;
+    a.out_np = 0;
+    a.amaxL = nullptr;
+}
+
 }  // namespace
 
 bool tc_available(const Plan &P, int level)
 {
     return P.tc != nullptr && level >= 1 && level <= P.d;
+}
+
+bool tc_translations(const Plan &P)
+{
+    return P.tc != nullptr && ((const TcState *)P.tc)->f16;
 }
 
 fmm_status tc_prepare(Plan &P)
@@ -682,7 +827,7 @@ fmm_status tc_prepare(Plan &P)
     if (S->f16) {
         // s(n,m) = sqrt((n+m)! (n-m)!) per real coefficient
         double h_s[(TC_PMAX + 1) * (TC_PMAX + 1)];
-        float h_s32[(TC_PMAX + 1) * (TC_PMAX + 1)];
+        float h_s32[(TC_PMAX + 1) * (TC_PMAX + 1)], h_inv[(TC_PMAX + 1) * (TC_PMAX + 1)];
         for (int n = 0; n <= P.p; ++n)
             for (int m = 0; m <= n; ++m) {
                 double f = 1.0;
@@ -693,25 +838,31 @@ fmm_status tc_prepare(Plan &P)
                 h_s[re] = v;
                 if (m > 0) h_s[re + 1] = v;
             }
-        for (int k = 0; k < P.nc; ++k) h_s32[k] = (float)h_s[k];
+        for (int k = 0; k < P.nc; ++k) {
+            h_s32[k] = (float)h_s[k];
+            h_inv[k] = (float)(1.0 / h_s[k]);
+        }
         FMM_CUDA_TRY(cudaMalloc(&S->s64, sizeof(double) * P.nc));
         FMM_CUDA_TRY(cudaMalloc(&S->s32, sizeof(float) * P.nc));
+        FMM_CUDA_TRY(cudaMalloc(&S->s32inv, sizeof(float) * P.nc));
         FMM_CUDA_TRY(cudaMalloc(&S->amax, sizeof(unsigned) * 9));
+        FMM_CUDA_TRY(cudaMalloc(&S->amaxL, sizeof(unsigned) * 9));
         FMM_CUDA_TRY(cudaMemcpyAsync(S->s64, h_s, sizeof(double) * P.nc, cudaMemcpyHostToDevice, P.stream));
         FMM_CUDA_TRY(cudaMemcpyAsync(S->s32, h_s32, sizeof(float) * P.nc, cudaMemcpyHostToDevice, P.stream));
+        FMM_CUDA_TRY(cudaMemcpyAsync(S->s32inv, h_inv, sizeof(float) * P.nc, cudaMemcpyHostToDevice, P.stream));
     }
     // operator tables
-    S->ops_part_elems = (size_t)NOFF * S->npad * S->kp;
+    S->ops_part_elems = (size_t)NSLOT * S->npad * S->kp;
     FMM_CUDA_TRY(cudaMalloc(&S->ops, sizeof(uint16_t) * S->ops_part_elems * S->parts));
     if (S->f16)
-        k_split_ops<true><<<1216, 256, 0, P.stream>>>(P.tab.Top64, P.nc, S->npad, S->kp, S->parts, S->s64, S->ops,
-                                                      S->ops_part_elems);
+        k_split_ops<true><<<1216, 256, 0, P.stream>>>(P.tab.Top64, P.tab.m2m64, P.tab.l2l64, P.nc, S->npad, S->kp,
+                                                      S->parts, S->s64, S->ops, S->ops_part_elems);
     else
-        k_split_ops<false><<<1216, 256, 0, P.stream>>>(P.tab.Top64, P.nc, S->npad, S->kp, S->parts, nullptr,
-                                                       S->ops, S->ops_part_elems);
+        k_split_ops<false><<<1216, 256, 0, P.stream>>>(P.tab.Top64, nullptr, nullptr, P.nc, S->npad, S->kp, S->parts,
+                                                       nullptr, S->ops, S->ops_part_elems);
     FMM_LAUNCH_CHECK(P);
     for (int j = 0; j < S->parts; ++j) {
-        cuuint64_t dims[3] = {(cuuint64_t)S->kp, (cuuint64_t)S->npad, (cuuint64_t)NOFF};
+        cuuint64_t dims[3] = {(cuuint64_t)S->kp, (cuuint64_t)S->npad, (cuuint64_t)NSLOT};
         cuuint64_t strides[2] = {(cuuint64_t)S->kp * 2, (cuuint64_t)S->kp * 2 * S->npad};
         cuuint32_t box[3] = {KCHUNK, (cuuint32_t)S->npad, 1};
         cuuint32_t es[3] = {1, 1, 1};
@@ -721,6 +872,12 @@ fmm_status tc_prepare(Plan &P)
             return FMM_ERR_INTERNAL;
     }
     for (int j = S->parts; j < 3; ++j) S->mapB[j] = S->mapB[0];  // unused kernel parameters
+    // natural-order planes of the parent-level local expansions (fused L2L), sized for level d - 1
+    if (S->f16) {
+        const int64_t n = (int64_t)1 << (P.d - 1);
+        S->partL_elems = (size_t)n * n * n * S->kp;
+        FMM_CUDA_TRY(cudaMalloc(&S->planesL, sizeof(uint16_t) * S->partL_elems * 2));
+    }
     // source planes per level
     size_t lpart_elems = 0;
     for (int l = 1; l <= P.d; ++l) {
@@ -731,27 +888,30 @@ fmm_status tc_prepare(Plan &P)
         S->bz[l] = tile_dim(np, TC_ROWS / (S->bx[l] * S->by[l]));
         S->part_elems[l] = (size_t)8 * np2 * np2 * np2 * S->kp;
         FMM_CUDA_TRY(cudaMalloc(&S->planes[l], sizeof(uint16_t) * S->part_elems[l] * S->parts));
-        for (int i = 0; i < S->parts; ++i) {
-            cuuint64_t dims[4] = {(cuuint64_t)S->kp, (cuuint64_t)np2, (cuuint64_t)np2, (cuuint64_t)(8 * np2)};
-            cuuint64_t strides[3] = {(cuuint64_t)S->kp * 2, (cuuint64_t)S->kp * 2 * np2,
-                                     (cuuint64_t)S->kp * 2 * np2 * np2};
-            cuuint32_t box[4] = {KCHUNK, (cuuint32_t)S->bx[l], (cuuint32_t)S->by[l], (cuuint32_t)S->bz[l]};
-            cuuint32_t es[4] = {1, 1, 1, 1};
-            if (enc(&S->mapA[l][i], dt, 4, S->planes[l] + i * S->part_elems[l], dims, strides, box, es,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-                return FMM_ERR_INTERNAL;
-        }
+        for (int i = 0; i < S->parts; ++i)
+            TRY_TC(encode_planes(enc, &S->mapA[l][i], dt, S->planes[l] + i * S->part_elems[l], S->kp, np2, np2,
+                                 8 * np2, S->bx[l], S->by[l], S->bz[l]));
         for (int i = S->parts; i < 3; ++i) S->mapA[l][i] = S->mapA[l][0];
-        // enough CTAs to fill the GPU twice: split the 189 offsets when tiles are few
-        int tiles = 8 * (np / S->bx[l]) * (np / S->by[l]) * (np / S->bz[l]);
-        int want = (2 * 152 + tiles - 1) / tiles;
-        if (want < 1) want = 1;
-        if (want > 27) want = 27;
-        S->per_group[l] = (NUM_IL + want - 1) / want;
-        S->groups[l] = (NUM_IL + S->per_group[l] - 1) / S->per_group[l];
+        if (S->f16) {
+            // L of level l - 1 (side np) in natural order, boxed like the level-l bricks; all levels share
+            // one buffer, used one level at a time
+            for (int i = 0; i < 2; ++i)
+                TRY_TC(encode_planes(enc, &S->mapL[l][i], dt, S->planesL + (size_t)i * np * np * np * S->kp, S->kp,
+                                     np, np, np, S->bx[l], S->by[l], S->bz[l]));
+        } else {
+            S->mapL[l][0] = S->mapL[l][1] = S->mapA[l][0];  // unused kernel parameters
+        }
+        const int tiles = 8 * (np / S->bx[l]) * (np / S->by[l]) * (np / S->bz[l]);
+        split_offsets(NUM_IL + (S->f16 ? 1 : 0), tiles, 27, S->groups[l], S->per_group[l]);
         if (S->groups[l] > 1) {
             size_t need = (size_t)S->groups[l] * 8 * np * np * np * P.nc;
+            if (need > lpart_elems) lpart_elems = need;
+        }
+        // M2M into level l - 1 (natural side np, bricks of the level-l planes)
+        const int mtiles = (np / S->bx[l]) * (np / S->by[l]) * (np / S->bz[l]);
+        split_offsets(8, mtiles, 8, S->mgroups[l - 1], S->mper_group[l - 1]);
+        if (S->f16 && S->mgroups[l - 1] > 1) {
+            size_t need = (size_t)S->mgroups[l - 1] * np * np * np * P.nc;
             if (need > lpart_elems) lpart_elems = need;
         }
     }
@@ -770,7 +930,68 @@ fmm_status tc_prepare(Plan &P)
     return FMM_OK;
 }
 
-fmm_status launch_m2l_tc(Plan &P, int l, bool precise)
+// fp16 split: largest |M^ s| and the balanced halo planes of M[l]
+fmm_status tc_split_moments(Plan &P, int l)
+{
+    TcState *S = (TcState *)P.tc;
+    if (!S || !S->f16 || l < 1 || l > P.d) return FMM_ERR_INTERNAL;
+    const int np = 1 << (l - 1);
+    const int64_t np2 = np + 2;
+    const int64_t ncell = (int64_t)8 * np * np * np;
+    const int64_t nhalo = 8 * np2 * np2 * np2;
+    FMM_CUDA_TRY(cudaMemsetAsync(S->amax + l, 0, sizeof(unsigned), P.stream));
+    k_absmax<<<(unsigned)((ncell + 7) / 8 < 1216 ? (ncell + 7) / 8 : 1216), 256, 0, P.stream>>>(
+        (const float *)P.M[l], ncell, P.nc, S->s32, S->amax + l);
+    FMM_LAUNCH_CHECK(P);
+    k_split_halo<true><<<(unsigned)((nhalo + 7) / 8 < 4864 ? (nhalo + 7) / 8 : 4864), 256, 0, P.stream>>>(
+        (const float *)P.M[l], np, P.nc, S->kp, 2, S->s32, S->amax + l, S->planes[l], S->part_elems[l]);
+    FMM_LAUNCH_CHECK(P);
+    return FMM_OK;
+}
+
+// fp16 split: M2M into level l (< d) from the split planes of level l + 1
+fmm_status launch_m2m_tc(Plan &P, int l)
+{
+    TcState *S = (TcState *)P.tc;
+    if (!S || !S->f16 || l < 0 || l >= P.d) return FMM_ERR_INTERNAL;
+    const int src = l + 1;
+    const int n = 1 << l;  // natural side of level l = parent side of the level-(l+1) planes
+    TcArgs a;
+    fill_common(P, S, S->pa, S->pb, a);
+    a.mode = 1;
+    a.np = n;
+    a.bx = S->bx[src];
+    a.by = S->by[src];
+    a.bz = S->bz[src];
+    a.rows = a.bx * a.by * a.bz;
+    a.tiles_x = n / a.bx;
+    a.tiles_y = n / a.by;
+    a.tiles_per_class = a.tiles_x * a.tiles_y * (n / a.bz);
+    a.groups = S->mgroups[l];
+    a.per_group = S->mper_group[l];
+    a.n_off = 8;
+    a.src_np2 = n + 2;
+    a.out_np = l == 0 ? 0 : n >> 1;
+    a.L = (float *)P.M[l];
+    a.post = S->s32inv;
+    a.amax = S->amax + src;
+    TcKernel k = pick_kernel(S->pa, S->pb, S->npad / 16);
+    if (!k) return FMM_ERR_INTERNAL;
+    const unsigned grid = (unsigned)a.tiles_per_class * (unsigned)a.groups;
+    k<<<grid, TC_THREADS, tc_smem_bytes(S->pa, S->pb, S->npad), P.stream>>>(
+        S->mapA[src][0], S->mapA[src][1], S->mapA[src][2], S->mapB[0], S->mapB[1], S->mapB[2], S->mapA[src][0],
+        S->mapA[src][0], a);
+    FMM_LAUNCH_CHECK(P);
+    if (a.groups > 1) {
+        const int64_t cnt = (int64_t)n * n * n * P.nc;
+        k_group_sum<<<(unsigned)((cnt + 255) / 256 < 2048 ? (cnt + 255) / 256 : 2048), 256, 0, P.stream>>>(
+            cnt, a.groups, S->Lpart, a.L);
+        FMM_LAUNCH_CHECK(P);
+    }
+    return FMM_OK;
+}
+
+fmm_status launch_m2l_tc(Plan &P, int l, bool precise, bool split)
 {
     TcState *S = (TcState *)P.tc;
     if (!S) return FMM_ERR_INTERNAL;
@@ -779,22 +1000,30 @@ fmm_status launch_m2l_tc(Plan &P, int l, bool precise)
     const int pb = precise && !S->f16 ? 3 : S->pb;
     int np = 1 << (l - 1);
     int64_t np2 = np + 2;
-    const int64_t nhalo = 8 * np2 * np2 * np2;
-    unsigned blocks = (unsigned)((nhalo + 7) / 8 < 4864 ? (nhalo + 7) / 8 : 4864);
     if (S->f16) {
-        FMM_CUDA_TRY(cudaMemsetAsync(S->amax + l, 0, sizeof(unsigned), P.stream));
-        const int64_t ncell = (int64_t)8 * np * np * np;
-        k_absmax<<<(unsigned)((ncell + 7) / 8 < 1216 ? (ncell + 7) / 8 : 1216), 256, 0, P.stream>>>(
-            (const float *)P.M[l], ncell, P.nc, S->s32, S->amax + l);
+        if (split) {
+            fmm_status st = tc_split_moments(P, l);
+            if (st != FMM_OK) return st;
+        }
+        // parent-level local expansion for the fused L2L
+        const int64_t ncl = (int64_t)np * np * np;
+        FMM_CUDA_TRY(cudaMemsetAsync(S->amaxL + l - 1, 0, sizeof(unsigned), P.stream));
+        k_absmax<<<(unsigned)((ncl + 7) / 8 < 1216 ? (ncl + 7) / 8 : 1216), 256, 0, P.stream>>>(
+            (const float *)P.L[l - 1], ncl, P.nc, S->s32inv, S->amaxL + l - 1);
         FMM_LAUNCH_CHECK(P);
-        k_split_halo<true><<<blocks, 256, 0, P.stream>>>((const float *)P.M[l], np, P.nc, S->kp, pa, S->s32,
-                                                         S->amax + l, S->planes[l], S->part_elems[l]);
+        k_split_L<<<(unsigned)((ncl + 7) / 8 < 1216 ? (ncl + 7) / 8 : 1216), 256, 0, P.stream>>>(
+            (const float *)P.L[l - 1], l - 1, P.nc, S->kp, S->s32inv, S->amaxL + l - 1, S->planesL,
+            (size_t)ncl * S->kp);
+        FMM_LAUNCH_CHECK(P);
     } else {
-        k_split_halo<false><<<blocks, 256, 0, P.stream>>>((const float *)P.M[l], np, P.nc, S->kp, pa, nullptr,
-                                                          nullptr, S->planes[l], S->part_elems[l]);
+        const int64_t nhalo = 8 * np2 * np2 * np2;
+        k_split_halo<false><<<(unsigned)((nhalo + 7) / 8 < 4864 ? (nhalo + 7) / 8 : 4864), 256, 0, P.stream>>>(
+            (const float *)P.M[l], np, P.nc, S->kp, pa, nullptr, nullptr, S->planes[l], S->part_elems[l]);
+        FMM_LAUNCH_CHECK(P);
     }
-    FMM_LAUNCH_CHECK(P);
     TcArgs a;
+    fill_common(P, S, pa, pb, a);
+    a.mode = 0;
     a.np = np;
     a.bx = S->bx[l];
     a.by = S->by[l];
@@ -803,29 +1032,21 @@ fmm_status launch_m2l_tc(Plan &P, int l, bool precise)
     a.tiles_x = np / a.bx;
     a.tiles_y = np / a.by;
     a.tiles_per_class = a.tiles_x * a.tiles_y * (np / a.bz);
-    a.nc = P.nc;
-    a.npad = S->npad;
-    a.kchunks = (S->kp + KCHUNK - 1) / KCHUNK;
-    a.ksteps = (P.nc + 15) / 16;
-    a.stages = tc_stages(pa, pb, S->npad);
-    // instruction descriptor: FP32 accumulator, A and B both bf16 (format 1) or both fp16 (format 0),
-    // K-major, N >> 3 at bit 17, M >> 4 at bit 24
-    const uint32_t ab = S->f16 ? 0u : 1u;
-    a.idesc = (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(S->npad >> 3) << 17) | ((uint32_t)(TC_ROWS >> 4) << 24);
-    a.L = (float *)P.L[l];
-    a.Lpart = S->Lpart;
-    a.post = S->f16 ? S->s32 : nullptr;
-    a.amax = S->f16 ? S->amax + l : nullptr;
     a.groups = S->groups[l];
     a.per_group = S->per_group[l];
-    a.err = P.d_err;
+    a.n_off = NUM_IL + (S->f16 ? 1 : 0);
+    a.L = (float *)P.L[l];
+    a.post = S->f16 ? S->s32 : nullptr;
+    a.amax = S->f16 ? S->amax + l : nullptr;
+    a.amaxL = S->f16 ? S->amaxL + l - 1 : nullptr;
     unsigned grid = 8u * (unsigned)a.tiles_per_class * (unsigned)a.groups;
     TcKernel k = pick_kernel(pa, pb, S->npad / 16);
     if (!k) return FMM_ERR_INTERNAL;
     const bool time_it = P.timings_on && l == P.d && P.ev_top[0] && !precise;
     if (time_it) cudaEventRecord(P.ev_top[0], P.stream);
     k<<<grid, TC_THREADS, tc_smem_bytes(pa, pb, S->npad), P.stream>>>(
-        S->mapA[l][0], S->mapA[l][1], S->mapA[l][2], S->mapB[0], S->mapB[1], S->mapB[2], a);
+        S->mapA[l][0], S->mapA[l][1], S->mapA[l][2], S->mapB[0], S->mapB[1], S->mapB[2], S->mapL[l][0],
+        S->mapL[l][1], a);
     FMM_LAUNCH_CHECK(P);
     if (time_it) {
         cudaEventRecord(P.ev_top[1], P.stream);
@@ -848,8 +1069,11 @@ void tc_free(Plan &P)
     cudaFree(S->ops);
     cudaFree(S->Lpart);
     cudaFree(S->s32);
+    cudaFree(S->s32inv);
     cudaFree(S->s64);
     cudaFree(S->amax);
+    cudaFree(S->amaxL);
+    cudaFree(S->planesL);
     delete S;
     P.tc = nullptr;
 }

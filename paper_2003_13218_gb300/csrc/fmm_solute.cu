@@ -627,7 +627,7 @@ fmm_status solute_sparse_t(Plan &P, SoluteScratch &S, int nu)
     for (int l = 1; l <= LD; ++l) {
         st = tc_available(P, l) ? launch_m2l_tc(P, l, true) : launch_m2l_simt(P, l);
         if (st != FMM_OK) return st;
-        st = launch_l2l(P, l);
+        if (!(tc_available(P, l) && tc_translations(P))) st = launch_l2l(P, l);  // else fused
         if (st != FMM_OK) return st;
     }
     // sparse finer levels
