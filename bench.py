@@ -40,13 +40,13 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 # FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.070 GHz
 FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
-# DRAM bytes (read + write) of one level-6 tensor-core M2L launch of the na_1m
-# workload, from the ncu capture summarised in profiles/k_m2l_tc_na_1m_level6.md,
-# with the sha256 of the kernel's device code it was taken on: the value is
-# reported only while that code is unchanged.
+# DRAM bytes (read + write) of one level-6 tensor-core M2L launch (fp16x2
+# split, fused L2L) of the na_1m workload, from the ncu capture summarised in
+# profiles/k_m2l_tc_na_1m_level6.md, with the sha256 of the kernel's device
+# code it was taken on: the value is reported only while that code is unchanged.
 M2L_TRAFFIC = {"src": "paper_2003_13218_gb300/csrc/fmm_m2l_tc.cu",
-               "sha256": "cd50ff008fde69b58629c4c3b3c7a3c8f98194a1e965a69a44b687ddfe6d6e2c",
-               "workload": "na_1m", "level": 6, "bytes_per_launch": 13.593296e9 + 0.175873792e9}
+               "sha256": "299d5cba70bb9000b48727c55b5ffa40eed9dfc185178c3b5048dfab93db8a9d",
+               "workload": "na_1m", "level": 6, "split": "fp16x2", "bytes_per_launch": 721.219072e6 + 173.285120e6}
 KERNEL_BEGIN = "// ------------------------------------------------------------------ the kernel"
 KERNEL_END = "// ------------------------------------------------------------------ operand preparation"
 
@@ -264,7 +264,7 @@ def run_ours(args):
                 "kernel": "k_m2l_tc, level %d (one launch%s)" % (d, ", M2L + fused L2L" if fused else "")}
         traffic = None
         if (M2L_TRAFFIC and M2L_TRAFFIC["workload"] == args.workload and M2L_TRAFFIC["level"] == d
-                and kernel_sha(M2L_TRAFFIC["src"]) == M2L_TRAFFIC["sha256"]):
+                and M2L_TRAFFIC["split"] == args.split and kernel_sha(M2L_TRAFFIC["src"]) == M2L_TRAFFIC["sha256"]):
             traffic = M2L_TRAFFIC["bytes_per_launch"]
     else:
         flops, launch_ms = stage_flops, stage_ms

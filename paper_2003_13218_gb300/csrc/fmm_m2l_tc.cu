@@ -6,7 +6,7 @@
 //     L[t][j] = sum_{delta in IL(c)} sum_k M[t + delta][k] T_delta[k][j]
 // i.e. 189 dense products (128 x K) . (K x N):
 //   M dimension = 128 targets, N = (p+1)^2 output coefficients padded to 16,
-//   K = (p+1)^2 input coefficients padded to 16 (rows stored padded to 32).
+//   K = (p+1)^2 input coefficients padded to 16 (rows stored padded to a whole copy box).
 // The A operand of offset delta is the same brick shifted to class
 // (c + delta) & 1 and parent offset (c + delta) >> 1 in {-1, 0, 1}^3; the
 // source planes carry a one-cell periodic halo so that every TMA box lies
@@ -25,8 +25,10 @@
 // largest |M^ s|, put both operands' largest entries at 2^13..2^15, far below
 // fp16's 65504 and far above its subnormal range.
 //
-// The operand rows are stored (p+1)^2 padded to 32 wide (whole, aligned
-// 64-byte copy pieces), but the MMAs stop at K = (p+1)^2 padded to 16.
+// The operand rows are stored padded to whole copy boxes (32 K elements = 64
+// bytes for the bf16 splits, 64 = 128 bytes for the fp16 split, whose 2-term
+// stages still fit twice in shared memory and move in half as many requests),
+// but the MMAs stop at K = (p+1)^2 padded to 16.
 //
 // Accumulation.  The tensor core's FP32 accumulation rounds with a bias, which
 // over thousands of MMAs into one accumulator shows up at the 1e-5 level.  So
@@ -34,7 +36,7 @@
 // and the epilogue warps drain it and add it to the row held in FP32 registers
 // (round to nearest) while the tensor core works on the next offset.
 //
-// Roles (6 warps): warp 0 lane 0 issues TMA loads into a 3..6-stage ring, warp 1
+// Roles (6 warps): warp 0 lane 0 issues TMA loads into a 2..6-stage ring, warp 1
 // lane 0 issues tcgen05.mma, warps 2..5 drain TMEM (warp w reads TMEM lanes
 // 32 (w mod 4) .. +31, one target row per thread) and write the FP32 level
 // array.  Every mbarrier wait is bounded (globaltimer); on a timeout the
@@ -58,8 +60,10 @@ namespace {
 constexpr int TC_THREADS = 192;
 constexpr int TC_MAX_STAGES = 6;
 constexpr int TC_ROWS = 128;          // MMA M
-constexpr int KCHUNK = 32;            // 16-bit elements per 64-byte swizzled row
-constexpr int ROW_BYTES = 64;
+// Operand rows in shared memory are SW = 64 (bf16 splits) or 128 (fp16 split)
+// bytes wide, swizzled with the matching pattern: one copy box carries SW / 2
+// K elements of 128 (A) or npad (B) rows.
+constexpr int kchunk_of(int sw) { return sw / 2; }
 constexpr uint32_t TMEM_COLS = 512;   // two accumulators of up to 256 columns
 constexpr int TC_PMAX = 15;           // N = (p+1)^2 rounded to 16 must not exceed 256
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // 2 s
@@ -78,6 +82,7 @@ struct TcState {
     int pa = 0, pb = 0;             // terms of the plan's split
     int parts = 0;                  // terms stored (3 for the bf16 splits: the solute pass uses 3 x 3)
     int npad = 0, kp = 0;
+    int sw = 64;                    // bytes per swizzled operand row in shared memory
     uint16_t *planes[9] = {};       // bf16 or fp16 bit patterns
     size_t part_elems[9] = {};
     uint16_t *ops = nullptr;
@@ -208,16 +213,18 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map
         : "memory");
 }
 
-// tcgen05 shared-memory matrix descriptor: K-major, 64-byte swizzle,
-// 8-row groups 512 bytes apart (stride byte offset), version field 1.
-__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr)
+// tcgen05 shared-memory matrix descriptor: K-major, SW-byte swizzle (layout
+// code 4 for 64 bytes, 2 for 128 bytes), 8-row groups 8 SW bytes apart
+// (stride byte offset), version field 1.
+template <int SW>
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr)
 {
     uint64_t d = 0;
     d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-    d |= (uint64_t)1 << 16;                       // leading byte offset (unused for swizzled K-major)
-    d |= (uint64_t)((512u >> 4) & 0x3FFFu) << 32; // stride byte offset
-    d |= (uint64_t)1 << 46;                       // descriptor version
-    d |= (uint64_t)4 << 61;                       // 64-byte swizzle
+    d |= (uint64_t)1 << 16;                              // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(((8u * SW) >> 4) & 0x3FFFu) << 32;   // stride byte offset
+    d |= (uint64_t)1 << 46;                              // descriptor version
+    d |= (uint64_t)(SW == 128 ? 2 : 4) << 61;            // swizzle mode
     return d;
 }
 
@@ -287,8 +294,8 @@ struct Products<2, 3> {
 //     targets are a brick of the parent level in natural order, written to its
 //     class layout.
 // PA, PB: terms of the A and B operands; NCH: output coefficients / 16 (the
-// accumulator width held in registers).
-template <int PA, int PB, int NCH>
+// accumulator width held in registers); SW: bytes per swizzled operand row.
+template <int PA, int PB, int NCH, int SW>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_m2l_tc(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
              const __grid_constant__ CUtensorMap mA2, const __grid_constant__ CUtensorMap mB0,
@@ -307,10 +314,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t smem0 = (smem_u32(smem_dyn) + 1023u) & ~1023u;
-    const uint32_t stageA = TC_ROWS * ROW_BYTES;
-    const uint32_t stageB = (uint32_t)a.npad * ROW_BYTES;
+    constexpr int KCH = kchunk_of(SW);  // K elements per stage
+    constexpr int K16 = SW / 32;        // MMAs (K = 16) per stage and product
+    const uint32_t stageA = TC_ROWS * SW;
+    const uint32_t stageB = (uint32_t)a.npad * SW;
     const uint32_t stage_bytes = PA * stageA + PB * stageB;
-    const uint32_t tx_bytes = (uint32_t)(PA * a.rows * ROW_BYTES) + PB * stageB;
+    const uint32_t tx_bytes = (uint32_t)(PA * a.rows * SW) + PB * stageB;
 
     // M2L: the 8 parity classes of one brick run side by side, so CTAs resident
     // at the same time read overlapping shifted bricks, which stay in L2
@@ -373,10 +382,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     mbar_expect_tx(full, tx_bytes);
                     const uint32_t base = smem0 + (uint32_t)s * stage_bytes;
 #pragma unroll
-                    for (int i = 0; i < PA; ++i) tma_load_4d(base + i * stageA, src[i], full, kc * KCHUNK, c1, c2, c3);
+                    for (int i = 0; i < PA; ++i) tma_load_4d(base + i * stageA, src[i], full, kc * KCH, c1, c2, c3);
 #pragma unroll
                     for (int j = 0; j < PB; ++j)
-                        tma_load_3d(base + PA * stageA + j * stageB, mB[j], full, kc * KCHUNK, 0, slot);
+                        tma_load_3d(base + PA * stageA + j * stageB, mB[j], full, kc * KCH, 0, slot);
                     ++it;
                     if (++s == a.stages) {
                         s = 0;
@@ -437,10 +446,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
                     for (int pr = 0; pr < PR::n; ++pr) {
 #pragma unroll
-                        for (int k16 = 0; k16 < 2; ++k16) {
-                            if (2 * kc + k16 >= a.ksteps) continue;  // zero fill beyond K
-                            const uint64_t ad = sdesc_sw64(base + PR::a(pr) * stageA + k16 * 32);
-                            const uint64_t bd = sdesc_sw64(base + PA * stageA + PR::b(pr) * stageB + k16 * 32);
+                        for (int k16 = 0; k16 < K16; ++k16) {
+                            if (K16 * kc + k16 >= a.ksteps) continue;  // zero fill beyond K
+                            const uint64_t ad = sdesc<SW>(base + PR::a(pr) * stageA + k16 * 32);
+                            const uint64_t bd = sdesc<SW>(base + PA * stageA + PR::b(pr) * stageB + k16 * 32);
                             mma_bf16(tmem_d, ad, bd, a.idesc, (kc | pr | k16) != 0 ? 1u : 0u);
                         }
                     }
@@ -707,44 +716,45 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 
 int tile_dim(int np, int cap) { return np < cap ? np : cap; }
 
-// stage ring of the split (pa, pb): as many stages as the shared-memory budget allows, 3..6
-int tc_stages(int pa, int pb, int npad)
+// stage ring of the split (pa, pb): as many stages as the shared-memory budget allows, 2..6
+int tc_stages(int pa, int pb, int npad, int sw)
 {
-    const size_t stage = (size_t)pa * TC_ROWS * ROW_BYTES + (size_t)pb * npad * ROW_BYTES;
+    const size_t stage = (size_t)pa * TC_ROWS * sw + (size_t)pb * npad * sw;
     size_t n = (TC_SMEM_BUDGET - 1024) / stage;
     if (n > (size_t)TC_MAX_STAGES) n = TC_MAX_STAGES;
-    return n < 3 ? 3 : (int)n;
+    return n < 2 ? 2 : (int)n;
 }
 
-size_t tc_smem_bytes(int pa, int pb, int npad)
+size_t tc_smem_bytes(int pa, int pb, int npad, int sw)
 {
     // at least 120 KB so that a second CTA (and its 512 TMEM columns) never shares the SM
-    size_t need = (size_t)tc_stages(pa, pb, npad) * (pa * TC_ROWS * ROW_BYTES + pb * npad * ROW_BYTES) + 1024;
+    size_t need = (size_t)tc_stages(pa, pb, npad, sw) * (pa * TC_ROWS * sw + pb * npad * sw) + 1024;
     return need < 120 * 1024 ? 120 * 1024 : need;
 }
 
 typedef void (*TcKernel)(CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap,
                          CUtensorMap, TcArgs);
 
-template <int PA, int PB>
+// NCH = ((p+1)^2 rounded to 16) / 16 takes the values below for p <= 15
+template <int PA, int PB, int SW>
 TcKernel pick_kernel_n(int nch)
 {
     switch (nch) {
 #define FMM_TC_CASE(n) \
-    case n: return (TcKernel)k_m2l_tc<PA, PB, n>;
-        FMM_TC_CASE(1) FMM_TC_CASE(2) FMM_TC_CASE(3) FMM_TC_CASE(4) FMM_TC_CASE(5) FMM_TC_CASE(6) FMM_TC_CASE(7)
-        FMM_TC_CASE(8) FMM_TC_CASE(9) FMM_TC_CASE(10) FMM_TC_CASE(11) FMM_TC_CASE(12) FMM_TC_CASE(13)
-        FMM_TC_CASE(14) FMM_TC_CASE(15) FMM_TC_CASE(16)
+    case n: return (TcKernel)k_m2l_tc<PA, PB, n, SW>;
+        FMM_TC_CASE(1) FMM_TC_CASE(2) FMM_TC_CASE(3) FMM_TC_CASE(4) FMM_TC_CASE(6) FMM_TC_CASE(7) FMM_TC_CASE(8)
+        FMM_TC_CASE(9) FMM_TC_CASE(11) FMM_TC_CASE(13) FMM_TC_CASE(15) FMM_TC_CASE(16)
 #undef FMM_TC_CASE
     default: return nullptr;
     }
 }
 
-TcKernel pick_kernel(int pa, int pb, int nch)
+TcKernel pick_kernel(int pa, int pb, int nch, int sw)
 {
-    if (pa == 3 && pb == 3) return pick_kernel_n<3, 3>(nch);
-    if (pa == 2 && pb == 3) return pick_kernel_n<2, 3>(nch);
-    if (pa == 2 && pb == 2) return pick_kernel_n<2, 2>(nch);
+    if (sw == 128) return pa == 2 && pb == 2 ? pick_kernel_n<2, 2, 128>(nch) : nullptr;
+    if (pa == 3 && pb == 3) return pick_kernel_n<3, 3, 64>(nch);
+    if (pa == 2 && pb == 3) return pick_kernel_n<2, 3, 64>(nch);
+    if (pa == 2 && pb == 2) return pick_kernel_n<2, 2, 64>(nch);
     return nullptr;
 }
 
@@ -764,14 +774,16 @@ void split_offsets(int n_off, int tiles, int max_groups, int &groups, int &per_g
     groups = (n_off + per_group - 1) / per_group;
 }
 
+CUtensorMapSwizzle swizzle_of(int sw) { return sw == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B; }
+
 fmm_status encode_planes(PFN_cuTensorMapEncodeTiled_v12000 enc, CUtensorMap *map, CUtensorMapDataType dt, void *base,
-                         int kp, int64_t d1, int64_t d2, int64_t d3, int b1, int b2, int b3)
+                         int kp, int64_t d1, int64_t d2, int64_t d3, int b1, int b2, int b3, int sw)
 {
     cuuint64_t dims[4] = {(cuuint64_t)kp, (cuuint64_t)d1, (cuuint64_t)d2, (cuuint64_t)d3};
     cuuint64_t strides[3] = {(cuuint64_t)kp * 2, (cuuint64_t)kp * 2 * d1, (cuuint64_t)kp * 2 * d1 * d2};
-    cuuint32_t box[4] = {KCHUNK, (cuuint32_t)b1, (cuuint32_t)b2, (cuuint32_t)b3};
+    cuuint32_t box[4] = {(cuuint32_t)kchunk_of(sw), (cuuint32_t)b1, (cuuint32_t)b2, (cuuint32_t)b3};
     cuuint32_t es[4] = {1, 1, 1, 1};
-    return enc(map, dt, 4, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+    return enc(map, dt, 4, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle_of(sw),
                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS
                ? FMM_OK
                : FMM_ERR_INTERNAL;
@@ -781,9 +793,9 @@ void fill_common(const Plan &P, const TcState *S, int pa, int pb, TcArgs &a)
 {
     a.nc = P.nc;
     a.npad = S->npad;
-    a.kchunks = (S->kp + KCHUNK - 1) / KCHUNK;
+    a.kchunks = (S->kp + kchunk_of(S->sw) - 1) / kchunk_of(S->sw);
     a.ksteps = (P.nc + 15) / 16;
-    a.stages = tc_stages(pa, pb, S->npad);
+    a.stages = tc_stages(pa, pb, S->npad, S->sw);
     // instruction descriptor: FP32 accumulator, A and B both bf16 (format 1) or both fp16 (format 0),
     // K-major, N >> 3 at bit 17, M >> 4 at bit 24
     const uint32_t ab = S->f16 ? 0u : 1u;
@@ -821,8 +833,10 @@ fmm_status tc_prepare(Plan &P)
     S->pb = (P.split == FMM_SPLIT_BF16X2 || S->f16) ? 2 : 3;
     S->parts = S->f16 ? 2 : 3;  // bf16: three terms always, the solute-only pass uses the 3 x 3 split
     S->npad = (P.nc + 15) / 16 * 16;
-    // rows padded to whole 64-byte copy boxes (aligned pieces); the MMAs stop at (p+1)^2 padded to 16
-    S->kp = (P.nc + KCHUNK - 1) / KCHUNK * KCHUNK;
+    // 128-byte swizzled rows for the fp16 split (two 2-term stages fit), 64 bytes for the bf16 splits;
+    // rows padded to whole copy boxes (aligned pieces); the MMAs stop at (p+1)^2 padded to 16
+    S->sw = S->f16 ? 128 : 64;
+    S->kp = (P.nc + kchunk_of(S->sw) - 1) / kchunk_of(S->sw) * kchunk_of(S->sw);
     const CUtensorMapDataType dt = S->f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     if (S->f16) {
         // s(n,m) = sqrt((n+m)! (n-m)!) per real coefficient
@@ -864,10 +878,10 @@ fmm_status tc_prepare(Plan &P)
     for (int j = 0; j < S->parts; ++j) {
         cuuint64_t dims[3] = {(cuuint64_t)S->kp, (cuuint64_t)S->npad, (cuuint64_t)NSLOT};
         cuuint64_t strides[2] = {(cuuint64_t)S->kp * 2, (cuuint64_t)S->kp * 2 * S->npad};
-        cuuint32_t box[3] = {KCHUNK, (cuuint32_t)S->npad, 1};
+        cuuint32_t box[3] = {(cuuint32_t)kchunk_of(S->sw), (cuuint32_t)S->npad, 1};
         cuuint32_t es[3] = {1, 1, 1};
         if (enc(&S->mapB[j], dt, 3, S->ops + j * S->ops_part_elems, dims, strides, box, es,
-                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle_of(S->sw), CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return FMM_ERR_INTERNAL;
     }
@@ -890,14 +904,14 @@ fmm_status tc_prepare(Plan &P)
         FMM_CUDA_TRY(cudaMalloc(&S->planes[l], sizeof(uint16_t) * S->part_elems[l] * S->parts));
         for (int i = 0; i < S->parts; ++i)
             TRY_TC(encode_planes(enc, &S->mapA[l][i], dt, S->planes[l] + i * S->part_elems[l], S->kp, np2, np2,
-                                 8 * np2, S->bx[l], S->by[l], S->bz[l]));
+                                 8 * np2, S->bx[l], S->by[l], S->bz[l], S->sw));
         for (int i = S->parts; i < 3; ++i) S->mapA[l][i] = S->mapA[l][0];
         if (S->f16) {
             // L of level l - 1 (side np) in natural order, boxed like the level-l bricks; all levels share
             // one buffer, used one level at a time
             for (int i = 0; i < 2; ++i)
                 TRY_TC(encode_planes(enc, &S->mapL[l][i], dt, S->planesL + (size_t)i * np * np * np * S->kp, S->kp,
-                                     np, np, np, S->bx[l], S->by[l], S->bz[l]));
+                                     np, np, np, S->bx[l], S->by[l], S->bz[l], S->sw));
         } else {
             S->mapL[l][0] = S->mapL[l][1] = S->mapA[l][0];  // unused kernel parameters
         }
@@ -916,15 +930,15 @@ fmm_status tc_prepare(Plan &P)
         }
     }
     if (lpart_elems) FMM_CUDA_TRY(cudaMalloc(&S->Lpart, sizeof(float) * lpart_elems));
-    TcKernel k = pick_kernel(S->pa, S->pb, S->npad / 16);
+    TcKernel k = pick_kernel(S->pa, S->pb, S->npad / 16, S->sw);
     if (!k) return FMM_ERR_INTERNAL;
     FMM_CUDA_TRY(cudaFuncSetAttribute((const void *)k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)tc_smem_bytes(S->pa, S->pb, S->npad)));
+                                      (int)tc_smem_bytes(S->pa, S->pb, S->npad, S->sw)));
     if (!S->f16) {
-        TcKernel kp = pick_kernel(3, 3, S->npad / 16);  // the solute-only pass
+        TcKernel kp = pick_kernel(3, 3, S->npad / 16, S->sw);  // the solute-only pass
         if (!kp) return FMM_ERR_INTERNAL;
         FMM_CUDA_TRY(cudaFuncSetAttribute((const void *)kp, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)tc_smem_bytes(3, 3, S->npad)));
+                                          (int)tc_smem_bytes(3, 3, S->npad, S->sw)));
     }
     FMM_CUDA_TRY(cudaStreamSynchronize(P.stream));
     return FMM_OK;
@@ -975,10 +989,10 @@ fmm_status launch_m2m_tc(Plan &P, int l)
     a.L = (float *)P.M[l];
     a.post = S->s32inv;
     a.amax = S->amax + src;
-    TcKernel k = pick_kernel(S->pa, S->pb, S->npad / 16);
+    TcKernel k = pick_kernel(S->pa, S->pb, S->npad / 16, S->sw);
     if (!k) return FMM_ERR_INTERNAL;
     const unsigned grid = (unsigned)a.tiles_per_class * (unsigned)a.groups;
-    k<<<grid, TC_THREADS, tc_smem_bytes(S->pa, S->pb, S->npad), P.stream>>>(
+    k<<<grid, TC_THREADS, tc_smem_bytes(S->pa, S->pb, S->npad, S->sw), P.stream>>>(
         S->mapA[src][0], S->mapA[src][1], S->mapA[src][2], S->mapB[0], S->mapB[1], S->mapB[2], S->mapA[src][0],
         S->mapA[src][0], a);
     FMM_LAUNCH_CHECK(P);
@@ -1040,11 +1054,11 @@ fmm_status launch_m2l_tc(Plan &P, int l, bool precise, bool split)
     a.amax = S->f16 ? S->amax + l : nullptr;
     a.amaxL = S->f16 ? S->amaxL + l - 1 : nullptr;
     unsigned grid = 8u * (unsigned)a.tiles_per_class * (unsigned)a.groups;
-    TcKernel k = pick_kernel(pa, pb, S->npad / 16);
+    TcKernel k = pick_kernel(pa, pb, S->npad / 16, S->sw);
     if (!k) return FMM_ERR_INTERNAL;
     const bool time_it = P.timings_on && l == P.d && P.ev_top[0] && !precise;
     if (time_it) cudaEventRecord(P.ev_top[0], P.stream);
-    k<<<grid, TC_THREADS, tc_smem_bytes(pa, pb, S->npad), P.stream>>>(
+    k<<<grid, TC_THREADS, tc_smem_bytes(pa, pb, S->npad, S->sw), P.stream>>>(
         S->mapA[l][0], S->mapA[l][1], S->mapA[l][2], S->mapB[0], S->mapB[1], S->mapB[2], S->mapL[l][0],
         S->mapL[l][1], a);
     FMM_LAUNCH_CHECK(P);
