@@ -100,7 +100,10 @@ enum {
                               <= 0 restores the default kappa = 2 / b */
     FMM_OPT_M2L_SPLIT = 4, /* ival: mixed-precision M2L operand split, FMM_SPLIT_* (default FP16X2) */
     FMM_OPT_STREAM = 5,    /* ival: cudaStream_t cast to int64 (0 = legacy default stream) */
-    FMM_OPT_TIMINGS = 6    /* ival: 1 records per-stage CUDA events (adds event overhead) */
+    FMM_OPT_TIMINGS = 6,   /* ival: 1 records per-stage CUDA events (adds event overhead) */
+    FMM_OPT_M2L_PAIR = 7   /* ival: 1 (default) lets the fp16x2 tensor-core M2L of levels with an even
+                              number of 128-cell tiles per class run on CTA pairs (2-SM MMAs, half the
+                              operator traffic per SM); 0 keeps every level on single-CTA MMAs */
 };
 enum { FMM_PREC_FP64 = 0, FMM_PREC_MIXED = 1 };
 enum {

@@ -81,6 +81,7 @@ struct Plan {
     double kappa = 0;  // 0 = default 2 / box
     cudaStream_t stream = 0;
     bool timings_on = false;
+    bool tc_pair = true;  // CTA-pair (2-SM) tensor-core M2L where the level allows it
     int nc = 0;
     int64_t nleaf = 0;  // 8^d
     int64_t launches = 0;

@@ -89,6 +89,7 @@ struct TcState {
     size_t ops_part_elems = 0;
     CUtensorMap mapA[9][3];
     CUtensorMap mapB[3];
+    CUtensorMap mapB2[2];           // fp16: operator tiles boxed N/2 rows (one half per CTA of a pair)
     CUtensorMap mapL[9][2];         // fp16: parent-level local expansions for the fused L2L of level l
     uint16_t *planesL = nullptr;    // natural order [part][z][y][x][kp], sized for level d - 1
     size_t partL_elems = 0;
@@ -257,6 +258,98 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
 }
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// ---- CTA pair (cluster of 2) helpers for the 2-SM MMA
+__device__ __forceinline__ uint32_t cluster_rank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// shared::cluster address of the object at local shared address `a` in CTA `rank`
+__device__ __forceinline__ uint32_t map_shared(uint32_t a, uint32_t rank)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+
+__device__ __forceinline__ void cluster_sync_all()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// bounded wait with cluster-scope acquire (barriers that receive arrivals from the peer CTA)
+__device__ bool mbar_wait_cluster(uint32_t bar, uint32_t parity, volatile int *abort_flag)
+{
+    uint64_t t0 = global_ns();
+    for (uint32_t i = 0;; ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if ((i & 63) == 63) {
+            if (*abort_flag) return false;
+            if (global_ns() - t0 > WAIT_LIMIT_NS) return false;
+        }
+    }
+}
+
+// arrive on an mbarrier of the peer CTA (shared::cluster address)
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t cluster_bar)
+{
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_bar) : "memory");
+}
+
+// TMA loads into this CTA's shared memory whose completion is counted on the
+// pair leader's mbarrier (`bar` a shared::cluster address)
+__device__ __forceinline__ void tma_load_4d_pair(uint32_t dst, const CUtensorMap *map, uint32_t bar, int c0, int c1,
+                                                 int c2, int c3)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+        "%4, %5}], [%6];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d_pair(uint32_t dst, const CUtensorMap *map, uint32_t bar, int c0, int c1,
+                                                 int c2)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+        "%4}], [%5];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+        : "memory");
+}
+
+// 2-SM MMA: D (128 lanes in each CTA's TMEM) += A (128 rows per CTA) . B (N/2 rows per CTA)
+__device__ __forceinline__ void mma_f16_pair(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                             uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+// arrive on the mbarrier at local offset `bar` in both CTAs of the pair once
+// every MMA issued so far by this thread has completed
+__device__ __forceinline__ void mma_commit_pair(uint32_t bar)
+{
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
+        "h"((uint16_t)3)
+        : "memory");
+}
 
 // ------------------------------------------------------------------ the kernel
 template <int PA, int PB>
@@ -553,6 +646,253 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
 }
 
+// Pair variant of mode 0 for the fp16 split (128-byte rows): a cluster of two
+// CTAs computes 256 target rows, tiles 2t and 2t + 1 of one class, with 2-SM
+// MMAs (M = 256).  Each CTA copies its own 128-row A brick and half of every
+// operator tile (N/2 rows); the MMAs, issued by the even CTA, read both CTAs'
+// shared memory and leave each CTA's 128 rows in its own TMEM, so each SM
+// streams half of the operator bytes of the single-CTA kernel.
+//   full[s]   even CTA only: its expect-tx covers both CTAs' copies, which all
+//             complete on it
+//   empty[s]  both CTAs: the even CTA's MMA commit, multicast to the pair
+//   tfull[b]  both CTAs: multicast commit; tempty[b] on the even CTA counts
+//             the 4 local and 4 remote epilogue warps
+//   done      both CTAs: multicast commit after the last MMA
+// Barriers are initialised and TMEM is allocated (collectively) only after a
+// cluster barrier, and both CTAs pass a cluster barrier before the collective
+// TMEM release, so neither touches the other after it has exited.
+template <int NCH>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TC_THREADS, 1)
+    k_m2l_tc_pair(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
+                  const __grid_constant__ CUtensorMap mB0, const __grid_constant__ CUtensorMap mB1,
+                  const __grid_constant__ CUtensorMap mL0, const __grid_constant__ CUtensorMap mL1, TcArgs a)
+{
+    constexpr int PA = 2, PB = 2, SW = 128;
+    constexpr int KCH = kchunk_of(SW), K16 = SW / 32;
+    using PR = Products<PA, PB>;
+    extern __shared__ uint8_t smem_dyn[];
+    __shared__ __align__(8) uint64_t bar_full[TC_MAX_STAGES];
+    __shared__ __align__(8) uint64_t bar_empty[TC_MAX_STAGES];
+    __shared__ __align__(8) uint64_t bar_tfull[2];
+    __shared__ __align__(8) uint64_t bar_tempty[2];
+    __shared__ __align__(8) uint64_t bar_done;
+    __shared__ uint32_t tmem_sh;
+    __shared__ int abort_sh;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = cluster_rank();
+    const bool leader = rank == 0;
+    const uint32_t smem0 = (smem_u32(smem_dyn) + 1023u) & ~1023u;
+    const uint32_t halfN = (uint32_t)a.npad / 2;
+    const uint32_t stageA = TC_ROWS * SW;
+    const uint32_t stageB = halfN * SW;
+    const uint32_t stage_bytes = PA * stageA + PB * stageB;
+    const uint32_t tx_bytes = 2u * ((uint32_t)(PA * a.rows * SW) + PB * stageB);  // both CTAs' copies
+
+    const int pair = blockIdx.x >> 1;
+    const int grp = pair % a.groups;
+    const int cls = (pair / a.groups) & 7;
+    const int tile = 2 * ((pair / a.groups) >> 3) + (int)rank;
+    const int o_begin = grp * a.per_group;
+    const int o_end = o_begin + a.per_group < a.n_off ? o_begin + a.per_group : a.n_off;
+    const int nloc = o_end > o_begin ? o_end - o_begin : 0;
+    const int x0 = (tile % a.tiles_x) * a.bx;
+    const int y0 = ((tile / a.tiles_x) % a.tiles_y) * a.by;
+    const int z0 = (tile / (a.tiles_x * a.tiles_y)) * a.bz;
+    const int cx = cls & 1, cy = (cls >> 1) & 1, cz = (cls >> 2) & 1;
+    const int np2 = a.np + 2;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < a.stages; ++s) {
+            mbar_init(smem_u32(&bar_full[s]), 1);
+            mbar_init(smem_u32(&bar_empty[s]), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&bar_tfull[b]), 1);
+            mbar_init(smem_u32(&bar_tempty[b]), 8);  // 4 epilogue warps in each CTA
+        }
+        mbar_init(smem_u32(&bar_done), 1);
+        abort_sh = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    cluster_sync_all();  // the pair's barriers are initialised and both CTAs are running
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_sh)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = tmem_sh;
+    volatile int *abort_flag = &abort_sh;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- producer (both CTAs): own A brick, own half of B, completing on the leader's barrier
+            const CUtensorMap *mA[2] = {&mA0, &mA1};
+            const CUtensorMap *mL[2] = {&mL0, &mL1};
+            const CUtensorMap *mB[2] = {&mB0, &mB1};
+            int it = 0, s = 0;
+            uint32_t round = 0;
+            bool ok = true;
+            auto load_offset = [&](const CUtensorMap *const *src, int c1, int c2, int c3, int slot) {
+                for (int kc = 0; kc < a.kchunks && ok; ++kc) {
+                    if (it >= a.stages && !mbar_wait_cluster(smem_u32(&bar_empty[s]), (round & 1u) ^ 1u, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t full_local = smem_u32(&bar_full[s]);
+                    if (leader) mbar_expect_tx(full_local, tx_bytes);
+                    const uint32_t full = map_shared(full_local, 0);
+                    const uint32_t base = smem0 + (uint32_t)s * stage_bytes;
+#pragma unroll
+                    for (int i = 0; i < PA; ++i)
+                        tma_load_4d_pair(base + i * stageA, src[i], full, kc * KCH, c1, c2, c3);
+#pragma unroll
+                    for (int j = 0; j < PB; ++j)
+                        tma_load_3d_pair(base + PA * stageA + j * stageB, mB[j], full, kc * KCH,
+                                         (int)(rank * halfN), slot);
+                    ++it;
+                    if (++s == a.stages) {
+                        s = 0;
+                        ++round;
+                    }
+                }
+            };
+            int oi = -1;
+            for (int dz = -2 - cz; dz <= 3 - cz && ok; ++dz)
+                for (int dy = -2 - cy; dy <= 3 - cy && ok; ++dy)
+                    for (int dx = -2 - cx; dx <= 3 - cx && ok; ++dx) {
+                        if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1 && dz >= -1 && dz <= 1) continue;
+                        ++oi;
+                        if (oi < o_begin || oi >= o_end) continue;
+                        const int sx = cx + dx, sy = cy + dy, sz = cz + dz;
+                        const int scls = (sx & 1) | ((sy & 1) << 1) | ((sz & 1) << 2);
+                        load_offset(mA, x0 + (sx >> 1) + 1, y0 + (sy >> 1) + 1, scls * np2 + z0 + (sz >> 1) + 1,
+                                    off_slot(dx, dy, dz));
+                    }
+            if (ok && a.n_off > NUM_IL && NUM_IL >= o_begin && NUM_IL < o_end)
+                load_offset(mL, x0, y0, z0, NOFF + 8 + cls);
+            if (!ok) {
+                abort_sh = 1;
+                atomicOr(a.err, ERRF_TIMEOUT);
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0 && leader) {
+            // ---------------- MMA issuer (even CTA): 256-row MMAs over both CTAs' operands
+            int s = 0;
+            uint32_t round = 0;
+            bool ok = true;
+            for (int o = 0; o < nloc && ok; ++o) {
+                const int acc = o & 1;
+                const uint32_t use = (uint32_t)(o >> 1);
+                if (o >= 2 && !mbar_wait_cluster(smem_u32(&bar_tempty[acc]), (use - 1u) & 1u, abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                fence_after();
+                const uint32_t tmem_d = tmem + (uint32_t)(acc * 256);
+                for (int kc = 0; kc < a.kchunks; ++kc) {
+                    if (!mbar_wait_cluster(smem_u32(&bar_full[s]), round & 1u, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    fence_after();
+                    const uint32_t base = smem0 + (uint32_t)s * stage_bytes;
+#pragma unroll
+                    for (int pr = 0; pr < PR::n; ++pr) {
+#pragma unroll
+                        for (int k16 = 0; k16 < K16; ++k16) {
+                            if (K16 * kc + k16 >= a.ksteps) continue;  // zero fill beyond K
+                            const uint64_t ad = sdesc<SW>(base + PR::a(pr) * stageA + k16 * 32);
+                            const uint64_t bd = sdesc<SW>(base + PA * stageA + PR::b(pr) * stageB + k16 * 32);
+                            mma_f16_pair(tmem_d, ad, bd, a.idesc, (kc | pr | k16) != 0 ? 1u : 0u);
+                        }
+                    }
+                    mma_commit_pair(smem_u32(&bar_empty[s]));
+                    if (++s == a.stages) {
+                        s = 0;
+                        ++round;
+                    }
+                }
+                if (ok) mma_commit_pair(smem_u32(&bar_tfull[acc]));
+            }
+            if (!ok) {
+                abort_sh = 1;
+                atomicOr(a.err, ERRF_TIMEOUT);
+            }
+            mma_commit_pair(smem_u32(&bar_done));  // arrives in both CTAs once every MMA has completed
+        }
+        __syncwarp();
+    } else {
+        // ---------------- epilogue warps (both CTAs): drain this CTA's 128 rows
+        const int quad = warp & 3;
+        const int row = quad * 32 + lane;
+        const float l2l_fac = a.amaxL ? pow2f(gain_m_exp(*a.amax) - gain_m_exp(*a.amaxL)) : 1.f;
+        float Lr[NCH * 16];
+#pragma unroll
+        for (int i = 0; i < NCH * 16; ++i) Lr[i] = 0.f;
+        bool ok = true;
+        for (int o = 0; o < nloc; ++o) {
+            const int acc = o & 1;
+            const uint32_t use = (uint32_t)(o >> 1);
+            if (!mbar_wait_cluster(smem_u32(&bar_tfull[acc]), use & 1u, abort_flag)) {
+                ok = false;
+                break;
+            }
+            fence_after();
+            const float fac = (o_begin + o == NUM_IL) ? l2l_fac : 1.f;
+            const uint32_t taddr = tmem + (uint32_t)(acc * 256) + ((uint32_t)(quad * 32) << 16);
+#pragma unroll
+            for (int c = 0; c < NCH; ++c) {
+                uint32_t r[16];
+                tmem_ld16(taddr + (uint32_t)(c * 16), r);
+                tmem_wait_ld();
+#pragma unroll
+                for (int j = 0; j < 16; ++j) Lr[c * 16 + j] = fmaf(__uint_as_float(r[j]), fac, Lr[c * 16 + j]);
+            }
+            fence_before();
+            __syncwarp();
+            if (lane == 0) {
+                const uint32_t te = smem_u32(&bar_tempty[acc]);
+                if (leader) mbar_arrive(te);
+                else mbar_arrive_remote(map_shared(te, 0));
+            }
+        }
+        if (!ok) {
+            abort_sh = 1;
+            if (lane == 0) atomicOr(a.err, ERRF_TIMEOUT);
+        } else if (row < a.rows) {
+            const int tx = row % a.bx, ty = (row / a.bx) % a.by, tz = row / (a.bx * a.by);
+            const int64_t np = a.np;
+            const int64_t idx = (int64_t)cls * np * np * np + (x0 + tx) + np * ((y0 + ty) + np * (int64_t)(z0 + tz));
+            float *dst = (a.groups == 1 ? a.L : a.Lpart + (int64_t)grp * 8 * np * np * np * a.nc) + idx * a.nc;
+            const float g = pow2f(-gain_m_exp(*a.amax) - GAIN_T_EXP);
+#pragma unroll
+            for (int i = 0; i < NCH * 16; ++i)
+                if (i < a.nc) dst[i] = Lr[i] * (__ldg(a.post + i) * g);
+        }
+    }
+
+    // ---------------- teardown: every MMA done (bounded wait), pair barrier, collective TMEM release
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile int no_abort = 0;
+        if (!mbar_wait_cluster(smem_u32(&bar_done), 0, &no_abort)) atomicOr(a.err, ERRF_TIMEOUT);
+    }
+    fence_before();
+    __syncthreads();
+    cluster_sync_all();
+    fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    cluster_sync_all();
+}
+
 // ------------------------------------------------------------------ operand preparation
 // x = x0 + x1 (+ x2) in bf16 or fp16 terms, each term the rounding of the
 // remaining residual; stored as bit patterns `stride` elements apart
@@ -734,6 +1074,34 @@ size_t tc_smem_bytes(int pa, int pb, int npad, int sw)
 
 typedef void (*TcKernel)(CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap,
                          CUtensorMap, TcArgs);
+typedef void (*TcPairKernel)(CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap, TcArgs);
+
+// CTA-pair kernel (fp16, 128-byte rows): stage = 2 A terms of 128 rows + 2 B terms of npad / 2 rows
+int tc_pair_stages(int npad)
+{
+    const size_t stage = (size_t)2 * TC_ROWS * 128 + (size_t)2 * (npad / 2) * 128;
+    size_t n = (TC_SMEM_BUDGET - 1024) / stage;
+    if (n > (size_t)TC_MAX_STAGES) n = TC_MAX_STAGES;
+    return n < 2 ? 2 : (int)n;
+}
+
+size_t tc_pair_smem_bytes(int npad)
+{
+    size_t need = (size_t)tc_pair_stages(npad) * ((size_t)2 * TC_ROWS * 128 + (size_t)2 * (npad / 2) * 128) + 1024;
+    return need < 120 * 1024 ? 120 * 1024 : need;
+}
+
+TcPairKernel pick_pair_kernel(int nch)
+{
+    switch (nch) {
+#define FMM_TC_CASE(n) \
+    case n: return (TcPairKernel)k_m2l_tc_pair<n>;
+        FMM_TC_CASE(1) FMM_TC_CASE(2) FMM_TC_CASE(3) FMM_TC_CASE(4) FMM_TC_CASE(6) FMM_TC_CASE(7) FMM_TC_CASE(8)
+        FMM_TC_CASE(9) FMM_TC_CASE(11) FMM_TC_CASE(13) FMM_TC_CASE(15) FMM_TC_CASE(16)
+#undef FMM_TC_CASE
+    default: return nullptr;
+    }
+}
 
 // NCH = ((p+1)^2 rounded to 16) / 16 takes the values below for p <= 15
 template <int PA, int PB, int SW>
@@ -886,6 +1254,22 @@ fmm_status tc_prepare(Plan &P)
             return FMM_ERR_INTERNAL;
     }
     for (int j = S->parts; j < 3; ++j) S->mapB[j] = S->mapB[0];  // unused kernel parameters
+    if (S->f16) {
+        for (int j = 0; j < 2; ++j) {
+            cuuint64_t dims[3] = {(cuuint64_t)S->kp, (cuuint64_t)S->npad, (cuuint64_t)NSLOT};
+            cuuint64_t strides[2] = {(cuuint64_t)S->kp * 2, (cuuint64_t)S->kp * 2 * S->npad};
+            cuuint32_t box[3] = {(cuuint32_t)kchunk_of(S->sw), (cuuint32_t)(S->npad / 2), 1};
+            cuuint32_t es[3] = {1, 1, 1};
+            if (enc(&S->mapB2[j], dt, 3, S->ops + j * S->ops_part_elems, dims, strides, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle_of(S->sw), CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+                return FMM_ERR_INTERNAL;
+        }
+        TcPairKernel kp2 = pick_pair_kernel(S->npad / 16);
+        if (!kp2) return FMM_ERR_INTERNAL;
+        FMM_CUDA_TRY(cudaFuncSetAttribute((const void *)kp2, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)tc_pair_smem_bytes(S->npad)));
+    }
     // natural-order planes of the parent-level local expansions (fused L2L), sized for level d - 1
     if (S->f16) {
         const int64_t n = (int64_t)1 << (P.d - 1);
@@ -1054,13 +1438,24 @@ fmm_status launch_m2l_tc(Plan &P, int l, bool precise, bool split)
     a.amax = S->f16 ? S->amax + l : nullptr;
     a.amaxL = S->f16 ? S->amaxL + l - 1 : nullptr;
     unsigned grid = 8u * (unsigned)a.tiles_per_class * (unsigned)a.groups;
-    TcKernel k = pick_kernel(pa, pb, S->npad / 16, S->sw);
-    if (!k) return FMM_ERR_INTERNAL;
+    // CTA pairs take two tiles of one class: an even number of full 128-row tiles per class
+    const bool pair = S->f16 && P.tc_pair && a.rows == TC_ROWS && a.tiles_per_class % 2 == 0;
     const bool time_it = P.timings_on && l == P.d && P.ev_top[0] && !precise;
     if (time_it) cudaEventRecord(P.ev_top[0], P.stream);
-    k<<<grid, TC_THREADS, tc_smem_bytes(pa, pb, S->npad, S->sw), P.stream>>>(
-        S->mapA[l][0], S->mapA[l][1], S->mapA[l][2], S->mapB[0], S->mapB[1], S->mapB[2], S->mapL[l][0],
-        S->mapL[l][1], a);
+    if (pair) {
+        TcPairKernel k2 = pick_pair_kernel(S->npad / 16);
+        if (!k2) return FMM_ERR_INTERNAL;
+        a.stages = tc_pair_stages(S->npad);
+        a.idesc = (1u << 4) | ((uint32_t)(S->npad >> 3) << 17) | ((uint32_t)((2 * TC_ROWS) >> 4) << 24);  // M = 256
+        k2<<<grid, TC_THREADS, tc_pair_smem_bytes(S->npad), P.stream>>>(S->mapA[l][0], S->mapA[l][1], S->mapB2[0],
+                                                                         S->mapB2[1], S->mapL[l][0], S->mapL[l][1], a);
+    } else {
+        TcKernel k = pick_kernel(pa, pb, S->npad / 16, S->sw);
+        if (!k) return FMM_ERR_INTERNAL;
+        k<<<grid, TC_THREADS, tc_smem_bytes(pa, pb, S->npad, S->sw), P.stream>>>(
+            S->mapA[l][0], S->mapA[l][1], S->mapA[l][2], S->mapB[0], S->mapB[1], S->mapB[2], S->mapL[l][0],
+            S->mapL[l][1], a);
+    }
     FMM_LAUNCH_CHECK(P);
     if (time_it) {
         cudaEventRecord(P.ev_top[1], P.stream);

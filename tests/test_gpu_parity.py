@@ -243,6 +243,23 @@ def test_fp16_split_charge_scale(qscale):
     assert _rms_rel(F_tc, F_64) < 1e-5
 
 
+@pytest.mark.parametrize("d", [4, 5])
+def test_cta_pair_m2l_matches_single_cta(d):
+    """The fp16x2 M2L on CTA pairs (2-SM MMAs over 256 rows, each CTA holding half of
+    every operator tile; used where a level has an even number of 128-cell tiles per
+    class: levels 4..d here) against the single-CTA kernel on the same input, and both
+    against the FP64 path."""
+    b = _sub_box(333333 // 64, 215.3 / 4, seed=7) if d == 4 else _sub_box(333333 // 8, 215.3 / 2, seed=7)
+    p = 12
+    t_2, _, F_2 = _run(b.pos, b.q, b.L, d, p, precision="mixed", m2l_pair=True)
+    t_1, _, F_1 = _run(b.pos, b.q, b.L, d, p, precision="mixed", m2l_pair=False)
+    t_64, _, F_64 = _run(b.pos, b.q, b.L, d, p)
+    assert abs(t_2["total"] - t_1["total"]) <= 1e-9 * abs(t_1["total"])
+    assert _rms_rel(F_2, F_1) < 1e-8
+    assert abs(t_2["total"] - t_64["total"]) <= 1e-6 * abs(t_64["total"])
+    assert _rms_rel(F_2, F_64) < 1e-5
+
+
 def test_tensor_core_backend_is_used():
     b = _sub_box(1000, 30.0)
     plan = _plan(b.L, b.N, 4, 12, precision="mixed")
