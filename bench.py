@@ -273,6 +273,15 @@ def run_ours(args):
                 "kernel": "k_m2l_simt<float> (all levels, one evaluation)"}
         traffic = None
     achieved = flops / (launch_ms / 1e3) / 1e12
+    if uses_tc:
+        # tensor work actually issued by the launch: every target row runs one 128 x npad x 16 MMA per
+        # K step (K = (p+1)^2 padded to 16), split product and offset
+        C = (p + 1) ** 2
+        ksteps, npad = (C + 15) // 16, (C + 15) // 16 * 16
+        products = {"fp16x2": 3, "bf16x3": 6, "bf16a2b3": 4, "bf16x2": 3}.get(args.split, 0)
+        issued = 8 ** d * (189 + (1 if fused else 0)) * products * ksteps * 2.0 * npad * 16
+        roof["issued_flops_per_launch"] = issued
+        roof["issued_tflops"] = issued / (launch_ms / 1e3) / 1e12
     roof.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                  "algorithmic_flops_per_launch": flops, "avg_launch_ms": launch_ms,
                  "m2l_all_levels": {"ms": stage_ms, "tflops": stage_flops / (stage_ms / 1e3) / 1e12}})

@@ -264,18 +264,20 @@ __global__ void k_lattice_operator(int p, const double *__restrict__ S, double *
 
 // ------------------------------------------------------------------ P2M
 // Eq. P2M in level-scaled form: Mhat_n^m = sum_j q_j R_n^m((r_M - r_j)/h).
-// One thread per (leaf, m): the column n = m..p of every particle.
-template <typename T>
+// One thread per (leaf, m): the column n = m..p of every particle.  PM >= p is
+// a compile-time bound so that the column accumulators stay in registers
+// (the loops over n are unrolled and predicated on m <= n <= p).
+template <typename T, int PM>
 __global__ void k_p2m(int p, int nside, const int *__restrict__ start, const Particle<T> *__restrict__ sp,
                       T inv_h, int d, T *__restrict__ M)
 {
     // reciprocals of the recurrences, once per block: -1/(2k) and 1/((n+m)(n-m))
-    __shared__ T s_half[P_MAX + 1];
-    __shared__ T s_inv[(P_MAX + 1) * (P_MAX + 1)];
-    for (int e = threadIdx.x; e < (p + 1) * (p + 1); e += blockDim.x) {
-        const int n = e / (p + 1), mm = e % (p + 1);
+    __shared__ T s_half[PM + 1];
+    __shared__ T s_inv[(PM + 1) * (PM + 1)];
+    for (int e = threadIdx.x; e < (PM + 1) * (PM + 1); e += blockDim.x) {
+        const int n = e / (PM + 1), mm = e % (PM + 1);
         s_inv[e] = n > mm ? T(1) / T((n + mm) * (n - mm)) : T(0);
-        if (e <= p) s_half[e] = e > 0 ? T(-0.5) / T(e) : T(0);
+        if (e <= PM) s_half[e] = e > 0 ? T(-0.5) / T(e) : T(0);
     }
     __syncthreads();
     int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -284,8 +286,9 @@ __global__ void k_p2m(int p, int nside, const int *__restrict__ start, const Par
     int64_t leaf = tid / (p + 1);
     int m = (int)(tid % (p + 1));
     int x = (int)(leaf % nside), y = (int)((leaf / nside) % nside), z = (int)(leaf / ((int64_t)nside * nside));
-    T acc_re[P_MAX + 1], acc_im[P_MAX + 1];
-    for (int n = 0; n <= p; ++n) acc_re[n] = acc_im[n] = 0;
+    T acc_re[PM + 1], acc_im[PM + 1];
+#pragma unroll
+    for (int n = 0; n <= PM; ++n) acc_re[n] = acc_im[n] = 0;
     for (int s = start[leaf]; s < start[leaf + 1]; ++s) {
         Particle<T> pt = sp[s];
         T vx = -pt.x * inv_h, vy = -pt.y * inv_h, vz = -pt.z * inv_h;
@@ -299,27 +302,46 @@ __global__ void k_p2m(int p, int nside, const int *__restrict__ start, const Par
             dim = nim;
         }
         T p2re = 0, p2im = 0, p1re = dre, p1im = dim;
-        acc_re[m] += pt.q * dre;
-        acc_im[m] += pt.q * dim;
-        for (int n = m + 1; n <= p; ++n) {
-            T a = T(2 * n - 1) * vz;
-            T inv = s_inv[n * (p + 1) + m];
-            T cr = (a * p1re - r2 * p2re) * inv;
-            T ci = (a * p1im - r2 * p2im) * inv;
-            acc_re[n] += pt.q * cr;
-            acc_im[n] += pt.q * ci;
-            p2re = p1re;
-            p2im = p1im;
-            p1re = cr;
-            p1im = ci;
+#pragma unroll
+        for (int n = 0; n <= PM; ++n) {
+            if (n == m) {
+                acc_re[n] += pt.q * dre;
+                acc_im[n] += pt.q * dim;
+            } else if (n > m && n <= p) {
+                T a = T(2 * n - 1) * vz;
+                T inv = s_inv[n * (PM + 1) + m];
+                T cr = (a * p1re - r2 * p2re) * inv;
+                T ci = (a * p1im - r2 * p2im) * inv;
+                acc_re[n] += pt.q * cr;
+                acc_im[n] += pt.q * ci;
+                p2re = p1re;
+                p2im = p1im;
+                p1re = cr;
+                p1im = ci;
+            }
         }
     }
     int nc = ncoef(p);
     T *out = M + cell_index(d, x, y, z) * nc;
-    for (int n = m; n <= p; ++n) {
+#pragma unroll
+    for (int n = 0; n <= PM; ++n) {
+        if (n < m || n > p) continue;
         out[cre(n, m)] = acc_re[n];
         if (m > 0) out[cim(n, m)] = acc_im[n];
     }
+}
+
+template <typename T>
+void launch_p2m(Plan &P, const Particle<T> *sp, T inv_h)
+{
+    const int p = P.p, nside = 1 << P.d;
+    const int64_t nthr = P.nleaf * (p + 1);
+    const unsigned blocks = (unsigned)((nthr + 127) / 128);
+    if (p <= 4) k_p2m<T, 4><<<blocks, 128, 0, P.stream>>>(p, nside, P.cell_start, sp, inv_h, P.d, (T *)P.M[P.d]);
+    else if (p <= 8) k_p2m<T, 8><<<blocks, 128, 0, P.stream>>>(p, nside, P.cell_start, sp, inv_h, P.d, (T *)P.M[P.d]);
+    else if (p <= 12) k_p2m<T, 12><<<blocks, 128, 0, P.stream>>>(p, nside, P.cell_start, sp, inv_h, P.d, (T *)P.M[P.d]);
+    else if (p <= 16) k_p2m<T, 16><<<blocks, 128, 0, P.stream>>>(p, nside, P.cell_start, sp, inv_h, P.d, (T *)P.M[P.d]);
+    else k_p2m<T, P_MAX><<<blocks, 128, 0, P.stream>>>(p, nside, P.cell_start, sp, inv_h, P.d, (T *)P.M[P.d]);
 }
 
 // ------------------------------------------------------------------ lattice apply
@@ -456,11 +478,10 @@ __global__ void k_l2p(int p, int d, int64_t N, const int *__restrict__ sleaf, co
 template <typename T>
 fmm_status upward_t(Plan &P, bool solute_only)
 {
-    int p = P.p, nside = 1 << P.d;
+    const int nside = 1 << P.d;
     const Particle<T> *sp = (const Particle<T> *)(solute_only ? P.sorted_u : P.sorted);
     T inv_h = (T)((double)nside / P.box);
-    int64_t nthr = P.nleaf * (p + 1);
-    k_p2m<T><<<blocks_for(nthr, 128), 128, 0, P.stream>>>(p, nside, P.cell_start, sp, inv_h, P.d, (T *)P.M[P.d]);
+    launch_p2m<T>(P, sp, inv_h);
     FMM_LAUNCH_CHECK(P);
     const bool tc = tc_translations(P);
     for (int l = P.d - 1; l >= 0; --l) {

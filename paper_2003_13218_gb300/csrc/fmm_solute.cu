@@ -423,7 +423,8 @@ __global__ void k_act_l2l(int p, int l, const int *__restrict__ cells, const int
 }
 
 template <typename T>
-__device__ T l2p_value(int p, const T *__restrict__ Lc, T vx, T vy, T vz);
+__device__ T l2p_value(int p, const T *__restrict__ Lc, T vx, T vy, T vz, const T *s_half = nullptr,
+                       const T *s_inv = nullptr);
 
 // at each solute charge: phi_ff = (solvent field from Lt) + phi_u (solute field
 // of the solute-only pass), so that A - B = sum_u q Phi_v holds term by term
@@ -449,15 +450,16 @@ __global__ void k_act_l2p(int p, int d, double inv_h, const int *__restrict__ li
     phi[s] = (T)(v + (double)phi_u[s]);
 }
 
-// Phi at (v) from the real-layout local coefficients Lc (scaled), v in cell units
+// Phi at (v) from the real-layout local coefficients Lc (scaled), v in cell units;
+// s_half[m] = -1/(2m) and s_inv[n (p+1) + m] = 1/((n+m)(n-m)) when given
 template <typename T>
-__device__ T l2p_value(int p, const T *__restrict__ Lc, T vx, T vy, T vz)
+__device__ T l2p_value(int p, const T *__restrict__ Lc, T vx, T vy, T vz, const T *s_half, const T *s_inv)
 {
     T r2 = vx * vx + vy * vy + vz * vz;
     T pot = 0, dre = 1, dim = 0;
     for (int m = 0; m <= p; ++m) {
         if (m > 0) {
-            T sc = T(-0.5) / T(m);
+            T sc = s_half ? s_half[m] : T(-0.5) / T(m);
             T nre = sc * (vx * dre - vy * dim), nim = sc * (vx * dim + vy * dre);
             dre = nre;
             dim = nim;
@@ -466,7 +468,7 @@ __device__ T l2p_value(int p, const T *__restrict__ Lc, T vx, T vy, T vz)
         T p2re = 0, p2im = 0, rre = dre, rim = dim;
         for (int n = m; n <= p; ++n) {
             if (n > m) {
-                T a = T(2 * n - 1) * vz, inv = T(1) / T((n + m) * (n - m));
+                T a = T(2 * n - 1) * vz, inv = s_inv ? s_inv[n * (p + 1) + m] : T(1) / T((n + m) * (n - m));
                 T cr = (a * rre - r2 * p2re) * inv, ci = (a * rim - r2 * p2im) * inv;
                 p2re = rre;
                 p2im = rim;
@@ -486,6 +488,14 @@ __global__ void k_sol_eval(int p, int d, int64_t N, T h_leaf, const int *__restr
                            const Particle<T> *__restrict__ sp, const T *__restrict__ Lld, const int *__restrict__ tlist,
                            const int *__restrict__ tcounts, const T *__restrict__ contrib, T *__restrict__ phi)
 {
+    __shared__ T s_half[P_MAX + 1];
+    __shared__ T s_inv[(P_MAX + 1) * (P_MAX + 1)];
+    for (int e = threadIdx.x; e < (p + 1) * (p + 1); e += blockDim.x) {
+        const int n = e / (p + 1), mm = e % (p + 1);
+        s_inv[e] = n > mm ? T(1) / T((n + mm) * (n - mm)) : T(0);
+        if (e <= p) s_half[e] = e > 0 ? T(-0.5) / T(e) : T(0);
+    }
+    __syncthreads();
     int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (s >= N) return;
     int nc = ncoef(p);
@@ -505,7 +515,7 @@ __global__ void k_sol_eval(int p, int d, int64_t N, T h_leaf, const int *__restr
         T inv = T(1) / (h_leaf * T(1 << sh));
         T vx = (pt.x + ox * h_leaf) * inv, vy = (pt.y + oy * h_leaf) * inv, vz = (pt.z + oz * h_leaf) * inv;
         if (l == LD) {
-            total += l2p_value<T>(p, Lld + cell_index(l, ax, ay, az) * nc, vx, vy, vz) * inv;
+            total += l2p_value<T>(p, Lld + cell_index(l, ax, ay, az) * nc, vx, vy, vz, s_half, s_inv) * inv;
             continue;
         }
         int cnt = tcounts[l];
@@ -519,7 +529,7 @@ __global__ void k_sol_eval(int p, int d, int64_t N, T h_leaf, const int *__restr
             else hi = mid;
         }
         if (lo < cnt && tl[lo] == key)
-            total += l2p_value<T>(p, contrib + ((size_t)l * MAX_TGT + lo) * nc, vx, vy, vz) * inv;
+            total += l2p_value<T>(p, contrib + ((size_t)l * MAX_TGT + lo) * nc, vx, vy, vz, s_half, s_inv) * inv;
     }
     phi[s] = total;
 }
