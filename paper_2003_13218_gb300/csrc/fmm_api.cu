@@ -119,9 +119,10 @@ struct StageTimer {
         if (s_ != FMM_OK) return s_;         \
     } while (0)
 
-fmm_status far_field_pass(Plan &P, bool gradient, bool solute_only, StageTimer *tm)
+fmm_status far_field_pass(Plan &P, bool gradient, bool solute_only, StageTimer *tm, bool fork_solute = false)
 {
     TRY(launch_upward(P, solute_only));
+    if (fork_solute) TRY(solute_prologue(P));
     if (tm) tm->mark();
     TRY(launch_lattice(P));
     if (tm) tm->mark();
@@ -174,9 +175,10 @@ fmm_status evaluate(Plan &P, const double *pos, const double *q, const uint8_t *
     tm.mark();
     FMM_CUDA_TRY(cudaMemsetAsync(P.d_err, 0, sizeof(int), P.stream));
     TRY(launch_assign_sort(P, dpos, dq, dsol));
+    if (want_uv) TRY(solute_count(P));
     tm.mark();
     TRY(launch_bc_moments(P, dq, dsol));
-    TRY(far_field_pass(P, forces != nullptr, false, &tm));
+    TRY(far_field_pass(P, forces != nullptr, false, &tm, want_uv));
     TRY(launch_p2p(P, forces != nullptr));
     tm.mark();
     if (want_uv) {

@@ -233,6 +233,12 @@ fmm_status launch_p2p_uv(Plan &P);
 // sparse solute-only pass of Eq. FMMcalc (fmm_solute.cu)
 fmm_status solute_prepare(Plan &P);
 void solute_free(Plan &P);
+// right after the sort: count the solute charges and copy the count to the host asynchronously
+fmm_status solute_count(Plan &P);
+// after the full pass's upward sweep: the pass's prologue (active cells, solute moments, FP64 solvent
+// expansions at the active cells) on a high-priority side stream, overlapping the full pass's M2L
+fmm_status solute_prologue(Plan &P);
+// joins the prologue and runs the rest (sparse pass); *done = false when the dense pass must run
 fmm_status launch_solute_pass(Plan &P, bool *done);
 
 // tensor-core M2L, and with the fp16 split also M2M and L2L (fmm_m2l_tc.cu)

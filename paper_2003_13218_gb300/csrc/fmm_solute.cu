@@ -44,6 +44,11 @@ struct SoluteScratch {
     int *tlist = nullptr;    // [9][MAX_TGT] sorted targets per fine level
     void *contrib = nullptr; // [9][MAX_TGT][nc] M2L sums at those targets
     int *h_count = nullptr;  // pinned
+    cudaStream_t side = nullptr;       // high-priority stream of the prologue (overlaps the full pass's M2L)
+    cudaEvent_t ev_count = nullptr;    // count copied to h_count
+    cudaEvent_t ev_up = nullptr;       // full upward pass done (fork)
+    cudaEvent_t ev_act = nullptr;      // prologue done (join)
+    bool count_pending = false, prologue_pending = false;
     void *Lt = nullptr;      // [9][NU_MAX][nc] full local expansions at the active cells (FP64)
     double *part = nullptr;  // [NU_MAX][189][nc] their M2L terms, one per offset
 };
@@ -74,7 +79,7 @@ __global__ void k_sol_cells(int d, const int *__restrict__ list, const int *__re
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     int n = list[NU_MAX];
-    if (n > NU_MAX) n = NU_MAX;
+    if (n > NU_MAX) n = 0;  // the dense pass runs instead: no active cells
     int cur[NU_MAX], cnt = 0;
     for (int i = 0; i < n; ++i) cur[cnt++] = sleaf[list[i]];
     for (int l = d; l >= 0; --l) {
@@ -301,9 +306,10 @@ __global__ void k_sol_m2l(int p, int l, const int *__restrict__ cells, const int
 // FP64 throughout, on the solvent moments M - M_u (the field of the solvent
 // at the solute charges): Lt[0][0] = T0 . (M(0) - M_u(0))
 template <typename T>
-__global__ void k_act_lattice(int p, const double *__restrict__ T0, const T *__restrict__ M0, const T *__restrict__ MU0,
-                              double *__restrict__ Lt)
+__global__ void k_act_lattice(int p, const int *__restrict__ ncells, const double *__restrict__ T0,
+                              const T *__restrict__ M0, const T *__restrict__ MU0, double *__restrict__ Lt)
 {
+    if (ncells[0] == 0) return;
     int nc = ncoef(p);
     for (int j = threadIdx.x; j < nc; j += blockDim.x) {
         double acc = 0;
@@ -590,42 +596,56 @@ __global__ void k_flag_scan_add(int64_t n, int *__restrict__ out, const int *__r
     if (i < n) out[i] += sums[i / 4096];
 }
 
+// prologue on stream `st`: active cells, solute moments MU of the active cells
+// and the FP64 local expansions Lt of the solvent field there (from the full
+// pass's moments minus MU), before the rest of the pass overwrites the coarse
+// moments.  Grids cover NU_MAX cells; the device count decides (no cells when
+// the sparse pass does not apply).
+template <typename T>
+fmm_status solute_prologue_t(Plan &P, SoluteScratch &S, cudaStream_t st)
+{
+    const int p = P.p, d = P.d, nc = P.nc;
+    const int nside = 1 << d;
+    const double h = P.box / nside;
+    const int nu = NU_MAX;
+    const T *Rw = std::is_same<T, double>::value ? (const T *)P.tab.Rw64 : (const T *)P.tab.Rw32;
+    T *MU = (T *)S.MU;
+    k_sol_cells<<<1, 32, 0, st>>>(d, S.list, P.sleaf, S.cells, S.ncells);
+    FMM_LAUNCH_CHECK(P);
+    k_sol_p2m<T><<<nu, 32, 0, st>>>(p, d, S.cells, S.ncells, P.cell_start, (const Particle<T> *)P.sorted_u,
+                                       (T)(1.0 / h), MU);
+    FMM_LAUNCH_CHECK(P);
+    for (int l = d - 1; l >= 0; --l) {
+        k_sol_m2m<T><<<dim3(nu, (p + 1) * (p + 2) / 2), 32, 0, st>>>(p, l, S.cells, S.ncells, Rw, MU);
+        FMM_LAUNCH_CHECK(P);
+    }
+    const int nth = ((nc + 31) / 32) * 32;
+    double *Lt = (double *)S.Lt;
+    k_act_lattice<T><<<1, nth, 0, st>>>(p, S.ncells, P.tab.T0, (const T *)P.M[0], MU, Lt);
+    FMM_LAUNCH_CHECK(P);
+    for (int l = 1; l <= d; ++l) {
+        k_act_m2l<T><<<dim3(nu, 189), nth, 0, st>>>(p, l, S.cells, S.ncells, P.tab.Top64, (const T *)P.M[l], MU,
+                                                     S.part);
+        FMM_LAUNCH_CHECK(P);
+        k_act_sum<<<dim3(nu, (nc + 7) / 8), 256, 0, st>>>(p, l, S.ncells, S.part, Lt);
+        FMM_LAUNCH_CHECK(P);
+        k_act_l2l<<<dim3(nu, (p + 1) * (p + 2) / 2), 32, 0, st>>>(p, l, S.cells, S.ncells, P.tab.Rw64, Lt, Lt);
+        FMM_LAUNCH_CHECK(P);
+    }
+    return FMM_OK;
+}
+
+// the rest, on the plan's stream once the prologue is joined: the dense coarse
+// levels, the sparse finer levels and Phi_u at every charge
 template <typename T>
 fmm_status solute_sparse_t(Plan &P, SoluteScratch &S, int nu)
 {
     const int p = P.p, d = P.d, nc = P.nc;
     const int nside = 1 << d;
     const double h = P.box / nside;
-    const T *Rw = std::is_same<T, double>::value ? (const T *)P.tab.Rw64 : (const T *)P.tab.Rw32;
     const T *Top = std::is_same<T, double>::value ? (const T *)P.tab.Top64 : (const T *)P.tab.Top32;
     T *MU = (T *)S.MU;
-    // active cells (leaves of the solute charges and their ancestors)
-    k_sol_cells<<<1, 32, 0, P.stream>>>(d, S.list, P.sleaf, S.cells, S.ncells);
-    FMM_LAUNCH_CHECK(P);
-    // solute moments of the active cells
-    k_sol_p2m<T><<<nu, 32, 0, P.stream>>>(p, d, S.cells, S.ncells, P.cell_start, (const Particle<T> *)P.sorted_u,
-                                             (T)(1.0 / h), MU);
-    FMM_LAUNCH_CHECK(P);
-    for (int l = d - 1; l >= 0; --l) {
-        k_sol_m2m<T><<<dim3(nu, (p + 1) * (p + 2) / 2), 32, 0, P.stream>>>(p, l, S.cells, S.ncells, Rw, MU);
-        FMM_LAUNCH_CHECK(P);
-    }
-    // FP64 expansions of the solvent field at the active cells, from the full
-    // pass's moments minus the solute moments, before this pass overwrites the
-    // coarse moments
-    const int nth = ((nc + 31) / 32) * 32;
     double *Lt = (double *)S.Lt;
-    k_act_lattice<T><<<1, nth, 0, P.stream>>>(p, P.tab.T0, (const T *)P.M[0], MU, Lt);
-    FMM_LAUNCH_CHECK(P);
-    for (int l = 1; l <= d; ++l) {
-        k_act_m2l<T><<<dim3(nu, 189), nth, 0, P.stream>>>(p, l, S.cells, S.ncells, P.tab.Top64,
-                                                               (const T *)P.M[l], MU, S.part);
-        FMM_LAUNCH_CHECK(P);
-        k_act_sum<<<dim3(nu, (nc + 7) / 8), 256, 0, P.stream>>>(p, l, S.ncells, S.part, Lt);
-        FMM_LAUNCH_CHECK(P);
-        k_act_l2l<<<dim3(nu, (p + 1) * (p + 2) / 2), 32, 0, P.stream>>>(p, l, S.cells, S.ncells, P.tab.Rw64, Lt, Lt);
-        FMM_LAUNCH_CHECK(P);
-    }
     // dense coarse levels 0..LD
     for (int l = 0; l <= LD; ++l)
         FMM_CUDA_TRY(cudaMemsetAsync(P.M[l], 0, sizeof(T) * ((size_t)1 << (3 * l)) * nc, P.stream));
@@ -691,6 +711,12 @@ fmm_status solute_prepare(Plan &P)
     FMM_CUDA_TRY(cudaMalloc(&S->tlist, sizeof(int) * 9 * MAX_TGT));
     FMM_CUDA_TRY(cudaMalloc(&S->contrib, sizeof(double) * (size_t)(P.d + 1) * MAX_TGT * P.nc));
     FMM_CUDA_TRY(cudaMallocHost((void **)&S->h_count, sizeof(int)));
+    int lo = 0, hi = 0;
+    FMM_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    FMM_CUDA_TRY(cudaStreamCreateWithPriority(&S->side, cudaStreamNonBlocking, hi));
+    FMM_CUDA_TRY(cudaEventCreateWithFlags(&S->ev_count, cudaEventDisableTiming));
+    FMM_CUDA_TRY(cudaEventCreateWithFlags(&S->ev_up, cudaEventDisableTiming));
+    FMM_CUDA_TRY(cudaEventCreateWithFlags(&S->ev_act, cudaEventDisableTiming));
     FMM_CUDA_TRY(cudaMalloc(&S->Lt, sizeof(double) * 9 * NU_MAX * P.nc));
     FMM_CUDA_TRY(cudaMalloc(&S->part, sizeof(double) * NU_MAX * 189 * P.nc));
     return FMM_OK;
@@ -712,8 +738,45 @@ void solute_free(Plan &P)
     cudaFree(S->Lt);
     cudaFree(S->part);
     if (S->h_count) cudaFreeHost(S->h_count);
+    if (S->side) {
+        cudaStreamSynchronize(S->side);
+        cudaStreamDestroy(S->side);
+    }
+    if (S->ev_count) cudaEventDestroy(S->ev_count);
+    if (S->ev_up) cudaEventDestroy(S->ev_up);
+    if (S->ev_act) cudaEventDestroy(S->ev_act);
     delete S;
     P.sol = nullptr;
+}
+
+fmm_status solute_count(Plan &P)
+{
+    SoluteScratch *S = (SoluteScratch *)P.sol;
+    if (!S) return FMM_OK;
+    FMM_CUDA_TRY(cudaMemsetAsync(S->list + NU_MAX, 0, sizeof(int), P.stream));
+    k_sol_list<<<blocks_for(P.N, 256), 256, 0, P.stream>>>(P.N, P.sorted_sol, S->list);
+    FMM_LAUNCH_CHECK(P);
+    FMM_CUDA_TRY(cudaMemcpyAsync(S->h_count, S->list + NU_MAX, sizeof(int), cudaMemcpyDeviceToHost, P.stream));
+    FMM_CUDA_TRY(cudaEventRecord(S->ev_count, P.stream));
+    S->count_pending = true;
+    return FMM_OK;
+}
+
+fmm_status solute_prologue(Plan &P)
+{
+    SoluteScratch *S = (SoluteScratch *)P.sol;
+    if (!S) return FMM_OK;
+    if (!S->count_pending) {
+        fmm_status s = solute_count(P);
+        if (s != FMM_OK) return s;
+    }
+    FMM_CUDA_TRY(cudaEventRecord(S->ev_up, P.stream));
+    FMM_CUDA_TRY(cudaStreamWaitEvent(S->side, S->ev_up, 0));
+    fmm_status s = P.precision == FMM_PREC_FP64 ? solute_prologue_t<double>(P, *S, S->side)
+                                                : solute_prologue_t<float>(P, *S, S->side);
+    FMM_CUDA_TRY(cudaEventRecord(S->ev_act, S->side));
+    S->prologue_pending = true;
+    return s;
 }
 
 // Phi_u into P.phi_u by the sparse pass; *done = false asks for the dense pass
@@ -722,11 +785,14 @@ fmm_status launch_solute_pass(Plan &P, bool *done)
     *done = false;
     SoluteScratch *S = (SoluteScratch *)P.sol;
     if (!S) return FMM_OK;
-    FMM_CUDA_TRY(cudaMemsetAsync(S->list + NU_MAX, 0, sizeof(int), P.stream));
-    k_sol_list<<<blocks_for(P.N, 256), 256, 0, P.stream>>>(P.N, P.sorted_sol, S->list);
-    FMM_LAUNCH_CHECK(P);
-    FMM_CUDA_TRY(cudaMemcpyAsync(S->h_count, S->list + NU_MAX, sizeof(int), cudaMemcpyDeviceToHost, P.stream));
-    FMM_CUDA_TRY(cudaStreamSynchronize(P.stream));
+    if (!S->prologue_pending) {
+        fmm_status s = solute_prologue(P);
+        if (s != FMM_OK) return s;
+    }
+    // the count was copied right after the sort; the join orders the prologue before the rest
+    FMM_CUDA_TRY(cudaEventSynchronize(S->ev_count));
+    FMM_CUDA_TRY(cudaStreamWaitEvent(P.stream, S->ev_act, 0));
+    S->count_pending = S->prologue_pending = false;
     int n = *S->h_count;
     if (n > NU_MAX) return FMM_OK;
     if (n == 0) {
