@@ -85,8 +85,10 @@ typedef struct {
 
 /* Per-stage device times of the last call, milliseconds (CUDA events on the
  * plan's stream).  m2l_l2l covers M2L and L2L of levels 1..l_max of the full
- * pass; m2l_kernels the M2L launches alone; solute_pass the solute-only pass
- * of Eq. FMMcalc (0 when not requested); m2l_top the single tensor-core M2L
+ * pass; m2l_kernels the M2L launches alone; solute_pass the part of the
+ * solute-only pass of Eq. FMMcalc that runs after the full pass (its prologue
+ * overlaps the full pass on a side stream; 0 when not requested); m2l_top the
+ * single tensor-core M2L
  * launch of level l_max (0 when that level runs on CUDA cores). */
 typedef struct {
     float sort, upward, lattice, m2l_l2l, l2p, p2p, solute_pass, reduce, total, m2l_kernels, m2l_top;
