@@ -41,12 +41,12 @@ FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 # FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.070 GHz
 FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # DRAM bytes (read + write) of one level-6 tensor-core M2L launch (fp16x2
-# split, fused L2L) of the na_1m workload, from the ncu capture summarised in
+# split, fused L2L, CTA pairs) of the na_1m workload, from the ncu capture summarised in
 # profiles/k_m2l_tc_na_1m_level6.md, with the sha256 of the kernel's device
 # code it was taken on: the value is reported only while that code is unchanged.
 M2L_TRAFFIC = {"src": "paper_2003_13218_gb300/csrc/fmm_m2l_tc.cu",
-               "sha256": "299d5cba70bb9000b48727c55b5ffa40eed9dfc185178c3b5048dfab93db8a9d",
-               "workload": "na_1m", "level": 6, "split": "fp16x2", "bytes_per_launch": 721.219072e6 + 173.285120e6}
+               "sha256": "5429f0131432c2ae13c8fb9568c3a586ffcc50fe4837f5b3ec9d75dd4ef4c56c",
+               "workload": "na_1m", "level": 6, "split": "fp16x2", "bytes_per_launch": 694.363648e6 + 170.471680e6}
 KERNEL_BEGIN = "// ------------------------------------------------------------------ the kernel"
 KERNEL_END = "// ------------------------------------------------------------------ operand preparation"
 
