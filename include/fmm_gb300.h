@@ -186,6 +186,59 @@ int fmm_plan_m2l_backend(fmm_plan plan, int level);
 void fmm_plan_destroy(fmm_plan plan);
 
 /*
+ * Batches of independent boxes (lambda windows or trajectory frames of uneven
+ * size), for the coupling scheme of Eq. Vswucheme: the Coulomb interaction
+ * between solute and solvent (charges and backgrounds) is scaled by
+ * (1 - lambda_C), so by Eq. FMMVTI the energy is linear in lambda_C:
+ *     V_lambda = E_total - lambda_C E_uv,   dV_lambda/dlambda_C = -E_uv,
+ * with E_total of Eq. Velecfull and E_uv the solute-solvent interaction of
+ * Eq. FMMcalc plus the background cross terms (as fmm_solute_solvent_energy).
+ */
+typedef struct fmm_batch_s *fmm_batch;
+
+/*
+ * Plans for nbox boxes: box[i] the cell side (A), N[i] the charges, depth[i]
+ * and p[i] as in fmm_plan_create.  depth == NULL or depth[i] <= 0: the depth is
+ * chosen by timing (for each group of boxes with the same starting guess
+ * round(log8(N / 3.8)), the box of median size is timed at the guess and one
+ * level either side on uniform test charges).  p == NULL or p[i] < 0: 12.
+ * precision: FMM_PREC_MIXED or FMM_PREC_FP64.  Work runs on up to 16 streams
+ * the batch owns.  Errors as fmm_plan_create (FMM_ERR_INVALID_ARG for any bad
+ * box, N, depth or p); on error nothing is left allocated.
+ */
+fmm_status fmm_batch_create(int nbox, const double *box, const int64_t *N, const int *depth, const int *p,
+                            int precision, fmm_batch *out);
+
+/*
+ * One evaluation of every box.  pos[i] (double[N_i][3]), q[i] (double[N_i]),
+ * is_solute[i] (uint8_t[N_i]): DEVICE pointers, which must stay valid and
+ * unchanged in place between calls that reuse them.  lambda_c: host double[nbox]
+ * (NULL: all 0).  Outputs (host double[nbox], each nullable): e_total, e_uv,
+ * v_lambda = e_total - lambda_c e_uv, dv_dlambda = -e_uv.  Synchronises.
+ *
+ * The first call runs the boxes through the streams and then records the whole
+ * batch as a CUDA graph; later calls with the same pointers replay it and
+ * check every box's solute count against the recorded one, falling back to
+ * the stream path (and recording again) when one differs.  Returns the first
+ * error among the boxes (FMM_ERR_NONFINITE, FMM_ERR_TIMEOUT, ...), after
+ * filling the outputs of all boxes.
+ */
+fmm_status fmm_batch_lambda_energies(fmm_batch batch, const double *const *pos, const double *const *q,
+                                     const uint8_t *const *is_solute, const double *lambda_c, double *e_total,
+                                     double *e_uv, double *v_lambda, double *dv_dlambda);
+
+/* Depth and order of box i, and how many calls replayed the graph or ran the
+ * stream path (each nullable). */
+fmm_status fmm_batch_info(fmm_batch batch, int i, int *depth, int *p, int64_t *replays, int64_t *enqueued);
+
+/* enable = 0 drops the recorded graph and keeps to the stream path; 1 (the
+ * default) allows recording. */
+fmm_status fmm_batch_set_graph(fmm_batch batch, int enable);
+
+/* Release the batch, its plans and streams.  Accepts NULL. */
+void fmm_batch_destroy(fmm_batch batch);
+
+/*
  * Background-charge terms without a plan and without allocating anything.
  * The paper has no counterpart to this entry point; it exists for callers
  * that cannot call cudaMalloc -- work recorded into a CUDA graph while a

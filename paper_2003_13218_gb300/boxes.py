@@ -173,3 +173,23 @@ def random_charges(N: int, L: float, seed: int = 0, neutral: bool = False) -> tu
     if neutral:
         q -= q.mean()
     return pos, q
+
+
+# The batched free-energy workload (lambda windows of uneven size): box b holds
+# n_w waters drawn uniformly from 3334..66666 (10,002..199,998 water atoms)
+# plus one ion; the species cycles Mg, Na, Cl with b, the coupling is
+# lambda_b = (b mod 16) / 15 and the ion's charge is scaled by lambda_b.
+LAMBDA_NW_LO, LAMBDA_NW_HI = 3334, 66666
+LAMBDA_STREAM = 7
+
+
+def lambda_windows(nbox: int = 64, seed: int = 0) -> list[tuple[Box, float]]:
+    u = uniform01(seed, LAMBDA_STREAM, nbox)
+    out = []
+    for b in range(nbox):
+        n_w = LAMBDA_NW_LO + int(u[b] * (LAMBDA_NW_HI - LAMBDA_NW_LO + 1))
+        ion = ("Mg", "Na", "Cl")[b % 3]
+        lam = (b % 16) / 15.0
+        box = ion_in_water(n_w, ion, seed=seed * 1000 + b, ion_charge=lam * ION_CHARGE[ion])
+        out.append((box, lam))
+    return out

@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfmm_gb300.so")
 SOURCES = ["fmm_api.cu", "fmm_sort.cu", "fmm_expand.cu", "fmm_translate.cu", "fmm_p2p.cu", "fmm_m2l_tc.cu", "fmm_solute.cu",
-           "fmm_noalloc.cu"]
+           "fmm_noalloc.cu", "fmm_batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include")]

@@ -12,10 +12,6 @@
 
 using namespace fmm;
 
-struct fmm_plan_s {
-    Plan P;
-};
-
 namespace {
 
 size_t reduction_scratch_bytes() { return sizeof(double) * 304 * 16 * 2; }
@@ -142,6 +138,71 @@ fmm_status far_field_pass(Plan &P, bool gradient, bool solute_only, StageTimer *
     return FMM_OK;
 }
 
+// front of one evaluation on device inputs: sort, solute count, background
+// moments, full far-field pass (with the solute prologue forked), near field
+fmm_status eval_front(Plan &P, const double *dpos, const double *dq, const uint8_t *dsol, bool want_uv,
+                      bool gradient, StageTimer *tm)
+{
+    if (tm) tm->mark();
+    FMM_CUDA_TRY(cudaMemsetAsync(P.d_err, 0, sizeof(int), P.stream));
+    TRY(launch_assign_sort(P, dpos, dq, dsol));
+    if (want_uv) TRY(solute_count(P));
+    if (tm) tm->mark();
+    TRY(launch_bc_moments(P, dq, dsol));
+    TRY(far_field_pass(P, gradient, false, tm, want_uv));
+    TRY(launch_p2p(P, gradient));
+    if (tm) tm->mark();
+    return FMM_OK;
+}
+
+// back of one evaluation: solute pass (its count is read from the host copy,
+// or P.known_count), reductions, forces, and the asynchronous copy of the
+// totals and the error flags into P.h_out
+fmm_status eval_back(Plan &P, const double *dq, bool want_uv, double *dforces, StageTimer *tm)
+{
+    if (want_uv) {
+        bool sparse_done = false;
+        TRY(launch_solute_pass(P, &sparse_done));
+        if (!sparse_done) TRY(far_field_pass(P, false, true, nullptr));
+        TRY(launch_p2p_uv(P));
+    }
+    if (tm) tm->mark();
+    TRY(launch_energy_reduce(P, want_uv));
+    if (dforces) TRY(launch_forces_out(P, dq, dforces));
+    if (tm) tm->mark();
+    FMM_CUDA_TRY(cudaMemcpyAsync(P.h_out, P.red_out, sizeof(double) * 29, cudaMemcpyDeviceToHost, P.stream));
+    FMM_CUDA_TRY(cudaMemcpyAsync(P.h_out + 32, P.d_err, sizeof(int), cudaMemcpyDeviceToHost, P.stream));
+    return FMM_OK;
+}
+
+// results of the last evaluation from P.h_out (the plan's stream synchronised)
+fmm_status eval_read(Plan &P, fmm_energy_terms *terms, fmm_uv_terms *uv)
+{
+    int err;
+    memcpy(&err, P.h_out + 32, sizeof(int));
+    if (terms) {
+        terms->near = P.h_out[16];
+        terms->far = P.h_out[17];
+        terms->charged = P.h_out[18];
+        terms->quad_surface = P.h_out[19];
+        terms->dipole_surface = P.h_out[20];
+        terms->total = P.h_out[21];
+    }
+    if (uv) {
+        uv->e_uv = P.h_out[22];
+        uv->W = P.h_out[23];
+        uv->A = P.h_out[24];
+        uv->B = P.h_out[25];
+        uv->C = P.h_out[26];
+        uv->nf_uv = P.h_out[27];
+        uv->bc_cross = P.h_out[28];
+    }
+    if (err & ERRF_NONFINITE) return FMM_ERR_NONFINITE;
+    if (err & ERRF_TIMEOUT) return FMM_ERR_TIMEOUT;
+    if (err) return FMM_ERR_INTERNAL;
+    return FMM_OK;
+}
+
 fmm_status evaluate(Plan &P, const double *pos, const double *q, const uint8_t *sol, double *forces,
                     fmm_energy_terms *terms, fmm_uv_terms *uv)
 {
@@ -172,78 +233,36 @@ fmm_status evaluate(Plan &P, const double *pos, const double *q, const uint8_t *
     if (kf == 1) dforces = P.out_forces;
 
     StageTimer tm(P);
-    tm.mark();
-    FMM_CUDA_TRY(cudaMemsetAsync(P.d_err, 0, sizeof(int), P.stream));
-    TRY(launch_assign_sort(P, dpos, dq, dsol));
-    if (want_uv) TRY(solute_count(P));
-    tm.mark();
-    TRY(launch_bc_moments(P, dq, dsol));
-    TRY(far_field_pass(P, forces != nullptr, false, &tm, want_uv));
-    TRY(launch_p2p(P, forces != nullptr));
-    tm.mark();
-    if (want_uv) {
-        bool sparse_done = false;
-        TRY(launch_solute_pass(P, &sparse_done));
-        if (!sparse_done) TRY(far_field_pass(P, false, true, nullptr));
-        TRY(launch_p2p_uv(P));
-    }
-    tm.mark();
-    TRY(launch_energy_reduce(P, want_uv));
-    if (forces) TRY(launch_forces_out(P, dq, dforces));
-    tm.mark();
-    bool sync = terms || uv || kf == 1;
+    TRY(eval_front(P, dpos, dq, dsol, want_uv, forces != nullptr, &tm));
+    TRY(eval_back(P, dq, want_uv, dforces, &tm));
     if (kf == 1)
         FMM_CUDA_TRY(cudaMemcpyAsync(forces, P.out_forces, sizeof(double) * 3 * P.N, cudaMemcpyDeviceToHost, P.stream));
-    if (sync) {
-        FMM_CUDA_TRY(cudaMemcpyAsync(P.h_out, P.red_out, sizeof(double) * 29, cudaMemcpyDeviceToHost, P.stream));
-        FMM_CUDA_TRY(cudaMemcpyAsync(P.h_out + 32, P.d_err, sizeof(int), cudaMemcpyDeviceToHost, P.stream));
-        FMM_CUDA_TRY(cudaStreamSynchronize(P.stream));
-        int err;
-        memcpy(&err, P.h_out + 32, sizeof(int));
-        if (terms) {
-            terms->near = P.h_out[16];
-            terms->far = P.h_out[17];
-            terms->charged = P.h_out[18];
-            terms->quad_surface = P.h_out[19];
-            terms->dipole_surface = P.h_out[20];
-            terms->total = P.h_out[21];
+    bool sync = terms || uv || kf == 1;
+    if (!sync) return FMM_OK;
+    FMM_CUDA_TRY(cudaStreamSynchronize(P.stream));
+    if (P.timings_on && tm.k >= 9) {
+        float t[12];
+        for (int i = 0; i + 1 < tm.k; ++i) cudaEventElapsedTime(&t[i], P.ev[i], P.ev[i + 1]);
+        P.last.sort = t[0];
+        P.last.upward = t[1];
+        P.last.lattice = t[2];
+        P.last.m2l_l2l = t[3];
+        P.last.l2p = t[4];
+        P.last.p2p = t[5];
+        P.last.solute_pass = t[6];
+        P.last.reduce = t[7];
+        cudaEventElapsedTime(&P.last.total, P.ev[0], P.ev[tm.k - 1]);
+        float m = 0;
+        for (int l = 1; l <= P.d; ++l) {
+            float x = 0;
+            cudaEventElapsedTime(&x, P.ev_m2l[2 * (l - 1)], P.ev_m2l[2 * (l - 1) + 1]);
+            m += x;
         }
-        if (uv) {
-            uv->e_uv = P.h_out[22];
-            uv->W = P.h_out[23];
-            uv->A = P.h_out[24];
-            uv->B = P.h_out[25];
-            uv->C = P.h_out[26];
-            uv->nf_uv = P.h_out[27];
-            uv->bc_cross = P.h_out[28];
-        }
-        if (P.timings_on && tm.k >= 9) {
-            float t[12];
-            for (int i = 0; i + 1 < tm.k; ++i) cudaEventElapsedTime(&t[i], P.ev[i], P.ev[i + 1]);
-            P.last.sort = t[0];
-            P.last.upward = t[1];
-            P.last.lattice = t[2];
-            P.last.m2l_l2l = t[3];
-            P.last.l2p = t[4];
-            P.last.p2p = t[5];
-            P.last.solute_pass = t[6];
-            P.last.reduce = t[7];
-            cudaEventElapsedTime(&P.last.total, P.ev[0], P.ev[tm.k - 1]);
-            float m = 0;
-            for (int l = 1; l <= P.d; ++l) {
-                float x = 0;
-                cudaEventElapsedTime(&x, P.ev_m2l[2 * (l - 1)], P.ev_m2l[2 * (l - 1) + 1]);
-                m += x;
-            }
-            P.last.m2l_kernels = m;
-            P.last.m2l_top = 0;
-            if (P.top_recorded) cudaEventElapsedTime(&P.last.m2l_top, P.ev_top[0], P.ev_top[1]);
-        }
-        if (err & ERRF_NONFINITE) return FMM_ERR_NONFINITE;
-        if (err & ERRF_TIMEOUT) return FMM_ERR_TIMEOUT;
-        if (err) return FMM_ERR_INTERNAL;
+        P.last.m2l_kernels = m;
+        P.last.m2l_top = 0;
+        if (P.top_recorded) cudaEventElapsedTime(&P.last.m2l_top, P.ev_top[0], P.ev_top[1]);
     }
-    return FMM_OK;
+    return eval_read(P, terms, uv);
 }
 
 // tensor-core operands follow the precision and split options
@@ -261,6 +280,23 @@ fmm_status rebuild(Plan &P)
 }
 
 }  // namespace
+
+namespace fmm {
+
+// the phases of one energy + solute-solvent evaluation without forces, for the
+// batch API (device inputs, no timings, results read after a stream sync)
+fmm_status eval_enqueue_front(Plan &P, const double *dpos, const double *dq, const uint8_t *dsol)
+{
+    P.launches = 0;
+    P.top_recorded = false;
+    return eval_front(P, dpos, dq, dsol, true, false, nullptr);
+}
+
+fmm_status eval_enqueue_back(Plan &P, const double *dq) { return eval_back(P, dq, true, nullptr, nullptr); }
+
+fmm_status eval_results(Plan &P, fmm_energy_terms *terms, fmm_uv_terms *uv) { return eval_read(P, terms, uv); }
+
+}  // namespace fmm
 
 extern "C" {
 

@@ -1,0 +1,371 @@
+// fmm_batch.cu -- many independent boxes per call: the lambda windows (or
+// trajectory frames) of a free-energy calculation, each box with its own size,
+// charges and solute set.  Per box and call: the total energy of Eq.
+// Velecfull, the solute-solvent interaction E_uv of Eq. FMMcalc with the
+// background cross terms, and with the Coulomb coupling lambda_C of Eq.
+// Vswucheme / Eq. FMMVTI, which is linear in lambda_C,
+//     V_lambda = E_total - lambda_C E_uv,   dV_lambda / dlambda_C = -E_uv.
+//
+// GB300 execution: one plan per box, the boxes spread over up to 16 streams
+// (longest first, round robin) so that the small, latency-bound boxes fill
+// the GPU together.  A call enqueues the front of every box (sort .. near
+// field) before any box waits for its solute count, then the back of every
+// box, and synchronises once.  The first call also captures the whole batch
+// into a CUDA graph with the solute counts it saw; later calls with the same
+// input pointers replay the graph and check the counts the graph copied back,
+// falling back to the enqueued path (and a new capture) when one changed.
+//
+// Depth: boxes given depth <= 0 get one chosen by timing: for each distinct
+// starting depth d0 = round(log8(N / 3.8)) (about 3.8 charges per leaf, as in
+// the paper's water boxes) the box of median size is timed at d0 - 1, d0 and
+// d0 + 1 on uniform test charges, and the fastest offset is used for that
+// group.
+#include <math.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "fmm_internal.cuh"
+
+using namespace fmm;
+
+namespace {
+
+constexpr int BATCH_MAX_STREAMS = 16;
+
+// uniform test charges for the depth tuner: alternating +-0.5 e, one solute
+__global__ void k_tune_fill(int64_t N, double box, double *__restrict__ pos, double *__restrict__ q,
+                            uint8_t *__restrict__ sol)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t z = 0x9E3779B97F4A7C15ull * (uint64_t)(i + 1);
+        for (int c = 0; c < 3; ++c) {
+            uint64_t x = z + 0xD1B54A32D192ED03ull * (uint64_t)(c + 1);
+            x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+            x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+            x ^= x >> 31;
+            pos[3 * i + c] = box * (double)(x >> 11) * (1.0 / 9007199254740992.0);
+        }
+        q[i] = (i & 1) ? 0.5 : -0.5;
+        sol[i] = i == 0;
+    }
+}
+
+int depth_guess(int64_t N)
+{
+    int d = (int)lround(log((double)N / 3.8) / log(8.0));
+    return d < 2 ? 2 : (d > 8 ? 8 : d);
+}
+
+fmm_status make_plan(double box, int64_t N, int d, int p, int precision, cudaStream_t st, fmm_plan *out)
+{
+    fmm_status s = fmm_plan_create(box, N, d, p, out);
+    if (s == FMM_OK) s = fmm_plan_set_option(*out, FMM_OPT_PRECISION, precision, 0.0);
+    if (s == FMM_OK) s = fmm_plan_set_option(*out, FMM_OPT_STREAM, (int64_t)(intptr_t)st, 0.0);
+    if (s != FMM_OK && *out) {
+        fmm_plan_destroy(*out);
+        *out = nullptr;
+    }
+    return s;
+}
+
+// device time of one evaluation of plan h on the tuner's charges
+fmm_status time_plan(fmm_plan h, const double *pos, const double *q, const uint8_t *sol, float *ms)
+{
+    Plan &P = h->P;
+    cudaEvent_t e0, e1;
+    FMM_CUDA_TRY(cudaEventCreate(&e0));
+    FMM_CUDA_TRY(cudaEventCreate(&e1));
+    fmm_status s = FMM_OK;
+    float best = 1e30f;
+    for (int it = 0; it < 3 && s == FMM_OK; ++it) {  // one warm-up, best of two
+        cudaEventRecord(e0, P.stream);
+        s = eval_enqueue_front(P, pos, q, sol);
+        if (s == FMM_OK) s = eval_enqueue_back(P, q);
+        cudaEventRecord(e1, P.stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) s = FMM_ERR_CUDA;
+        float t = 0;
+        cudaEventElapsedTime(&t, e0, e1);
+        if (it > 0 && t < best) best = t;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *ms = best;
+    return s;
+}
+
+}  // namespace
+
+struct fmm_batch_s {
+    int nbox = 0;
+    int precision = FMM_PREC_MIXED;
+    std::vector<fmm_plan> plans;
+    std::vector<int> depth, order;  // order: boxes by descending N
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> ev_done;
+    cudaStream_t origin = nullptr;
+    cudaEvent_t ev_start = nullptr;
+    bool use_graph = true;
+    cudaGraphExec_t graph = nullptr;
+    std::vector<const void *> gptr;  // input pointers the graph was captured with
+    std::vector<int> gcount;         // solute counts it was captured with
+    int64_t replays = 0, enqueued = 0;
+};
+
+namespace {
+
+void batch_free(fmm_batch b)
+{
+    if (!b) return;
+    for (cudaStream_t s : b->streams) cudaStreamSynchronize(s);
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    for (fmm_plan h : b->plans)
+        if (h) fmm_plan_destroy(h);
+    for (cudaEvent_t e : b->ev_done) cudaEventDestroy(e);
+    for (cudaStream_t s : b->streams) cudaStreamDestroy(s);
+    if (b->ev_start) cudaEventDestroy(b->ev_start);
+    if (b->origin) cudaStreamDestroy(b->origin);
+    delete b;
+}
+
+// the whole batch once: fronts of all boxes, then backs (each back waits for
+// its box's solute count unless the plan carries a known count)
+fmm_status batch_enqueue(fmm_batch b, const double *const *pos, const double *const *q, const uint8_t *const *sol)
+{
+    for (int i : b->order) {
+        fmm_status s = eval_enqueue_front(b->plans[i]->P, pos[i], q[i], sol[i]);
+        if (s != FMM_OK) return s;
+    }
+    for (int i : b->order) {
+        fmm_status s = eval_enqueue_back(b->plans[i]->P, q[i]);
+        if (s != FMM_OK) return s;
+    }
+    return FMM_OK;
+}
+
+fmm_status batch_sync(fmm_batch b)
+{
+    for (cudaStream_t s : b->streams) FMM_CUDA_TRY(cudaStreamSynchronize(s));
+    return FMM_OK;
+}
+
+// capture the batch with the solute counts of the call just completed
+void batch_capture(fmm_batch b, const double *const *pos, const double *const *q, const uint8_t *const *sol)
+{
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    b->gcount.assign(b->nbox, -1);
+    for (int i = 0; i < b->nbox; ++i) {
+        b->gcount[i] = solute_count_host(b->plans[i]->P);
+        b->plans[i]->P.known_count = b->gcount[i];
+    }
+    cudaGraph_t g = nullptr;
+    bool ok = cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+        ok = cudaEventRecord(b->ev_start, b->origin) == cudaSuccess;
+        for (cudaStream_t s : b->streams) ok = ok && cudaStreamWaitEvent(s, b->ev_start, 0) == cudaSuccess;
+        ok = ok && batch_enqueue(b, pos, q, sol) == FMM_OK;
+        for (size_t k = 0; k < b->streams.size(); ++k) {
+            ok = ok && cudaEventRecord(b->ev_done[k], b->streams[k]) == cudaSuccess;
+            ok = ok && cudaStreamWaitEvent(b->origin, b->ev_done[k], 0) == cudaSuccess;
+        }
+        if (cudaStreamEndCapture(b->origin, &g) != cudaSuccess) ok = false;
+    }
+    if (ok && g) ok = cudaGraphInstantiate(&b->graph, g, 0) == cudaSuccess;
+    if (g) cudaGraphDestroy(g);
+    if (!ok) {
+        if (b->graph) cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+        b->use_graph = false;  // this batch stays on the enqueued path
+    }
+    cudaGetLastError();
+    for (int i = 0; i < b->nbox; ++i) b->plans[i]->P.known_count = -1;
+    b->gptr.clear();
+    for (int i = 0; i < b->nbox; ++i) {
+        b->gptr.push_back(pos[i]);
+        b->gptr.push_back(q[i]);
+        b->gptr.push_back(sol[i]);
+    }
+}
+
+bool graph_matches(fmm_batch b, const double *const *pos, const double *const *q, const uint8_t *const *sol)
+{
+    if (!b->graph || (int)b->gptr.size() != 3 * b->nbox) return false;
+    for (int i = 0; i < b->nbox; ++i)
+        if (b->gptr[3 * i] != pos[i] || b->gptr[3 * i + 1] != q[i] || b->gptr[3 * i + 2] != sol[i]) return false;
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+fmm_status fmm_batch_create(int nbox, const double *box, const int64_t *N, const int *depth, const int *p,
+                            int precision, fmm_batch *out)
+{
+    if (!out) return FMM_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (nbox < 1 || !box || !N || (precision != FMM_PREC_MIXED && precision != FMM_PREC_FP64))
+        return FMM_ERR_INVALID_ARG;
+    for (int i = 0; i < nbox; ++i)
+        if (!(box[i] > 0.0) || !isfinite(box[i]) || N[i] < 1 || (p && p[i] > P_MAX) ||
+            (depth && depth[i] > 8))
+            return FMM_ERR_INVALID_ARG;
+    fmm_batch b = new (std::nothrow) fmm_batch_s();
+    if (!b) return FMM_ERR_OOM;
+    b->nbox = nbox;
+    b->precision = precision;
+    b->plans.assign(nbox, nullptr);
+    b->depth.assign(nbox, 0);
+    const int ns = nbox < BATCH_MAX_STREAMS ? nbox : BATCH_MAX_STREAMS;
+    fmm_status s = FMM_OK;
+    int lo = 0, hi = 0;
+    if (cudaDeviceGetStreamPriorityRange(&lo, &hi) != cudaSuccess) s = FMM_ERR_CUDA;
+    for (int k = 0; k < ns && s == FMM_OK; ++k) {
+        cudaStream_t st;
+        cudaEvent_t ev;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) s = FMM_ERR_CUDA;
+        else b->streams.push_back(st);
+        if (s == FMM_OK && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) s = FMM_ERR_CUDA;
+        else if (s == FMM_OK) b->ev_done.push_back(ev);
+    }
+    if (s == FMM_OK && cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking) != cudaSuccess) s = FMM_ERR_CUDA;
+    if (s == FMM_OK && cudaEventCreateWithFlags(&b->ev_start, cudaEventDisableTiming) != cudaSuccess) s = FMM_ERR_CUDA;
+    b->order.resize(nbox);
+    for (int i = 0; i < nbox; ++i) b->order[i] = i;
+    std::stable_sort(b->order.begin(), b->order.end(), [&](int x, int y) { return N[x] > N[y]; });
+
+    // depth: given, or tuned per group of boxes with the same starting guess
+    std::vector<int> offset(9, 0);
+    std::vector<bool> tuned(9, false);
+    double *tpos = nullptr, *tq = nullptr;
+    uint8_t *tsol = nullptr;
+    for (int i = 0; i < nbox && s == FMM_OK; ++i) {
+        if (depth && depth[i] > 0) {
+            b->depth[i] = depth[i];
+            continue;
+        }
+        const int d0 = depth_guess(N[i]);
+        if (!tuned[d0]) {
+            // the group's box of median size
+            std::vector<int> grp;
+            for (int j = 0; j < nbox; ++j)
+                if (!(depth && depth[j] > 0) && depth_guess(N[j]) == d0) grp.push_back(j);
+            std::sort(grp.begin(), grp.end(), [&](int x, int y) { return N[x] < N[y]; });
+            const int r = grp[grp.size() / 2];
+            const int pr = (p && p[r] >= 0) ? p[r] : 12;
+            cudaFree(tpos);
+            cudaFree(tq);
+            cudaFree(tsol);
+            tpos = tq = nullptr;
+            tsol = nullptr;
+            if (cudaMalloc(&tpos, sizeof(double) * 3 * N[r]) != cudaSuccess ||
+                cudaMalloc(&tq, sizeof(double) * N[r]) != cudaSuccess || cudaMalloc(&tsol, N[r]) != cudaSuccess) {
+                s = FMM_ERR_OOM;
+                break;
+            }
+            k_tune_fill<<<1216, 256, 0, b->streams[0]>>>(N[r], box[r], tpos, tq, tsol);
+            float best = 1e30f;
+            int best_off = 0;
+            for (int off = -1; off <= 1 && s == FMM_OK; ++off) {
+                const int dc = d0 + off;
+                if (dc < 2 || dc > 8) continue;
+                fmm_plan h = nullptr;
+                if (make_plan(box[r], N[r], dc, pr, precision, b->streams[0], &h) != FMM_OK) continue;
+                float ms = 0;
+                if (time_plan(h, tpos, tq, tsol, &ms) == FMM_OK && ms < best) {
+                    best = ms;
+                    best_off = off;
+                }
+                fmm_plan_destroy(h);
+            }
+            if (best >= 1e30f) s = FMM_ERR_INTERNAL;
+            offset[d0] = best_off;
+            tuned[d0] = true;
+        }
+        b->depth[i] = d0 + offset[d0];
+    }
+    cudaFree(tpos);
+    cudaFree(tq);
+    cudaFree(tsol);
+    // the plans, on the streams round robin in size order
+    for (int k = 0; k < nbox && s == FMM_OK; ++k) {
+        const int i = b->order[k];
+        const int pi = (p && p[i] >= 0) ? p[i] : 12;
+        s = make_plan(box[i], N[i], b->depth[i], pi, precision, b->streams[k % ns], &b->plans[i]);
+    }
+    if (s != FMM_OK) {
+        batch_free(b);
+        return s;
+    }
+    *out = b;
+    return FMM_OK;
+}
+
+fmm_status fmm_batch_lambda_energies(fmm_batch b, const double *const *pos, const double *const *q,
+                                     const uint8_t *const *is_solute, const double *lambda_c, double *e_total,
+                                     double *e_uv, double *v_lambda, double *dv_dlambda)
+{
+    if (!b || !pos || !q || !is_solute) return FMM_ERR_INVALID_ARG;
+    for (int i = 0; i < b->nbox; ++i)
+        if (!pos[i] || !q[i] || !is_solute[i]) return FMM_ERR_INVALID_ARG;
+    bool fresh = false;  // results come from the enqueued path
+    if (b->use_graph && graph_matches(b, pos, q, is_solute)) {
+        FMM_CUDA_TRY(cudaGraphLaunch(b->graph, b->origin));
+        FMM_CUDA_TRY(cudaStreamSynchronize(b->origin));
+        ++b->replays;
+        for (int i = 0; i < b->nbox; ++i)
+            if (solute_count_host(b->plans[i]->P) != b->gcount[i]) fresh = true;  // a count changed: redo
+        if (!fresh) goto results;
+    }
+    {
+        fmm_status s = batch_enqueue(b, pos, q, is_solute);
+        if (s != FMM_OK) return s;
+        s = batch_sync(b);
+        if (s != FMM_OK) return s;
+        ++b->enqueued;
+        if (b->use_graph) batch_capture(b, pos, q, is_solute);
+    }
+results:
+    fmm_status worst = FMM_OK;
+    for (int i = 0; i < b->nbox; ++i) {
+        fmm_energy_terms t;
+        fmm_uv_terms u;
+        fmm_status s = eval_results(b->plans[i]->P, &t, &u);
+        if (s != FMM_OK && worst == FMM_OK) worst = s;
+        const double lam = lambda_c ? lambda_c[i] : 0.0;
+        if (e_total) e_total[i] = t.total;
+        if (e_uv) e_uv[i] = u.e_uv;
+        if (v_lambda) v_lambda[i] = t.total - lam * u.e_uv;
+        if (dv_dlambda) dv_dlambda[i] = -u.e_uv;
+    }
+    return worst;
+}
+
+fmm_status fmm_batch_info(fmm_batch b, int i, int *depth, int *p, int64_t *replays, int64_t *enqueued)
+{
+    if (!b || i < 0 || i >= b->nbox) return FMM_ERR_INVALID_ARG;
+    if (depth) *depth = b->plans[i]->P.d;
+    if (p) *p = b->plans[i]->P.p;
+    if (replays) *replays = b->replays;
+    if (enqueued) *enqueued = b->enqueued;
+    return FMM_OK;
+}
+
+fmm_status fmm_batch_set_graph(fmm_batch b, int enable)
+{
+    if (!b || (enable != 0 && enable != 1)) return FMM_ERR_INVALID_ARG;
+    b->use_graph = enable != 0;
+    if (!b->use_graph && b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    return FMM_OK;
+}
+
+void fmm_batch_destroy(fmm_batch b) { batch_free(b); }
+
+}  // extern "C"

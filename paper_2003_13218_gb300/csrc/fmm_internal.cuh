@@ -82,6 +82,7 @@ struct Plan {
     cudaStream_t stream = 0;
     bool timings_on = false;
     bool tc_pair = true;  // CTA-pair (2-SM) tensor-core M2L where the level allows it
+    int known_count = -1; // >= 0: the solute count the caller already knows (no host wait; graph capture)
     int nc = 0;
     int64_t nleaf = 0;  // 8^d
     int64_t launches = 0;
@@ -235,6 +236,9 @@ fmm_status solute_prepare(Plan &P);
 void solute_free(Plan &P);
 // right after the sort: count the solute charges and copy the count to the host asynchronously
 fmm_status solute_count(Plan &P);
+// the host copy of the last solute count (valid once the plan's stream has passed the copy); -1 when the
+// plan has no sparse pass
+int solute_count_host(const Plan &P);
 // after the full pass's upward sweep: the pass's prologue (active cells, solute moments, FP64 solvent
 // expansions at the active cells) on a high-priority side stream, overlapping the full pass's M2L
 fmm_status solute_prologue(Plan &P);
@@ -256,6 +260,14 @@ fmm_status launch_m2m_tc(Plan &P, int level);
 fmm_status launch_m2l_tc(Plan &P, int level, bool precise = false, bool split = true);
 void tc_free(Plan &P);
 
+// phases of one energy + solute-solvent evaluation on device inputs (fmm_api.cu), for the batch API:
+// front (sort .. near field) and back (solute pass, reductions, asynchronous copy of the results into
+// P.h_out) only enqueue work, except that back waits for the host copy of the solute count unless
+// P.known_count >= 0; results are read after the plan's stream is synchronised
+fmm_status eval_enqueue_front(Plan &P, const double *dpos, const double *dq, const uint8_t *dsol);
+fmm_status eval_enqueue_back(Plan &P, const double *dq);
+fmm_status eval_results(Plan &P, fmm_energy_terms *terms, fmm_uv_terms *uv);
+
 #define FMM_CUDA_TRY(expr)                                        \
     do {                                                          \
         cudaError_t e_ = (expr);                                  \
@@ -270,3 +282,8 @@ void tc_free(Plan &P);
     } while (0)
 
 }  // namespace fmm
+
+struct fmm_plan_s {
+    fmm::Plan P;
+};
+

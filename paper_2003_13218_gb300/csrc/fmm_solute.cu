@@ -749,6 +749,12 @@ void solute_free(Plan &P)
     P.sol = nullptr;
 }
 
+int solute_count_host(const Plan &P)
+{
+    const SoluteScratch *S = (const SoluteScratch *)P.sol;
+    return S ? *S->h_count : -1;
+}
+
 fmm_status solute_count(Plan &P)
 {
     SoluteScratch *S = (SoluteScratch *)P.sol;
@@ -789,11 +795,12 @@ fmm_status launch_solute_pass(Plan &P, bool *done)
         fmm_status s = solute_prologue(P);
         if (s != FMM_OK) return s;
     }
-    // the count was copied right after the sort; the join orders the prologue before the rest
-    FMM_CUDA_TRY(cudaEventSynchronize(S->ev_count));
+    // the count was copied right after the sort (or the caller knows it); the join orders the
+    // prologue before the rest
+    if (P.known_count < 0) FMM_CUDA_TRY(cudaEventSynchronize(S->ev_count));
     FMM_CUDA_TRY(cudaStreamWaitEvent(P.stream, S->ev_act, 0));
     S->count_pending = S->prologue_pending = false;
-    int n = *S->h_count;
+    int n = P.known_count >= 0 ? P.known_count : *S->h_count;
     if (n > NU_MAX) return FMM_OK;
     if (n == 0) {
         size_t bytes = (P.precision == FMM_PREC_FP64 ? sizeof(double) : sizeof(float)) * P.N;

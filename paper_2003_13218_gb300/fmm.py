@@ -89,6 +89,18 @@ def load_library(path: str = LIB_PATH):
     L.fmm_plan_m2l_backend.restype = c_int
     L.fmm_plan_destroy.argtypes = [vp]
     L.fmm_plan_destroy.restype = None
+    pp = ctypes.POINTER(vp)
+    L.fmm_batch_create.argtypes = [c_int, vp, vp, vp, vp, c_int, ctypes.POINTER(vp)]
+    L.fmm_batch_create.restype = c_int
+    L.fmm_batch_lambda_energies.argtypes = [vp, pp, pp, pp, vp, vp, vp, vp, vp]
+    L.fmm_batch_lambda_energies.restype = c_int
+    L.fmm_batch_info.argtypes = [vp, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int), ctypes.POINTER(i64),
+                                 ctypes.POINTER(i64)]
+    L.fmm_batch_info.restype = c_int
+    L.fmm_batch_set_graph.argtypes = [vp, c_int]
+    L.fmm_batch_set_graph.restype = c_int
+    L.fmm_batch_destroy.argtypes = [vp]
+    L.fmm_batch_destroy.restype = None
     L.fmm_status_string.argtypes = [c_int]
     L.fmm_status_string.restype = ctypes.c_char_p
     _LIB = L
@@ -204,6 +216,64 @@ class FMMPlan:
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             self._lib.fmm_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class FMMBatch:
+    """Independent boxes evaluated together (fmm_batch_*): per box the total energy, the
+    solute-solvent interaction E_uv, V_lambda = E - lambda_C E_uv and dV/dlambda_C = -E_uv.
+
+    Inputs are lists of CUDA tensors; keep the same tensors (updated in place) between
+    calls so that the batch can replay its recorded CUDA graph."""
+
+    def __init__(self, boxes, Ns, depths=None, ps=None, precision: str = "mixed"):
+        self._lib = load_library()
+        n = len(boxes)
+        self.n = n
+        self._box = np.ascontiguousarray(boxes, np.float64)
+        self._N = np.ascontiguousarray(Ns, np.int64)
+        self._d = None if depths is None else np.ascontiguousarray(depths, np.int32)
+        self._p = None if ps is None else np.ascontiguousarray(ps, np.int32)
+        h = ctypes.c_void_p()
+        _check(self._lib.fmm_batch_create(n, self._box.ctypes.data, self._N.ctypes.data,
+                                          None if self._d is None else self._d.ctypes.data,
+                                          None if self._p is None else self._p.ctypes.data,
+                                          PRECISION[precision], ctypes.byref(h)), "fmm_batch_create")
+        self._h = h
+
+    def lambda_energies(self, pos, q, is_solute, lambda_c=None):
+        n = self.n
+        keep = list(pos) + list(q) + list(is_solute)
+        arr = lambda xs: (ctypes.c_void_p * n)(*[ctypes.c_void_p(x.data_ptr()) for x in xs])
+        P, Q, S = arr(pos), arr(q), arr(is_solute)
+        lam = None if lambda_c is None else np.ascontiguousarray(lambda_c, np.float64)
+        out = {k: np.zeros(n) for k in ("e_total", "e_uv", "v_lambda", "dv_dlambda")}
+        _check(self._lib.fmm_batch_lambda_energies(self._h, P, Q, S, None if lam is None else lam.ctypes.data,
+                                                   out["e_total"].ctypes.data, out["e_uv"].ctypes.data,
+                                                   out["v_lambda"].ctypes.data, out["dv_dlambda"].ctypes.data),
+               "fmm_batch_lambda_energies")
+        del keep
+        return out
+
+    def info(self, i: int):
+        d, p = ctypes.c_int(), ctypes.c_int()
+        r, e = ctypes.c_int64(), ctypes.c_int64()
+        _check(self._lib.fmm_batch_info(self._h, i, ctypes.byref(d), ctypes.byref(p), ctypes.byref(r),
+                                        ctypes.byref(e)), "fmm_batch_info")
+        return {"depth": d.value, "p": p.value, "replays": r.value, "enqueued": e.value}
+
+    def set_graph(self, enable: bool):
+        _check(self._lib.fmm_batch_set_graph(self._h, 1 if enable else 0), "fmm_batch_set_graph")
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.fmm_batch_destroy(self._h)
             self._h = ctypes.c_void_p()
 
     def __del__(self):
