@@ -69,6 +69,23 @@ def kernel_sha(rel):
         return None
 
 
+def max_over_ranks(ms: float, device) -> float:
+    """The slowest rank's time: every rank returns the maximum of `ms` over the process group."""
+    import torch
+    import torch.distributed as dist
+    if not dist.is_initialized() or dist.get_world_size() == 1:
+        return ms
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(n_per_rank: int, steps: int, world: int, ms_total: float) -> float:
+    """Whole-job particle-evals/s: every rank evaluates its own replica `steps` times; the job
+    takes the slowest rank's time."""
+    return n_per_rank * steps * world / (ms_total / 1e3)
+
+
 def load_peaks():
     try:
         with open(PEAKS_FILE) as f:
@@ -199,9 +216,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     clocks = sampler.stop()
     if ws > 1:
-        t = torch.tensor([ms_total], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+        ms_total = max_over_ranks(ms_total, dev)
         dist.barrier()
     stage = plan.timings()
     F_mixed = F.cpu().numpy()
@@ -214,6 +229,27 @@ def run_ours(args):
     for _ in range(args.steps):
         plan.evaluate(hpos, hq, hsol, forces=hF)
     e2e_s = time.perf_counter() - t0
+
+    # cost of the solute-solvent energy: the reduced scheme (Eq. FMMcalc, one extra sparse pass)
+    # against the conventional three passes (Eq. FMMconv: u+v, u alone, v alone), energies only
+    def ev_ms(fn, k=3):
+        fn()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / k
+    qu = torch.where(sol == 1, q, torch.zeros_like(q))
+    qv = q - qu
+    t_e = ev_ms(lambda: plan.evaluate(pos, q, None, forces=None))
+    t_uv = ev_ms(lambda: plan.evaluate(pos, q, sol, forces=None))
+    t_u = ev_ms(lambda: plan.evaluate(pos, qu, None, forces=None))
+    t_v = ev_ms(lambda: plan.evaluate(pos, qv, None, forces=None))
+    uv_cost = {"energy_only_ms": t_e, "energy_and_e_uv_reduced_ms": t_uv, "three_pass_ms": t_e + t_u + t_v,
+               "e_uv_extra_reduced_ms": t_uv - t_e, "e_uv_extra_three_pass_ms": t_u + t_v}
     plan.close()
 
     # the FP64 path on the same input
@@ -249,7 +285,7 @@ def run_ours(args):
         if ws > 1:
             dist.destroy_process_group()
         return
-    value = N * args.steps * ws / (ms_total / 1e3)
+    value = job_throughput(N, args.steps, ws, ms_total)
     peaks, peak_kind = load_peaks()
     uses_tc = backend == "tcgen05"
     fused = uses_tc and args.split == "fp16x2"  # the fp16 split fuses the L2L into each level's launch
@@ -304,6 +340,7 @@ def run_ours(args):
                    "l2": "flushed between timed steps (256 MB write)", "parallelism": "replicas" if ws > 1 else "1 GPU",
                    "m2l_split": args.split},
         "roofline": roof,
+        "solute_solvent_cost": uv_cost,
         "e2e": {"value": N * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": N * (24 + 8 + 1),
                 "d2h_bytes_per_step": N * 24 + 29 * 8 + 4},
         "gpu_launches": launches * args.steps,

@@ -49,3 +49,29 @@ def test_sparse_solute_pass_against_oracle(n_solute):
         for k in KEYS:
             assert abs(uv[k] - ref[k]) <= tol * scale, (precision, k, uv[k], ref[k])
         assert abs((uv["A"] - uv["B"]) - uv["C"]) <= 10 * tol * scale  # reciprocity (P10)
+
+
+@pytest.mark.parametrize("n_solute", [1, 40])
+def test_three_pass_solute_solvent_matches_reduced(n_solute):
+    """The conventional scheme (Eq. FMMconv: three full passes, u+v, u alone and v alone, each
+    set with its own background) against the reduced far field of Eq. FMMcalc.  The potentials
+    are linear in the charges for a fixed tree, so E(u+v) - E(u) - E(v) and (A - B + C)/2 plus
+    the near-field and background cross terms are the same quantity, equal up to rounding (FP64
+    path)."""
+    from paper_2003_13218_gb300.fmm import FMMPlan
+    b = _box()
+    sol = np.zeros(b.N, np.uint8)
+    sol[:n_solute] = 1
+    d, p = 4, 8
+    dev = "cuda:0"
+    plan = FMMPlan(b.L, b.N, d, p, precision="fp64")
+    pos = torch.from_numpy(b.pos).to(dev)
+    q = torch.from_numpy(b.q).to(dev)
+    t, uv = plan.evaluate(pos, q, torch.from_numpy(sol).to(dev), forces=None)
+    qu = torch.from_numpy(np.where(sol == 1, b.q, 0.0)).to(dev)
+    qv = torch.from_numpy(np.where(sol == 1, 0.0, b.q)).to(dev)
+    e_u, _ = plan.energy(pos, qu)
+    e_v, _ = plan.energy(pos, qv)
+    plan.close()
+    three_pass = t["total"] - e_u - e_v
+    assert abs(three_pass - uv["e_uv"]) <= 1e-10 * abs(t["total"])
