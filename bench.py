@@ -193,6 +193,8 @@ def run_ours(args):
     launches = plan.last_launch_count()
     backend = plan.m2l_backend(d)
 
+    jgen = torch.Generator(device=dev)
+    jgen.manual_seed(1234 + rank)
     sampler = ClockSampler(local)
     if ws > 1:
         dist.barrier()
@@ -202,7 +204,9 @@ def run_ours(args):
     ms_total = 0.0
     m2l_ms = []
     terms = uv = None
-    for _ in range(args.steps):
+    for k in range(args.steps):
+        if args.jitter > 0 and k > 0:  # new coordinates every call, as in a trajectory (before e0: not timed)
+            pos.add_(torch.randn(pos.shape, generator=jgen, device=dev, dtype=torch.float64) * args.jitter)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -337,7 +341,7 @@ def run_ours(args):
         "config": {"workload": "%s: %s+ + %d TIP3P waters, N=%d, L=%.2f A, depth %d, p %d, ws 1, mixed precision, "
                                "energy+forces+solute-solvent per step" % (args.workload, box.ion, box.n_waters, N,
                                                                           box.L, d, p),
-                   "l2": "flushed between timed steps (256 MB write)", "parallelism": "replicas" if ws > 1 else "1 GPU",
+                   "l2": "flushed between timed steps (256 MB write)", "jitter_A": args.jitter, "parallelism": "replicas" if ws > 1 else "1 GPU",
                    "m2l_split": args.split},
         "roofline": roof,
         "solute_solvent_cost": uv_cost,
@@ -500,6 +504,8 @@ def main():
     ap.add_argument("--split", default="fp16x2", choices=["fp16x2", "bf16x3", "bf16x2", "bf16a2b3", "fp32"])
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--jitter", type=float, default=0.0,
+                    help="jitter every position by N(0, jitter^2) A between timed calls (untimed)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

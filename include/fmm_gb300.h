@@ -103,10 +103,15 @@ enum {
     FMM_OPT_M2L_SPLIT = 4, /* ival: mixed-precision M2L operand split, FMM_SPLIT_* (default FP16X2) */
     FMM_OPT_STREAM = 5,    /* ival: cudaStream_t cast to int64 (0 = legacy default stream) */
     FMM_OPT_TIMINGS = 6,   /* ival: 1 records per-stage CUDA events (adds event overhead) */
-    FMM_OPT_M2L_PAIR = 7   /* ival: 1 (default) lets the fp16x2 tensor-core M2L of levels with an even
+    FMM_OPT_M2L_PAIR = 7,  /* ival: 1 (default) lets the fp16x2 tensor-core M2L of levels with an even
                               number of 128-cell tiles per class run on CTA pairs (2-SM MMAs, half the
                               operator traffic per SM); 0 keeps every level on single-CTA MMAs */
+    FMM_OPT_BOUNDARY = 8   /* ival: FMM_BOUNDARY_CONDUCTING (default; Eq. Velecfull, with the dipole surface
+                              term -(2 pi/3V) mu.mu of App. D) or FMM_BOUNDARY_VACUUM (App. D: FMM's own
+                              boundary, without that term, its force and its solute-solvent cross term
+                              -(4 pi/3V) mu_u.mu_v) */
 };
+enum { FMM_BOUNDARY_CONDUCTING = 0, FMM_BOUNDARY_VACUUM = 1 };
 enum { FMM_PREC_FP64 = 0, FMM_PREC_MIXED = 1 };
 enum {
     FMM_SPLIT_BF16X3 = 0,    /* tensor-core M2L: both operands as 3 bf16 terms, 6 products */

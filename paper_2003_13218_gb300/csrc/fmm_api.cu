@@ -362,6 +362,10 @@ fmm_status fmm_plan_set_option(fmm_plan plan, int key, int64_t ival, double dval
     case FMM_OPT_TIMINGS:
         P.timings_on = ival != 0;
         return FMM_OK;
+    case FMM_OPT_BOUNDARY:
+        if (ival != FMM_BOUNDARY_CONDUCTING && ival != FMM_BOUNDARY_VACUUM) return FMM_ERR_INVALID_ARG;
+        P.boundary = (int)ival;
+        return FMM_OK;
     case FMM_OPT_M2L_PAIR:
         if (ival != 0 && ival != 1) return FMM_ERR_INVALID_ARG;
         P.tc_pair = ival != 0;

@@ -83,6 +83,7 @@ struct Plan {
     bool timings_on = false;
     bool tc_pair = true;  // CTA-pair (2-SM) tensor-core M2L where the level allows it
     int known_count = -1; // >= 0: the solute count the caller already knows (no host wait; graph capture)
+    int boundary = 0;     // FMM_BOUNDARY_CONDUCTING (Eq. Velecfull) or FMM_BOUNDARY_VACUUM (App. D)
     int nc = 0;
     int64_t nleaf = 0;  // 8^d
     int64_t launches = 0;

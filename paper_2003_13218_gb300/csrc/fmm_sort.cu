@@ -286,8 +286,11 @@ __global__ void k_bc_final(const double *__restrict__ partial, int nb, double *_
 // Combine into the terms of Eq. Velecfull and Eq. FMMcalc.
 // out layout: [0..9] moments (Q, mu, S2, Qu, mu_u, S2u), [10..15] energy parts,
 // [16..21] terms (near, far, charged, quad, dipole, total), [22..28] uv terms.
+// vacuum: the boundary at infinity is vacuum (App. D): the dipole surface term
+// -(2 pi / 3V) mu.mu that gives the conducting boundary is left out, and so is
+// its solute-solvent cross term -(4 pi / 3V) mu_u.mu_v
 __global__ void k_energy_final(const double *__restrict__ partial, int nb, double *__restrict__ out, double box,
-                               double kappa, int with_uv)
+                               double kappa, int with_uv, int vacuum)
 {
     final_sum<6>(partial, nb, out + 10);
     __syncthreads();
@@ -298,7 +301,7 @@ __global__ void k_energy_final(const double *__restrict__ partial, int nb, doubl
     double e_near = out[10], e_far = out[11];
     double e_cha = -PI / (2.0 * V * kappa * kappa) * Q * Q;
     double e_quad = 2.0 * PI / (3.0 * V) * Q * S2;
-    double e_dip = -2.0 * PI / (3.0 * V) * (mx * mx + my * my + mz * mz);
+    double e_dip = vacuum ? 0.0 : -2.0 * PI / (3.0 * V) * (mx * mx + my * my + mz * mz);
     KSum t{0, 0};
     t.add(e_near);
     t.add(e_far);
@@ -315,8 +318,8 @@ __global__ void k_energy_final(const double *__restrict__ partial, int nb, doubl
         double Qu = out[5], mux = out[6], muy = out[7], muz = out[8], S2u = out[9];
         double Qv = Q - Qu, mvx = mx - mux, mvy = my - muy, mvz = mz - muz, S2v = S2 - S2u;
         double A = out[12], B = out[13], C = out[14], nf = out[15];
-        double bc = -PI * Qu * Qv / (V * kappa * kappa) + 2.0 * PI / (3.0 * V) * (Qu * S2v + Qv * S2u) -
-                    4.0 * PI / (3.0 * V) * (mux * mvx + muy * mvy + muz * mvz);
+        double bc = -PI * Qu * Qv / (V * kappa * kappa) + 2.0 * PI / (3.0 * V) * (Qu * S2v + Qv * S2u);
+        if (!vacuum) bc -= 4.0 * PI / (3.0 * V) * (mux * mvx + muy * mvy + muz * mvz);
         KSum w{0, 0};
         w.add(A);
         w.add(-B);
@@ -336,11 +339,13 @@ __global__ void k_energy_final(const double *__restrict__ partial, int nb, doubl
     }
 }
 
-// F_i = q_i (E_nf - grad Phi_ff) - (4 pi / 3V) q_i (Q r_i - mu), scattered to input order
+// F_i = q_i (E_nf - grad Phi_ff) - (4 pi / 3V) q_i (Q r_i - mu), scattered to
+// input order; with the vacuum boundary the mu part (the dipole surface term's
+// force) is left out
 template <typename T>
 __global__ void k_forces_out(int64_t N, const int *__restrict__ perm, const Particle<T> *__restrict__ sp,
                              const T *__restrict__ f_nf, const T *__restrict__ g_ff, const double *__restrict__ wpos,
-                             const double *__restrict__ q, const double *__restrict__ mom, double box,
+                             const double *__restrict__ q, const double *__restrict__ mom, double box, int vacuum,
                              double *__restrict__ forces)
 {
     int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -353,7 +358,7 @@ __global__ void k_forces_out(int64_t N, const int *__restrict__ perm, const Part
     double Q = mom[0];
     for (int a = 0; a < 3; ++a) {
         double f = qi * ((double)f_nf[3 * s + a] - (double)g_ff[3 * s + a]);
-        f -= c * qi * (Q * wpos[3 * (int64_t)i + a] - mom[1 + a]);
+        f -= c * qi * (Q * wpos[3 * (int64_t)i + a] - (vacuum ? 0.0 : mom[1 + a]));
         forces[3 * (int64_t)i + a] = f;
     }
 }
@@ -422,7 +427,8 @@ fmm_status launch_energy_reduce(Plan &P, bool with_uv)
     }
     FMM_LAUNCH_CHECK(P);
     double kappa = P.kappa > 0 ? P.kappa : 2.0 / P.box;
-    k_energy_final<<<1, RED_THREADS, 0, P.stream>>>(part, RED_BLOCKS, P.red_out, P.box, kappa, with_uv ? 1 : 0);
+    k_energy_final<<<1, RED_THREADS, 0, P.stream>>>(part, RED_BLOCKS, P.red_out, P.box, kappa, with_uv ? 1 : 0,
+                                                    P.boundary);
     FMM_LAUNCH_CHECK(P);
     return FMM_OK;
 }
@@ -432,11 +438,11 @@ fmm_status launch_forces_out(Plan &P, const double *q, double *forces)
     if (P.precision == FMM_PREC_FP64)
         k_forces_out<double><<<blocks_for(P.N, 256), 256, 0, P.stream>>>(
             P.N, P.perm, (const Particle<double> *)P.sorted, (const double *)P.f_nf, (const double *)P.g_ff, P.wpos,
-            q, P.red_out, P.box, forces);
+            q, P.red_out, P.box, P.boundary, forces);
     else
         k_forces_out<float><<<blocks_for(P.N, 256), 256, 0, P.stream>>>(
             P.N, P.perm, (const Particle<float> *)P.sorted, (const float *)P.f_nf, (const float *)P.g_ff, P.wpos, q,
-            P.red_out, P.box, forces);
+            P.red_out, P.box, P.boundary, forces);
     FMM_LAUNCH_CHECK(P);
     return FMM_OK;
 }

@@ -21,6 +21,8 @@ LIB_PATH = os.path.join(_HERE, "libfmm_gb300.so")
 
 FMM_OPT_WS, FMM_OPT_PRECISION, FMM_OPT_KAPPA, FMM_OPT_M2L_SPLIT, FMM_OPT_STREAM, FMM_OPT_TIMINGS = 1, 2, 3, 4, 5, 6
 FMM_OPT_M2L_PAIR = 7
+FMM_OPT_BOUNDARY = 8
+BOUNDARY = {"conducting": 0, "vacuum": 1}
 PRECISION = {"fp64": 0, "mixed": 1}
 SPLIT = {"bf16x3": 0, "bf16x2": 1, "fp32": 2, "bf16a2b3": 3, "fp16x2": 4}
 STATUS = ["ok", "invalid argument", "non-finite input", "CUDA error", "out of memory", "timeout",
@@ -128,7 +130,7 @@ class FMMPlan:
     """A plan for N charges in a cubic box of side ``box`` (A), depth d, order p."""
 
     def __init__(self, box: float, N: int, depth: int, p: int, precision: str = "fp64", kappa: float | None = None,
-                 split: str = "fp16x2", timings: bool = False, m2l_pair: bool = True):
+                 split: str = "fp16x2", timings: bool = False, m2l_pair: bool = True, boundary: str = "conducting"):
         self._lib = load_library()
         h = ctypes.c_void_p()
         _check(self._lib.fmm_plan_create(float(box), int(N), int(depth), int(p), ctypes.byref(h)), "fmm_plan_create")
@@ -144,6 +146,8 @@ class FMMPlan:
             self.set_option(FMM_OPT_TIMINGS, 1)
         if not m2l_pair:
             self.set_option(FMM_OPT_M2L_PAIR, 0)
+        if boundary != "conducting":
+            self.set_option(FMM_OPT_BOUNDARY, BOUNDARY[boundary])
         self.precision = precision
 
     def set_option(self, key: int, ival: int = 0, dval: float = 0.0):

@@ -286,3 +286,27 @@ def test_100k_workload_sampled_against_oracle():
     assert np.sqrt(np.mean((F_m[idx] - ref["forces"]) ** 2)) < 1e-5 * scale
     assert abs(t_m["total"] - t_64["total"]) <= 1e-6 * abs(t_64["total"])
     assert abs(uv_m["e_uv"] - uv_64["e_uv"]) <= 1e-5 * (abs(uv_64["A"]) + abs(uv_64["C"]))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_vacuum_boundary_differs_by_the_dipole_surface_term(precision):
+    """App. D: FMM's own boundary at infinity is vacuum; the conducting boundary of Eq. Velecfull
+    subtracts the dipole surface term (2 pi / 3V) mu.mu.  The vacuum option therefore adds that
+    term back to the energy, -(4 pi / 3V) q_i mu to every force, and (4 pi / 3V) mu_u.mu_v to the
+    solute-solvent energy (mu = sum q r over the wrapped coordinates, origin at the box corner)."""
+    b = boxes.ion_in_water(1500, "Mg", seed=12)
+    b.pos[5] += [b.L, -b.L, 0.25]  # one charge outside the cell: the wrapped position counts
+    d, p = 3, 8
+    sol = b.is_solute
+    tc, uvc, Fc = _run(b.pos, b.q, b.L, d, p, precision=precision, sol=sol)
+    tv, uvv, Fv = _run(b.pos, b.q, b.L, d, p, precision=precision, sol=sol, boundary="vacuum")
+    r = np.mod(b.pos, b.L)
+    mu = (b.q[:, None] * r).sum(0)
+    mu_u = (b.q[sol == 1, None] * r[sol == 1]).sum(0)
+    V = b.L ** 3
+    scale = abs(tc["total"])
+    assert abs((tv["total"] - tc["total"]) - 2 * np.pi / (3 * V) * mu @ mu) <= 1e-12 * scale
+    assert tv["dipole_surface"] == 0.0
+    dF = -(4 * np.pi / (3 * V)) * b.q[:, None] * mu[None, :]
+    assert np.max(np.abs((Fv - Fc) - dF)) <= 1e-9 * np.max(np.abs(Fc))
+    assert abs((uvv["e_uv"] - uvc["e_uv"]) - 4 * np.pi / (3 * V) * mu_u @ (mu - mu_u)) <= 1e-12 * scale
