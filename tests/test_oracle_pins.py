@@ -343,6 +343,29 @@ def test_fmm_converges_to_ewald_in_p():
     assert errs[2] < 1e-6
 
 
+def test_fmm_ws2_converges_faster_than_ws1():
+    """ws = 2 (the paper's near field of second-nearest neighbour leaves): interaction lists of
+    875 cells, 125 near-field leaves, a 5^3 block left to the M2L levels.  Against Ewald on the
+    Mg2+ box the error falls with p and stays below the ws = 1 error at the same p (the nearest
+    M2L sources are twice as far)."""
+    b, d, _ = boxes.workload("mg_3k")
+    e = oracle.ewald(b.pos, b.q, b.L)["energy"]
+    e1 = [rel(oracle.fmm(b.pos, b.q, b.L, d, p, ws=1, forces=False)["total"], e) for p in (4, 8)]
+    e2 = [rel(oracle.fmm(b.pos, b.q, b.L, d, p, ws=2, forces=False)["total"], e) for p in (4, 8)]
+    assert e2[0] > e2[1]
+    assert e2[0] < e1[0] and e2[1] < e1[1]
+    assert e2[1] < 1e-6
+
+
+@pytest.mark.parametrize("N", [3, 17])
+def test_fmm_ws2_tiny_boxes_against_ewald(N):
+    """P8 at ws = 2: brute force on tiny net-charged sets, d = 3 (8 > 2 ws + 1), p = 16."""
+    pos, q = boxes.random_charges(N, 1.0, seed=300 + N)
+    e = oracle.ewald(pos, q, 1.0)["energy"]
+    f = oracle.fmm(pos, q, 1.0, 3, 16, ws=2, forces=False)["total"]
+    assert rel(f, e) < 2e-7
+
+
 @pytest.mark.parametrize("N", [2, 5, 11, 24])
 def test_fmm_tiny_boxes_against_ewald(N):
     """P8: brute force on tiny net-charged sets, d = 2, p = 20."""
