@@ -96,7 +96,9 @@ typedef struct {
 
 /* Options for fmm_plan_set_option. */
 enum {
-    FMM_OPT_WS = 1,        /* well-separatedness; ival must be 1 (the only one built) */
+    FMM_OPT_WS = 1,        /* well-separatedness ws of App. B: 1 (default; 189-cell interaction lists,
+                              27-leaf near field) or 2 (the paper's setting: 875 and 125; needs 2^depth > 5);
+                              other values FMM_ERR_UNSUPPORTED (> 2) or FMM_ERR_INVALID_ARG */
     FMM_OPT_PRECISION = 2, /* ival: FMM_PREC_FP64 (default) or FMM_PREC_MIXED */
     FMM_OPT_KAPPA = 3,     /* dval: splitting parameter kappa of Eq. 12 and Eq. 6 in 1/A;
                               <= 0 restores the default kappa = 2 / b */

@@ -337,9 +337,15 @@ fmm_status fmm_plan_set_option(fmm_plan plan, int key, int64_t ival, double dval
     if (!plan) return FMM_ERR_INVALID_ARG;
     Plan &P = plan->P;
     switch (key) {
-    case FMM_OPT_WS:
-        if (ival == 1) return FMM_OK;
-        return ival >= 2 ? FMM_ERR_UNSUPPORTED : FMM_ERR_INVALID_ARG;
+    case FMM_OPT_WS: {
+        if (ival < 1) return FMM_ERR_INVALID_ARG;
+        if (ival > WS_MAX) return FMM_ERR_UNSUPPORTED;
+        if ((1 << P.d) <= 2 * ival + 1) return FMM_ERR_INVALID_ARG;  // the near field would hold own images
+        if (P.ws == (int)ival) return FMM_OK;
+        P.ws = (int)ival;
+        fmm_status st = solute_prepare(P);  // interaction-list sized buffers
+        return st == FMM_OK ? rebuild(P) : st;
+    }
     case FMM_OPT_PRECISION:
         if (ival != FMM_PREC_FP64 && ival != FMM_PREC_MIXED) return FMM_ERR_INVALID_ARG;
         if (P.precision == (int)ival) return FMM_OK;

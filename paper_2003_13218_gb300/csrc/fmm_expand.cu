@@ -96,15 +96,16 @@ __device__ void build_real_operator(int p, const Cx<double> *O, double *__restri
     }
 }
 
-// one block per offset slot delta in [-3, 3]^3 (the 27 near slots stay zero)
-__global__ void k_m2l_operators(int p, double *__restrict__ T64, float *__restrict__ T32)
+// one block per offset slot delta in [-(2 ws + 1), 2 ws + 1]^3 (the (2 ws + 1)^3 near slots stay zero)
+__global__ void k_m2l_operators(int p, int ws, double *__restrict__ T64, float *__restrict__ T32)
 {
     extern __shared__ Cx<double> Ish[];
     int slot = blockIdx.x;
-    int dx = slot % 7 - 3, dy = (slot / 7) % 7 - 3, dz = slot / 49 - 3;
+    const int side = off_side(ws), h = 2 * ws + 1;
+    int dx = slot % side - h, dy = (slot / side) % side - h, dz = slot / (side * side) - h;
     int nc = ncoef(p);
     double *T = T64 + (size_t)slot * nc * nc;
-    if (abs(dx) <= 1 && abs(dy) <= 1 && abs(dz) <= 1) {
+    if (abs(dx) <= ws && abs(dy) <= ws && abs(dz) <= ws) {
         for (int e = threadIdx.x; e < nc * nc; e += blockDim.x) {
             T[e] = 0.0;
             T32[(size_t)slot * nc * nc + e] = 0.0f;
@@ -182,7 +183,7 @@ __device__ void block_merge(KS &v, double (*sh)[2])
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(LAT_THREADS) k_lattice_sum(int jmax, double kb, int nu_max, int nk_max,
+__global__ void __launch_bounds__(LAT_THREADS) k_lattice_sum(int jmax, double kb, int ws, int nu_max, int nk_max,
                                                               double *__restrict__ S)
 {
     __shared__ double sh[LAT_THREADS][2];
@@ -207,7 +208,7 @@ __global__ void __launch_bounds__(LAT_THREADS) k_lattice_sum(int jmax, double kb
             g *= a;  // Gamma(i + 3/2)
             Q += exp(a * log(x) - x) / g;
         }
-        bool near = abs(nx) <= 1 && abs(ny) <= 1 && abs(nz) <= 1;
+        bool near = abs(nx) <= ws && abs(ny) <= ws && abs(nz) <= ws;
         double w = near ? Q - 1.0 : Q;
         Cx<double> I = irregular_one(j, k, nx, ny, nz);
         re.add(w * I.re);
@@ -362,7 +363,8 @@ __global__ void k_lattice_apply(int p, const double *__restrict__ T0, const T *_
 // real operators per offset.  Block: TT targets of one parity class, one
 // thread per output coefficient.  Sources are read with periodic wrap.
 template <typename T, int TT>
-__global__ void k_m2l_simt(int p, int l, int cls, const T *__restrict__ Top, const T *__restrict__ M, T *__restrict__ L)
+__global__ void k_m2l_simt(int p, int l, int cls, int ws, const T *__restrict__ Top, const T *__restrict__ M,
+                           T *__restrict__ L)
 {
     extern __shared__ unsigned char smem_raw[];
     T *S = reinterpret_cast<T *>(smem_raw);  // [TT][nc]
@@ -375,11 +377,13 @@ __global__ void k_m2l_simt(int p, int l, int cls, const T *__restrict__ Top, con
     T acc[TT];
 #pragma unroll
     for (int t = 0; t < TT; ++t) acc[t] = 0;
-    for (int dz = -2 - cz; dz <= 3 - cz; ++dz)
-        for (int dy = -2 - cy; dy <= 3 - cy; ++dy)
-            for (int dx = -2 - cx; dx <= 3 - cx; ++dx) {
-                if (abs(dx) <= 1 && abs(dy) <= 1 && abs(dz) <= 1) continue;
-                int sx = cx + dx, sy = cy + dy, sz = cz + dz;  // in [-2, 3]
+    // delta per axis in [-2 ws - c, 2 ws + 1 - c]: the children of the parent's
+    // (2 ws + 1)^3 neighbours that are not the target's own neighbours
+    for (int dz = -2 * ws - cz; dz <= 2 * ws + 1 - cz; ++dz)
+        for (int dy = -2 * ws - cy; dy <= 2 * ws + 1 - cy; ++dy)
+            for (int dx = -2 * ws - cx; dx <= 2 * ws + 1 - cx; ++dx) {
+                if (abs(dx) <= ws && abs(dy) <= ws && abs(dz) <= ws) continue;
+                int sx = cx + dx, sy = cy + dy, sz = cz + dz;  // in [-2 ws, 2 ws + 1]
                 int scls = (sx & 1) | ((sy & 1) << 1) | ((sz & 1) << 2);
                 int Dx = sx >> 1, Dy = sy >> 1, Dz = sz >> 1;  // floor division
                 __syncthreads();
@@ -389,7 +393,8 @@ __global__ void k_m2l_simt(int p, int l, int cls, const T *__restrict__ Top, con
                     T v = 0;
                     if (tg < ncls) {
                         int Px = (int)(tg % np), Py = (int)((tg / np) % np), Pz = (int)(tg / ((int64_t)np * np));
-                        int Qx = (Px + Dx + np) % np, Qy = (Py + Dy + np) % np, Qz = (Pz + Dz + np) % np;
+                        int Qx = ((Px + Dx) % np + np) % np, Qy = ((Py + Dy) % np + np) % np,
+                            Qz = ((Pz + Dz) % np + np) % np;
                         int64_t src = scls * ncls + Qx + (int64_t)np * (Qy + (int64_t)np * Qz);
                         v = M[src * nc + k];
                     }
@@ -397,7 +402,7 @@ __global__ void k_m2l_simt(int p, int l, int cls, const T *__restrict__ Top, con
                 }
                 __syncthreads();
                 if (j < nc) {
-                    const T *Tp = Top + (size_t)off_slot(dx, dy, dz) * nc * nc + j;
+                    const T *Tp = Top + (size_t)off_slot(dx, dy, dz, ws) * nc * nc + j;
                     for (int k = 0; k < nc; ++k) {
                         T w = Tp[(size_t)k * nc];
 #pragma unroll
@@ -504,8 +509,8 @@ fmm_status build_tables(Plan &P)
     int ntri2 = (2 * p + 1) * (2 * p + 2) / 2;
     FMM_CUDA_TRY(cudaMalloc(&P.tab.S, sizeof(double) * 2 * ntri2));
     FMM_CUDA_TRY(cudaMalloc(&P.tab.T0, sizeof(double) * nc * nc));
-    FMM_CUDA_TRY(cudaMalloc(&P.tab.Top64, sizeof(double) * (size_t)NOFF * nc * nc));
-    FMM_CUDA_TRY(cudaMalloc(&P.tab.Top32, sizeof(float) * (size_t)NOFF * nc * nc));
+    FMM_CUDA_TRY(cudaMalloc(&P.tab.Top64, sizeof(double) * (size_t)noff(P.ws) * nc * nc));
+    FMM_CUDA_TRY(cudaMalloc(&P.tab.Top32, sizeof(float) * (size_t)noff(P.ws) * nc * nc));
     k_octant_table<<<1, 32, 0, P.stream>>>(p, P.tab.Rw64, P.tab.Rw32);
     FMM_LAUNCH_CHECK(P);
     {
@@ -513,13 +518,13 @@ fmm_status build_tables(Plan &P)
         if (st != FMM_OK) return st;
     }
     size_t shI = sizeof(Cx<double>) * ntri2;
-    k_m2l_operators<<<NOFF, 256, shI, P.stream>>>(p, P.tab.Top64, P.tab.Top32);
+    k_m2l_operators<<<noff(P.ws), 256, shI, P.stream>>>(p, P.ws, P.tab.Top64, P.tab.Top32);
     FMM_LAUNCH_CHECK(P);
     double kappa = P.kappa > 0 ? P.kappa : 2.0 / P.box;
     double kb = kappa * P.box;
-    int nu_max = (int)ceil(8.0 / kb) + 3;
+    int nu_max = (int)ceil(8.0 / kb) + 3 + P.ws;
     int nk_max = (int)ceil(2.2 * kb) + 3;
-    k_lattice_sum<<<ntri2, LAT_THREADS, 0, P.stream>>>(2 * p, kb, nu_max, nk_max, P.tab.S);
+    k_lattice_sum<<<ntri2, LAT_THREADS, 0, P.stream>>>(2 * p, kb, P.ws, nu_max, nk_max, P.tab.S);
     FMM_LAUNCH_CHECK(P);
     k_lattice_operator<<<1, 256, shI, P.stream>>>(p, P.tab.S, P.tab.T0);
     FMM_LAUNCH_CHECK(P);
@@ -534,9 +539,9 @@ fmm_status build_lattice(Plan &P)
     int ntri2 = (2 * p + 1) * (2 * p + 2) / 2;
     double kappa = P.kappa > 0 ? P.kappa : 2.0 / P.box;
     double kb = kappa * P.box;
-    int nu_max = (int)ceil(8.0 / kb) + 3;
+    int nu_max = (int)ceil(8.0 / kb) + 3 + P.ws;
     int nk_max = (int)ceil(2.2 * kb) + 3;
-    k_lattice_sum<<<ntri2, LAT_THREADS, 0, P.stream>>>(2 * p, kb, nu_max, nk_max, P.tab.S);
+    k_lattice_sum<<<ntri2, LAT_THREADS, 0, P.stream>>>(2 * p, kb, P.ws, nu_max, nk_max, P.tab.S);
     FMM_LAUNCH_CHECK(P);
     k_lattice_operator<<<1, 256, sizeof(Cx<double>) * ntri2, P.stream>>>(p, P.tab.S, P.tab.T0);
     FMM_LAUNCH_CHECK(P);
@@ -597,12 +602,12 @@ fmm_status launch_m2l_simt(Plan &P, int l)
             constexpr int TT = 16;
             size_t sh = sizeof(double) * TT * nc;
             k_m2l_simt<double, TT><<<blocks_for(ncls, TT), threads, sh, P.stream>>>(
-                P.p, l, cls, P.tab.Top64, (const double *)P.M[l], (double *)P.L[l]);
+                P.p, l, cls, P.ws, P.tab.Top64, (const double *)P.M[l], (double *)P.L[l]);
         } else {
             constexpr int TT = 32;
             size_t sh = sizeof(float) * TT * nc;
             k_m2l_simt<float, TT><<<blocks_for(ncls, TT), threads, sh, P.stream>>>(
-                P.p, l, cls, P.tab.Top32, (const float *)P.M[l], (float *)P.L[l]);
+                P.p, l, cls, P.ws, P.tab.Top32, (const float *)P.M[l], (float *)P.L[l]);
         }
         FMM_LAUNCH_CHECK(P);
     }

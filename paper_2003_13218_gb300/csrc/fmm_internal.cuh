@@ -26,14 +26,30 @@ namespace fmm {
 
 constexpr int P_MAX = 20;
 constexpr int NC_MAX = (P_MAX + 1) * (P_MAX + 1);
-constexpr int NOFF = 343;  // 7^3 offset slots for delta in [-3, 3]^3 (316 used for ws = 1)
+// Offsets delta (in cells of one level) between a target and the sources of
+// its interaction list lie in [-(2 ws + 1), 2 ws + 1]^3: operator slots are
+// numbered on that cube (7^3 for ws = 1, 11^3 for ws = 2); the (2 ws + 1)^3
+// near slots stay zero.  An interaction list holds (4 ws + 2)^3 - (2 ws + 1)^3
+// cells: 189 for ws = 1, 875 for ws = 2.
+constexpr int WS_MAX = 2;
+__host__ __device__ inline int off_side(int ws) { return 4 * ws + 3; }
+__host__ __device__ inline int noff(int ws) { return off_side(ws) * off_side(ws) * off_side(ws); }
+__host__ __device__ inline int n_il(int ws)
+{
+    const int a = 4 * ws + 2, b = 2 * ws + 1;
+    return a * a * a - b * b * b;
+}
 
 enum : int { ERRF_NONFINITE = 1, ERRF_INTERNAL = 2, ERRF_TIMEOUT = 4 };
 
 __host__ __device__ inline int ncoef(int p) { return (p + 1) * (p + 1); }
 __host__ __device__ inline int cre(int n, int m) { return m == 0 ? n * n : n * n + 2 * m - 1; }
 __host__ __device__ inline int cim(int n, int m) { return n * n + 2 * m; }
-__host__ __device__ inline int off_slot(int dx, int dy, int dz) { return (dx + 3) + 7 * ((dy + 3) + 7 * (dz + 3)); }
+__host__ __device__ inline int off_slot(int dx, int dy, int dz, int ws)
+{
+    const int h = 2 * ws + 1, side = 2 * h + 1;
+    return (dx + h) + side * ((dy + h) + side * (dz + h));
+}
 
 __host__ __device__ inline int64_t cell_index(int l, int x, int y, int z)
 {
@@ -61,7 +77,7 @@ struct Tables {
     float *Rw32 = nullptr;
     double *S = nullptr;      // [NC2] complex lattice sum S_j^k (j <= 2p, k >= 0), scaled to a unit box
     double *T0 = nullptr;     // [NC][NC] real lattice operator (input-major: T0[k * NC + j])
-    double *Top64 = nullptr;  // [NOFF][NC][NC] real M2L operators (input-major), FP64 path
+    double *Top64 = nullptr;  // [noff(ws)][NC][NC] real M2L operators (input-major), FP64 path
     float *Top32 = nullptr;   // same in FP32 for the SIMT FP32 path
     double *l2l64 = nullptr;  // [8 NC][NC] L2L operators of the 8 child octants (row-major)
     float *l2l32 = nullptr;

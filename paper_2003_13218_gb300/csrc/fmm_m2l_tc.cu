@@ -67,21 +67,18 @@ constexpr int kchunk_of(int sw) { return sw / 2; }
 constexpr uint32_t TMEM_COLS = 512;   // two accumulators of up to 256 columns
 constexpr int TC_PMAX = 15;           // N = (p+1)^2 rounded to 16 must not exceed 256
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // 2 s
-constexpr int NUM_IL = 189;
 constexpr int GAIN_T_EXP = 14;        // gT = 2^14 (fp16 split)
 constexpr int GAIN_M_EXP = 14;        // gM = 2^(14 - E)
 constexpr size_t TC_SMEM_BUDGET = 224 * 1024;
 
-// operator slots of the B tables: the M2L offsets (NOFF), then M2M and L2L per child octant
-constexpr int SLOT_M2M = NOFF;
-constexpr int SLOT_L2L = NOFF + 8;
-constexpr int NSLOT = NOFF + 16;
+// operator slots of the B tables: the noff(ws) M2L offsets, then M2M and L2L per child octant
 
 struct TcState {
     bool f16 = false;               // fp16x2 split with balanced scaling (and tensor-core translations)
     int pa = 0, pb = 0;             // terms of the plan's split
     int parts = 0;                  // terms stored (3 for the bf16 splits: the solute pass uses 3 x 3)
     int npad = 0, kp = 0;
+    int noff = 0;                   // M2L operator slots (the slot cube of the plan's ws)
     int sw = 64;                    // bytes per swizzled operand row in shared memory
     uint16_t *planes[9] = {};       // bf16 or fp16 bit patterns
     size_t part_elems[9] = {};
@@ -111,6 +108,7 @@ struct TcArgs {
     int groups, per_group;  // the offsets split over `groups` CTAs per tile (small levels)
     int n_off;              // offsets: 189 (+1 with the fused L2L) or 8 (M2M)
     int src_np2;            // M2M: halo'd side of the child level's planes
+    int ws, n_il, noff;     // well-separatedness, interaction-list length, M2L operator slots
     int out_np;             // M2M: class-layout side of the parent level (0 at level 0)
     uint32_t idesc;
     float *L;               // output level array (L of the level, or M of the parent level)
@@ -426,7 +424,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int y0 = ((tile / a.tiles_x) % a.tiles_y) * a.by;
     const int z0 = (tile / (a.tiles_x * a.tiles_y)) * a.bz;
     const int cx = cls & 1, cy = (cls >> 1) & 1, cz = (cls >> 2) & 1;
-    const int np2 = a.np + 2;
+    const int np2 = a.np + 2 * a.ws;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < a.stages; ++s) {
@@ -488,23 +486,26 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             };
             if (a.mode == 0) {
                 int oi = -1;  // position of the offset in the interaction-list order
-                for (int dz = -2 - cz; dz <= 3 - cz && ok; ++dz)
-                    for (int dy = -2 - cy; dy <= 3 - cy && ok; ++dy)
-                        for (int dx = -2 - cx; dx <= 3 - cx && ok; ++dx) {
-                            if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1 && dz >= -1 && dz <= 1) continue;
+                // delta per axis in [-2 ws - c, 2 ws + 1 - c], the near (2 ws + 1)^3 block left out;
+                // the source brick sits at parent offset (c + delta) >> 1 in [-ws, ws], halo width ws
+                const int w = a.ws;
+                for (int dz = -2 * w - cz; dz <= 2 * w + 1 - cz && ok; ++dz)
+                    for (int dy = -2 * w - cy; dy <= 2 * w + 1 - cy && ok; ++dy)
+                        for (int dx = -2 * w - cx; dx <= 2 * w + 1 - cx && ok; ++dx) {
+                            if (dx >= -w && dx <= w && dy >= -w && dy <= w && dz >= -w && dz <= w) continue;
                             ++oi;
                             if (oi < o_begin || oi >= o_end) continue;
                             const int sx = cx + dx, sy = cy + dy, sz = cz + dz;
                             const int scls = (sx & 1) | ((sy & 1) << 1) | ((sz & 1) << 2);
-                            load_offset(mA, x0 + (sx >> 1) + 1, y0 + (sy >> 1) + 1, scls * np2 + z0 + (sz >> 1) + 1,
-                                        off_slot(dx, dy, dz));
+                            load_offset(mA, x0 + (sx >> 1) + w, y0 + (sy >> 1) + w, scls * np2 + z0 + (sz >> 1) + w,
+                                        off_slot(dx, dy, dz, w));
                         }
                 // fused L2L: the parents' local expansions (natural order, no halo)
-                if (ok && a.n_off > NUM_IL && NUM_IL >= o_begin && NUM_IL < o_end)
-                    load_offset(mL, x0, y0, z0, NOFF + 8 + cls);
+                if (ok && a.n_off > a.n_il && a.n_il >= o_begin && a.n_il < o_end)
+                    load_offset(mL, x0, y0, z0, a.noff + 8 + cls);
             } else {
                 for (int o = o_begin; o < o_end && ok; ++o)
-                    load_offset(mA, x0 + 1, y0 + 1, o * a.src_np2 + z0 + 1, NOFF + o);
+                    load_offset(mA, x0 + a.ws, y0 + a.ws, o * a.src_np2 + z0 + a.ws, a.noff + o);
             }
             produced_sh = it;
             if (!ok) {
@@ -582,7 +583,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 break;
             }
             fence_after();
-            const float fac = (a.mode == 0 && o_begin + o == NUM_IL) ? l2l_fac : 1.f;
+            const float fac = (a.mode == 0 && o_begin + o == a.n_il) ? l2l_fac : 1.f;
             const uint32_t taddr = tmem + (uint32_t)(acc * 256) + ((uint32_t)(quad * 32) << 16);
 #pragma unroll
             for (int c = 0; c < NCH; ++c) {
@@ -700,7 +701,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TC_THREADS, 1)
     const int y0 = ((tile / a.tiles_x) % a.tiles_y) * a.by;
     const int z0 = (tile / (a.tiles_x * a.tiles_y)) * a.bz;
     const int cx = cls & 1, cy = (cls >> 1) & 1, cz = (cls >> 2) & 1;
-    const int np2 = a.np + 2;
+    const int np2 = a.np + 2 * a.ws;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < a.stages; ++s) {
@@ -762,19 +763,20 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TC_THREADS, 1)
                 }
             };
             int oi = -1;
-            for (int dz = -2 - cz; dz <= 3 - cz && ok; ++dz)
-                for (int dy = -2 - cy; dy <= 3 - cy && ok; ++dy)
-                    for (int dx = -2 - cx; dx <= 3 - cx && ok; ++dx) {
-                        if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1 && dz >= -1 && dz <= 1) continue;
+            const int w = a.ws;
+            for (int dz = -2 * w - cz; dz <= 2 * w + 1 - cz && ok; ++dz)
+                for (int dy = -2 * w - cy; dy <= 2 * w + 1 - cy && ok; ++dy)
+                    for (int dx = -2 * w - cx; dx <= 2 * w + 1 - cx && ok; ++dx) {
+                        if (dx >= -w && dx <= w && dy >= -w && dy <= w && dz >= -w && dz <= w) continue;
                         ++oi;
                         if (oi < o_begin || oi >= o_end) continue;
                         const int sx = cx + dx, sy = cy + dy, sz = cz + dz;
                         const int scls = (sx & 1) | ((sy & 1) << 1) | ((sz & 1) << 2);
-                        load_offset(mA, x0 + (sx >> 1) + 1, y0 + (sy >> 1) + 1, scls * np2 + z0 + (sz >> 1) + 1,
-                                    off_slot(dx, dy, dz));
+                        load_offset(mA, x0 + (sx >> 1) + w, y0 + (sy >> 1) + w, scls * np2 + z0 + (sz >> 1) + w,
+                                    off_slot(dx, dy, dz, w));
                     }
-            if (ok && a.n_off > NUM_IL && NUM_IL >= o_begin && NUM_IL < o_end)
-                load_offset(mL, x0, y0, z0, NOFF + 8 + cls);
+            if (ok && a.n_off > a.n_il && a.n_il >= o_begin && a.n_il < o_end)
+                load_offset(mL, x0, y0, z0, a.noff + 8 + cls);
             if (!ok) {
                 abort_sh = 1;
                 atomicOr(a.err, ERRF_TIMEOUT);
@@ -845,7 +847,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TC_THREADS, 1)
                 break;
             }
             fence_after();
-            const float fac = (o_begin + o == NUM_IL) ? l2l_fac : 1.f;
+            const float fac = (o_begin + o == a.n_il) ? l2l_fac : 1.f;
             const uint32_t taddr = tmem + (uint32_t)(acc * 256) + ((uint32_t)(quad * 32) << 16);
 #pragma unroll
             for (int c = 0; c < NCH; ++c) {
@@ -933,11 +935,11 @@ __global__ void k_absmax(const float *__restrict__ M, int64_t ncell, int nc, con
 // periodic halo; rows kp wide (zero beyond nc).  fp16: balanced by s(k) gM.
 // One warp per halo cell, lanes over the coefficients.
 template <bool F16>
-__global__ void k_split_halo(const float *__restrict__ M, int np, int nc, int kp, int parts,
+__global__ void k_split_halo(const float *__restrict__ M, int np, int hw, int nc, int kp, int parts,
                              const float *__restrict__ s, const unsigned *__restrict__ amax,
                              uint16_t *__restrict__ planes, size_t part_elems)
 {
-    const int np2 = np + 2;
+    const int np2 = np + 2 * hw;
     const int64_t ncell = 8 * (int64_t)np2 * np2 * np2;
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -947,7 +949,7 @@ __global__ void k_split_halo(const float *__restrict__ M, int np, int nc, int kp
         const int hy = (int)((cell / np2) % np2);
         const int hzc = (int)(cell / ((int64_t)np2 * np2));
         const int c = hzc / np2, hz = hzc % np2;
-        const int px = (hx - 1 + np) % np, py = (hy - 1 + np) % np, pz = (hz - 1 + np) % np;
+        const int px = ((hx - hw) % np + np) % np, py = ((hy - hw) % np + np) % np, pz = ((hz - hw) % np + np) % np;
         const float *row = M + ((int64_t)c * np * np * np + px + (int64_t)np * (py + (int64_t)np * pz)) * nc;
         uint16_t *out = planes + cell * kp;
         for (int k = lane; k < kp; k += 32) {
@@ -987,17 +989,17 @@ __global__ void k_split_L(const float *__restrict__ L, int lev, int nc, int kp, 
 }
 
 // FP64 operators -> split B tables [part][slot][j][k] (K-major, rows kp wide):
-// slots < NOFF the M2L operators T[slot][k][j] (input-major), then per child
+// slots < noff the M2L operators T[slot][k][j] (input-major), then per child
 // octant o the M2M operator (M2M[j][o nc + k], parent output j) and the L2L
 // operator (L2L[o nc + j][k], child output j).  fp16: balanced with gT,
 //   M2L  T~ = T / (s(k) s(j)),  M2M  S~ = S s(j) / s(k),  L2L  U~ = U s(k) / s(j);
 // bf16: the translation slots stay zero (unused).
 template <bool F16>
-__global__ void k_split_ops(const double *__restrict__ T, const double *__restrict__ m2m,
+__global__ void k_split_ops(int noff, const double *__restrict__ T, const double *__restrict__ m2m,
                             const double *__restrict__ l2l, int nc, int npad, int kp, int parts,
                             const double *__restrict__ s, uint16_t *__restrict__ ops, size_t part_elems)
 {
-    const int64_t total = (int64_t)NSLOT * npad * kp;
+    const int64_t total = (int64_t)(noff + 16) * npad * kp;
     const double gT = (double)pow2f(GAIN_T_EXP);
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int k = (int)(e % kp);
@@ -1005,14 +1007,14 @@ __global__ void k_split_ops(const double *__restrict__ T, const double *__restri
         const int slot = (int)(e / ((int64_t)kp * npad));
         double r = 0.0;
         if (j < nc && k < nc) {
-            if (slot < NOFF) {
+            if (slot < noff) {
                 r = T[((int64_t)slot * nc + k) * nc + j];
                 if (F16) r = r / (s[k] * s[j]) * gT;
-            } else if (F16 && slot < SLOT_L2L) {
-                const int o = slot - SLOT_M2M;
+            } else if (F16 && slot < noff + 8) {
+                const int o = slot - noff;
                 r = m2m[(int64_t)j * 8 * nc + o * nc + k] * s[j] / s[k] * gT;
             } else if (F16) {
-                const int o = slot - SLOT_L2L;
+                const int o = slot - noff - 8;
                 r = l2l[((int64_t)o * nc + j) * nc + k] * s[k] / s[j] * gT;
             }
         }
@@ -1173,6 +1175,9 @@ void fill_common(const Plan &P, const TcState *S, int pa, int pb, TcArgs &a)
     a.src_np2 = 0;
     a.out_np = 0;
     a.amaxL = nullptr;
+    a.ws = P.ws;
+    a.n_il = n_il(P.ws);
+    a.noff = noff(P.ws);
 }
 
 }  // namespace
@@ -1201,6 +1206,7 @@ fmm_status tc_prepare(Plan &P)
     S->pb = (P.split == FMM_SPLIT_BF16X2 || S->f16) ? 2 : 3;
     S->parts = S->f16 ? 2 : 3;  // bf16: three terms always, the solute-only pass uses the 3 x 3 split
     S->npad = (P.nc + 15) / 16 * 16;
+    S->noff = noff(P.ws);
     // 128-byte swizzled rows for the fp16 split (two 2-term stages fit), 64 bytes for the bf16 splits;
     // rows padded to whole copy boxes (aligned pieces); the MMAs stop at (p+1)^2 padded to 16
     S->sw = S->f16 ? 128 : 64;
@@ -1234,17 +1240,17 @@ fmm_status tc_prepare(Plan &P)
         FMM_CUDA_TRY(cudaMemcpyAsync(S->s32inv, h_inv, sizeof(float) * P.nc, cudaMemcpyHostToDevice, P.stream));
     }
     // operator tables
-    S->ops_part_elems = (size_t)NSLOT * S->npad * S->kp;
+    S->ops_part_elems = (size_t)(S->noff + 16) * S->npad * S->kp;
     FMM_CUDA_TRY(cudaMalloc(&S->ops, sizeof(uint16_t) * S->ops_part_elems * S->parts));
     if (S->f16)
-        k_split_ops<true><<<1216, 256, 0, P.stream>>>(P.tab.Top64, P.tab.m2m64, P.tab.l2l64, P.nc, S->npad, S->kp,
+        k_split_ops<true><<<1216, 256, 0, P.stream>>>(S->noff, P.tab.Top64, P.tab.m2m64, P.tab.l2l64, P.nc, S->npad, S->kp,
                                                       S->parts, S->s64, S->ops, S->ops_part_elems);
     else
-        k_split_ops<false><<<1216, 256, 0, P.stream>>>(P.tab.Top64, nullptr, nullptr, P.nc, S->npad, S->kp, S->parts,
+        k_split_ops<false><<<1216, 256, 0, P.stream>>>(S->noff, P.tab.Top64, nullptr, nullptr, P.nc, S->npad, S->kp, S->parts,
                                                        nullptr, S->ops, S->ops_part_elems);
     FMM_LAUNCH_CHECK(P);
     for (int j = 0; j < S->parts; ++j) {
-        cuuint64_t dims[3] = {(cuuint64_t)S->kp, (cuuint64_t)S->npad, (cuuint64_t)NSLOT};
+        cuuint64_t dims[3] = {(cuuint64_t)S->kp, (cuuint64_t)S->npad, (cuuint64_t)(S->noff + 16)};
         cuuint64_t strides[2] = {(cuuint64_t)S->kp * 2, (cuuint64_t)S->kp * 2 * S->npad};
         cuuint32_t box[3] = {(cuuint32_t)kchunk_of(S->sw), (cuuint32_t)S->npad, 1};
         cuuint32_t es[3] = {1, 1, 1};
@@ -1256,7 +1262,7 @@ fmm_status tc_prepare(Plan &P)
     for (int j = S->parts; j < 3; ++j) S->mapB[j] = S->mapB[0];  // unused kernel parameters
     if (S->f16) {
         for (int j = 0; j < 2; ++j) {
-            cuuint64_t dims[3] = {(cuuint64_t)S->kp, (cuuint64_t)S->npad, (cuuint64_t)NSLOT};
+            cuuint64_t dims[3] = {(cuuint64_t)S->kp, (cuuint64_t)S->npad, (cuuint64_t)(S->noff + 16)};
             cuuint64_t strides[2] = {(cuuint64_t)S->kp * 2, (cuuint64_t)S->kp * 2 * S->npad};
             cuuint32_t box[3] = {(cuuint32_t)kchunk_of(S->sw), (cuuint32_t)(S->npad / 2), 1};
             cuuint32_t es[3] = {1, 1, 1};
@@ -1280,7 +1286,7 @@ fmm_status tc_prepare(Plan &P)
     size_t lpart_elems = 0;
     for (int l = 1; l <= P.d; ++l) {
         int np = 1 << (l - 1);
-        int64_t np2 = np + 2;
+        int64_t np2 = np + 2 * P.ws;  // periodic halo of ws cells
         S->bx[l] = tile_dim(np, TC_ROWS);
         S->by[l] = tile_dim(np, TC_ROWS / S->bx[l]);
         S->bz[l] = tile_dim(np, TC_ROWS / (S->bx[l] * S->by[l]));
@@ -1300,7 +1306,7 @@ fmm_status tc_prepare(Plan &P)
             S->mapL[l][0] = S->mapL[l][1] = S->mapA[l][0];  // unused kernel parameters
         }
         const int tiles = 8 * (np / S->bx[l]) * (np / S->by[l]) * (np / S->bz[l]);
-        split_offsets(NUM_IL + (S->f16 ? 1 : 0), tiles, 27, S->groups[l], S->per_group[l]);
+        split_offsets(n_il(P.ws) + (S->f16 ? 1 : 0), tiles, 27, S->groups[l], S->per_group[l]);
         if (S->groups[l] > 1) {
             size_t need = (size_t)S->groups[l] * 8 * np * np * np * P.nc;
             if (need > lpart_elems) lpart_elems = need;
@@ -1334,7 +1340,7 @@ fmm_status tc_split_moments(Plan &P, int l)
     TcState *S = (TcState *)P.tc;
     if (!S || !S->f16 || l < 1 || l > P.d) return FMM_ERR_INTERNAL;
     const int np = 1 << (l - 1);
-    const int64_t np2 = np + 2;
+    const int64_t np2 = np + 2 * P.ws;
     const int64_t ncell = (int64_t)8 * np * np * np;
     const int64_t nhalo = 8 * np2 * np2 * np2;
     FMM_CUDA_TRY(cudaMemsetAsync(S->amax + l, 0, sizeof(unsigned), P.stream));
@@ -1342,7 +1348,7 @@ fmm_status tc_split_moments(Plan &P, int l)
         (const float *)P.M[l], ncell, P.nc, S->s32, S->amax + l);
     FMM_LAUNCH_CHECK(P);
     k_split_halo<true><<<(unsigned)((nhalo + 7) / 8 < 4864 ? (nhalo + 7) / 8 : 4864), 256, 0, P.stream>>>(
-        (const float *)P.M[l], np, P.nc, S->kp, 2, S->s32, S->amax + l, S->planes[l], S->part_elems[l]);
+        (const float *)P.M[l], np, P.ws, P.nc, S->kp, 2, S->s32, S->amax + l, S->planes[l], S->part_elems[l]);
     FMM_LAUNCH_CHECK(P);
     return FMM_OK;
 }
@@ -1368,7 +1374,7 @@ fmm_status launch_m2m_tc(Plan &P, int l)
     a.groups = S->mgroups[l];
     a.per_group = S->mper_group[l];
     a.n_off = 8;
-    a.src_np2 = n + 2;
+    a.src_np2 = n + 2 * P.ws;
     a.out_np = l == 0 ? 0 : n >> 1;
     a.L = (float *)P.M[l];
     a.post = S->s32inv;
@@ -1397,7 +1403,7 @@ fmm_status launch_m2l_tc(Plan &P, int l, bool precise, bool split)
     const int pa = precise && !S->f16 ? 3 : S->pa;
     const int pb = precise && !S->f16 ? 3 : S->pb;
     int np = 1 << (l - 1);
-    int64_t np2 = np + 2;
+    int64_t np2 = np + 2 * P.ws;
     if (S->f16) {
         if (split) {
             fmm_status st = tc_split_moments(P, l);
@@ -1416,7 +1422,7 @@ fmm_status launch_m2l_tc(Plan &P, int l, bool precise, bool split)
     } else {
         const int64_t nhalo = 8 * np2 * np2 * np2;
         k_split_halo<false><<<(unsigned)((nhalo + 7) / 8 < 4864 ? (nhalo + 7) / 8 : 4864), 256, 0, P.stream>>>(
-            (const float *)P.M[l], np, P.nc, S->kp, pa, nullptr, nullptr, S->planes[l], S->part_elems[l]);
+            (const float *)P.M[l], np, P.ws, P.nc, S->kp, pa, nullptr, nullptr, S->planes[l], S->part_elems[l]);
         FMM_LAUNCH_CHECK(P);
     }
     TcArgs a;
@@ -1432,7 +1438,7 @@ fmm_status launch_m2l_tc(Plan &P, int l, bool precise, bool split)
     a.tiles_per_class = a.tiles_x * a.tiles_y * (np / a.bz);
     a.groups = S->groups[l];
     a.per_group = S->per_group[l];
-    a.n_off = NUM_IL + (S->f16 ? 1 : 0);
+    a.n_off = a.n_il + (S->f16 ? 1 : 0);
     a.L = (float *)P.L[l];
     a.post = S->f16 ? S->s32 : nullptr;
     a.amax = S->f16 ? S->amax + l : nullptr;

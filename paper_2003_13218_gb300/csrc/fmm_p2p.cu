@@ -1,5 +1,6 @@
 // fmm_p2p.cu -- near field (Eq. EqNF): direct Coulomb sums over the
-// (2 ws + 1)^3 = 27 leaves around each charge's leaf, periodic, j != i.
+// (2 ws + 1)^3 leaves around each charge's leaf (27 for ws = 1, 125 for ws = 2),
+// periodic, j != i.
 //
 // Coordinates are relative to each leaf's centre, so the separation of a
 // charge in leaf c from one in neighbour leaf c + delta is
@@ -23,10 +24,8 @@ template <>
 __device__ inline double inv_sqrt<double>(double x) { return 1.0 / sqrt(x); }
 
 // One thread per sorted charge i: phi_i = sum q_j / r_ij, e_i = sum q_j r_ij / r_ij^3.
-// The leaf's 27 neighbours are visited as one x-row of three leaves at a
-// time; a row's particles are contiguous in the sorted order.
 template <typename T>
-__global__ void k_p2p(int64_t N, int d, T h, const int *__restrict__ start, const int *__restrict__ sleaf,
+__global__ void k_p2p(int64_t N, int d, int ws, T h, const int *__restrict__ start, const int *__restrict__ sleaf,
                       const Particle<T> *__restrict__ sp, T *__restrict__ phi, T *__restrict__ field)
 {
     int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -36,11 +35,11 @@ __global__ void k_p2p(int64_t N, int d, T h, const int *__restrict__ start, cons
     int x = leaf % nside, y = (leaf / nside) % nside, z = leaf / (nside * nside);
     Particle<T> pi = sp[s];
     T acc = 0, ex = 0, ey = 0, ez = 0;
-    for (int dz = -1; dz <= 1; ++dz) {
+    for (int dz = -ws; dz <= ws; ++dz) {
         int zz = (z + dz + nside) & (nside - 1);
-        for (int dy = -1; dy <= 1; ++dy) {
+        for (int dy = -ws; dy <= ws; ++dy) {
             int yy = (y + dy + nside) & (nside - 1);
-            for (int dx = -1; dx <= 1; ++dx) {
+            for (int dx = -ws; dx <= ws; ++dx) {
                 int xx = (x + dx + nside) & (nside - 1);
                 int c = xx + nside * (yy + nside * zz);
                 T ox = pi.x - T(dx) * h, oy = pi.y - T(dy) * h, oz = pi.z - T(dz) * h;
@@ -71,7 +70,7 @@ __global__ void k_p2p(int64_t N, int d, T h, const int *__restrict__ start, cons
 // near-field solute-solvent pair sum: out_i = q_i sum_{j in NF(i), j solvent} q_j / r_ij
 // for solute i, 0 otherwise
 template <typename T>
-__global__ void k_p2p_uv(int64_t N, int d, T h, const int *__restrict__ start, const int *__restrict__ sleaf,
+__global__ void k_p2p_uv(int64_t N, int d, int ws, T h, const int *__restrict__ start, const int *__restrict__ sleaf,
                          const Particle<T> *__restrict__ sp, const uint8_t *__restrict__ sol, T *__restrict__ out)
 {
     int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -85,9 +84,9 @@ __global__ void k_p2p_uv(int64_t N, int d, T h, const int *__restrict__ start, c
     int x = leaf % nside, y = (leaf / nside) % nside, z = leaf / (nside * nside);
     Particle<T> pi = sp[s];
     T acc = 0;
-    for (int dz = -1; dz <= 1; ++dz)
-        for (int dy = -1; dy <= 1; ++dy)
-            for (int dx = -1; dx <= 1; ++dx) {
+    for (int dz = -ws; dz <= ws; ++dz)
+        for (int dy = -ws; dy <= ws; ++dy)
+            for (int dx = -ws; dx <= ws; ++dx) {
                 int xx = (x + dx + nside) & (nside - 1), yy = (y + dy + nside) & (nside - 1),
                     zz = (z + dz + nside) & (nside - 1);
                 int c = xx + nside * (yy + nside * zz);
@@ -110,11 +109,11 @@ fmm_status launch_p2p(Plan &P, bool forces)
     double h = P.box / nside;
     if (P.precision == FMM_PREC_FP64)
         k_p2p<double><<<blocks_for(P.N, 128), 128, 0, P.stream>>>(
-            P.N, P.d, h, P.cell_start, P.sleaf, (const Particle<double> *)P.sorted, (double *)P.phi_nf,
+            P.N, P.d, P.ws, h, P.cell_start, P.sleaf, (const Particle<double> *)P.sorted, (double *)P.phi_nf,
             forces ? (double *)P.f_nf : nullptr);
     else
         k_p2p<float><<<blocks_for(P.N, 128), 128, 0, P.stream>>>(
-            P.N, P.d, (float)h, P.cell_start, P.sleaf, (const Particle<float> *)P.sorted, (float *)P.phi_nf,
+            P.N, P.d, P.ws, (float)h, P.cell_start, P.sleaf, (const Particle<float> *)P.sorted, (float *)P.phi_nf,
             forces ? (float *)P.f_nf : nullptr);
     FMM_LAUNCH_CHECK(P);
     return FMM_OK;
@@ -126,11 +125,11 @@ fmm_status launch_p2p_uv(Plan &P)
     double h = P.box / nside;
     if (P.precision == FMM_PREC_FP64)
         k_p2p_uv<double><<<blocks_for(P.N, 128), 128, 0, P.stream>>>(
-            P.N, P.d, h, P.cell_start, P.sleaf, (const Particle<double> *)P.sorted, P.sorted_sol,
+            P.N, P.d, P.ws, h, P.cell_start, P.sleaf, (const Particle<double> *)P.sorted, P.sorted_sol,
             (double *)P.phi_nf + P.N);
     else
         k_p2p_uv<float><<<blocks_for(P.N, 128), 128, 0, P.stream>>>(
-            P.N, P.d, (float)h, P.cell_start, P.sleaf, (const Particle<float> *)P.sorted, P.sorted_sol,
+            P.N, P.d, P.ws, (float)h, P.cell_start, P.sleaf, (const Particle<float> *)P.sorted, P.sorted_sol,
             (float *)P.phi_nf + P.N);
     FMM_LAUNCH_CHECK(P);
     return FMM_OK;

@@ -10,7 +10,7 @@
 //    after the level-0 lattice operator, giving the full local expansion at
 //    level LD;
 //  * on the finer levels evaluates M2L only onto the targets whose interaction
-//    list contains an active source (at most 189 per source), kept as a
+//    list contains an active source (at most n_il(ws) per source), kept as a
 //    sorted list per level;
 //  * evaluates Phi_u at every charge as the level-LD expansion plus the sparse
 //    contributions found at its finer ancestors.  A local expansion is a
@@ -31,7 +31,8 @@ namespace {
 
 constexpr int NU_MAX = 64;      // solute charges handled by the sparse pass
 constexpr int LD = 3;           // levels 0..LD treated densely
-constexpr int MAX_TGT = NU_MAX * 189;
+// targets per fine level: at most NU_MAX * n_il(ws) (mt below)
+__host__ __device__ inline int max_tgt(int ws) { return NU_MAX * n_il(ws); }
 
 struct SoluteScratch {
     int *list = nullptr;     // [NU_MAX] sorted slots of solute charges; [NU_MAX] = count
@@ -41,8 +42,8 @@ struct SoluteScratch {
     int *flags = nullptr;    // [8^d] target marks of one level
     int *pos = nullptr;      // [8^d + 1] exclusive scan of the marks
     int *scan_tmp = nullptr;
-    int *tlist = nullptr;    // [9][MAX_TGT] sorted targets per fine level
-    void *contrib = nullptr; // [9][MAX_TGT][nc] M2L sums at those targets
+    int *tlist = nullptr;    // [9][mt] sorted targets per fine level
+    void *contrib = nullptr; // [9][mt][nc] M2L sums at those targets
     int *h_count = nullptr;  // pinned
     cudaStream_t side = nullptr;       // high-priority stream of the prologue (overlaps the full pass's M2L)
     cudaEvent_t ev_count = nullptr;    // count copied to h_count
@@ -50,7 +51,7 @@ struct SoluteScratch {
     cudaEvent_t ev_act = nullptr;      // prologue done (join)
     bool count_pending = false, prologue_pending = false;
     void *Lt = nullptr;      // [9][NU_MAX][nc] full local expansions at the active cells (FP64)
-    double *part = nullptr;  // [NU_MAX][189][nc] their M2L terms, one per offset
+    double *part = nullptr;  // [NU_MAX][n_il][nc] their M2L terms, one per offset
 };
 
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -225,12 +226,13 @@ __global__ void k_sol_scatter(int p, int lmax, const int *__restrict__ cells, co
 }
 
 // interaction-list test: is s = t + delta in IL(t)?  (per axis delta in
-// [-2 - c, 3 - c] for target parity c, and not all |delta| <= 1)
-__device__ inline bool in_il(int dx, int dy, int dz, int tx, int ty, int tz)
+// [-2 ws - c, 2 ws + 1 - c] for target parity c, and not all |delta| <= ws)
+__device__ inline bool in_il(int dx, int dy, int dz, int tx, int ty, int tz, int ws)
 {
-    if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1 && dz >= -1 && dz <= 1) return false;
+    if (dx >= -ws && dx <= ws && dy >= -ws && dy <= ws && dz >= -ws && dz <= ws) return false;
     int cx = tx & 1, cy = ty & 1, cz = tz & 1;
-    return dx >= -2 - cx && dx <= 3 - cx && dy >= -2 - cy && dy <= 3 - cy && dz >= -2 - cz && dz <= 3 - cz;
+    return dx >= -2 * ws - cx && dx <= 2 * ws + 1 - cx && dy >= -2 * ws - cy && dy <= 2 * ws + 1 - cy &&
+           dz >= -2 * ws - cz && dz <= 2 * ws + 1 - cz;
 }
 
 __device__ inline int wrap_delta(int d, int n)  // representative of d mod n in [-n/2, n/2)
@@ -241,41 +243,43 @@ __device__ inline int wrap_delta(int d, int n)  // representative of d mod n in 
     return d;
 }
 
-// mark the targets of active source blockIdx.x at level l (one thread per candidate offset)
-__global__ void k_sol_mark(int l, const int *__restrict__ cells, const int *__restrict__ ncells, int *__restrict__ flags)
+// mark the targets of active source blockIdx.x at level l (threads over the candidate offsets)
+__global__ void k_sol_mark(int l, int ws, const int *__restrict__ cells, const int *__restrict__ ncells,
+                           int *__restrict__ flags)
 {
     int i = blockIdx.x;
     if (i >= ncells[l]) return;
-    int o = threadIdx.x;
-    if (o >= 343) return;
-    int dx = o % 7 - 3, dy = (o / 7) % 7 - 3, dz = o / 49 - 3;
+    const int side = off_side(ws), h = 2 * ws + 1;
     int n = 1 << l;
     int sx, sy, sz;
     cell_xyz(cells[l * NU_MAX + i], n, sx, sy, sz);
-    int tx = (sx - dx + n) & (n - 1), ty = (sy - dy + n) & (n - 1), tz = (sz - dz + n) & (n - 1);
-    if (!in_il(dx, dy, dz, tx, ty, tz)) return;
-    flags[tx + n * (ty + n * tz)] = 1;
+    for (int o = threadIdx.x; o < side * side * side; o += blockDim.x) {
+        int dx = o % side - h, dy = (o / side) % side - h, dz = o / (side * side) - h;
+        int tx = (sx - dx + 2 * n) & (n - 1), ty = (sy - dy + 2 * n) & (n - 1), tz = (sz - dz + 2 * n) & (n - 1);
+        if (in_il(dx, dy, dz, tx, ty, tz, ws)) flags[tx + n * (ty + n * tz)] = 1;
+    }
 }
 
-__global__ void k_sol_compact(int64_t n, const int *__restrict__ flags, const int *__restrict__ pos,
+__global__ void k_sol_compact(int64_t n, int mt, const int *__restrict__ flags, const int *__restrict__ pos,
                               int *__restrict__ tlist)
 {
     int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (c < n && flags[c]) {
         int k = pos[c];
-        if (k < MAX_TGT) tlist[k] = (int)c;
+        if (k < mt) tlist[k] = (int)c;
     }
 }
 
 // contribution of every active source to target tlist[blockIdx.x] (Eq. Lcoeffdef)
 template <typename T>
-__global__ void k_sol_m2l(int p, int l, const int *__restrict__ cells, const int *__restrict__ ncells,
+__global__ void k_sol_m2l(int p, int l, int ws, const int *__restrict__ cells, const int *__restrict__ ncells,
                           const int *__restrict__ tlist, const int *__restrict__ tcount, const T *__restrict__ Top,
                           const T *__restrict__ MU, T *__restrict__ contrib)
 {
     int b = blockIdx.x;
+    const int mt = max_tgt(ws);
     int cnt = *tcount;
-    if (cnt > MAX_TGT) cnt = MAX_TGT;
+    if (cnt > mt) cnt = mt;
     if (b >= cnt) return;
     int nc = ncoef(p);
     int n = 1 << l;
@@ -287,12 +291,12 @@ __global__ void k_sol_m2l(int p, int l, const int *__restrict__ cells, const int
             int sx, sy, sz;
             cell_xyz(cells[l * NU_MAX + s], n, sx, sy, sz);
             int dx = wrap_delta(sx - tx, n), dy = wrap_delta(sy - ty, n), dz = wrap_delta(sz - tz, n);
-            if (!in_il(dx, dy, dz, tx, ty, tz)) continue;
-            const T *Tp = Top + (size_t)off_slot(dx, dy, dz) * nc * nc + j;
+            if (!in_il(dx, dy, dz, tx, ty, tz, ws)) continue;
+            const T *Tp = Top + (size_t)off_slot(dx, dy, dz, ws) * nc * nc + j;
             const T *Ms = MU + ((size_t)l * NU_MAX + s) * nc;
             for (int k = 0; k < nc; ++k) acc += Tp[(size_t)k * nc] * Ms[k];
         }
-        contrib[((size_t)l * MAX_TGT + b) * nc + j] = acc;
+        contrib[((size_t)l * mt + b) * nc + j] = acc;
     }
 }
 
@@ -321,7 +325,7 @@ __global__ void k_act_lattice(int p, const int *__restrict__ ncells, const doubl
 // part[i][o] = the M2L term of the o-th interaction-list offset of active cell
 // i at level l (one block per (cell, offset))
 template <typename T>
-__global__ void k_act_m2l(int p, int l, const int *__restrict__ cells, const int *__restrict__ ncells,
+__global__ void k_act_m2l(int p, int l, int ws, const int *__restrict__ cells, const int *__restrict__ ncells,
                           const double *__restrict__ Top, const T *__restrict__ M, const T *__restrict__ MU,
                           double *__restrict__ part)
 {
@@ -333,37 +337,38 @@ __global__ void k_act_m2l(int p, int l, const int *__restrict__ cells, const int
     cell_xyz(cells[l * NU_MAX + i], n, tx, ty, tz);
     int cx = tx & 1, cy = ty & 1, cz = tz & 1;
     int dx = 0, dy = 0, dz = 0, c = -1;
-    for (int z = -2 - cz; z <= 3 - cz && c < o; ++z)
-        for (int y = -2 - cy; y <= 3 - cy && c < o; ++y)
-            for (int x = -2 - cx; x <= 3 - cx && c < o; ++x) {
-                if (x >= -1 && x <= 1 && y >= -1 && y <= 1 && z >= -1 && z <= 1) continue;
+    for (int z = -2 * ws - cz; z <= 2 * ws + 1 - cz && c < o; ++z)
+        for (int y = -2 * ws - cy; y <= 2 * ws + 1 - cy && c < o; ++y)
+            for (int x = -2 * ws - cx; x <= 2 * ws + 1 - cx && c < o; ++x) {
+                if (x >= -ws && x <= ws && y >= -ws && y <= ws && z >= -ws && z <= ws) continue;
                 if (++c == o) {
                     dx = x;
                     dy = y;
                     dz = z;
                 }
             }
-    int sx = (tx + dx + n) & (n - 1), sy = (ty + dy + n) & (n - 1), sz = (tz + dz + n) & (n - 1);
+    int sx = ((tx + dx) % n + n) % n, sy = ((ty + dy) % n + n) % n, sz = ((tz + dz) % n + n) % n;
     const T *Ms = M + cell_index(l, sx, sy, sz) * nc;
     // the solute part of this source, if it is an active cell
     const T *Mu = nullptr;
     int slin = sx + n * (sy + n * sz);
     for (int k = 0; k < ncells[l]; ++k)
         if (cells[l * NU_MAX + k] == slin) Mu = MU + ((size_t)l * NU_MAX + k) * nc;
-    const double *Tp = Top + (size_t)off_slot(dx, dy, dz) * nc * nc;
+    const double *Tp = Top + (size_t)off_slot(dx, dy, dz, ws) * nc * nc;
+    const int nil = n_il(ws);
     for (int j = threadIdx.x; j < nc; j += blockDim.x) {
         double acc = 0;
         if (Mu)
             for (int k = 0; k < nc; ++k) acc += Tp[(size_t)k * nc + j] * ((double)Ms[k] - (double)Mu[k]);
         else
             for (int k = 0; k < nc; ++k) acc += Tp[(size_t)k * nc + j] * (double)Ms[k];
-        part[((size_t)i * 189 + o) * nc + j] = acc;
+        part[((size_t)i * nil + o) * nc + j] = acc;
     }
 }
 
-// Lt[l][i] = sum of the 189 terms: one warp per (active cell, coefficient j),
+// Lt[l][i] = sum of the n_il terms: one warp per (active cell, coefficient j),
 // lanes take every 32nd offset, then a fixed shuffle tree (deterministic)
-__global__ void k_act_sum(int p, int l, const int *__restrict__ ncells, const double *__restrict__ part,
+__global__ void k_act_sum(int p, int l, int nil, const int *__restrict__ ncells, const double *__restrict__ part,
                           double *__restrict__ Lt)
 {
     const int i = blockIdx.x;
@@ -373,7 +378,7 @@ __global__ void k_act_sum(int p, int l, const int *__restrict__ ncells, const do
     const int lane = threadIdx.x & 31;
     if (j >= nc) return;
     double s = 0;
-    for (int o = lane; o < 189; o += 32) s += part[((size_t)i * 189 + o) * nc + j];
+    for (int o = lane; o < nil; o += 32) s += part[((size_t)i * nil + o) * nc + j];
     for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
     if (lane == 0) Lt[((size_t)l * NU_MAX + i) * nc + j] = s;
 }
@@ -490,7 +495,7 @@ __device__ T l2p_value(int p, const T *__restrict__ Lc, T vx, T vy, T vz, const 
 
 // Phi_u at every charge: level-LD expansion plus the sparse finer-level sums
 template <typename T>
-__global__ void k_sol_eval(int p, int d, int64_t N, T h_leaf, const int *__restrict__ sleaf,
+__global__ void k_sol_eval(int p, int d, int mt, int64_t N, T h_leaf, const int *__restrict__ sleaf,
                            const Particle<T> *__restrict__ sp, const T *__restrict__ Lld, const int *__restrict__ tlist,
                            const int *__restrict__ tcounts, const T *__restrict__ contrib, T *__restrict__ phi)
 {
@@ -525,9 +530,9 @@ __global__ void k_sol_eval(int p, int d, int64_t N, T h_leaf, const int *__restr
             continue;
         }
         int cnt = tcounts[l];
-        if (cnt > MAX_TGT) cnt = MAX_TGT;
+        if (cnt > mt) cnt = mt;
         int key = ax + (1 << l) * (ay + (1 << l) * az);
-        const int *tl = tlist + (size_t)l * MAX_TGT;
+        const int *tl = tlist + (size_t)l * mt;
         int lo = 0, hi = cnt;
         while (lo < hi) {
             int mid = (lo + hi) >> 1;
@@ -535,7 +540,7 @@ __global__ void k_sol_eval(int p, int d, int64_t N, T h_leaf, const int *__restr
             else hi = mid;
         }
         if (lo < cnt && tl[lo] == key)
-            total += l2p_value<T>(p, contrib + ((size_t)l * MAX_TGT + lo) * nc, vx, vy, vz, s_half, s_inv) * inv;
+            total += l2p_value<T>(p, contrib + ((size_t)l * mt + lo) * nc, vx, vy, vz, s_half, s_inv) * inv;
     }
     phi[s] = total;
 }
@@ -624,10 +629,10 @@ fmm_status solute_prologue_t(Plan &P, SoluteScratch &S, cudaStream_t st)
     k_act_lattice<T><<<1, nth, 0, st>>>(p, S.ncells, P.tab.T0, (const T *)P.M[0], MU, Lt);
     FMM_LAUNCH_CHECK(P);
     for (int l = 1; l <= d; ++l) {
-        k_act_m2l<T><<<dim3(nu, 189), nth, 0, st>>>(p, l, S.cells, S.ncells, P.tab.Top64, (const T *)P.M[l], MU,
-                                                     S.part);
+        k_act_m2l<T><<<dim3(nu, n_il(P.ws)), nth, 0, st>>>(p, l, P.ws, S.cells, S.ncells, P.tab.Top64,
+                                                            (const T *)P.M[l], MU, S.part);
         FMM_LAUNCH_CHECK(P);
-        k_act_sum<<<dim3(nu, (nc + 7) / 8), 256, 0, st>>>(p, l, S.ncells, S.part, Lt);
+        k_act_sum<<<dim3(nu, (nc + 7) / 8), 256, 0, st>>>(p, l, n_il(P.ws), S.ncells, S.part, Lt);
         FMM_LAUNCH_CHECK(P);
         k_act_l2l<<<dim3(nu, (p + 1) * (p + 2) / 2), 32, 0, st>>>(p, l, S.cells, S.ncells, P.tab.Rw64, Lt, Lt);
         FMM_LAUNCH_CHECK(P);
@@ -664,7 +669,7 @@ fmm_status solute_sparse_t(Plan &P, SoluteScratch &S, int nu)
     for (int l = LD + 1; l <= d; ++l) {
         int64_t n = (int64_t)1 << (3 * l);
         FMM_CUDA_TRY(cudaMemsetAsync(S.flags, 0, sizeof(int) * n, P.stream));
-        k_sol_mark<<<nu, 352, 0, P.stream>>>(l, S.cells, S.ncells, S.flags);
+        k_sol_mark<<<nu, 256, 0, P.stream>>>(l, P.ws, S.cells, S.ncells, S.flags);
         FMM_LAUNCH_CHECK(P);
         int nb = (int)((n + 4095) / 4096);
         k_flag_scan_blocks<<<nb, 256, 0, P.stream>>>(n, S.flags, S.pos, S.scan_tmp);
@@ -673,14 +678,16 @@ fmm_status solute_sparse_t(Plan &P, SoluteScratch &S, int nu)
         FMM_LAUNCH_CHECK(P);
         k_flag_scan_add<<<blocks_for(n, 256), 256, 0, P.stream>>>(n, S.pos, S.scan_tmp);
         FMM_LAUNCH_CHECK(P);
-        k_sol_compact<<<blocks_for(n, 256), 256, 0, P.stream>>>(n, S.flags, S.pos, S.tlist + (size_t)l * MAX_TGT);
+        k_sol_compact<<<blocks_for(n, 256), 256, 0, P.stream>>>(n, max_tgt(P.ws), S.flags, S.pos,
+                                                                 S.tlist + (size_t)l * max_tgt(P.ws));
         FMM_LAUNCH_CHECK(P);
-        k_sol_m2l<T><<<nu * 189, ((nc + 31) / 32) * 32, 0, P.stream>>>(p, l, S.cells, S.ncells,
-                                                                       S.tlist + (size_t)l * MAX_TGT,
+        k_sol_m2l<T><<<nu * n_il(P.ws), ((nc + 31) / 32) * 32, 0, P.stream>>>(p, l, P.ws, S.cells, S.ncells,
+                                                                       S.tlist + (size_t)l * max_tgt(P.ws),
                                                                        S.ncells + 16 + l, Top, MU, (T *)S.contrib);
         FMM_LAUNCH_CHECK(P);
     }
-    k_sol_eval<T><<<blocks_for(P.N, 128), 128, 0, P.stream>>>(p, d, P.N, (T)h, P.sleaf, (const Particle<T> *)P.sorted,
+    k_sol_eval<T><<<blocks_for(P.N, 128), 128, 0, P.stream>>>(p, d, max_tgt(P.ws), P.N, (T)h, P.sleaf,
+                                                              (const Particle<T> *)P.sorted,
                                                               (const T *)P.L[LD], S.tlist, S.ncells + 16,
                                                               (const T *)S.contrib, (T *)P.phi_u);
     FMM_LAUNCH_CHECK(P);
@@ -708,8 +715,8 @@ fmm_status solute_prepare(Plan &P)
     FMM_CUDA_TRY(cudaMalloc(&S->flags, sizeof(int) * nleaf));
     FMM_CUDA_TRY(cudaMalloc(&S->pos, sizeof(int) * (nleaf + 1)));
     FMM_CUDA_TRY(cudaMalloc(&S->scan_tmp, sizeof(int) * (nleaf / 4096 + 2)));
-    FMM_CUDA_TRY(cudaMalloc(&S->tlist, sizeof(int) * 9 * MAX_TGT));
-    FMM_CUDA_TRY(cudaMalloc(&S->contrib, sizeof(double) * (size_t)(P.d + 1) * MAX_TGT * P.nc));
+    FMM_CUDA_TRY(cudaMalloc(&S->tlist, sizeof(int) * 9 * max_tgt(P.ws)));
+    FMM_CUDA_TRY(cudaMalloc(&S->contrib, sizeof(double) * (size_t)(P.d + 1) * max_tgt(P.ws) * P.nc));
     FMM_CUDA_TRY(cudaMallocHost((void **)&S->h_count, sizeof(int)));
     int lo = 0, hi = 0;
     FMM_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&lo, &hi));
@@ -718,7 +725,7 @@ fmm_status solute_prepare(Plan &P)
     FMM_CUDA_TRY(cudaEventCreateWithFlags(&S->ev_up, cudaEventDisableTiming));
     FMM_CUDA_TRY(cudaEventCreateWithFlags(&S->ev_act, cudaEventDisableTiming));
     FMM_CUDA_TRY(cudaMalloc(&S->Lt, sizeof(double) * 9 * NU_MAX * P.nc));
-    FMM_CUDA_TRY(cudaMalloc(&S->part, sizeof(double) * NU_MAX * 189 * P.nc));
+    FMM_CUDA_TRY(cudaMalloc(&S->part, sizeof(double) * NU_MAX * n_il(P.ws) * P.nc));
     return FMM_OK;
 }
 

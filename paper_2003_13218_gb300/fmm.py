@@ -130,12 +130,15 @@ class FMMPlan:
     """A plan for N charges in a cubic box of side ``box`` (A), depth d, order p."""
 
     def __init__(self, box: float, N: int, depth: int, p: int, precision: str = "fp64", kappa: float | None = None,
-                 split: str = "fp16x2", timings: bool = False, m2l_pair: bool = True, boundary: str = "conducting"):
+                 split: str = "fp16x2", timings: bool = False, m2l_pair: bool = True, boundary: str = "conducting",
+                 ws: int = 1):
         self._lib = load_library()
         h = ctypes.c_void_p()
         _check(self._lib.fmm_plan_create(float(box), int(N), int(depth), int(p), ctypes.byref(h)), "fmm_plan_create")
         self._h = h
         self.box, self.N, self.depth, self.p = float(box), int(N), int(depth), int(p)
+        if ws != 1:
+            self.set_option(FMM_OPT_WS, int(ws))
         if split != "fp16x2":
             self.set_option(FMM_OPT_M2L_SPLIT, SPLIT[split])
         if precision != "fp64":

@@ -144,8 +144,11 @@ def test_invalid_arguments_are_rejected():
         assert e.value.code == 1
     plan = _plan(2.0, 10, 2, 4)
     with pytest.raises(FMMError) as e:
-        plan.set_option(1, 2)  # ws = 2 not built
+        plan.set_option(1, 3)  # ws = 3 is not built
     assert e.value.code == 7
+    with pytest.raises(FMMError) as e:
+        plan.set_option(1, 2)  # ws = 2 needs more than 5 leaves per side
+    assert e.value.code == 1
     plan.close()
 
 
