@@ -45,18 +45,24 @@ FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # profiles/k_m2l_tc_na_1m_level6.md, with the sha256 of the kernel's device
 # code it was taken on: the value is reported only while that code is unchanged.
 M2L_TRAFFIC = {"src": "paper_2003_13218_gb300/csrc/fmm_m2l_tc.cu",
-               "sha256": "5429f0131432c2ae13c8fb9568c3a586ffcc50fe4837f5b3ec9d75dd4ef4c56c",
-               "workload": "na_1m", "level": 6, "split": "fp16x2", "bytes_per_launch": 694.363648e6 + 170.471680e6}
+               "sha256": "c0b12966792e4de8869b0c85e1dc1aaf0888b14f4595b57e3cd8906f8ddd4554",
+               "workload": "na_1m", "level": 6, "split": "fp16x2", "ws": 1, "p": 12,
+               "bytes_per_launch": 753.414656e6 + 177.790720e6}
 KERNEL_BEGIN = "// ------------------------------------------------------------------ the kernel"
 KERNEL_END = "// ------------------------------------------------------------------ operand preparation"
 
 
-def m2l_flops(d: int, p: int, levels=None, fused_l2l=False) -> float:
+def n_il(ws: int) -> int:
+    """Interaction-list length: (4 ws + 2)^3 - (2 ws + 1)^3 (189 for ws = 1, 875 for ws = 2)."""
+    return (4 * ws + 2) ** 3 - (2 * ws + 1) ** 3
+
+
+def m2l_flops(d: int, p: int, levels=None, fused_l2l=False, ws: int = 1) -> float:
     """Algorithmic flops of M2L: 2 C^2 per (target, source) pair, 189 sources per target,
     plus one dense C x C product per target when the L2L is fused into the same launch."""
     C = (p + 1) ** 2
     levels = range(1, d + 1) if levels is None else levels
-    pairs = (189 + (1 if fused_l2l else 0)) * sum(8 ** l for l in levels)
+    pairs = (n_il(ws) + (1 if fused_l2l else 0)) * sum(8 ** l for l in levels)
     return 2.0 * C * C * pairs
 
 
@@ -179,6 +185,8 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     box, d, p = boxes.workload(args.workload, seed=rank)
+    if args.p is not None:
+        p = args.p
     N = box.N
     pos = torch.from_numpy(box.pos).to(dev)
     q = torch.from_numpy(box.q).to(dev)
@@ -186,7 +194,7 @@ def run_ours(args):
     F = torch.empty((N, 3), dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
 
-    plan = FMMPlan(box.L, N, d, p, precision="mixed", split=args.split, timings=True)
+    plan = FMMPlan(box.L, N, d, p, precision="mixed", split=args.split, timings=True, ws=args.ws)
     for _ in range(args.warmup):
         plan.evaluate(pos, q, sol, forces=F)
     torch.cuda.synchronize()
@@ -259,7 +267,7 @@ def run_ours(args):
     # the FP64 path on the same input
     fp64 = None
     if args.fp64_steps > 0:
-        p64 = FMMPlan(box.L, N, d, p, precision="fp64", timings=True)
+        p64 = FMMPlan(box.L, N, d, p, precision="fp64", timings=True, ws=args.ws)
         F64 = torch.empty_like(F)
         t64, uv64 = p64.evaluate(pos, q, sol, forces=F64)
         torch.cuda.synchronize()
@@ -293,17 +301,18 @@ def run_ours(args):
     peaks, peak_kind = load_peaks()
     uses_tc = backend == "tcgen05"
     fused = uses_tc and args.split == "fp16x2"  # the fp16 split fuses the L2L into each level's launch
-    stage_flops = m2l_flops(d, p, fused_l2l=fused)
+    stage_flops = m2l_flops(d, p, fused_l2l=fused, ws=args.ws)
     stage_ms = statistics.mean(x[1] for x in m2l_ms)
     if uses_tc:
         # the dominant launch: the tensor-core M2L of the finest level
-        flops = m2l_flops(d, p, levels=[d], fused_l2l=fused)
+        flops = m2l_flops(d, p, levels=[d], fused_l2l=fused, ws=args.ws)
         launch_ms = statistics.mean(x[0] for x in m2l_ms)
         peak = peaks.get("bf16_tflops", FALLBACK_PEAKS["bf16_tflops"])
         roof = {"bound": "tensor", "peak_source": peak_kind + " bf16 dense burst (MEASURED_PEAKS.json)",
                 "kernel": "k_m2l_tc, level %d (one launch%s)" % (d, ", M2L + fused L2L" if fused else "")}
         traffic = None
         if (M2L_TRAFFIC and M2L_TRAFFIC["workload"] == args.workload and M2L_TRAFFIC["level"] == d
+                and M2L_TRAFFIC.get("ws", 1) == args.ws and M2L_TRAFFIC.get("p", p) == p
                 and M2L_TRAFFIC["split"] == args.split and kernel_sha(M2L_TRAFFIC["src"]) == M2L_TRAFFIC["sha256"]):
             traffic = M2L_TRAFFIC["bytes_per_launch"]
     else:
@@ -319,7 +328,7 @@ def run_ours(args):
         C = (p + 1) ** 2
         ksteps, npad = (C + 15) // 16, (C + 15) // 16 * 16
         products = {"fp16x2": 3, "bf16x3": 6, "bf16a2b3": 4, "bf16x2": 3}.get(args.split, 0)
-        issued = 8 ** d * (189 + (1 if fused else 0)) * products * ksteps * 2.0 * npad * 16
+        issued = 8 ** d * (n_il(args.ws) + (1 if fused else 0)) * products * ksteps * 2.0 * npad * 16
         roof["issued_flops_per_launch"] = issued
         roof["issued_tflops"] = issued / (launch_ms / 1e3) / 1e12
     roof.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
@@ -338,9 +347,9 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": ("f32+%s-tensor+f64" % args.split) if uses_tc else "f32+f64",
         "data": "synthetic (seeded ion-in-water boxes standing in for the paper's MD snapshots)",
-        "config": {"workload": "%s: %s+ + %d TIP3P waters, N=%d, L=%.2f A, depth %d, p %d, ws 1, mixed precision, "
+        "config": {"workload": "%s: %s+ + %d TIP3P waters, N=%d, L=%.2f A, depth %d, p %d, ws %d, mixed precision, "
                                "energy+forces+solute-solvent per step" % (args.workload, box.ion, box.n_waters, N,
-                                                                          box.L, d, p),
+                                                                          box.L, d, p, args.ws),
                    "l2": "flushed between timed steps (256 MB write)", "jitter_A": args.jitter, "parallelism": "replicas" if ws > 1 else "1 GPU",
                    "m2l_split": args.split},
         "roofline": roof,
@@ -504,6 +513,8 @@ def main():
     ap.add_argument("--split", default="fp16x2", choices=["fp16x2", "bf16x3", "bf16x2", "bf16a2b3", "fp32"])
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ws", type=int, default=1, choices=[1, 2], help="well-separatedness (2: the paper's setting)")
+    ap.add_argument("--p", type=int, default=None, help="expansion order (default: the workload's)")
     ap.add_argument("--jitter", type=float, default=0.0,
                     help="jitter every position by N(0, jitter^2) A between timed calls (untimed)")
     args = ap.parse_args()
