@@ -178,30 +178,42 @@ __global__ void k_gather(int64_t N, const int *__restrict__ perm, const int *__r
     }
 }
 
-// block-level reduction of NQ compensated sums -> partial[block][NQ][2]
-template <int NQ>
-__device__ void block_reduce_store(KSum (&acc)[NQ], double *__restrict__ partial)
+// merge (s, c) across the lanes of a warp, fixed xor tree (deterministic); lane 0 holds the total
+__device__ inline KSum warp_merge(KSum k)
 {
-    __shared__ double sh[RED_THREADS][2];
+    for (int o = 16; o > 0; o >>= 1) {
+        KSum b{__shfl_xor_sync(0xffffffffu, k.s, o), __shfl_xor_sync(0xffffffffu, k.c, o)};
+        k.merge(b);
+    }
+    return k;
+}
+
+// block-level reduction of NQ per-thread sums -> partial[block][NQ][2]: warps
+// first, then the first warp over the warps' results
+template <int NQ>
+__device__ void block_reduce_store(const double (&acc)[NQ], double *__restrict__ partial)
+{
+    __shared__ double sh[RED_THREADS / 32][NQ][2];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
     for (int q = 0; q < NQ; ++q) {
-        sh[threadIdx.x][0] = acc[q].s;
-        sh[threadIdx.x][1] = acc[q].c;
-        __syncthreads();
-        for (int o = RED_THREADS / 2; o > 0; o >>= 1) {
-            if ((int)threadIdx.x < o) {
-                KSum a{sh[threadIdx.x][0], sh[threadIdx.x][1]};
-                KSum b{sh[threadIdx.x + o][0], sh[threadIdx.x + o][1]};
-                a.merge(b);
-                sh[threadIdx.x][0] = a.s;
-                sh[threadIdx.x][1] = a.c;
+        KSum k = warp_merge(KSum{acc[q], 0.0});
+        if (lane == 0) {
+            sh[w][q][0] = k.s;
+            sh[w][q][1] = k.c;
+        }
+    }
+    __syncthreads();
+    if (w == 0) {
+        for (int q = 0; q < NQ; ++q) {
+            KSum k{0.0, 0.0};
+            if (lane < RED_THREADS / 32) k = KSum{sh[lane][q][0], sh[lane][q][1]};
+            k = warp_merge(k);
+            if (lane == 0) {
+                partial[(blockIdx.x * NQ + q) * 2] = k.s;
+                partial[(blockIdx.x * NQ + q) * 2 + 1] = k.c;
             }
-            __syncthreads();
         }
-        if (threadIdx.x == 0) {
-            partial[(blockIdx.x * NQ + q) * 2] = sh[0][0];
-            partial[(blockIdx.x * NQ + q) * 2 + 1] = sh[0][1];
-        }
-        __syncthreads();
     }
 }
 
@@ -209,16 +221,21 @@ __device__ void block_reduce_store(KSum (&acc)[NQ], double *__restrict__ partial
 __global__ void k_bc_partial(int64_t N, const double *__restrict__ wpos, const double *__restrict__ q,
                              const uint8_t *__restrict__ sol, double *__restrict__ partial)
 {
-    KSum acc[10];
-    for (int k = 0; k < 10; ++k) acc[k] = {0, 0};
+    // a thread's own elements (N / 77,824, about 13 at N = 1M) are summed plainly; the
+    // compensated sums start at the warp level
+    double acc[10];
+#pragma unroll
+    for (int k = 0; k < 10; ++k) acc[k] = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         double qi = q[i];
         if (!isfinite(qi)) qi = 0.0;
         double x = wpos[3 * i], y = wpos[3 * i + 1], z = wpos[3 * i + 2];
         double v[5] = {qi, qi * x, qi * y, qi * z, qi * (x * x + y * y + z * z)};
-        for (int k = 0; k < 5; ++k) acc[k].add(v[k]);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) acc[k] += v[k];
         if (sol && sol[i])
-            for (int k = 0; k < 5; ++k) acc[5 + k].add(v[k]);
+#pragma unroll
+            for (int k = 0; k < 5; ++k) acc[5 + k] += v[k];
     }
     block_reduce_store<10>(acc, partial);
 }
@@ -230,51 +247,40 @@ __global__ void k_energy_partial(int64_t N, const Particle<T> *__restrict__ sp, 
                                  const uint8_t *__restrict__ sol, const T *__restrict__ nfuv,
                                  double *__restrict__ partial)
 {
-    KSum acc[6];
-    for (int k = 0; k < 6; ++k) acc[k] = {0, 0};
+    double acc[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) acc[k] = 0.0;
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
         double qs = (double)sp[s].q;
-        acc[0].add(0.5 * qs * (double)phi_nf[s]);
-        acc[1].add(0.5 * qs * (double)phi_ff[s]);
+        acc[0] += 0.5 * qs * (double)phi_nf[s];
+        acc[1] += 0.5 * qs * (double)phi_ff[s];
         if (sol) {
             if (sol[s]) {
-                acc[2].add(qs * (double)phi_ff[s]);
-                acc[3].add(qs * (double)phi_u[s]);
-                acc[5].add((double)nfuv[s]);
+                acc[2] += qs * (double)phi_ff[s];
+                acc[3] += qs * (double)phi_u[s];
+                acc[5] += (double)nfuv[s];
             } else {
-                acc[4].add(qs * (double)phi_u[s]);
+                acc[4] += qs * (double)phi_u[s];
             }
         }
     }
     block_reduce_store<6>(acc, partial);
 }
 
-// block partials -> totals; blockDim.x == RED_THREADS, fixed-order tree per quantity
+// block partials -> totals; blockDim.x == RED_THREADS: warp w takes the
+// quantities w, w + 8, ...; its lanes stride over the blocks, then a fixed xor tree
 template <int NQ>
 __device__ void final_sum(const double *__restrict__ partial, int nb, double *out)
 {
-    __shared__ double sh[RED_THREADS][2];
-    for (int q = 0; q < NQ; ++q) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int q = w; q < NQ; q += RED_THREADS / 32) {
         KSum k{0, 0};
-        for (int b = threadIdx.x; b < nb; b += RED_THREADS) {
+        for (int b = lane; b < nb; b += 32) {
             k.add(partial[(b * NQ + q) * 2]);
             k.add(partial[(b * NQ + q) * 2 + 1]);
         }
-        sh[threadIdx.x][0] = k.s;
-        sh[threadIdx.x][1] = k.c;
-        __syncthreads();
-        for (int o = RED_THREADS / 2; o > 0; o >>= 1) {
-            if ((int)threadIdx.x < o) {
-                KSum a{sh[threadIdx.x][0], sh[threadIdx.x][1]};
-                a.add(sh[threadIdx.x + o][0]);
-                a.add(sh[threadIdx.x + o][1]);
-                sh[threadIdx.x][0] = a.s;
-                sh[threadIdx.x][1] = a.c;
-            }
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) out[q] = sh[0][0] + sh[0][1];
-        __syncthreads();
+        k = warp_merge(k);
+        if (lane == 0) out[q] = k.val();
     }
 }
 
