@@ -194,7 +194,8 @@ def run_ours(args):
     F = torch.empty((N, 3), dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
 
-    plan = FMMPlan(box.L, N, d, p, precision="mixed", split=args.split, timings=True, ws=args.ws)
+    plan = FMMPlan(box.L, N, d, p, precision="mixed", split=args.split, timings=True, ws=args.ws,
+                   overlap=bool(args.overlap))
     for _ in range(args.warmup):
         plan.evaluate(pos, q, sol, forces=F)
     torch.cuda.synchronize()
@@ -351,7 +352,7 @@ def run_ours(args):
                                "energy+forces+solute-solvent per step" % (args.workload, box.ion, box.n_waters, N,
                                                                           box.L, d, p, args.ws),
                    "l2": "flushed between timed steps (256 MB write)", "jitter_A": args.jitter, "parallelism": "replicas" if ws > 1 else "1 GPU",
-                   "m2l_split": args.split},
+                   "m2l_split": args.split, "overlap": bool(args.overlap)},
         "roofline": roof,
         "solute_solvent_cost": uv_cost,
         "e2e": {"value": N * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": N * (24 + 8 + 1),
@@ -515,6 +516,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ws", type=int, default=1, choices=[1, 2], help="well-separatedness (2: the paper's setting)")
     ap.add_argument("--p", type=int, default=None, help="expansion order (default: the workload's)")
+    ap.add_argument("--overlap", type=int, default=1, choices=[0, 1],
+                    help="1: near field and sparse solute pass beside the far field (plan-owned streams)")
     ap.add_argument("--jitter", type=float, default=0.0,
                     help="jitter every position by N(0, jitter^2) A between timed calls (untimed)")
     args = ap.parse_args()

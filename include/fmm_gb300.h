@@ -31,7 +31,9 @@
  *    memory, operator tables and stream binding.
  *  - Work is enqueued on the plan's stream (default: the legacy default stream;
  *    see FMM_OPT_STREAM).  Calls that return host scalars synchronise that
- *    stream before returning.
+ *    stream before returning.  With FMM_OPT_OVERLAP (default on) a call forks
+ *    from that stream onto plan-owned streams and joins back into it before it
+ *    returns: work enqueued on the plan's stream afterwards sees its results.
  *  - A plan is not thread-safe: use one plan per host thread or stream.
  *  - Positions may lie outside [0, b); each atom is wrapped into the cell.
  *  - Non-finite positions or charges yield FMM_ERR_NONFINITE (detected on the
@@ -84,12 +86,14 @@ typedef struct {
 } fmm_uv_terms;
 
 /* Per-stage device times of the last call, milliseconds (CUDA events on the
- * plan's stream).  m2l_l2l covers M2L and L2L of levels 1..l_max of the full
- * pass; m2l_kernels the M2L launches alone; solute_pass the part of the
- * solute-only pass of Eq. FMMcalc that runs after the full pass (its prologue
- * overlaps the full pass on a side stream; 0 when not requested); m2l_top the
- * single tensor-core M2L
- * launch of level l_max (0 when that level runs on CUDA cores). */
+ * stream that runs the far field).  m2l_l2l covers M2L and L2L of levels
+ * 1..l_max of the full pass; m2l_kernels the M2L launches alone; solute_pass
+ * the part of the solute-only pass of Eq. FMMcalc that runs after the full
+ * pass (its prologue overlaps the full pass on a side stream; 0 when not
+ * requested); m2l_top the single tensor-core M2L launch of level l_max (0 when
+ * that level runs on CUDA cores).  With FMM_OPT_OVERLAP the near field and the
+ * sparse solute pass run beside the far field: p2p is then about 0 and
+ * solute_pass holds the wait for both and the last solute kernel. */
 typedef struct {
     float sort, upward, lattice, m2l_l2l, l2p, p2p, solute_pass, reduce, total, m2l_kernels, m2l_top;
 } fmm_timings;
@@ -111,7 +115,12 @@ enum {
     FMM_OPT_BOUNDARY = 8   /* ival: FMM_BOUNDARY_CONDUCTING (default; Eq. Velecfull, with the dipole surface
                               term -(2 pi/3V) mu.mu of App. D) or FMM_BOUNDARY_VACUUM (App. D: FMM's own
                               boundary, without that term, its force and its solute-solvent cross term
-                              -(4 pi/3V) mu_u.mu_v) */
+                              -(4 pi/3V) mu_u.mu_v) */,
+    FMM_OPT_OVERLAP = 9    /* ival: 1 (default) runs a call on plan-owned streams: the far field on one above
+                              the default priority, the near field (P2P, which needs only the sort) on one
+                              of the lowest priority filling the SMs the far field leaves idle, the sparse
+                              solute pass of Eq. FMMcalc beside the L2P; 0 runs every stage in order on the
+                              plan's stream (the per-stage times then add up) */
 };
 enum { FMM_BOUNDARY_CONDUCTING = 0, FMM_BOUNDARY_VACUUM = 1 };
 enum { FMM_PREC_FP64 = 0, FMM_PREC_MIXED = 1 };

@@ -118,7 +118,10 @@ struct StageTimer {
 fmm_status far_field_pass(Plan &P, bool gradient, bool solute_only, StageTimer *tm, bool fork_solute = false)
 {
     TRY(launch_upward(P, solute_only));
-    if (fork_solute) TRY(solute_prologue(P));
+    if (fork_solute) {
+        TRY(solute_prologue(P));
+        TRY(solute_sparse_fork(P));
+    }
     if (tm) tm->mark();
     TRY(launch_lattice(P));
     if (tm) tm->mark();
@@ -138,6 +141,32 @@ fmm_status far_field_pass(Plan &P, bool gradient, bool solute_only, StageTimer *
     return FMM_OK;
 }
 
+// the work of one call that needs only the sort, on the plan's near stream (P.overlap): the background
+// moments, the near field and the solute-solvent near-field sum
+fmm_status fork_near_field(Plan &P, const double *dq, const uint8_t *dsol, bool gradient, bool want_uv)
+{
+    FMM_CUDA_TRY(cudaEventRecord(P.ev_sorted, P.stream));
+    FMM_CUDA_TRY(cudaStreamWaitEvent(P.near, P.ev_sorted, 0));
+    P.near_forked = P.near_p2p = true;
+    cudaStream_t main_stream = P.stream;
+    P.stream = P.near;
+    fmm_status s = launch_bc_moments(P, dq, dsol);
+    if (s == FMM_OK) s = launch_p2p(P, gradient);
+    if (s == FMM_OK && want_uv) s = launch_p2p_uv(P);
+    P.stream = main_stream;
+    return s;
+}
+
+// the near stream's work of the call (the forked solute pass may have added to it) into the plan's stream
+fmm_status join_near_field(Plan &P)
+{
+    if (!P.near_forked) return FMM_OK;
+    P.near_forked = false;
+    FMM_CUDA_TRY(cudaEventRecord(P.ev_near, P.near));
+    FMM_CUDA_TRY(cudaStreamWaitEvent(P.stream, P.ev_near, 0));
+    return FMM_OK;
+}
+
 // front of one evaluation on device inputs: sort, solute count, background
 // moments, full far-field pass (with the solute prologue forked), near field
 fmm_status eval_front(Plan &P, const double *dpos, const double *dq, const uint8_t *dsol, bool want_uv,
@@ -145,12 +174,14 @@ fmm_status eval_front(Plan &P, const double *dpos, const double *dq, const uint8
 {
     if (tm) tm->mark();
     FMM_CUDA_TRY(cudaMemsetAsync(P.d_err, 0, sizeof(int), P.stream));
+    P.near_forked = P.near_p2p = false;
     TRY(launch_assign_sort(P, dpos, dq, dsol));
     if (want_uv) TRY(solute_count(P));
     if (tm) tm->mark();
-    TRY(launch_bc_moments(P, dq, dsol));
+    if (P.overlap && P.near) TRY(fork_near_field(P, dq, dsol, gradient, want_uv));
+    else TRY(launch_bc_moments(P, dq, dsol));
     TRY(far_field_pass(P, gradient, false, tm, want_uv));
-    TRY(launch_p2p(P, gradient));
+    if (!P.near_p2p) TRY(launch_p2p(P, gradient));
     if (tm) tm->mark();
     return FMM_OK;
 }
@@ -160,11 +191,12 @@ fmm_status eval_front(Plan &P, const double *dpos, const double *dq, const uint8
 // totals and the error flags into P.h_out
 fmm_status eval_back(Plan &P, const double *dq, bool want_uv, double *dforces, StageTimer *tm)
 {
+    TRY(join_near_field(P));
     if (want_uv) {
         bool sparse_done = false;
         TRY(launch_solute_pass(P, &sparse_done));
         if (!sparse_done) TRY(far_field_pass(P, false, true, nullptr));
-        TRY(launch_p2p_uv(P));
+        if (!P.near_p2p) TRY(launch_p2p_uv(P));
     }
     if (tm) tm->mark();
     TRY(launch_energy_reduce(P, want_uv));
@@ -203,6 +235,38 @@ fmm_status eval_read(Plan &P, fmm_energy_terms *terms, fmm_uv_terms *uv)
     return FMM_OK;
 }
 
+// one call on the plan's execution stream (P.overlap): forked from the caller's stream on entry, joined
+// back into it on every exit (a failed call's near field included)
+struct ExecScope {
+    Plan &P;
+    cudaStream_t caller = 0;
+    bool active = false;
+    fmm_status status = FMM_OK;
+    explicit ExecScope(Plan &p) : P(p)
+    {
+        if (!P.overlap || !P.exec) return;
+        caller = P.stream;
+        if (cudaEventRecord(P.ev_in, caller) != cudaSuccess || cudaStreamWaitEvent(P.exec, P.ev_in, 0) != cudaSuccess) {
+            status = FMM_ERR_CUDA;
+            return;
+        }
+        P.stream = P.exec;
+        active = true;
+    }
+    ~ExecScope()
+    {
+        if (!active) return;
+        if (P.near_forked) {  // a failed call
+            cudaEventRecord(P.ev_near, P.near);
+            cudaStreamWaitEvent(P.exec, P.ev_near, 0);
+            P.near_forked = false;
+        }
+        cudaEventRecord(P.ev_out, P.exec);
+        cudaStreamWaitEvent(caller, P.ev_out, 0);
+        P.stream = caller;
+    }
+};
+
 fmm_status evaluate(Plan &P, const double *pos, const double *q, const uint8_t *sol, double *forces,
                     fmm_energy_terms *terms, fmm_uv_terms *uv)
 {
@@ -213,6 +277,8 @@ fmm_status evaluate(Plan &P, const double *pos, const double *q, const uint8_t *
     int kf = pointer_kind(forces);
     bool host_any = kp == 1 || kq == 1 || ks == 1 || kf == 1;
     if (host_any) TRY(ensure_staging(P));
+    ExecScope xs(P);
+    TRY(xs.status);
     P.launches = 0;
     P.top_recorded = false;
     const double *dpos = pos, *dq = q;
@@ -263,6 +329,21 @@ fmm_status evaluate(Plan &P, const double *pos, const double *q, const uint8_t *
         if (P.top_recorded) cudaEventElapsedTime(&P.last.m2l_top, P.ev_top[0], P.ev_top[1]);
     }
     return eval_read(P, terms, uv);
+}
+
+// the plan's execution stream (one priority level above the default) and its near-field stream (the
+// default, lowest priority): the block scheduler serves the far field first and gives the near field the
+// SMs, registers and warp slots the far field leaves free
+fmm_status create_streams(Plan &P)
+{
+    int lo = 0, hi = 0;
+    FMM_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    const int mid = hi < lo ? lo - 1 : lo;  // numerically smaller = higher priority
+    FMM_CUDA_TRY(cudaStreamCreateWithPriority(&P.exec, cudaStreamNonBlocking, mid));
+    FMM_CUDA_TRY(cudaStreamCreateWithPriority(&P.near, cudaStreamNonBlocking, lo));
+    for (cudaEvent_t *e : {&P.ev_in, &P.ev_out, &P.ev_sorted, &P.ev_near})
+        FMM_CUDA_TRY(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    return FMM_OK;
 }
 
 // tensor-core operands follow the precision and split options
@@ -321,7 +402,8 @@ fmm_status fmm_plan_create(double box, int64_t N, int depth, int p, fmm_plan *ou
         for (int i = 0; i < 12; ++i) cudaEventCreate(&P.ev[i]);
         for (int i = 0; i < 18; ++i) cudaEventCreate(&P.ev_m2l[i]);
         for (int i = 0; i < 2; ++i) cudaEventCreate(&P.ev_top[i]);
-        s = solute_prepare(P);
+        s = create_streams(P);
+        if (s == FMM_OK) s = solute_prepare(P);
         if (s == FMM_OK) s = rebuild(P);
     }
     if (s != FMM_OK) {
@@ -375,6 +457,10 @@ fmm_status fmm_plan_set_option(fmm_plan plan, int key, int64_t ival, double dval
     case FMM_OPT_M2L_PAIR:
         if (ival != 0 && ival != 1) return FMM_ERR_INVALID_ARG;
         P.tc_pair = ival != 0;
+        return FMM_OK;
+    case FMM_OPT_OVERLAP:
+        if (ival != 0 && ival != 1) return FMM_ERR_INVALID_ARG;
+        P.overlap = ival != 0;
         return FMM_OK;
     default:
         return FMM_ERR_INVALID_ARG;
@@ -442,6 +528,8 @@ void fmm_plan_destroy(fmm_plan plan)
     if (!plan) return;
     Plan &P = plan->P;
     cudaStreamSynchronize(P.stream);
+    if (P.exec) cudaStreamSynchronize(P.exec);
+    if (P.near) cudaStreamSynchronize(P.near);
     tc_free(P);
     solute_free(P);
     free_tables(P);
@@ -452,6 +540,10 @@ void fmm_plan_destroy(fmm_plan plan)
         if (P.ev_m2l[i]) cudaEventDestroy(P.ev_m2l[i]);
     for (int i = 0; i < 2; ++i)
         if (P.ev_top[i]) cudaEventDestroy(P.ev_top[i]);
+    for (cudaEvent_t e : {P.ev_in, P.ev_out, P.ev_sorted, P.ev_near})
+        if (e) cudaEventDestroy(e);
+    if (P.exec) cudaStreamDestroy(P.exec);
+    if (P.near) cudaStreamDestroy(P.near);
     delete plan;
 }
 

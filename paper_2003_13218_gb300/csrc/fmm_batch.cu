@@ -174,7 +174,7 @@ void batch_capture(fmm_batch b, const double *const *pos, const double *const *q
         }
         if (cudaStreamEndCapture(b->origin, &g) != cudaSuccess) ok = false;
     }
-    if (ok && g) ok = cudaGraphInstantiate(&b->graph, g, 0) == cudaSuccess;
+    if (ok && g) ok = cudaGraphInstantiate(&b->graph, g, cudaGraphInstantiateFlagUseNodePriority) == cudaSuccess;
     if (g) cudaGraphDestroy(g);
     if (!ok) {
         if (b->graph) cudaGraphExecDestroy(b->graph);
@@ -227,7 +227,10 @@ fmm_status fmm_batch_create(int nbox, const double *box, const int64_t *N, const
     for (int k = 0; k < ns && s == FMM_OK; ++k) {
         cudaStream_t st;
         cudaEvent_t ev;
-        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) s = FMM_ERR_CUDA;
+        // one level above the default priority, like a plan's own execution stream: the near fields
+        // (default priority) fill the SMs the far fields leave free
+        if (cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, hi < lo ? lo - 1 : lo) != cudaSuccess)
+            s = FMM_ERR_CUDA;
         else b->streams.push_back(st);
         if (s == FMM_OK && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) s = FMM_ERR_CUDA;
         else if (s == FMM_OK) b->ev_done.push_back(ev);

@@ -100,6 +100,13 @@ struct Plan {
     bool tc_pair = true;  // CTA-pair (2-SM) tensor-core M2L where the level allows it
     int known_count = -1; // >= 0: the solute count the caller already knows (no host wait; graph capture)
     int boundary = 0;     // FMM_BOUNDARY_CONDUCTING (Eq. Velecfull) or FMM_BOUNDARY_VACUUM (App. D)
+    // FMM_OPT_OVERLAP: evaluate() runs on `exec` (priority above the default), the near field on `near`
+    // (lowest priority: it fills what the far field leaves idle), both joined before the reductions
+    bool overlap = true;
+    cudaStream_t exec = nullptr, near = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_sorted = nullptr, ev_near = nullptr;
+    bool near_forked = false;  // work of the current call on `near`, not yet joined
+    bool near_p2p = false;     // the current call's near field (P2P) runs on `near`
     int nc = 0;
     int64_t nleaf = 0;  // 8^d
     int64_t launches = 0;
@@ -259,7 +266,11 @@ int solute_count_host(const Plan &P);
 // after the full pass's upward sweep: the pass's prologue (active cells, solute moments, FP64 solvent
 // expansions at the active cells) on a high-priority side stream, overlapping the full pass's M2L
 fmm_status solute_prologue(Plan &P);
-// joins the prologue and runs the rest (sparse pass); *done = false when the dense pass must run
+// right after the prologue (P.overlap): the rest of the sparse pass on the side stream (it touches none of
+// the full pass's expansions) and Phi_u at every charge on the near stream when that is forked; grids
+// cover the largest count and the device count decides
+fmm_status solute_sparse_fork(Plan &P);
+// joins the prologue (or the forked sparse pass) and runs the rest; *done = false when the dense pass must run
 fmm_status launch_solute_pass(Plan &P, bool *done);
 
 // tensor-core M2L, and with the fp16 split also M2M and L2L (fmm_m2l_tc.cu)

@@ -49,8 +49,11 @@ struct SoluteScratch {
     cudaEvent_t ev_count = nullptr;    // count copied to h_count
     cudaEvent_t ev_up = nullptr;       // full upward pass done (fork)
     cudaEvent_t ev_act = nullptr;      // prologue done (join)
-    bool count_pending = false, prologue_pending = false;
+    cudaEvent_t ev_ready = nullptr;    // forked pass's expansions ready (Phi_u on the near stream waits)
+    cudaEvent_t ev_sparse = nullptr;   // forked sparse pass done (join)
+    bool count_pending = false, prologue_pending = false, sparse_forked = false;
     void *Lt = nullptr;      // [9][NU_MAX][nc] full local expansions at the active cells (FP64)
+    void *Lu = nullptr;      // solute-only local expansions of every cell of levels 0..LD (class layout), T
     double *part = nullptr;  // [NU_MAX][n_il][nc] their M2L terms, one per offset
 };
 
@@ -206,25 +209,6 @@ __global__ void k_sol_m2m(int p, int l, const int *__restrict__ cells, const int
     }
 }
 
-// copy the active cells' moments of the coarse levels into the zeroed dense arrays
-template <typename T>
-__global__ void k_sol_scatter(int p, int lmax, const int *__restrict__ cells, const int *__restrict__ ncells,
-                              const T *__restrict__ MU, T *M0, T *M1, T *M2, T *M3)
-{
-    int l = blockIdx.y;
-    if (l > lmax) return;
-    int i = blockIdx.x;
-    if (i >= ncells[l]) return;
-    int nc = ncoef(p);
-    int nl = 1 << l;
-    int x, y, z;
-    cell_xyz(cells[l * NU_MAX + i], nl, x, y, z);
-    T *M = l == 0 ? M0 : l == 1 ? M1 : l == 2 ? M2 : M3;
-    T *dst = M + cell_index(l, x, y, z) * nc;
-    const T *src = MU + ((size_t)l * NU_MAX + i) * nc;
-    for (int k = threadIdx.x; k < nc; k += blockDim.x) dst[k] = src[k];
-}
-
 // interaction-list test: is s = t + delta in IL(t)?  (per axis delta in
 // [-2 ws - c, 2 ws + 1 - c] for target parity c, and not all |delta| <= ws)
 __device__ inline bool in_il(int dx, int dy, int dz, int tx, int ty, int tz, int ws)
@@ -241,6 +225,118 @@ __device__ inline int wrap_delta(int d, int n)  // representative of d mod n in 
     if (d < -n / 2) d += n;
     if (d >= n / 2) d -= n;
     return d;
+}
+
+// offset of level l in the dense arrays of levels 0..LD (8^0 + ... + 8^(l-1) cells before it)
+__host__ __device__ inline int64_t dense_off(int l, int nc) { return (((int64_t)1 << (3 * l)) - 1) / 7 * nc; }
+
+// solute-only expansion of the root: the lattice operator of Eq. 12 applied to the root's solute moments
+// (zero without solute charges)
+template <typename T>
+__global__ void k_sol_lattice(int p, const int *__restrict__ ncells, const double *__restrict__ T0,
+                              const T *__restrict__ MU, T *__restrict__ Lu0)
+{
+    const int nc = ncoef(p);
+    const bool any = ncells[0] > 0;
+    for (int j = threadIdx.x; j < nc; j += blockDim.x) {
+        double acc = 0;
+        if (any)
+            for (int k = 0; k < nc; ++k) acc += T0[(size_t)k * nc + j] * (double)MU[k];
+        Lu0[j] = (T)acc;
+    }
+}
+
+// M2L terms of the dense levels 1..LD, one block per (active source a, offset d of the window
+// [-2ws-1, 2ws+1]^3): part[a][d] = T(d) . MU_a (Eq. Lcoeffdef) when the source lies in the interaction
+// list of the target t = s_a - d (wrapped).  At coarse levels several offsets reach the same target (its
+// periodic images): each has its own term.
+template <typename T>
+__global__ void k_sol_dense_m2l(int p, int l, int ws, const int *__restrict__ cells, const int *__restrict__ ncells,
+                                const T *__restrict__ Top, const T *__restrict__ MU, T *__restrict__ part)
+{
+    const int a = blockIdx.x, b = blockIdx.y;
+    if (a >= ncells[l]) return;
+    const int nc = ncoef(p), n = 1 << l, h = 2 * ws + 1, side = 2 * h + 1;
+    const int dx = b % side - h, dy = (b / side) % side - h, dz = b / (side * side) - h;
+    int sx, sy, sz;
+    cell_xyz(cells[l * NU_MAX + a], n, sx, sy, sz);
+    const int tx = (sx - dx + 4 * n) & (n - 1), ty = (sy - dy + 4 * n) & (n - 1), tz = (sz - dz + 4 * n) & (n - 1);
+    if (!in_il(dx, dy, dz, tx, ty, tz, ws)) return;
+    const T *Tp = Top + (size_t)off_slot(dx, dy, dz, ws) * nc * nc;
+    const T *Ms = MU + ((size_t)l * NU_MAX + a) * nc;
+    T *out = part + ((size_t)a * side * side * side + b) * nc;
+    for (int j = threadIdx.x; j < nc; j += blockDim.x) {
+        T acc = 0;
+        for (int k = 0; k < nc; ++k) acc += Tp[(size_t)k * nc + j] * Ms[k];
+        out[j] = acc;
+    }
+}
+
+// dense level 1 <= l <= LD of the solute-only pass, every target cell (one block each, thread j =
+// coefficient j): the L2L of the parent's expansion (Eq. L2L: Lhat_k^m = 2^-(k+1) sum_{n >= k}
+// Lhat_n^q R_{n-k}^{q-m}(w_c)) plus the M2L terms of k_sol_dense_m2l whose target this is, summed in
+// the window's offset order (the sums do not depend on the schedule)
+template <typename T>
+__global__ void k_sol_dense(int p, int l, int ws, const int *__restrict__ cells, const int *__restrict__ ncells,
+                            const T *__restrict__ part, const T *__restrict__ Rw, const T *__restrict__ Lpar,
+                            T *__restrict__ Lout)
+{
+    __shared__ short hit[(4 * WS_MAX + 3) * (4 * WS_MAX + 3) * (4 * WS_MAX + 3)];
+    __shared__ T sL[NC_MAX], sR[NC_MAX];
+    const int nc = ncoef(p), n = 1 << l, h = 2 * ws + 1, side = 2 * h + 1, W = side * side * side;
+    int tx, ty, tz;
+    cell_xyz(blockIdx.x, n, tx, ty, tz);
+    const int na = ncells[l];
+    const int *act = cells + l * NU_MAX;
+    const int oct = (tx & 1) | ((ty & 1) << 1) | ((tz & 1) << 2);
+    const T *Lp = Lpar + cell_index(l - 1, tx >> 1, ty >> 1, tz >> 1) * nc;
+    for (int j = threadIdx.x; j < nc; j += blockDim.x) {
+        sL[j] = Lp[j];
+        sR[j] = Rw[oct * nc + j];
+    }
+    for (int b = threadIdx.x; b < W; b += blockDim.x) {
+        const int dx = b % side - h, dy = (b / side) % side - h, dz = b / (side * side) - h;
+        int a = -1;
+        if (in_il(dx, dy, dz, tx, ty, tz, ws)) {
+            const int key = ((tx + dx + 4 * n) & (n - 1)) + n * (((ty + dy + 4 * n) & (n - 1)) +
+                                                                 n * ((tz + dz + 4 * n) & (n - 1)));
+            int lo = 0, hi = na;  // active cells are sorted and unique
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (act[mid] < key) lo = mid + 1;
+                else hi = mid;
+            }
+            if (lo < na && act[lo] == key) a = lo;
+        }
+        hit[b] = (short)a;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < nc; j += blockDim.x) {
+        // output coefficient j = (k, m, real or imaginary part)
+        int k = 0;
+        while ((k + 1) * (k + 1) <= j) ++k;
+        const int r = j - k * k;
+        const int m = (r + 1) >> 1;
+        const bool imag = r > 0 && (r & 1) == 0;
+        T accr = 0, acci = 0;
+        for (int nn = k; nn <= p; ++nn) {
+            const int dn = nn - k;
+            for (int q = m - dn; q <= m + dn; ++q) {
+                if (q < -nn || q > nn) continue;
+                Cx<T> pr = cmul(coef(sL, nn, q), coef(sR, dn, q - m));
+                accr += pr.re;
+                acci += pr.im;
+            }
+        }
+        T scale = 1;
+        for (int e = 0; e <= k; ++e) scale *= T(0.5);
+        T acc = scale * (imag ? acci : accr);
+        for (int b = 0; b < W; ++b) {
+            const int a = hit[b];
+            if (a >= 0) acc += part[((size_t)a * W + b) * nc + j];
+        }
+        Lout[cell_index(l, tx, ty, tz) * nc + j] = acc;
+    }
 }
 
 // mark the targets of active source blockIdx.x at level l (threads over the candidate offsets)
@@ -640,30 +736,29 @@ fmm_status solute_prologue_t(Plan &P, SoluteScratch &S, cudaStream_t st)
     return FMM_OK;
 }
 
-// the rest, on the plan's stream once the prologue is joined: the dense coarse
-// levels, the sparse finer levels and Phi_u at every charge
+// the rest of the pass (it reads only the prologue's active cells and moments): the dense coarse levels
+// into the pass's own arrays and the target lists and M2L sums of the sparse finer levels
 template <typename T>
 fmm_status solute_sparse_t(Plan &P, SoluteScratch &S, int nu)
 {
     const int p = P.p, d = P.d, nc = P.nc;
-    const int nside = 1 << d;
-    const double h = P.box / nside;
     const T *Top = std::is_same<T, double>::value ? (const T *)P.tab.Top64 : (const T *)P.tab.Top32;
+    const T *Rw = std::is_same<T, double>::value ? (const T *)P.tab.Rw64 : (const T *)P.tab.Rw32;
     T *MU = (T *)S.MU;
-    double *Lt = (double *)S.Lt;
+    T *Lu = (T *)S.Lu;
+    const int nth = ((nc + 31) / 32) * 32;
     // dense coarse levels 0..LD
-    for (int l = 0; l <= LD; ++l)
-        FMM_CUDA_TRY(cudaMemsetAsync(P.M[l], 0, sizeof(T) * ((size_t)1 << (3 * l)) * nc, P.stream));
-    k_sol_scatter<T><<<dim3(nu, LD + 1), 128, 0, P.stream>>>(p, LD, S.cells, S.ncells, MU, (T *)P.M[0],
-                                                                 (T *)P.M[1], (T *)P.M[2], (T *)P.M[3]);
+    k_sol_lattice<T><<<1, nth, 0, P.stream>>>(p, S.ncells, P.tab.T0, MU, Lu);
     FMM_LAUNCH_CHECK(P);
-    fmm_status st = launch_lattice(P);
-    if (st != FMM_OK) return st;
+    // the M2L terms of one dense level at a time in the (unused) level 0..LD part of the sparse sums
+    T *part = (T *)S.contrib;
+    const int win = off_side(P.ws) * off_side(P.ws) * off_side(P.ws);
     for (int l = 1; l <= LD; ++l) {
-        st = tc_available(P, l) ? launch_m2l_tc(P, l, true) : launch_m2l_simt(P, l);
-        if (st != FMM_OK) return st;
-        if (!(tc_available(P, l) && tc_translations(P))) st = launch_l2l(P, l);  // else fused
-        if (st != FMM_OK) return st;
+        k_sol_dense_m2l<T><<<dim3(nu, win), nth, 0, P.stream>>>(p, l, P.ws, S.cells, S.ncells, Top, MU, part);
+        FMM_LAUNCH_CHECK(P);
+        k_sol_dense<T><<<1u << (3 * l), nth, 0, P.stream>>>(p, l, P.ws, S.cells, S.ncells, part, Rw,
+                                                              Lu + dense_off(l - 1, nc), Lu + dense_off(l, nc));
+        FMM_LAUNCH_CHECK(P);
     }
     // sparse finer levels
     for (int l = LD + 1; l <= d; ++l) {
@@ -686,14 +781,31 @@ fmm_status solute_sparse_t(Plan &P, SoluteScratch &S, int nu)
                                                                        S.ncells + 16 + l, Top, MU, (T *)S.contrib);
         FMM_LAUNCH_CHECK(P);
     }
-    k_sol_eval<T><<<blocks_for(P.N, 128), 128, 0, P.stream>>>(p, d, max_tgt(P.ws), P.N, (T)h, P.sleaf,
+    return FMM_OK;
+}
+
+// Phi_u at every charge: the level-LD expansion plus the sparse finer-level sums
+template <typename T>
+fmm_status solute_eval_t(Plan &P, SoluteScratch &S)
+{
+    const double h = P.box / (1 << P.d);
+    k_sol_eval<T><<<blocks_for(P.N, 128), 128, 0, P.stream>>>(P.p, P.d, max_tgt(P.ws), P.N, (T)h, P.sleaf,
                                                               (const Particle<T> *)P.sorted,
-                                                              (const T *)P.L[LD], S.tlist, S.ncells + 16,
-                                                              (const T *)S.contrib, (T *)P.phi_u);
+                                                              (const T *)S.Lu + dense_off(LD, P.nc), S.tlist,
+                                                              S.ncells + 16, (const T *)S.contrib, (T *)P.phi_u);
     FMM_LAUNCH_CHECK(P);
-    // full-field potential at the solute charges: solvent field + solute field
-    k_act_l2p<T><<<1, NU_MAX, 0, P.stream>>>(p, d, 1.0 / h, S.list, S.cells, S.ncells, P.sleaf,
-                                             (const Particle<T> *)P.sorted, Lt, (const T *)P.phi_u, (T *)P.phi_ff);
+    return FMM_OK;
+}
+
+// full-field potential at the solute charges (solvent field + solute field) into phi_ff, after the full
+// pass's L2P has written phi_ff
+template <typename T>
+fmm_status solute_act_l2p_t(Plan &P, SoluteScratch &S)
+{
+    const double h = P.box / (1 << P.d);
+    k_act_l2p<T><<<1, NU_MAX, 0, P.stream>>>(P.p, P.d, 1.0 / h, S.list, S.cells, S.ncells, P.sleaf,
+                                             (const Particle<T> *)P.sorted, (const double *)S.Lt,
+                                             (const T *)P.phi_u, (T *)P.phi_ff);
     FMM_LAUNCH_CHECK(P);
     return FMM_OK;
 }
@@ -724,7 +836,10 @@ fmm_status solute_prepare(Plan &P)
     FMM_CUDA_TRY(cudaEventCreateWithFlags(&S->ev_count, cudaEventDisableTiming));
     FMM_CUDA_TRY(cudaEventCreateWithFlags(&S->ev_up, cudaEventDisableTiming));
     FMM_CUDA_TRY(cudaEventCreateWithFlags(&S->ev_act, cudaEventDisableTiming));
+    FMM_CUDA_TRY(cudaEventCreateWithFlags(&S->ev_ready, cudaEventDisableTiming));
+    FMM_CUDA_TRY(cudaEventCreateWithFlags(&S->ev_sparse, cudaEventDisableTiming));
     FMM_CUDA_TRY(cudaMalloc(&S->Lt, sizeof(double) * 9 * NU_MAX * P.nc));
+    FMM_CUDA_TRY(cudaMalloc(&S->Lu, sizeof(double) * dense_off(LD + 1, P.nc)));
     FMM_CUDA_TRY(cudaMalloc(&S->part, sizeof(double) * NU_MAX * n_il(P.ws) * P.nc));
     return FMM_OK;
 }
@@ -743,6 +858,7 @@ void solute_free(Plan &P)
     cudaFree(S->tlist);
     cudaFree(S->contrib);
     cudaFree(S->Lt);
+    cudaFree(S->Lu);
     cudaFree(S->part);
     if (S->h_count) cudaFreeHost(S->h_count);
     if (S->side) {
@@ -752,6 +868,8 @@ void solute_free(Plan &P)
     if (S->ev_count) cudaEventDestroy(S->ev_count);
     if (S->ev_up) cudaEventDestroy(S->ev_up);
     if (S->ev_act) cudaEventDestroy(S->ev_act);
+    if (S->ev_ready) cudaEventDestroy(S->ev_ready);
+    if (S->ev_sparse) cudaEventDestroy(S->ev_sparse);
     delete S;
     P.sol = nullptr;
 }
@@ -766,6 +884,7 @@ fmm_status solute_count(Plan &P)
 {
     SoluteScratch *S = (SoluteScratch *)P.sol;
     if (!S) return FMM_OK;
+    S->sparse_forked = false;  // a new call (a failed one may have left it set)
     FMM_CUDA_TRY(cudaMemsetAsync(S->list + NU_MAX, 0, sizeof(int), P.stream));
     k_sol_list<<<blocks_for(P.N, 256), 256, 0, P.stream>>>(P.N, P.sorted_sol, S->list);
     FMM_LAUNCH_CHECK(P);
@@ -792,12 +911,57 @@ fmm_status solute_prologue(Plan &P)
     return s;
 }
 
+fmm_status solute_sparse_fork(Plan &P)
+{
+    SoluteScratch *S = (SoluteScratch *)P.sol;
+    if (!S || !P.overlap || !S->prologue_pending || S->sparse_forked) return FMM_OK;
+    int nu = NU_MAX;  // unknown count: grids for the largest, the device count decides
+    if (P.known_count >= 0) {
+        if (P.known_count == 0 || P.known_count > NU_MAX) return FMM_OK;  // nothing to overlap
+        nu = P.known_count;
+    }
+    // behind the prologue on the side stream; Phi_u at every charge (a full-size launch) on the near
+    // stream, where it fills idle SMs instead of taking them from the far field
+    cudaStream_t main_stream = P.stream;
+    P.stream = S->side;
+    fmm_status s = P.precision == FMM_PREC_FP64 ? solute_sparse_t<double>(P, *S, nu) : solute_sparse_t<float>(P, *S, nu);
+    if (s == FMM_OK && P.near_forked) {
+        if (cudaEventRecord(S->ev_ready, S->side) != cudaSuccess || cudaStreamWaitEvent(P.near, S->ev_ready, 0) != cudaSuccess)
+            s = FMM_ERR_CUDA;
+        P.stream = P.near;
+    }
+    if (s == FMM_OK) s = P.precision == FMM_PREC_FP64 ? solute_eval_t<double>(P, *S) : solute_eval_t<float>(P, *S);
+    P.stream = main_stream;
+    if (s != FMM_OK) return s;
+    FMM_CUDA_TRY(cudaEventRecord(S->ev_sparse, S->side));
+    S->sparse_forked = true;
+    return FMM_OK;
+}
+
 // Phi_u into P.phi_u by the sparse pass; *done = false asks for the dense pass
 fmm_status launch_solute_pass(Plan &P, bool *done)
 {
     *done = false;
     SoluteScratch *S = (SoluteScratch *)P.sol;
     if (!S) return FMM_OK;
+    if (S->sparse_forked) {
+        // forked after the prologue (Phi_u on the near stream, joined before this call): join the side
+        // stream; the dense pass overwrites the (empty) result when the count is above NU_MAX
+        if (P.known_count < 0) FMM_CUDA_TRY(cudaEventSynchronize(S->ev_count));
+        FMM_CUDA_TRY(cudaStreamWaitEvent(P.stream, S->ev_sparse, 0));
+        S->count_pending = S->prologue_pending = S->sparse_forked = false;
+        int n = P.known_count >= 0 ? P.known_count : *S->h_count;
+        if (n > NU_MAX) return FMM_OK;
+        if (n == 0) {
+            size_t bytes = (P.precision == FMM_PREC_FP64 ? sizeof(double) : sizeof(float)) * P.N;
+            FMM_CUDA_TRY(cudaMemsetAsync(P.phi_u, 0, bytes, P.stream));
+            *done = true;
+            return FMM_OK;
+        }
+        fmm_status s = P.precision == FMM_PREC_FP64 ? solute_act_l2p_t<double>(P, *S) : solute_act_l2p_t<float>(P, *S);
+        if (s == FMM_OK) *done = true;
+        return s;
+    }
     if (!S->prologue_pending) {
         fmm_status s = solute_prologue(P);
         if (s != FMM_OK) return s;
@@ -816,6 +980,8 @@ fmm_status launch_solute_pass(Plan &P, bool *done)
         return FMM_OK;
     }
     fmm_status s = P.precision == FMM_PREC_FP64 ? solute_sparse_t<double>(P, *S, n) : solute_sparse_t<float>(P, *S, n);
+    if (s == FMM_OK) s = P.precision == FMM_PREC_FP64 ? solute_eval_t<double>(P, *S) : solute_eval_t<float>(P, *S);
+    if (s == FMM_OK) s = P.precision == FMM_PREC_FP64 ? solute_act_l2p_t<double>(P, *S) : solute_act_l2p_t<float>(P, *S);
     if (s == FMM_OK) *done = true;
     return s;
 }

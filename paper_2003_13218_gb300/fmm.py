@@ -22,6 +22,7 @@ LIB_PATH = os.path.join(_HERE, "libfmm_gb300.so")
 FMM_OPT_WS, FMM_OPT_PRECISION, FMM_OPT_KAPPA, FMM_OPT_M2L_SPLIT, FMM_OPT_STREAM, FMM_OPT_TIMINGS = 1, 2, 3, 4, 5, 6
 FMM_OPT_M2L_PAIR = 7
 FMM_OPT_BOUNDARY = 8
+FMM_OPT_OVERLAP = 9
 BOUNDARY = {"conducting": 0, "vacuum": 1}
 PRECISION = {"fp64": 0, "mixed": 1}
 SPLIT = {"bf16x3": 0, "bf16x2": 1, "fp32": 2, "bf16a2b3": 3, "fp16x2": 4}
@@ -131,7 +132,7 @@ class FMMPlan:
 
     def __init__(self, box: float, N: int, depth: int, p: int, precision: str = "fp64", kappa: float | None = None,
                  split: str = "fp16x2", timings: bool = False, m2l_pair: bool = True, boundary: str = "conducting",
-                 ws: int = 1):
+                 ws: int = 1, overlap: bool = True):
         self._lib = load_library()
         h = ctypes.c_void_p()
         _check(self._lib.fmm_plan_create(float(box), int(N), int(depth), int(p), ctypes.byref(h)), "fmm_plan_create")
@@ -151,6 +152,8 @@ class FMMPlan:
             self.set_option(FMM_OPT_M2L_PAIR, 0)
         if boundary != "conducting":
             self.set_option(FMM_OPT_BOUNDARY, BOUNDARY[boundary])
+        if not overlap:
+            self.set_option(FMM_OPT_OVERLAP, 0)
         self.precision = precision
 
     def set_option(self, key: int, ival: int = 0, dval: float = 0.0):

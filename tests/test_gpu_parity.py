@@ -291,6 +291,57 @@ def test_100k_workload_sampled_against_oracle():
     assert abs(uv_m["e_uv"] - uv_64["e_uv"]) <= 1e-5 * (abs(uv_64["A"]) + abs(uv_64["C"]))
 
 
+def test_1m_workload_adjoint_against_oracle_and_finite_differences():
+    """Na+ + 333,333 waters (N = 1,000,000, d = 6, p = 12), mixed precision in the configuration
+    the benchmark runs (fp16x2 tensor-core M2L on CTA pairs), forces through the hand-written
+    adjoint behind FmmEnergy.  On 64 random charges: the mixed and FP64 forces against the oracle
+    computed one by one, and central differences (h = 1e-4 A) of the FP64 energy along four random
+    directions that move the 64 charges at once (one unit vector per charge) against the forces
+    projected on them.  Moving all 64 per difference costs 8 energies instead of 384; the
+    third-order remainder (h^2 times a third derivative) is below 1e-8 of the projection."""
+    from paper_2003_13218_gb300.fmm import FmmEnergy
+    b, d, p = boxes.workload("na_1m")
+    leaf = b.L / 2 ** d
+    h = 1e-4
+    rng = np.random.default_rng(11)
+    cand = rng.choice(b.N, 256, replace=False)
+    fr = np.mod(b.pos[cand], b.L) / leaf
+    away = np.min(np.abs(fr - np.round(fr)), axis=1) * leaf > 3 * h  # no leaf face within 3h
+    idx = np.sort(cand[away][:64])
+    assert idx.size == 64
+    ref = oracle.fmm_sampled(b.pos, b.q, b.L, d, p, idx)["forces"]
+    scale = np.sqrt(np.mean(ref ** 2))
+
+    pm = _plan(b.L, b.N, d, p, precision="mixed")
+    x = _t(b.pos).requires_grad_(True)
+    e_m = FmmEnergy.apply(x, _t(b.q), pm)
+    e_m.backward()
+    F_m = -x.grad.cpu().numpy()
+    pm.close()
+    p64 = _plan(b.L, b.N, d, p)
+    F_64, e_64 = p64.forces(_t(b.pos), _t(b.q))
+    F_64 = F_64.cpu().numpy()
+    assert np.max(np.abs(F_64[idx] - ref)) < 1e-10 * scale
+    assert np.sqrt(np.mean((F_m[idx] - ref) ** 2)) < 1e-5 * scale
+    assert abs(e_m.item() - e_64) <= 1e-6 * abs(e_64)
+
+    for k in range(4):
+        u = rng.normal(size=(64, 3))
+        u /= np.linalg.norm(u, axis=1, keepdims=True)
+        U = np.zeros_like(b.pos)
+        U[idx] = u
+        e_p = p64.energy(_t(b.pos + h * U), _t(b.q))[0]
+        e_n = p64.energy(_t(b.pos - h * U), _t(b.q))[0]
+        fd = (e_p - e_n) / (2 * h)
+        proj64 = -np.sum(F_64[idx] * u)
+        proj_m = -np.sum(F_m[idx] * u)
+        mag = np.sum(np.abs(F_64[idx] * u))
+        print("\nFD 1M direction %d: fd %.9f  FP64 adjoint %.9f  mixed adjoint %.9f" % (k, fd, proj64, proj_m))
+        assert abs(fd - proj64) < 1e-6 * mag
+        assert abs(fd - proj_m) < 1e-5 * np.sqrt(np.sum(F_64[idx] ** 2))
+    p64.close()
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_vacuum_boundary_differs_by_the_dipole_surface_term(precision):
     """App. D: FMM's own boundary at infinity is vacuum; the conducting boundary of Eq. Velecfull
