@@ -480,6 +480,121 @@ __global__ void k_l2p(int p, int d, int64_t N, const int *__restrict__ sleaf, co
     }
 }
 
+// The same L2P at a compile-time order PP: the loops unroll, the recurrences' reciprocals fold into
+// constants and the coefficient indices into immediates.  The expansions of the block's leaves
+// (consecutive in the sorted order) are staged in shared memory when at most L2P_LEAVES of them span
+// the block: a warp's particles sit in several leaves, and each of its coefficient loads would touch
+// as many L1 lines.
+constexpr int L2P_LEAVES = 48;
+constexpr int L2P_THREADS = 128;
+
+template <typename T, int PP>
+__global__ void __launch_bounds__(L2P_THREADS) k_l2p_fixed(int d, int64_t N, const int *__restrict__ sleaf,
+                                                           const Particle<T> *__restrict__ sp, T inv_h,
+                                                           const T *__restrict__ L, T *__restrict__ phi,
+                                                           T *__restrict__ grad)
+{
+    constexpr int NC = (PP + 1) * (PP + 1);
+    extern __shared__ __align__(16) unsigned char l2p_smem[];
+    T *sL = reinterpret_cast<T *>(l2p_smem);
+    const int64_t s0 = (int64_t)blockIdx.x * L2P_THREADS;
+    const int64_t slast = (s0 + L2P_THREADS < N ? s0 + L2P_THREADS : N) - 1;
+    const int nside = 1 << d, mask = nside - 1;
+    const int leaf0 = sleaf[s0];
+    const int nl = sleaf[slast] - leaf0 + 1;
+    const bool staged = nl <= L2P_LEAVES;
+    if (staged) {
+        for (int e = threadIdx.x; e < nl * NC; e += L2P_THREADS) {
+            const int li = e / NC, c = e - li * NC;
+            const int leaf = leaf0 + li;
+            sL[e] = L[cell_index(d, leaf & mask, (leaf >> d) & mask, leaf >> (2 * d)) * NC + c];
+        }
+    }
+    __syncthreads();
+    const int64_t s = s0 + threadIdx.x;
+    if (s >= N) return;
+    const int leaf = sleaf[s];
+    const T *Lc = staged ? sL + (leaf - leaf0) * NC : L + cell_index(d, leaf & mask, (leaf >> d) & mask, leaf >> (2 * d)) * NC;
+    const Particle<T> pt = sp[s];
+    const T vx = pt.x * inv_h, vy = pt.y * inv_h, vz = pt.z * inv_h;
+    const T r2 = vx * vx + vy * vy + vz * vz;
+    T pot = 0, gx = 0, gy = 0, gz = 0;
+    T dre = 1, dim = 0;
+#pragma unroll
+    for (int m = 0; m <= PP; ++m) {
+        if (m > 0) {
+            const T sc = T(-0.5) / T(m);
+            const T nre = sc * (vx * dre - vy * dim);
+            const T nim = sc * (vx * dim + vy * dre);
+            dre = nre;
+            dim = nim;
+        }
+        const T w = m == 0 ? T(1) : T(2);
+        T p2re = 0, p2im = 0, rre = dre, rim = dim;
+#pragma unroll
+        for (int n = m; n <= PP; ++n) {
+            if (n > m) {
+                const T a = T(2 * n - 1) * vz;
+                const T inv = T(1) / T((n + m) * (n - m));
+                const T cr = (a * rre - r2 * p2re) * inv;
+                const T ci = (a * rim - r2 * p2im) * inv;
+                p2re = rre;
+                p2im = rim;
+                rre = cr;
+                rim = ci;
+            }
+            const Cx<T> Lnm = coef(Lc, n, m);
+            pot += w * (Lnm.re * rre - Lnm.im * rim);
+            if (grad && n < PP) {
+                const Cx<T> a = coef(Lc, n + 1, m - 1), b = coef(Lc, n + 1, m + 1), c = coef(Lc, n + 1, m);
+                const Cx<T> Gx = {T(0.5) * (a.re - b.re), T(0.5) * (a.im - b.im)};
+                const Cx<T> Gy = {T(0.5) * (a.im + b.im), -T(0.5) * (a.re + b.re)};
+                gx += w * (Gx.re * rre - Gx.im * rim);
+                gy += w * (Gy.re * rre - Gy.im * rim);
+                gz += w * (c.re * rre - c.im * rim);
+            }
+        }
+    }
+    phi[s] = pot * inv_h;
+    if (grad) {
+        const T s2 = inv_h * inv_h;
+        grad[3 * s] = gx * s2;
+        grad[3 * s + 1] = gy * s2;
+        grad[3 * s + 2] = gz * s2;
+    }
+}
+
+template <typename T, int PP>
+fmm_status launch_l2p_fixed(Plan &P, T inv_h, const T *L, T *phi, T *grad)
+{
+    const size_t sh = sizeof(T) * L2P_LEAVES * (PP + 1) * (PP + 1);
+    static bool attr = false;
+    if (!attr) {
+        FMM_CUDA_TRY(cudaFuncSetAttribute(k_l2p_fixed<T, PP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+        attr = true;
+    }
+    k_l2p_fixed<T, PP><<<blocks_for(P.N, L2P_THREADS), L2P_THREADS, sh, P.stream>>>(
+        P.d, P.N, P.sleaf, (const Particle<T> *)(P.sorted), inv_h, L, phi, grad);
+    return FMM_OK;
+}
+
+// L2P of the plan at its order: the fixed-order kernel for the usual orders, else the generic one
+template <typename T>
+fmm_status l2p_t(Plan &P, T inv_h, const T *L, T *phi, T *grad)
+{
+    switch (P.p) {
+    case 4: return launch_l2p_fixed<T, 4>(P, inv_h, L, phi, grad);
+    case 6: return launch_l2p_fixed<T, 6>(P, inv_h, L, phi, grad);
+    case 8: return launch_l2p_fixed<T, 8>(P, inv_h, L, phi, grad);
+    case 10: return launch_l2p_fixed<T, 10>(P, inv_h, L, phi, grad);
+    case 12: return launch_l2p_fixed<T, 12>(P, inv_h, L, phi, grad);
+    default:
+        k_l2p<T><<<blocks_for(P.N, 128), 128, 0, P.stream>>>(P.p, P.d, P.N, P.sleaf, (const Particle<T> *)P.sorted,
+                                                             inv_h, L, phi, grad);
+        return FMM_OK;
+    }
+}
+
 template <typename T>
 fmm_status upward_t(Plan &P, bool solute_only)
 {
@@ -618,14 +733,14 @@ fmm_status launch_l2p(Plan &P, bool gradient, bool solute_only)
 {
     int nside = 1 << P.d;
     double inv_h = (double)nside / P.box;
+    fmm_status st;
     if (P.precision == FMM_PREC_FP64)
-        k_l2p<double><<<blocks_for(P.N, 128), 128, 0, P.stream>>>(
-            P.p, P.d, P.N, P.sleaf, (const Particle<double> *)P.sorted, inv_h, (const double *)P.L[P.d],
-            (double *)(solute_only ? P.phi_u : P.phi_ff), gradient ? (double *)P.g_ff : nullptr);
+        st = l2p_t<double>(P, inv_h, (const double *)P.L[P.d], (double *)(solute_only ? P.phi_u : P.phi_ff),
+                           gradient ? (double *)P.g_ff : nullptr);
     else
-        k_l2p<float><<<blocks_for(P.N, 128), 128, 0, P.stream>>>(
-            P.p, P.d, P.N, P.sleaf, (const Particle<float> *)P.sorted, (float)inv_h, (const float *)P.L[P.d],
-            (float *)(solute_only ? P.phi_u : P.phi_ff), gradient ? (float *)P.g_ff : nullptr);
+        st = l2p_t<float>(P, (float)inv_h, (const float *)P.L[P.d], (float *)(solute_only ? P.phi_u : P.phi_ff),
+                          gradient ? (float *)P.g_ff : nullptr);
+    if (st != FMM_OK) return st;
     FMM_LAUNCH_CHECK(P);
     return FMM_OK;
 }
