@@ -149,6 +149,10 @@ def test_invalid_arguments_are_rejected():
     with pytest.raises(FMMError) as e:
         plan.set_option(1, 2)  # ws = 2 needs more than 5 leaves per side
     assert e.value.code == 1
+    for key in (7, 9):  # M2L_PAIR, OVERLAP: 0 or 1
+        with pytest.raises(FMMError) as e:
+            plan.set_option(key, 2)
+        assert e.value.code == 1
     plan.close()
 
 
