@@ -170,6 +170,19 @@ fmm_status fmm_energy(fmm_plan plan, const double *pos, const double *q, double 
 fmm_status fmm_forces(fmm_plan plan, const double *pos, const double *q, double *forces, double *energy);
 
 /*
+ * Potentials phi_i = dV_elec/dq_i (V_elec of Eq. Velecfull is a quadratic form
+ * in the charges, so sum_i q_i phi_i = 2 V_elec): the near-field pair potential
+ * of Eq. EqNF plus the far-field potential of Eq. EqFF (L2P; it includes the
+ * charge's own periodic images), plus the derivatives of the background terms,
+ * -pi Q_C/(V kappa^2) + (2 pi/3V)(S_2 + Q_C |r_i|^2) - (4 pi/3V) mu.r_i (the
+ * last one under the conducting boundary only), r_i the wrapped position.
+ * potentials: [N] out, same memory kind as pos.  forces: [N][3] out, nullable
+ * (the same evaluation).  energy: host out, nullable (non-null synchronises).
+ */
+fmm_status fmm_potentials(fmm_plan plan, const double *pos, const double *q, double *potentials, double *forces,
+                          double *energy);
+
+/*
  * Solute-solvent interaction energy with the reduced far field (Eq. FMMcalc):
  * one full pass gives A; one pass over the solute charges alone gives B and C.
  * is_solute: uint8 [N] (nonzero = solute).  e_uv: host out (required);

@@ -18,7 +18,7 @@ size_t reduction_scratch_bytes() { return sizeof(double) * 304 * 16 * 2; }
 
 void free_buffers(Plan &P)
 {
-    void *bufs[] = {P.in_pos, P.in_q,   P.out_forces, P.in_sol,   P.wpos,       P.key,    P.perm,   P.sleaf,
+    void *bufs[] = {P.in_pos, P.in_q,   P.out_forces, P.out_phi, P.in_sol, P.wpos,    P.key,    P.perm,   P.sleaf,
                     P.cell_start, P.cell_fill, P.scan_tmp, P.sorted, P.sorted_u, P.sorted_sol, P.phi_nf, P.phi_ff,
                     P.phi_u, P.f_nf, P.g_ff, P.red_partial, P.red_out, P.d_err};
     for (void *b : bufs) cudaFree(b);
@@ -28,7 +28,7 @@ void free_buffers(Plan &P)
         P.M[l] = P.L[l] = nullptr;
     }
     if (P.h_out) cudaFreeHost(P.h_out);
-    P.in_pos = P.in_q = P.out_forces = nullptr;
+    P.in_pos = P.in_q = P.out_forces = P.out_phi = nullptr;
     P.in_sol = nullptr;
     P.wpos = nullptr;
     P.key = P.perm = P.sleaf = P.cell_start = P.cell_fill = P.scan_tmp = nullptr;
@@ -96,6 +96,7 @@ fmm_status ensure_staging(Plan &P)
     if (!P.in_q) FMM_CUDA_TRY(dalloc(&P.in_q, sizeof(double) * P.N));
     if (!P.in_sol) FMM_CUDA_TRY(dalloc(&P.in_sol, P.N));
     if (!P.out_forces) FMM_CUDA_TRY(dalloc(&P.out_forces, sizeof(double) * 3 * P.N));
+    if (!P.out_phi) FMM_CUDA_TRY(dalloc(&P.out_phi, sizeof(double) * P.N));
     return FMM_OK;
 }
 
@@ -189,7 +190,8 @@ fmm_status eval_front(Plan &P, const double *dpos, const double *dq, const uint8
 // back of one evaluation: solute pass (its count is read from the host copy,
 // or P.known_count), reductions, forces, and the asynchronous copy of the
 // totals and the error flags into P.h_out
-fmm_status eval_back(Plan &P, const double *dq, bool want_uv, double *dforces, StageTimer *tm)
+fmm_status eval_back(Plan &P, const double *dq, bool want_uv, double *dforces, StageTimer *tm,
+                     double *dphi = nullptr)
 {
     TRY(join_near_field(P));
     if (want_uv) {
@@ -201,6 +203,7 @@ fmm_status eval_back(Plan &P, const double *dq, bool want_uv, double *dforces, S
     if (tm) tm->mark();
     TRY(launch_energy_reduce(P, want_uv));
     if (dforces) TRY(launch_forces_out(P, dq, dforces));
+    if (dphi) TRY(launch_potentials_out(P, dphi));
     if (tm) tm->mark();
     FMM_CUDA_TRY(cudaMemcpyAsync(P.h_out, P.red_out, sizeof(double) * 29, cudaMemcpyDeviceToHost, P.stream));
     FMM_CUDA_TRY(cudaMemcpyAsync(P.h_out + 32, P.d_err, sizeof(int), cudaMemcpyDeviceToHost, P.stream));
@@ -268,14 +271,15 @@ struct ExecScope {
 };
 
 fmm_status evaluate(Plan &P, const double *pos, const double *q, const uint8_t *sol, double *forces,
-                    fmm_energy_terms *terms, fmm_uv_terms *uv)
+                    fmm_energy_terms *terms, fmm_uv_terms *uv, double *potentials = nullptr)
 {
     if (!pos || !q) return FMM_ERR_INVALID_ARG;
     bool want_uv = sol && uv;
     int kp = pointer_kind(pos), kq = pointer_kind(q);
     int ks = want_uv ? pointer_kind(sol) : -1;
     int kf = pointer_kind(forces);
-    bool host_any = kp == 1 || kq == 1 || ks == 1 || kf == 1;
+    int kphi = pointer_kind(potentials);
+    bool host_any = kp == 1 || kq == 1 || ks == 1 || kf == 1 || kphi == 1;
     if (host_any) TRY(ensure_staging(P));
     ExecScope xs(P);
     TRY(xs.status);
@@ -297,13 +301,16 @@ fmm_status evaluate(Plan &P, const double *pos, const double *q, const uint8_t *
         dsol = P.in_sol;
     }
     if (kf == 1) dforces = P.out_forces;
+    double *dphi = kphi == 1 ? P.out_phi : potentials;
 
     StageTimer tm(P);
     TRY(eval_front(P, dpos, dq, dsol, want_uv, forces != nullptr, &tm));
-    TRY(eval_back(P, dq, want_uv, dforces, &tm));
+    TRY(eval_back(P, dq, want_uv, dforces, &tm, dphi));
     if (kf == 1)
         FMM_CUDA_TRY(cudaMemcpyAsync(forces, P.out_forces, sizeof(double) * 3 * P.N, cudaMemcpyDeviceToHost, P.stream));
-    bool sync = terms || uv || kf == 1;
+    if (kphi == 1)
+        FMM_CUDA_TRY(cudaMemcpyAsync(potentials, P.out_phi, sizeof(double) * P.N, cudaMemcpyDeviceToHost, P.stream));
+    bool sync = terms || uv || kf == 1 || kphi == 1;
     if (!sync) return FMM_OK;
     FMM_CUDA_TRY(cudaStreamSynchronize(P.stream));
     if (P.timings_on && tm.k >= 9) {
@@ -483,6 +490,17 @@ fmm_status fmm_forces(fmm_plan plan, const double *pos, const double *q, double 
     if (!plan || !forces) return FMM_ERR_INVALID_ARG;
     fmm_energy_terms t;
     fmm_status s = evaluate(plan->P, pos, q, nullptr, forces, energy ? &t : nullptr, nullptr);
+    if (s != FMM_OK) return s;
+    if (energy) *energy = t.total;
+    return FMM_OK;
+}
+
+fmm_status fmm_potentials(fmm_plan plan, const double *pos, const double *q, double *potentials, double *forces,
+                          double *energy)
+{
+    if (!plan || !potentials) return FMM_ERR_INVALID_ARG;
+    fmm_energy_terms t;
+    fmm_status s = evaluate(plan->P, pos, q, nullptr, forces, energy ? &t : nullptr, nullptr, potentials);
     if (s != FMM_OK) return s;
     if (energy) *energy = t.total;
     return FMM_OK;

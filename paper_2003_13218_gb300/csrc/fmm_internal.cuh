@@ -113,6 +113,7 @@ struct Plan {
 
     // particles
     double *in_pos = nullptr, *in_q = nullptr, *out_forces = nullptr;  // staging for host pointers
+    double *out_phi = nullptr;
     uint8_t *in_sol = nullptr;
     double *wpos = nullptr;        // [N][3] wrapped input positions (original order)
     int *key = nullptr;            // [N] leaf of each particle
@@ -236,6 +237,7 @@ fmm_status launch_assign_sort(Plan &P, const double *pos, const double *q, const
 fmm_status launch_bc_moments(Plan &P, const double *q, const uint8_t *sol);
 fmm_status launch_energy_reduce(Plan &P, bool with_uv);
 fmm_status launch_forces_out(Plan &P, const double *q, double *forces);
+fmm_status launch_potentials_out(Plan &P, double *potentials);
 
 // expansions (fmm_expand.cu)
 fmm_status build_tables(Plan &P);

@@ -369,6 +369,31 @@ __global__ void k_forces_out(int64_t N, const int *__restrict__ perm, const Part
     }
 }
 
+// phi_i = dV/dq_i in input order: pair potentials (near + far) plus the
+// derivatives of the background terms of Eq. Velecfull,
+//   d/dq_i [-pi Q^2/(2 V kappa^2)]      = -pi Q/(V kappa^2),
+//   d/dq_i [(2 pi/3V) Q S2]             = (2 pi/3V)(S2 + Q r_i^2),
+//   d/dq_i [-(2 pi/3V) mu.mu]           = -(4 pi/3V) mu.r_i   (conducting boundary)
+template <typename T>
+__global__ void k_potentials_out(int64_t N, const int *__restrict__ perm, const T *__restrict__ phi_nf,
+                                 const T *__restrict__ phi_ff, const double *__restrict__ wpos,
+                                 const double *__restrict__ mom, double box, double kappa, int vacuum,
+                                 double *__restrict__ out)
+{
+    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= N) return;
+    const double PI = 3.14159265358979323846;
+    const double V = box * box * box;
+    const int i = perm[s];
+    const double Q = mom[0], S2 = mom[4];
+    const double x = wpos[3 * (int64_t)i], y = wpos[3 * (int64_t)i + 1], z = wpos[3 * (int64_t)i + 2];
+    double v = (double)phi_nf[s] + (double)phi_ff[s];
+    v += -PI * Q / (V * kappa * kappa);
+    v += 2.0 * PI / (3.0 * V) * (S2 + Q * (x * x + y * y + z * z));
+    if (!vacuum) v -= 4.0 * PI / (3.0 * V) * (mom[1] * x + mom[2] * y + mom[3] * z);
+    out[i] = v;
+}
+
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
@@ -449,6 +474,21 @@ fmm_status launch_forces_out(Plan &P, const double *q, double *forces)
         k_forces_out<float><<<blocks_for(P.N, 256), 256, 0, P.stream>>>(
             P.N, P.perm, (const Particle<float> *)P.sorted, (const float *)P.f_nf, (const float *)P.g_ff, P.wpos, q,
             P.red_out, P.box, P.boundary, forces);
+    FMM_LAUNCH_CHECK(P);
+    return FMM_OK;
+}
+
+fmm_status launch_potentials_out(Plan &P, double *potentials)
+{
+    const double kappa = P.kappa > 0 ? P.kappa : 2.0 / P.box;
+    if (P.precision == FMM_PREC_FP64)
+        k_potentials_out<double><<<blocks_for(P.N, 256), 256, 0, P.stream>>>(
+            P.N, P.perm, (const double *)P.phi_nf, (const double *)P.phi_ff, P.wpos, P.red_out, P.box, kappa,
+            P.boundary, potentials);
+    else
+        k_potentials_out<float><<<blocks_for(P.N, 256), 256, 0, P.stream>>>(
+            P.N, P.perm, (const float *)P.phi_nf, (const float *)P.phi_ff, P.wpos, P.red_out, P.box, kappa,
+            P.boundary, potentials);
     FMM_LAUNCH_CHECK(P);
     return FMM_OK;
 }

@@ -80,6 +80,8 @@ def load_library(path: str = LIB_PATH):
     L.fmm_energy.restype = c_int
     L.fmm_forces.argtypes = [vp, vp, vp, vp, ctypes.POINTER(dbl)]
     L.fmm_forces.restype = c_int
+    L.fmm_potentials.argtypes = [vp, vp, vp, vp, vp, ctypes.POINTER(dbl)]
+    L.fmm_potentials.restype = c_int
     L.fmm_solute_solvent_energy.argtypes = [vp, vp, vp, vp, ctypes.POINTER(dbl), ctypes.POINTER(UVTerms)]
     L.fmm_solute_solvent_energy.restype = c_int
     L.fmm_evaluate.argtypes = [vp, vp, vp, vp, vp, ctypes.POINTER(EnergyTerms), ctypes.POINTER(UVTerms)]
@@ -200,6 +202,23 @@ class FMMPlan:
         _check(self._lib.fmm_forces(self._h, pp, pq, pf, ctypes.byref(e) if with_energy else None), "fmm_forces")
         return out, (e.value if with_energy else None)
 
+    def potentials(self, pos, q, out=None, forces=None, with_energy=True):
+        """fmm_potentials: phi_i = dE/dq_i (and, if `forces` is given, the forces of the same evaluation)."""
+        if out is None:
+            if isinstance(pos, torch.Tensor):
+                out = torch.empty((self.N,), dtype=torch.float64, device=pos.device)
+            else:
+                out = np.empty((self.N,), dtype=np.float64)
+        self._bind_stream(pos, q, out, forces)
+        pp, kp = _ptr(pos)
+        pq, kq = _ptr(q)
+        po, ko = _ptr(out)
+        pf, kf = _ptr(forces)
+        e = ctypes.c_double()
+        _check(self._lib.fmm_potentials(self._h, pp, pq, po, pf, ctypes.byref(e) if with_energy else None),
+               "fmm_potentials")
+        return out, (e.value if with_energy else None)
+
     def solute_solvent_energy(self, pos, q, is_solute):
         self._bind_stream(pos, q, is_solute)
         pp, kp = _ptr(pos)
@@ -294,15 +313,21 @@ class FMMBatch:
 
 
 class FmmEnergy(torch.autograd.Function):
-    """E = V_elec(pos, q) with the hand-written adjoint: dE/dpos = -F (fmm_forces)."""
+    """E = V_elec(pos, q) with the hand-written adjoint: dE/dpos = -F (fmm_forces) and, when q needs a
+    gradient, dE/dq = phi (fmm_potentials, from the same evaluation)."""
 
     @staticmethod
     def forward(ctx, pos, q, plan: FMMPlan):
-        F, e = plan.forces(pos.detach(), q.detach())
-        ctx.save_for_backward(F)
+        if ctx.needs_input_grad[1]:
+            F = torch.empty((plan.N, 3), dtype=torch.float64, device=pos.device)
+            phi, e = plan.potentials(pos.detach(), q.detach(), forces=F)
+        else:
+            F, e = plan.forces(pos.detach(), q.detach())
+            phi = None
+        ctx.save_for_backward(F, phi)
         return torch.tensor(e, dtype=torch.float64, device=pos.device)
 
     @staticmethod
     def backward(ctx, grad_e):
-        (F,) = ctx.saved_tensors
-        return -F * grad_e, None, None
+        F, phi = ctx.saved_tensors
+        return -F * grad_e, (phi * grad_e if phi is not None else None), None
