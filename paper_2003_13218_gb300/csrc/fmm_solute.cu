@@ -6,9 +6,11 @@
 // ancestors carry solute moments.  The pass therefore
 //  * builds the list of active cells per level (at most NU_MAX per level),
 //    P2M at the active leaves and M2M along the active ancestors;
-//  * runs the ordinary dense M2L + L2L on the coarse levels 1..LD (few cells)
-//    after the level-0 lattice operator, giving the full local expansion at
-//    level LD;
+//  * on the coarse levels 1..LD (few cells) computes the local expansion of
+//    every cell in the pass's own arrays: the level-0 lattice operator, then
+//    per level the M2L terms of the active cells (one block per active cell and
+//    offset, every periodic image counted) summed per target with the L2L of
+//    its parent, giving the full local expansion at level LD;
 //  * on the finer levels evaluates M2L only onto the targets whose interaction
 //    list contains an active source (at most n_il(ws) per source), kept as a
 //    sorted list per level;
