@@ -425,6 +425,33 @@ def test_fmm_forces_match_finite_differences():
             assert abs(-(ep - em) / (2 * h) - F[i, a]) < 1e-6 * (1 + abs(F[i, a]))
 
 
+def test_fmm_potentials_are_the_charge_gradient():
+    """Eq. Velecfull is a quadratic form in the charges, so dE/dq_i is the charge's pair potential
+    (near + far, own images included) plus the derivatives of the background terms,
+    -pi Q/(V kappa^2) + (2 pi/3V)(S2 + Q r_i^2) - (4 pi/3V) mu.r_i; central differences in q_i are
+    exact up to rounding, and sum_i q_i phi_i = 2E (Euler).  This pins the oracle's per-charge
+    potentials against its own energy, including the symmetry of the FMM bilinear form."""
+    pos, q = boxes.random_charges(40, 2.0, seed=13)
+    q[0] = 1.3  # net charge: every background term contributes
+    L, d, p = 2.0, 2, 8
+    out = oracle.fmm(pos, q, L, d, p, forces=False)
+    kappa = oracle.default_kappa(L)
+    V = L ** 3
+    r = np.mod(pos, L)
+    Q, mu, S2 = q.sum(), (q[:, None] * r).sum(0), float((q * (r * r).sum(1)).sum())
+    phi = (out["phi_nf"] + out["phi_ff"] - PI * Q / (V * kappa ** 2)
+           + 2 * PI / (3 * V) * (S2 + Q * (r * r).sum(1)) - 4 * PI / (3 * V) * (r @ mu))
+    assert abs(float(q @ phi) - 2 * out["total"]) <= 1e-12 * float(np.abs(q * phi).sum())
+    h = 1e-3
+    for i in (0, 1, 7, 39):
+        qp, qm = q.copy(), q.copy()
+        qp[i] += h
+        qm[i] -= h
+        fd = (oracle.fmm(pos, qp, L, d, p, forces=False)["total"] -
+              oracle.fmm(pos, qm, L, d, p, forces=False)["total"]) / (2 * h)
+        assert abs(fd - phi[i]) < 1e-9 * (1 + abs(phi[i]))
+
+
 def test_fmm_forces_approach_ewald_forces():
     pos, q = boxes.random_charges(30, 2.0, seed=12)
     Fe = oracle.ewald(pos, q, 2.0, forces=True)["forces"]
