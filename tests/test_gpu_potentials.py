@@ -7,9 +7,12 @@ So, in the FP64 path,
   * sum_i q_i phi_i = 2 V (Euler's theorem for a function homogeneous of degree 2),
 and the autograd wrapper's charge gradient is phi.  Host and device pointers,
 both boundaries of App. D, and the mixed path against FP64."""
+import math
+
 import numpy as np
 import pytest
 
+import oracle
 from paper_2003_13218_gb300 import boxes
 
 torch = pytest.importorskip("torch")
@@ -82,3 +85,26 @@ def test_mixed_potentials_against_fp64():
     assert np.sqrt(np.mean((phi_m - ref) ** 2)) < 1e-5 * np.sqrt(np.mean(ref ** 2))
     # the mixed energy sums q_i phi_i with the charges rounded to FP32
     assert abs(float(np.dot(b.q, phi_m)) - 2.0 * em) <= 1e-6 * float(np.sum(np.abs(b.q * phi_m)))
+
+
+def test_potentials_against_oracle():
+    """phi against the oracle's per-charge potentials (near + far) plus the background terms'
+    derivatives (the oracle pins this sum against central differences of its energy)."""
+    pos, q = boxes.random_charges(700, 5.0, seed=2)
+    q[0] += 0.75  # net charge
+    L, d, p = 5.0, 3, 8
+    ref = oracle.fmm(pos, q, L, d, p, forces=False)
+    kappa = oracle.default_kappa(L)
+    V = L ** 3
+    r = np.mod(pos, L)
+    Q, mu, S2 = q.sum(), (q[:, None] * r).sum(0), float((q * (r * r).sum(1)).sum())
+    phi_ref = (ref["phi_nf"] + ref["phi_ff"] - math.pi * Q / (V * kappa ** 2)
+               + 2 * math.pi / (3 * V) * (S2 + Q * (r * r).sum(1)) - 4 * math.pi / (3 * V) * (r @ mu))
+    scale = np.sqrt(np.mean(phi_ref ** 2))
+    for prec, tol in (("fp64", 1e-11), ("mixed", 1e-5)):
+        from paper_2003_13218_gb300.fmm import FMMPlan
+        plan = FMMPlan(L, len(q), d, p, precision=prec)
+        phi, _ = plan.potentials(_t(pos), _t(q))
+        plan.close()
+        err = np.sqrt(np.mean((phi.cpu().numpy() - phi_ref) ** 2)) / scale
+        assert err < tol, (prec, err)
