@@ -41,13 +41,14 @@ FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 # FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.070 GHz
 FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # DRAM bytes (read + write) of one level-6 tensor-core M2L launch (fp16x2
-# split, fused L2L, CTA pairs) of the na_1m workload, from the ncu capture summarised in
-# profiles/k_m2l_tc_na_1m_level6.md, with the sha256 of the kernel's device
+# split, fused L2L, CTA pairs) of the na_1m workload, from the ncu capture of
+# that launch summarised under profiles/, with the sha256 of the kernel's device
 # code it was taken on: the value is reported only while that code is unchanged.
 M2L_TRAFFIC = {"src": "paper_2003_13218_gb300/csrc/fmm_m2l_tc.cu",
                "sha256": "c0b12966792e4de8869b0c85e1dc1aaf0888b14f4595b57e3cd8906f8ddd4554",
                "workload": "na_1m", "level": 6, "split": "fp16x2", "ws": 1, "p": 12,
                "bytes_per_launch": 753.414656e6 + 177.790720e6}
+ION_LABEL = {"Na": "Na+", "Cl": "Cl-", "Mg": "Mg2+"}
 KERNEL_BEGIN = "// ------------------------------------------------------------------ the kernel"
 KERNEL_END = "// ------------------------------------------------------------------ operand preparation"
 
@@ -348,8 +349,8 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": ("f32+%s-tensor+f64" % args.split) if uses_tc else "f32+f64",
         "data": "synthetic (seeded ion-in-water boxes standing in for the paper's MD snapshots)",
-        "config": {"workload": "%s: %s+ + %d TIP3P waters, N=%d, L=%.2f A, depth %d, p %d, ws %d, mixed precision, "
-                               "energy+forces+solute-solvent per step" % (args.workload, box.ion, box.n_waters, N,
+        "config": {"workload": "%s: %s + %d TIP3P waters, N=%d, L=%.2f A, depth %d, p %d, ws %d, mixed precision, "
+                               "energy+forces+solute-solvent per step" % (args.workload, ION_LABEL[box.ion], box.n_waters, N,
                                                                           box.L, d, p, args.ws),
                    "l2": "flushed between timed steps (256 MB write)", "jitter_A": args.jitter, "parallelism": "replicas" if ws > 1 else "1 GPU",
                    "m2l_split": args.split, "overlap": bool(args.overlap)},

@@ -59,7 +59,7 @@ typedef enum {
     FMM_ERR_OOM = 4,         /* device or host allocation failed */
     FMM_ERR_TIMEOUT = 5,     /* a bounded device wait ran out */
     FMM_ERR_INTERNAL = 6,    /* a device-side consistency check failed */
-    FMM_ERR_UNSUPPORTED = 7  /* option value not built (e.g. ws != 1) */
+    FMM_ERR_UNSUPPORTED = 7  /* option value not built (e.g. ws > 2) */
 } fmm_status;
 
 /* Energy decomposition of Eq. Velecfull, e^2/A. */
@@ -270,27 +270,31 @@ void fmm_batch_destroy(fmm_batch batch);
 /*
  * Background-charge terms without a plan and without allocating anything.
  * The paper has no counterpart to this entry point; it exists for callers
- * that cannot call cudaMalloc -- work recorded into a CUDA graph while a
- * stream is being captured, code whose device memory all belongs to another
- * allocator or budget, and loops that cannot pay for the synchronisation an
- * allocation may cause.
+ * that cannot call cudaMalloc: a host application or plug-in whose device
+ * memory all belongs to another allocator or a fixed budget, and loops that
+ * cannot pay for the synchronisation an allocation may cause.
  *
  * pos: device double[N][3]; q: device double[N]; box: cell side (A);
- * kappa: splitting parameter of Eq. 6 in 1/A (<= 0 selects 2 / box, the plan
- * default).  out: device double[8], written with
+ * kappa: the splitting parameter in 1/A that the plan would use (<= 0 selects
+ * 2 / box, the plan default).  out: device double[8], written with
  *   {Q, mu_x, mu_y, mu_z, S2 = sum q r^2, charged, quad_surface, dipole_surface}
- * where the last three equal the fmm_energy_terms fields of the same names.
- * Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default stream);
- * nothing is synchronised.
+ * where the last three equal the fmm_energy_terms fields of the same names for
+ * a plan with the conducting boundary (FMM_BOUNDARY_CONDUCTING, the default);
+ * a caller using the vacuum boundary drops out[7].  Coordinates are wrapped
+ * into [0, box) as the plans do.  Work is enqueued on `stream` (a
+ * cudaStream_t; NULL = legacy default stream); nothing is synchronised, so no
+ * device-side status comes back: a NaN or Inf charge or coordinate makes the
+ * affected outputs non-finite instead of returning FMM_ERR_NONFINITE.
  *
  * The only scratch is a file-scope device array of 80 KiB that every GPU
  * loading the library keeps until the process exits; it bounds N to
  * 4,194,304 charges (larger N: FMM_ERR_INVALID_ARG, nothing launched).  The
  * first call on each device looks up that array's device address, so make the
  * first call on a device before capturing any stream on it.  All calls share
- * the array: calls that overlap on the GPU race.  Other errors:
- * FMM_ERR_INVALID_ARG for null pointers, N < 1 or a non-finite or non-positive
- * box; FMM_ERR_CUDA if the lookup or a launch fails.
+ * the array: calls that overlap on the GPU (other streams, other host threads)
+ * race, so serialise them.  Other errors: FMM_ERR_INVALID_ARG for null
+ * pointers, N < 1 or a non-finite or non-positive box; FMM_ERR_CUDA if the
+ * lookup or a launch fails.
  */
 fmm_status fmm_background_terms_noalloc(const double *pos, const double *q, int64_t N, double box, double kappa,
                                         double *out, void *stream);

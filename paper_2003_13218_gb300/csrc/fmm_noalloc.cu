@@ -4,11 +4,13 @@
 // energy (charged-system, quadrupole-surface and dipole-surface terms) and the
 // moments they are built from, exactly as fmm_energy reports them, but without
 // a plan and without any device allocation.  It is meant for callers that
-// cannot call cudaMalloc: code running while a stream is being captured into a
-// CUDA graph (cudaMalloc is not a capturable operation), code whose device
-// memory is entirely owned by another allocator or memory budget, and
-// latency-sensitive loops that cannot afford the device-wide synchronisation
-// cudaMalloc/cudaFree may imply.
+// cannot call cudaMalloc: a host application or plug-in whose device memory is
+// entirely owned by another allocator or a fixed memory budget (a second
+// allocator would fragment or exceed it), and latency-sensitive loops that
+// cannot afford the device-wide synchronisation cudaMalloc/cudaFree may imply.
+// Non-finite charges or coordinates are not filtered: they make the affected
+// outputs non-finite, which is how the caller sees them (nothing here returns
+// a device-side status).
 //
 // Its only scratch -- one row of compensated partial sums per block of 4096
 // charges -- lives in the file-scope device array below (80 KiB, held by every
@@ -57,12 +59,10 @@ __global__ void k_na_partial(int64_t N, const double *__restrict__ pos, const do
     const int64_t begin = (int64_t)blockIdx.x * NA_CHUNK;
     const int64_t end = begin + NA_CHUNK < N ? begin + NA_CHUNK : N;
     for (int64_t i = begin + threadIdx.x; i < end; i += NA_THREADS) {
-        double qi = q[i];
-        if (!isfinite(qi)) qi = 0.0;
+        const double qi = q[i];  // NaN / Inf flow into the sums
         double w[3];
         for (int a = 0; a < 3; ++a) {
-            double x = pos[3 * i + a];
-            if (!isfinite(x)) x = 0.0;
+            const double x = pos[3 * i + a];  // NaN or Inf: floor and the subtraction yield NaN
             double f = floor(__ddiv_rn(x, box));
             double v = __dsub_rn(x, __dmul_rn(box, f));
             if (v >= box) v = __dsub_rn(v, box);

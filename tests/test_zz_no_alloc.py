@@ -1,10 +1,12 @@
 """The allocation-free entry point fmm_background_terms_noalloc, through the C ABI.
 
-It serves callers that cannot allocate device memory (for example while a
-stream is being captured into a CUDA graph, or when another allocator owns all
-device memory).  Its output must equal the background-charge terms that
-fmm_energy reports for the same input, call after call, although every call
-reuses the same static scratch array.
+It serves callers that cannot allocate device memory: an application or
+plug-in whose device memory all belongs to another allocator or a fixed
+budget, or a loop that cannot pay for an allocation's synchronisation.  Its
+output must equal the background-charge terms that fmm_energy reports for the
+same input, call after call, although every call reuses the same static
+scratch array.  It returns no device-side status, so a NaN input must show up
+as non-finite outputs rather than be dropped.
 """
 import ctypes
 
@@ -82,3 +84,25 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(lib):
     assert rc == 1
     torch.cuda.synchronize()
     assert float(out.abs().sum()) == 0.0  # nothing was launched
+
+
+def test_noalloc_nonfinite_input_reaches_the_outputs(lib):
+    """A NaN charge (or an infinite coordinate) is not filtered out: the sums that contain it
+    come out non-finite, and the next call with clean inputs is exact again."""
+    b = boxes.ion_in_water(700, "Mg", seed=4, L=30.0)
+    q = b.q.copy()
+    q[17] = float("nan")
+    rc, out = _noalloc(lib, b.pos, q, b.L)
+    assert rc == 0
+    assert not np.isfinite(out[0]) and not np.isfinite(out[5]) and not np.isfinite(out[6])
+    pos = b.pos.copy()
+    pos[3, 1] = float("inf")
+    rc, out = _noalloc(lib, pos, b.q, b.L)
+    assert rc == 0
+    assert np.isfinite(out[0])  # Q does not involve coordinates
+    assert not np.isfinite(out[2]) and not np.isfinite(out[7])
+    rc, out = _noalloc(lib, b.pos, b.q, b.L)
+    assert rc == 0
+    ref = _reference_terms(b.pos, b.q, b.L)
+    assert _close(out[5], ref["charged"]) and _close(out[6], ref["quad_surface"])
+    assert _close(out[7], ref["dipole_surface"])
