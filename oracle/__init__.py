@@ -45,6 +45,9 @@ def lib():
         L.oracle_fmm_sampled.restype = c_int
         L.oracle_fmm_solute_solvent.argtypes = [c_int, vp, vp, vp, c_double, c_int, c_int, c_int, c_double, vp]
         L.oracle_fmm_solute_solvent.restype = c_int
+        L.oracle_softcore_nf_uv.argtypes = [c_int, vp, vp, vp, c_double, c_int, c_int, c_double, c_double, c_double,
+                                            c_int, vp]
+        L.oracle_softcore_nf_uv.restype = c_int
         L.oracle_ewald.argtypes = [c_int, vp, vp, c_double, c_double, c_double, c_double, vp, vp, vp]
         L.oracle_ewald.restype = c_int
         L.oracle_num_threads.restype = c_int
@@ -190,6 +193,25 @@ def solute_solvent(pos, q, is_solute, L, d, p, ws=1, kappa=None):
         raise ValueError("oracle_fmm_solute_solvent: invalid arguments")
     names = ["e_uv", "W", "A", "B", "C", "nf_uv", "bc_cross"]
     return dict(zip(names, out[:7].tolist()))
+
+
+SOFTCORE_ALPHA = 0.2  # the paper's soft-core parameters (Calculation detail)
+SOFTCORE_C = 6
+
+
+def softcore_nf_uv(pos, q, is_solute, L, d, lam, A, ws=1, alpha=SOFTCORE_ALPHA, c=SOFTCORE_C):
+    """Soft-core solute-solvent near-field energy and its lambda derivative: r -> (alpha lambda A^c +
+    r^c)^(1/c) on the u-v pairs of the near-field stencil (the paper's soft-core form applied to the
+    electrostatic NF term, as it remarks after the soft-core LJ equation)."""
+    pos = _f64(pos, (-1, 3))
+    q = _f64(q)
+    sol = np.ascontiguousarray(is_solute, np.uint8)
+    out = np.zeros(2)
+    rc = lib().oracle_softcore_nf_uv(q.shape[0], _ptr(pos), _ptr(q), _ptr(sol), L, d, ws, lam, alpha, A, c,
+                                     _ptr(out))
+    if rc:
+        raise ValueError("oracle_softcore_nf_uv: invalid arguments")
+    return {"e_sc": float(out[0]), "de_sc_dlambda": float(out[1])}
 
 
 # ---------------------------------------------------------------- O1: Ewald

@@ -773,6 +773,57 @@ int oracle_fmm_solute_solvent(int N, const double *pos, const double *q, const u
     return 0;
 }
 
+/*
+ * Soft-core solute-solvent near field.  The paper's soft-core form for the
+ * solute-solvent LJ interaction (Calculation detail) replaces r_ij by
+ * (alpha lambda A^c + r_ij^c)^(1/c), alpha = 0.2, c = 6, and remarks that
+ * the same approach applies to the electrostatic NF term.  Reading: on the
+ * solute-solvent pairs of the near field (Eq. EqNF's stencil of (2 ws + 1)^3
+ * leaves), with one length A for every pair,
+ *   E_sc(lambda) = sum_{i in u} sum_{j in v, j in NF(i)} q_i q_j
+ *                                    / (alpha lambda A^c + r_ij^c)^(1/c),
+ *   dE_sc/dlambda = -(alpha A^c / c) sum q_i q_j
+ *                                    (alpha lambda A^c + r_ij^c)^(-1/c - 1).
+ * At lambda = 0 E_sc is the plain NF_uv of Eq. FMMcalc's near-field part.
+ * out[2] = {E_sc, dE_sc/dlambda}.
+ */
+int oracle_softcore_nf_uv(int N, const double *pos, const double *q, const unsigned char *is_solute, double L, int d,
+                          int ws, double lambda, double alpha, double A, int c, double *out)
+{
+    fmm_t F;
+    if (c < 1 || !(A >= 0.0) || fmm_setup(&F, N, pos, q, L, d, 0, ws, 1.0)) return 1;
+    int n = F.nleaf;
+    double Ac = pow(A, (double)c);
+    ksum ke = {0, 0}, kd = {0, 0};
+    for (int i = 0; i < N; ++i) {
+        if (!is_solute[i]) continue;
+        int cl = F.leaf_of[i];
+        int cx = cl % n, cy = (cl / n) % n, cz = cl / (n * n);
+        for (int dz = -ws; dz <= ws; ++dz)
+            for (int dy = -ws; dy <= ws; ++dy)
+                for (int dx = -ws; dx <= ws; ++dx) {
+                    int sx = cx + dx, sy = cy + dy, sz = cz + dz;
+                    double shift[3] = {L * floor((double)sx / n), L * floor((double)sy / n), L * floor((double)sz / n)};
+                    int sl = lin(wrapi(sx, n), wrapi(sy, n), wrapi(sz, n), n);
+                    for (int t = F.start[sl]; t < F.start[sl + 1]; ++t) {
+                        int j = F.list[t];
+                        if (is_solute[j]) continue;
+                        double v[3] = {F.w[3 * i] - (F.w[3 * j] + shift[0]), F.w[3 * i + 1] - (F.w[3 * j + 1] + shift[1]),
+                                       F.w[3 * i + 2] - (F.w[3 * j + 2] + shift[2])};
+                        double r = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+                        double base = alpha * lambda * Ac + pow(r, (double)c);
+                        double reff = pow(base, 1.0 / c);
+                        kadd(&ke, q[i] * q[j] / reff);
+                        kadd(&kd, -(alpha * Ac / c) * q[i] * q[j] / (reff * base));
+                    }
+                }
+    }
+    out[0] = kval(&ke);
+    out[1] = kval(&kd);
+    fmm_free(&F);
+    return 0;
+}
+
 /* ------------------------------------------------------------------------ */
 /* O1: Ewald sum with point charges and background charge, conducting       */
 /* boundary (Appendix A).                                                     */

@@ -512,3 +512,53 @@ def test_solute_solvent_linear_in_ion_charge():
     r1 = oracle.solute_solvent(b1.pos, b1.q, b1.is_solute, b1.L, 2, 8)
     r2 = oracle.solute_solvent(b2.pos, b2.q, b2.is_solute, b2.L, 2, 8)
     assert rel(r2["e_uv"], 0.36 * r1["e_uv"]) < 1e-12
+
+
+# ---------------------------------------------------------------- soft-core near field
+def test_softcore_at_lambda_zero_is_the_plain_near_field():
+    """At lambda = 0 the soft-core distance (alpha lambda A^c + r^c)^(1/c) is r: the sum is the plain
+    solute-solvent near-field Coulomb sum of Eq. FMMcalc's NF part, whatever A."""
+    b = boxes.ion_in_water(200, "Mg", seed=8, L=18.0)
+    ref = oracle.solute_solvent(b.pos, b.q, b.is_solute, b.L, 3, 4)["nf_uv"]
+    for A in (0.5, 1.0, 3.0):
+        r = oracle.softcore_nf_uv(b.pos, b.q, b.is_solute, b.L, 3, 0.0, A)
+        assert rel(r["e_sc"], ref) < 1e-14
+    # A = 0: no softening at any lambda
+    r = oracle.softcore_nf_uv(b.pos, b.q, b.is_solute, b.L, 3, 0.7, 0.0)
+    assert rel(r["e_sc"], ref) < 1e-14 and r["de_sc_dlambda"] == 0.0
+
+
+def test_softcore_far_pairs_reduce_to_coulomb():
+    """For r >> A the soft-core pair energy is q q' / r (1 - alpha lambda (A/r)^c / c + ...): a single
+    solute-solvent pair at r = 2.5 A with A = 0.25 A differs from Coulomb by alpha lambda 1e-6 / 6."""
+    L = 12.0
+    pos = np.array([[1.0, 1.0, 1.0], [3.5, 1.0, 1.0]])
+    q = np.array([1.0, -0.8])
+    sol = np.array([1, 0], np.uint8)
+    lam, A = 0.5, 0.25
+    r = oracle.softcore_nf_uv(pos, q, sol, L, 2, lam, A)
+    coul = q[0] * q[1] / 2.5
+    assert abs(r["e_sc"] / coul - 1.0 - (-0.2 * lam * (A / 2.5) ** 6 / 6)) < 1e-12
+    assert r["e_sc"] > coul  # softening weakens the attraction
+
+
+def test_softcore_lambda_derivative_matches_central_differences():
+    b = boxes.ion_in_water(120, "Na", seed=3, L=16.0)
+    A = 1.2
+    for lam in (0.1, 0.5, 0.9):
+        r = oracle.softcore_nf_uv(b.pos, b.q, b.is_solute, b.L, 2, lam, A)
+        h = 1e-5
+        ep = oracle.softcore_nf_uv(b.pos, b.q, b.is_solute, b.L, 2, lam + h, A)["e_sc"]
+        em = oracle.softcore_nf_uv(b.pos, b.q, b.is_solute, b.L, 2, lam - h, A)["e_sc"]
+        assert abs((ep - em) / (2 * h) - r["de_sc_dlambda"]) < 1e-7 * abs(r["de_sc_dlambda"]) + 1e-12
+
+
+def test_softcore_removes_the_overlap_divergence():
+    """The purpose of the soft-core form: a solvent charge on top of the solute charge gives a finite
+    energy for lambda > 0, q q' / (alpha lambda A^c)^(1/c)."""
+    L = 10.0
+    pos = np.array([[2.0, 2.0, 2.0], [2.0, 2.0, 2.0 + 1e-9]])
+    q = np.array([1.0, -1.0])
+    sol = np.array([1, 0], np.uint8)
+    r = oracle.softcore_nf_uv(pos, q, sol, L, 2, 1.0, 1.0)
+    assert abs(r["e_sc"] - (-1.0 / 0.2 ** (1 / 6))) < 1e-9
