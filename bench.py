@@ -363,6 +363,13 @@ def run_ours(args):
         "stage_ms": stage,
         "fp64_path": fp64,
     }
+    if ws == 1 and args.batch_leg:
+        # the batched lambda-window workload (64 boxes of uneven size), timed here so that every default
+        # run carries it
+        m = measure_batch(max(3, args.steps // 2), 3, rank, local, serial=False)
+        out["lambda64"] = {"value": m["Ntot"] / m["t_graph"], "unit": UNIT, "ms_per_step": m["t_graph"] * 1e3,
+                           "workload": m["workload"], "timing": "host wall time around the synchronous batch call",
+                           **m["batch"]}
     if ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.workload)
     print(json.dumps(out), flush=True)
@@ -388,16 +395,39 @@ def oracle_step(b, d, p):
     oracle.solute_solvent(b.pos, b.q, b.is_solute, b.L, d, p)
 
 
+SAMPLE_SHRINK = 8  # the oracle's bounded sample: a 1/512 sub-box (both the cpu_baseline leg and --impl reference)
+
+
+def one_core_seconds(workload: str):
+    """One oracle step on the sample sub-box with a single OpenMP thread (fresh process)."""
+    code = ("import sys, time; sys.path.insert(0, %r); import bench; b, d, p = bench.sample_box(%r, %d); "
+            "t = time.perf_counter(); bench.oracle_step(b, d, p); print(time.perf_counter() - t)" %
+            (ROOT, workload, SAMPLE_SHRINK))
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+        return float(out.stdout.strip().splitlines()[-1])
+    except Exception:
+        return None
+
+
 def cpu_baseline(workload: str):
     import oracle
-    b, d, p = sample_box(workload, 4)
-    t0 = time.perf_counter()
-    oracle_step(b, d, p)
-    dt = time.perf_counter() - t0
-    return {"value": b.N / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": "one energy+forces+solute-solvent evaluation of a 1/64 sub-box of the workload "
-                      "(N=%d, L=%.2f A, depth %d, p %d: same density, leaf occupancy and order), %.1f s" %
-                      (b.N, b.L, d, p, dt)}
+    b, d, p = sample_box(workload, SAMPLE_SHRINK)
+    oracle_step(b, d, p)  # builds the oracle's tables once
+    n, t0 = 0, time.perf_counter()
+    while True:  # about 10 s of the oracle on all host cores
+        oracle_step(b, d, p)
+        n += 1
+        dt = time.perf_counter() - t0
+        if dt > 10.0:
+            break
+    t1 = one_core_seconds(workload)
+    return {"value": b.N * n / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": "%d energy+forces+solute-solvent evaluations of a 1/512 sub-box of the workload "
+                      "(N=%d, L=%.2f A, depth %d, p %d: same density, leaf occupancy and order), %.1f s; "
+                      "the same sub-box as --impl reference" % (n, b.N, b.L, d, p, dt),
+            "one_core": None if t1 is None else {"value": b.N / t1, "unit": UNIT, "cores": 1, "seconds": t1}}
 
 
 def run_reference(args):
@@ -405,7 +435,7 @@ def run_reference(args):
     if rank != 0:
         return
     import oracle
-    b, d, p = sample_box(args.workload, 8)
+    b, d, p = sample_box(args.workload, SAMPLE_SHRINK)
     for _ in range(args.warmup):
         oracle_step(b, d, p)
     t0 = time.perf_counter()
@@ -427,22 +457,25 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
-def run_batch(args):
+def measure_batch(steps: int, warmup: int, rank: int, local: int, serial: bool = True, shard_world: int = 0):
     """The batched free-energy workload: 64 ion-in-water boxes of uneven size (lambda
     windows, ion charge scaled by lambda), per box E_total, E_uv, V_lambda and dV/dlambda_C
-    through fmm_batch_*; the recorded-graph path is timed, beside the stream path and the
-    same boxes on single plans one after the other."""
+    through fmm_batch_*; the recorded-graph path is timed, beside the stream path and (serial)
+    the same boxes on single plans one after the other."""
     import torch
 
     from paper_2003_13218_gb300 import boxes
     from paper_2003_13218_gb300.fmm import FMMBatch, FMMPlan
 
-    rank = int(os.environ.get("RANK", 0))
-    ws = int(os.environ.get("WORLD_SIZE", 1))
-    local = int(os.environ.get("LOCAL_RANK", 0))
-    torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    win = boxes.lambda_windows(64, seed=rank)
+    if shard_world > 1:
+        # one 64-box batch split across the ranks by estimated cost (each rank evaluates its share)
+        from paper_2003_13218_gb300 import shard
+        allwin = boxes.lambda_windows(64, seed=0)
+        mine = shard.partition_boxes([shard.box_cost(b.N) for b, _ in allwin], shard_world)[rank]
+        win = [allwin[i] for i in mine]
+    else:
+        win = boxes.lambda_windows(64, seed=rank)
     Ntot = sum(b.N for b, _ in win)
     lam = np.array([l for _, l in win])
     pos = [torch.from_numpy(b.pos).to(dev) for b, _ in win]
@@ -462,45 +495,82 @@ def run_batch(args):
         return (time.perf_counter() - t) / k
 
     sampler = ClockSampler(local)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         r = bt.lambda_energies(pos, q, sol, lam)
     sampler.start()
-    t_graph = timed(lambda: bt.lambda_energies(pos, q, sol, lam), args.steps)
+    t_graph = timed(lambda: bt.lambda_energies(pos, q, sol, lam), steps)
     clocks = sampler.stop()
     info = bt.info(0)
     bt.set_graph(False)
     bt.lambda_energies(pos, q, sol, lam)
-    t_stream = timed(lambda: bt.lambda_energies(pos, q, sol, lam), args.steps)
+    t_stream = timed(lambda: bt.lambda_energies(pos, q, sol, lam), steps)
     r_stream = bt.lambda_energies(pos, q, sol, lam)
     bt.close()
-    # the same boxes and depths on single plans, one after the other
-    plans = [FMMPlan(b.L, b.N, d, 12, precision="mixed") for (b, _), d in zip(win, depths)]
-    def serial():
-        for pl, x, y, z in zip(plans, pos, q, sol):
-            pl.evaluate(x, y, z, forces=None)
-    serial()
-    t_serial = timed(serial, max(1, args.steps // 2))
-    e_single = np.array([pl.evaluate(x, y, z, forces=None)[1]["e_uv"] for pl, x, y, z in zip(plans, pos, q, sol)])
-    for pl in plans:
-        pl.close()
+    batch = {"graph_ms": t_graph * 1e3, "stream_path_ms": t_stream * 1e3, "plan_create_s": create_s,
+             "depths": depths, "replays": info["replays"]}
+    if serial:
+        # the same boxes and depths on single plans, one after the other
+        plans = [FMMPlan(b.L, b.N, d, 12, precision="mixed") for (b, _), d in zip(win, depths)]
+        def serial_run():
+            for pl, x, y, z in zip(plans, pos, q, sol):
+                pl.evaluate(x, y, z, forces=None)
+        serial_run()
+        t_serial = timed(serial_run, max(1, steps // 2))
+        e_single = np.array([pl.evaluate(x, y, z, forces=None)[1]["e_uv"] for pl, x, y, z in zip(plans, pos, q, sol)])
+        for pl in plans:
+            pl.close()
+        batch["single_plans_serial_ms"] = t_serial * 1e3
+        batch["max_rel_diff_e_uv_vs_single_plans"] = float(np.max(np.abs(r_stream["e_uv"] - e_single) /
+                                                                  np.maximum(np.abs(e_single), 1e-30)))
+    workload = ("lambda64: 64 boxes, %d charges in all (%d..%d per box), species Mg/Na/Cl, lambda = (b mod 16)/15, "
+                "p 12, depth chosen by timing" % (Ntot, min(b.N for b, _ in win), max(b.N for b, _ in win)))
+    out = {"Ntot": Ntot, "t_graph": t_graph, "batch": batch, "clocks": clocks, "workload": workload}
+    if shard_world > 1:
+        from paper_2003_13218_gb300 import shard
+        out["gathered"] = shard.gather_box_results({"e_total": r_stream["e_total"], "e_uv": r_stream["e_uv"]},
+                                                   mine, 64)
+    return out
+
+
+def run_batch(args):
+    import torch
+    rank = int(os.environ.get("RANK", 0))
+    ws = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(local)
+    sharded = args.shard and ws > 1
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")  # host-side gather of per-box FP64 results only
+    m = measure_batch(args.steps, args.warmup, rank, local, shard_world=ws if sharded else 0)
+    t_graph = m["t_graph"]
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([t_graph], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_graph = float(t.item())
+        n = torch.tensor([float(m["Ntot"])], dtype=torch.float64)
+        dist.all_reduce(n, op=dist.ReduceOp.SUM)
+        n_all = float(n.item())
+        dist.destroy_process_group()
+    else:
+        n_all = float(m["Ntot"])
     if rank != 0:
         return
+    Ntot = m["Ntot"]
     out = {
         "metric": "particle-evals/s, batched lambda windows: E_total, E_uv, V_lambda, dV/dlambda_C per box",
-        "value": Ntot * ws / t_graph, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": t_graph * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "value": n_all / t_graph, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_graph * 1e3, "higher_is_better": True, "scaling": "strong" if sharded else "weak",
+        "vs_baseline": None,
         "dtype": "f32+fp16x2-tensor+f64", "data": "synthetic (seeded ion-in-water boxes, lambda-scaled ion charge)",
-        "config": {"workload": "lambda64: 64 boxes, %d charges in all (%d..%d per box), species Mg/Na/Cl, "
-                               "lambda = (b mod 16)/15, p 12, depth chosen by timing" %
-                               (Ntot, min(b.N for b, _ in win), max(b.N for b, _ in win)),
-                   "l2": "inputs (%.0f MB) larger than L2" % (Ntot * 33 / 1e6), "parallelism": "1 GPU"},
+        "config": {"workload": m["workload"], "l2": "inputs (%.0f MB) larger than L2" % (Ntot * 33 / 1e6),
+                   "parallelism": ("boxes sharded by cost across %d GPUs" % ws) if sharded else
+                   ("replicas" if ws > 1 else "1 GPU")},
         "roofline": None,
-        "batch": {"graph_ms": t_graph * 1e3, "stream_path_ms": t_stream * 1e3, "single_plans_serial_ms":
-                  t_serial * 1e3, "plan_create_s": create_s, "depths": depths, "replays": info["replays"],
-                  "max_rel_diff_e_uv_vs_single_plans": float(np.max(np.abs(r_stream["e_uv"] - e_single) /
-                                                                    np.maximum(np.abs(e_single), 1e-30)))},
+        "batch": m["batch"],
         "note": "host wall time around the synchronous batch call (results read back); the batch owns its streams",
-        "clocks": clocks,
+        "clocks": m["clocks"],
     }
     print(json.dumps(out), flush=True)
 
@@ -515,6 +585,10 @@ def main():
     ap.add_argument("--split", default="fp16x2", choices=["fp16x2", "bf16x3", "bf16x2", "bf16a2b3", "fp32"])
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--shard", action="store_true",
+                    help="lambda64 on N GPUs: split one 64-box batch across the ranks (else every rank its own)")
+    ap.add_argument("--batch-leg", type=int, default=1, choices=[0, 1],
+                    help="1: also time the 64-box lambda-window batch and add it to the line")
     ap.add_argument("--ws", type=int, default=1, choices=[1, 2], help="well-separatedness (2: the paper's setting)")
     ap.add_argument("--p", type=int, default=None, help="expansion order (default: the workload's)")
     ap.add_argument("--overlap", type=int, default=1, choices=[0, 1],

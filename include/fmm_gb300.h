@@ -83,6 +83,9 @@ typedef struct {
     double nf_uv;    /* near-field solute-solvent pair sum */
     double bc_cross; /* -pi Q_u Q_v/(V kappa^2) + (2 pi/3V)(Q_u S2_v + Q_v S2_u)
                         - (4 pi/3V) mu_u . mu_v */
+    double nf_sc;    /* FMM_OPT_SOFTCORE: sum over the near-field solute-solvent pairs of
+                        q_i q_j / (alpha lambda A^c + r_ij^c)^(1/c) (0 when off) */
+    double dnf_sc;   /* its derivative in lambda, -(alpha A^c / c) sum q_i q_j (alpha lambda A^c + r^c)^(-1/c-1) */
 } fmm_uv_terms;
 
 /* Per-stage device times of the last call, milliseconds (CUDA events on the
@@ -120,8 +123,40 @@ enum {
                               the default priority, the near field (P2P, which needs only the sort) on one
                               of the lowest priority filling the SMs the far field leaves idle, the sparse
                               solute pass of Eq. FMMcalc beside the L2P; 0 runs every stage in order on the
-                              plan's stream (the per-stage times then add up) */
+                              plan's stream (the per-stage times then add up) */,
+    FMM_OPT_M2L_GRADE = 10 /* ival = D2 | (D1 << 8), fp16x2 tensor-core M2L only: per K chunk of input coefficients
+                              (64 per chunk), by the chunk's lowest degree lambda: lambda >= D2 drops the moments'
+                              second fp16 term (2 products: ~2^-12 relative on those terms), lambda >= D1 drops
+                              the operators' second term as well (1 product, ~2^-11), and two consecutive
+                              1-product chunks share one pipeline stage; 0 = never.  Contributions of high input
+                              degrees to a well-separated cell's local expansion are small, so the error stays far
+                              below the first-term precision of the low degrees.  D2, D1 in 0..20; default
+                              FMM_GRADE_DEFAULT.  M2M, the fused L2L and the solute-only pass always use 3
+                              products */,
+    FMM_OPT_M2L_ACC_GROUP = 11 /* ival in 1..64: tensor-core M2L / M2M offsets whose products are summed in
+                              one FP32 TMEM accumulator before it is drained into registers (the fused L2L
+                              always alone); longer chains drain less often but carry more of the tensor
+                              core's accumulation rounding; default FMM_ACC_GROUP_DEFAULT */,
+    FMM_OPT_SOFTCORE = 12,  /* ival = c (1..12; 0 = off, the default), dval = A (A, > 0): the soft-core form the
+                              paper gives for the solute-solvent LJ term (Calculation detail), which it notes
+                              applies to the electrostatic NF term too, r_ij -> (alpha lambda A^c + r_ij^c)^(1/c)
+                              on the near-field solute-solvent pairs: evaluations that return fmm_uv_terms also
+                              return that pair sum and its lambda derivative (nf_sc, dnf_sc; FP64 arithmetic).
+                              The paper uses alpha = 0.2 and c = 6 for its LJ lengths A_ij; A is the caller's */
+    FMM_OPT_SOFTCORE_LAMBDA = 13, /* dval in [0, 1]: the lambda of that sum (default 0); read when the call runs,
+                              so a recorded batch graph sees the current value */
+    FMM_OPT_SOFTCORE_ALPHA = 14,  /* dval > 0: alpha (default 0.2) */
+    FMM_OPT_WAIT_BUDGET_NS = 15,  /* ival in 1000..10^10: budget (ns) of each bounded wait in the tensor-core
+                              kernels (default 2 s); a wait that runs out makes the call return FMM_ERR_TIMEOUT
+                              after the kernel has waited, with its own 2 s limit, for its copies and MMAs in
+                              flight; the plan stays usable */
+    FMM_OPT_INJECT_STALL = 16     /* ival 0 / 1, a test hook for the timeout path: with 1 the single-CTA
+                              tensor-core kernels first wait on a barrier that nothing arrives on, so every
+                              evaluation returns FMM_ERR_TIMEOUT after the wait budget (use with
+                              FMM_OPT_M2L_PAIR = 0 and a short budget) */
 };
+#define FMM_GRADE_DEFAULT (8 << 8)  /* D2 = 0, D1 = 8: input degrees >= 8 with one product */
+#define FMM_ACC_GROUP_DEFAULT 2
 enum { FMM_BOUNDARY_CONDUCTING = 0, FMM_BOUNDARY_VACUUM = 1 };
 enum { FMM_PREC_FP64 = 0, FMM_PREC_MIXED = 1 };
 enum {
@@ -243,7 +278,8 @@ fmm_status fmm_batch_create(int nbox, const double *box, const int64_t *N, const
  * is_solute[i] (uint8_t[N_i]): DEVICE pointers, which must stay valid and
  * unchanged in place between calls that reuse them.  lambda_c: host double[nbox]
  * (NULL: all 0).  Outputs (host double[nbox], each nullable): e_total, e_uv,
- * v_lambda = e_total - lambda_c e_uv, dv_dlambda = -e_uv.  Synchronises.
+ * v_lambda = e_total - lambda_c e_uv, dv_dlambda = -e_uv (with the soft-core
+ * near field on: see fmm_batch_set_softcore).  Synchronises.
  *
  * The first call runs the boxes through the streams and then records the whole
  * batch as a CUDA graph; later calls with the same pointers replay it and
@@ -255,6 +291,16 @@ fmm_status fmm_batch_create(int nbox, const double *box, const int64_t *N, const
 fmm_status fmm_batch_lambda_energies(fmm_batch batch, const double *const *pos, const double *const *q,
                                      const uint8_t *const *is_solute, const double *lambda_c, double *e_total,
                                      double *e_uv, double *v_lambda, double *dv_dlambda);
+
+/*
+ * Soft-core near field for every box (FMM_OPT_SOFTCORE on each plan): c (0 = off), A (A), alpha.  With it
+ * on, the solute-solvent near-field pairs of box i interact through (alpha lambda_i A^c + r^c)^(1/c), so
+ * with E_uv^sc = E_uv - NF_uv + NF_sc(lambda_i) (Eq. Vswucheme with the softened NF pairs):
+ *     v_lambda   = e_total - e_uv + (1 - lambda_i) E_uv^sc,
+ *     dv_dlambda = -E_uv^sc + (1 - lambda_i) dNF_sc/dlambda.
+ * Errors: FMM_ERR_INVALID_ARG for c outside 0..12 or, with c > 0, A or alpha not finite and positive.
+ */
+fmm_status fmm_batch_set_softcore(fmm_batch batch, int c, double A, double alpha);
 
 /* Depth and order of box i, and how many calls replayed the graph or ran the
  * stream path (each nullable). */

@@ -14,13 +14,13 @@ using namespace fmm;
 
 namespace {
 
-size_t reduction_scratch_bytes() { return sizeof(double) * 304 * 16 * 2; }
+size_t reduction_scratch_bytes() { return sizeof(double) * 304 * 20 * 2; }
 
 void free_buffers(Plan &P)
 {
     void *bufs[] = {P.in_pos, P.in_q,   P.out_forces, P.out_phi, P.in_sol, P.wpos,    P.key,    P.perm,   P.sleaf,
                     P.cell_start, P.cell_fill, P.scan_tmp, P.sorted, P.sorted_u, P.sorted_sol, P.phi_nf, P.phi_ff,
-                    P.phi_u, P.f_nf, P.g_ff, P.red_partial, P.red_out, P.d_err};
+                    P.phi_u, P.f_nf, P.g_ff, P.red_partial, P.red_out, P.d_err, P.sc_out, P.sc_lambda};
     for (void *b : bufs) cudaFree(b);
     for (int l = 0; l <= 8; ++l) {
         cudaFree(P.M[l]);
@@ -28,6 +28,8 @@ void free_buffers(Plan &P)
         P.M[l] = P.L[l] = nullptr;
     }
     if (P.h_out) cudaFreeHost(P.h_out);
+    if (P.h_sc_lambda) cudaFreeHost(P.h_sc_lambda);
+    P.sc_out = P.sc_lambda = P.h_sc_lambda = nullptr;
     P.in_pos = P.in_q = P.out_forces = P.out_phi = nullptr;
     P.in_sol = nullptr;
     P.wpos = nullptr;
@@ -71,7 +73,7 @@ fmm_status alloc_buffers(Plan &P)
         FMM_CUDA_TRY(dalloc(&P.L[l], sizeof(double) * cells * nc));
     }
     FMM_CUDA_TRY(dalloc(&P.red_partial, reduction_scratch_bytes()));
-    FMM_CUDA_TRY(dalloc(&P.red_out, sizeof(double) * 32));
+    FMM_CUDA_TRY(dalloc(&P.red_out, sizeof(double) * 48));
     FMM_CUDA_TRY(dalloc(&P.d_err, sizeof(int)));
     FMM_CUDA_TRY(cudaMallocHost((void **)&P.h_out, sizeof(double) * 40));
     return FMM_OK;
@@ -175,6 +177,8 @@ fmm_status eval_front(Plan &P, const double *dpos, const double *dq, const uint8
 {
     if (tm) tm->mark();
     FMM_CUDA_TRY(cudaMemsetAsync(P.d_err, 0, sizeof(int), P.stream));
+    if (want_uv && P.sc_c > 0)  // the soft-core lambda as it is when the call runs
+        FMM_CUDA_TRY(cudaMemcpyAsync(P.sc_lambda, P.h_sc_lambda, sizeof(double), cudaMemcpyHostToDevice, P.stream));
     P.near_forked = P.near_p2p = false;
     TRY(launch_assign_sort(P, dpos, dq, dsol));
     if (want_uv) TRY(solute_count(P));
@@ -205,7 +209,7 @@ fmm_status eval_back(Plan &P, const double *dq, bool want_uv, double *dforces, S
     if (dforces) TRY(launch_forces_out(P, dq, dforces));
     if (dphi) TRY(launch_potentials_out(P, dphi));
     if (tm) tm->mark();
-    FMM_CUDA_TRY(cudaMemcpyAsync(P.h_out, P.red_out, sizeof(double) * 29, cudaMemcpyDeviceToHost, P.stream));
+    FMM_CUDA_TRY(cudaMemcpyAsync(P.h_out, P.red_out, sizeof(double) * 31, cudaMemcpyDeviceToHost, P.stream));
     FMM_CUDA_TRY(cudaMemcpyAsync(P.h_out + 32, P.d_err, sizeof(int), cudaMemcpyDeviceToHost, P.stream));
     return FMM_OK;
 }
@@ -231,6 +235,8 @@ fmm_status eval_read(Plan &P, fmm_energy_terms *terms, fmm_uv_terms *uv)
         uv->C = P.h_out[26];
         uv->nf_uv = P.h_out[27];
         uv->bc_cross = P.h_out[28];
+        uv->nf_sc = P.sc_c > 0 ? P.h_out[29] : 0.0;
+        uv->dnf_sc = P.sc_c > 0 ? P.h_out[30] : 0.0;
     }
     if (err & ERRF_NONFINITE) return FMM_ERR_NONFINITE;
     if (err & ERRF_TIMEOUT) return FMM_ERR_TIMEOUT;
@@ -464,6 +470,45 @@ fmm_status fmm_plan_set_option(fmm_plan plan, int key, int64_t ival, double dval
     case FMM_OPT_M2L_PAIR:
         if (ival != 0 && ival != 1) return FMM_ERR_INVALID_ARG;
         P.tc_pair = ival != 0;
+        return FMM_OK;
+    case FMM_OPT_M2L_GRADE: {
+        const int64_t d2 = ival & 0xFF, d1 = (ival >> 8) & 0xFF;
+        if (ival < 0 || (ival >> 16) != 0 || d2 > P_MAX || d1 > P_MAX) return FMM_ERR_INVALID_ARG;
+        P.grade = (int)ival;
+        return FMM_OK;
+    }
+    case FMM_OPT_M2L_ACC_GROUP:
+        if (ival < 1 || ival > 64) return FMM_ERR_INVALID_ARG;
+        P.acc_group = (int)ival;
+        return FMM_OK;
+    case FMM_OPT_SOFTCORE:
+        if (ival < 0 || ival > 12) return FMM_ERR_INVALID_ARG;
+        if (ival > 0 && !(dval > 0.0 && isfinite(dval))) return FMM_ERR_INVALID_ARG;
+        if (ival > 0 && !P.sc_out) {  // buffers on first use, never inside an evaluation
+            FMM_CUDA_TRY(dalloc(&P.sc_out, sizeof(double) * 2 * P.N));
+            FMM_CUDA_TRY(dalloc(&P.sc_lambda, sizeof(double)));
+            FMM_CUDA_TRY(cudaMallocHost((void **)&P.h_sc_lambda, sizeof(double)));
+            *P.h_sc_lambda = 0.0;
+        }
+        P.sc_c = (int)ival;
+        P.sc_A = ival > 0 ? dval : 0.0;
+        return FMM_OK;
+    case FMM_OPT_SOFTCORE_LAMBDA:
+        if (!(dval >= 0.0 && dval <= 1.0)) return FMM_ERR_INVALID_ARG;
+        if (!P.h_sc_lambda) return P.sc_c > 0 ? FMM_ERR_INTERNAL : FMM_ERR_INVALID_ARG;  // set FMM_OPT_SOFTCORE first
+        *P.h_sc_lambda = dval;
+        return FMM_OK;
+    case FMM_OPT_SOFTCORE_ALPHA:
+        if (!(dval > 0.0 && isfinite(dval))) return FMM_ERR_INVALID_ARG;
+        P.sc_alpha = dval;
+        return FMM_OK;
+    case FMM_OPT_WAIT_BUDGET_NS:
+        if (ival < 1000 || ival > 10000000000ll) return FMM_ERR_INVALID_ARG;
+        P.wait_ns = (uint64_t)ival;
+        return FMM_OK;
+    case FMM_OPT_INJECT_STALL:
+        if (ival != 0 && ival != 1) return FMM_ERR_INVALID_ARG;
+        P.inject_stall = ival != 0;
         return FMM_OK;
     case FMM_OPT_OVERLAP:
         if (ival != 0 && ival != 1) return FMM_ERR_INVALID_ARG;

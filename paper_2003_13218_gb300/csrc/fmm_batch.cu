@@ -107,6 +107,7 @@ struct fmm_batch_s {
     cudaStream_t origin = nullptr;
     cudaEvent_t ev_start = nullptr;
     bool use_graph = true;
+    int sc_c = 0;  // soft-core near field on every plan (fmm_batch_set_softcore)
     cudaGraphExec_t graph = nullptr;
     std::vector<const void *> gptr;  // input pointers the graph was captured with
     std::vector<int> gcount;         // solute counts it was captured with
@@ -314,7 +315,10 @@ fmm_status fmm_batch_lambda_energies(fmm_batch b, const double *const *pos, cons
 {
     if (!b || !pos || !q || !is_solute) return FMM_ERR_INVALID_ARG;
     for (int i = 0; i < b->nbox; ++i)
-        if (!pos[i] || !q[i] || !is_solute[i]) return FMM_ERR_INVALID_ARG;
+        if (!pos[i] || !q[i] || !is_solute[i] || (lambda_c && !(lambda_c[i] >= 0.0 && lambda_c[i] <= 1.0)))
+            return FMM_ERR_INVALID_ARG;
+    if (b->sc_c > 0)  // each box's soft-core lambda, read by its next (enqueued or replayed) evaluation
+        for (int i = 0; i < b->nbox; ++i) *b->plans[i]->P.h_sc_lambda = lambda_c ? lambda_c[i] : 0.0;
     bool fresh = false;  // results come from the enqueued path
     if (b->use_graph && graph_matches(b, pos, q, is_solute)) {
         FMM_CUDA_TRY(cudaGraphLaunch(b->graph, b->origin));
@@ -342,8 +346,14 @@ results:
         const double lam = lambda_c ? lambda_c[i] : 0.0;
         if (e_total) e_total[i] = t.total;
         if (e_uv) e_uv[i] = u.e_uv;
-        if (v_lambda) v_lambda[i] = t.total - lam * u.e_uv;
-        if (dv_dlambda) dv_dlambda[i] = -u.e_uv;
+        if (b->sc_c > 0) {  // the near-field solute-solvent pairs through the soft-core distance
+            const double e_sc = u.e_uv - u.nf_uv + u.nf_sc;
+            if (v_lambda) v_lambda[i] = t.total - u.e_uv + (1.0 - lam) * e_sc;
+            if (dv_dlambda) dv_dlambda[i] = -e_sc + (1.0 - lam) * u.dnf_sc;
+        } else {
+            if (v_lambda) v_lambda[i] = t.total - lam * u.e_uv;
+            if (dv_dlambda) dv_dlambda[i] = -u.e_uv;
+        }
     }
     return worst;
 }
@@ -355,6 +365,24 @@ fmm_status fmm_batch_info(fmm_batch b, int i, int *depth, int *p, int64_t *repla
     if (p) *p = b->plans[i]->P.p;
     if (replays) *replays = b->replays;
     if (enqueued) *enqueued = b->enqueued;
+    return FMM_OK;
+}
+
+fmm_status fmm_batch_set_softcore(fmm_batch b, int c, double A, double alpha)
+{
+    if (!b || c < 0 || c > 12) return FMM_ERR_INVALID_ARG;
+    if (c > 0 && !(A > 0.0 && isfinite(A) && alpha > 0.0 && isfinite(alpha))) return FMM_ERR_INVALID_ARG;
+    for (fmm_plan h : b->plans) {
+        fmm_status s = fmm_plan_set_option(h, FMM_OPT_SOFTCORE, c, c > 0 ? A : 0.0);
+        if (s == FMM_OK && c > 0) s = fmm_plan_set_option(h, FMM_OPT_SOFTCORE_ALPHA, 0, alpha);
+        if (s != FMM_OK) return s;
+    }
+    b->sc_c = c;
+    if (b->graph) {  // the recorded work changed
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+        b->gptr.clear();
+    }
     return FMM_OK;
 }
 

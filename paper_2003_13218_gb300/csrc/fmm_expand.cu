@@ -332,6 +332,111 @@ __global__ void k_p2m(int p, int nside, const int *__restrict__ start, const Par
     }
 }
 
+// The same P2M at a compile-time order PP in FP32, one lane per leaf: a warp takes 32 leaves of one
+// parity class with consecutive parent coordinates (32 consecutive rows of the level's class layout),
+// each lane runs the recurrences of Eq. P2M for its leaf's charges with all (PP+1)^2 coefficients in
+// registers (indices fold into immediates).  The rows go through shared memory (row stride (PP+1)^2, odd,
+// so the 32 lanes hit 32 banks) and leave as 32 contiguous rows.  When `amax` is set (fp16x2 split) the
+// warp also folds max_k |Mhat_k s(k)| into *amax (positive floats order as their bit patterns), which
+// the tensor-core operand split needs for the level gain.
+constexpr int P2M_WARPS = 4;
+
+template <int PP>
+__global__ void __launch_bounds__(32 * P2M_WARPS) k_p2m_fixed(int d, const int *__restrict__ start,
+                                                              const Particle<float> *__restrict__ sp, float inv_h,
+                                                              float *__restrict__ M, const float *__restrict__ s,
+                                                              unsigned *__restrict__ amax)
+{
+    constexpr int NC = (PP + 1) * (PP + 1);
+    extern __shared__ float p2m_tile[];  // [P2M_WARPS][32][NC]
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    float *tile = p2m_tile + w * 32 * NC;
+    const int np = 1 << (d - 1);
+    const int64_t ncls = (int64_t)np * np * np;
+    const int64_t row0 = ((int64_t)blockIdx.x * P2M_WARPS + w) * 32;
+    if (row0 >= 8 * ncls) return;
+    const int64_t row = row0 + lane;
+    const bool valid = row < 8 * ncls;
+    float acc[NC];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) acc[k] = 0.f;
+    if (valid) {
+        const int c = (int)(row / ncls);
+        const int64_t P = row - c * ncls;
+        const int x = 2 * (int)(P % np) + (c & 1), y = 2 * (int)((P / np) % np) + ((c >> 1) & 1),
+                  z = 2 * (int)(P / ((int64_t)np * np)) + ((c >> 2) & 1);
+        const int nside = 2 * np;
+        const int leaf = x + nside * (y + nside * z);
+        const int b = start[leaf], e = start[leaf + 1];
+        for (int j = b; j < e; ++j) {
+            const Particle<float> pt = sp[j];
+            const float vx = -pt.x * inv_h, vy = -pt.y * inv_h, vz = -pt.z * inv_h;
+            const float r2 = vx * vx + vy * vy + vz * vz;
+            float dre = pt.q, dim = 0.f;  // q R_m^m
+#pragma unroll
+            for (int m = 0; m <= PP; ++m) {
+                if (m > 0) {
+                    const float sc = -0.5f / (float)m;
+                    const float nre = sc * (vx * dre - vy * dim);
+                    const float nim = sc * (vx * dim + vy * dre);
+                    dre = nre;
+                    dim = nim;
+                }
+                acc[cre(m, m)] += dre;
+                if (m > 0) acc[cim(m, m)] += dim;
+                float p2re = 0.f, p2im = 0.f, p1re = dre, p1im = dim;
+                // a trip count fixed at compile time (n = m + 1 + i, dead steps folded away) so that both
+                // loops unroll completely and acc[] stays in registers
+#pragma unroll
+                for (int i = 0; i < PP; ++i) {
+                    const int n = m + 1 + i;
+                    if (n > PP) break;
+                    const float a = (float)(2 * n - 1) * vz;
+                    const float inv = 1.f / (float)((n + m) * (n - m));
+                    const float cr = (a * p1re - r2 * p2re) * inv;
+                    const float ci = (a * p1im - r2 * p2im) * inv;
+                    acc[cre(n, m)] += cr;
+                    if (m > 0) acc[cim(n, m)] += ci;
+                    p2re = p1re;
+                    p2im = p1im;
+                    p1re = cr;
+                    p1im = ci;
+                }
+            }
+        }
+    }
+    float mx = 0.f;
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+        tile[lane * NC + k] = acc[k];
+        if (amax) mx = fmaxf(mx, fabsf(acc[k] * __ldg(s + k)));
+    }
+    __syncwarp();
+    const int64_t nrows = 8 * ncls - row0 < 32 ? 8 * ncls - row0 : 32;
+    float *dst = M + row0 * NC;
+    for (int64_t e = lane; e < nrows * NC; e += 32) dst[e] = tile[e];
+    if (amax) {
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0 && mx > 0.f) atomicMax(amax, __float_as_uint(mx));
+    }
+}
+
+template <int PP>
+fmm_status launch_p2m_fixed(Plan &P, const Particle<float> *sp, float inv_h, unsigned *amax, const float *s)
+{
+    constexpr int NC = (PP + 1) * (PP + 1);
+    const size_t sh = sizeof(float) * P2M_WARPS * 32 * NC;
+    static bool attr = false;
+    if (!attr) {
+        FMM_CUDA_TRY(cudaFuncSetAttribute(k_p2m_fixed<PP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+        attr = true;
+    }
+    const int64_t rows = P.nleaf;
+    const unsigned blocks = (unsigned)((rows + 32 * P2M_WARPS - 1) / (32 * P2M_WARPS));
+    k_p2m_fixed<PP><<<blocks, 32 * P2M_WARPS, sh, P.stream>>>(P.d, P.cell_start, sp, inv_h, (float *)P.M[P.d], s, amax);
+    return FMM_OK;
+}
+
 template <typename T>
 void launch_p2m(Plan &P, const Particle<T> *sp, T inv_h)
 {
@@ -601,13 +706,37 @@ fmm_status upward_t(Plan &P, bool solute_only)
     const int nside = 1 << P.d;
     const Particle<T> *sp = (const Particle<T> *)(solute_only ? P.sorted_u : P.sorted);
     T inv_h = (T)((double)nside / P.box);
-    launch_p2m<T>(P, sp, inv_h);
-    FMM_LAUNCH_CHECK(P);
     const bool tc = tc_translations(P);
+    // fp16 split: the P2M at a compile-time order folds the level maximum of |Mhat s| in as it writes
+    bool amax_ready = false;
+    if (std::is_same<T, float>::value && (P.p == 4 || P.p == 6 || P.p == 8 || P.p == 10 || P.p == 12)) {
+        unsigned *amax = nullptr;
+        if (tc) {
+            fmm_status st = tc_clear_amax(P, P.d);
+            if (st != FMM_OK) return st;
+            amax = tc_amax(P, P.d);
+        }
+        const Particle<float> *spf = (const Particle<float> *)sp;
+        const float ih = (float)inv_h;
+        const float *sc = tc ? tc_scale(P) : nullptr;
+        fmm_status st = P.p == 4    ? launch_p2m_fixed<4>(P, spf, ih, amax, sc)
+                        : P.p == 6  ? launch_p2m_fixed<6>(P, spf, ih, amax, sc)
+                        : P.p == 8  ? launch_p2m_fixed<8>(P, spf, ih, amax, sc)
+                        : P.p == 10 ? launch_p2m_fixed<10>(P, spf, ih, amax, sc)
+                                    : launch_p2m_fixed<12>(P, spf, ih, amax, sc);
+        if (st != FMM_OK) return st;
+        amax_ready = tc;
+    } else {
+        launch_p2m<T>(P, sp, inv_h);
+    }
+    FMM_LAUNCH_CHECK(P);
     for (int l = P.d - 1; l >= 0; --l) {
-        fmm_status st = tc ? tc_split_moments(P, l + 1) : FMM_OK;
+        // the tensor-core M2M into level l folds level l's maximum in (amax of level l + 1 is ready from
+        // the P2M or the previous M2M)
+        fmm_status st = tc ? tc_split_moments(P, l + 1, amax_ready) : FMM_OK;
         if (st == FMM_OK) st = tc ? launch_m2m_tc(P, l) : launch_m2m(P, l);
         if (st != FMM_OK) return st;
+        amax_ready = tc;
     }
     return FMM_OK;
 }

@@ -100,6 +100,18 @@ struct Plan {
     bool tc_pair = true;  // CTA-pair (2-SM) tensor-core M2L where the level allows it
     int known_count = -1; // >= 0: the solute count the caller already knows (no host wait; graph capture)
     int boundary = 0;     // FMM_BOUNDARY_CONDUCTING (Eq. Velecfull) or FMM_BOUNDARY_VACUUM (App. D)
+    // FMM_OPT_SOFTCORE: soft-core solute-solvent near field (c = 0: off); lambda lives in pinned host memory
+    // and is copied to the device at the start of each call (a recorded graph sees the current value)
+    int sc_c = 0;
+    double sc_A = 0, sc_alpha = 0.2;
+    double *sc_out = nullptr;        // device [2N]: per sorted slot q_i sum q_j / reff, and the lambda derivative
+    double *sc_lambda = nullptr;     // device [1]
+    double *h_sc_lambda = nullptr;   // pinned host [1]
+    int acc_group = FMM_ACC_GROUP_DEFAULT;  // FMM_OPT_M2L_ACC_GROUP: offsets per TMEM accumulator drain
+    uint64_t wait_ns = 2000000000ull;       // FMM_OPT_WAIT_BUDGET_NS: budget of each tensor-core pipeline wait
+    bool inject_stall = false;              // FMM_OPT_INJECT_STALL (test hook)
+    int grade = FMM_GRADE_DEFAULT;  // FMM_OPT_M2L_GRADE: D2 | D1 << 8 (input degrees from which the fp16x2 M2L
+                                    // drops the moments' / also the operators' second term; 0 = never)
     // FMM_OPT_OVERLAP: evaluate() runs on `exec` (priority above the default), the near field on `near`
     // (lowest priority: it fills what the far field leaves idle), both joined before the reductions
     bool overlap = true;
@@ -280,8 +292,15 @@ bool tc_available(const Plan &P, int level);
 // fp16 split: M2M on the tensor cores and L2L fused into each level's M2L
 bool tc_translations(const Plan &P);
 fmm_status tc_prepare(Plan &P);
-// fp16 split: balanced halo planes of M[level] (done by the upward pass before the M2M into level - 1)
-fmm_status tc_split_moments(Plan &P, int level);
+// fp16 split: balanced halo planes of M[level] (done by the upward pass before the M2M into level - 1);
+// amax_ready: the kernel that wrote M[level] has already folded the level's largest |Mhat s| into
+// tc_amax(P, level) (else it is computed here)
+fmm_status tc_split_moments(Plan &P, int level, bool amax_ready);
+// fp16 split: the device word of level l's largest |Mhat s| (float bits), cleared by tc_clear_amax before
+// the kernel that produces M[l] folds its maximum in; s(n,m) per real coefficient
+unsigned *tc_amax(Plan &P, int level);
+fmm_status tc_clear_amax(Plan &P, int level);
+const float *tc_scale(const Plan &P);
 // fp16 split: M2M into level (< d) from the planes of level + 1
 fmm_status launch_m2m_tc(Plan &P, int level);
 // precise: at least the accuracy of the 3 x 3 bf16 split whatever the plan's option (solute-only pass);

@@ -66,7 +66,7 @@ constexpr int TC_ROWS = 128;          // MMA M
 constexpr int kchunk_of(int sw) { return sw / 2; }
 constexpr uint32_t TMEM_COLS = 512;   // two accumulators of up to 256 columns
 constexpr int TC_PMAX = 15;           // N = (p+1)^2 rounded to 16 must not exceed 256
-constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // 2 s
+constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // 2 s: the teardown's own limit (and the default budget)
 constexpr int GAIN_T_EXP = 14;        // gT = 2^14 (fp16 split)
 constexpr int GAIN_M_EXP = 14;        // gM = 2^(14 - E)
 constexpr size_t TC_SMEM_BUDGET = 224 * 1024;
@@ -111,11 +111,17 @@ struct TcArgs {
     int ws, n_il, noff;     // well-separatedness, interaction-list length, M2L operator slots
     int out_np;             // M2M: class-layout side of the parent level (0 at level 0)
     uint32_t idesc;
+    uint32_t gchunks;       // fp16x2 M2L offsets: products per K chunk, 2 bits per chunk (0 = all 3), FMM_OPT_M2L_GRADE
+    int acc_group;          // offsets summed in one TMEM accumulator before it is drained (>= 1)
+    uint64_t wait_ns;       // budget of every pipeline wait (FMM_OPT_WAIT_BUDGET_NS); the teardown keeps its own
+    int inject_stall;       // test hook (single-CTA kernel): the MMA issuer first waits on a barrier nothing arrives on
     float *L;               // output level array (L of the level, or M of the parent level)
     float *Lpart;           // [groups][level cells][nc] partial sums when groups > 1
     const float *post;      // fp16 split: s(j) (M2L) or 1 / s(j) (M2M) per output coefficient, else null
     const unsigned *amax;   // fp16 split: largest |M^ s| of the A planes (gM follows from it)
     const unsigned *amaxL;  // fused L2L: largest |L^ / s| of the parent planes (gL), else null
+    unsigned *amax_out;     // fp16 split, one offset group: fold max_i |out_i sx(i)| of the written rows in here
+    const float *sx;        // with amax_out: s(i) (M2M output, |M^ s|) or 1 / s(i) (M2L output, |L^ / s|)
     int *err;
 };
 
@@ -141,6 +147,33 @@ __device__ inline int gain_m_exp(unsigned bits)
     const int e = GAIN_M_EXP - exp_of_bits(bits);
     return e < -100 ? -100 : (e > 100 ? 100 : e);
 }
+
+// Products of K chunk kc of a graded M2L offset: x0 y0 (+ x0 y1 (+ x1 y0)), 2 bits per chunk (0 = all 3).
+__device__ __forceinline__ int chunk_products(uint32_t g, int kc)
+{
+    const int c = (int)((g >> (2 * kc)) & 3u);
+    return c == 0 ? 3 : c;
+}
+
+// A graded offset's stages: two consecutive chunks of one product each (x0 y0 only) share one stage, their
+// A0 / B0 boxes in the places of the two terms; returns how many chunks the stage starting at kc covers.
+__device__ __forceinline__ int stage_chunks(uint32_t g, int kc, int kchunks)
+{
+    return (chunk_products(g, kc) == 1 && kc + 1 < kchunks && chunk_products(g, kc + 1) == 1) ? 2 : 1;
+}
+
+// Accumulation groups of one CTA's offsets: the M2L (or M2M) offsets, local indices 0 .. nm - 1, in runs
+// of G that share one TMEM accumulator; the fused L2L offset (when present it is the CTA's last) alone,
+// since its drain is scaled by gM / gL.
+struct AccGroups {
+    int nm, ng, G;
+    __device__ AccGroups(int nloc, bool has_l2l, int g) : nm(nloc - (has_l2l ? 1 : 0)), ng(0), G(g < 1 ? 1 : g)
+    {
+        ng = (nm + G - 1) / G + (has_l2l ? 1 : 0);
+    }
+    __device__ int begin(int g) const { return g * G < nm ? g * G : nm; }
+    __device__ int end(int g) const { return g * G < nm ? min((g + 1) * G, nm) : nm + 1; }
+};
 
 // ------------------------------------------------------------------ PTX wrappers
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -180,15 +213,16 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
     return ok != 0;
 }
 
-// bounded wait on phase `parity`; false on timeout or when the CTA aborts
-__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag)
+// bounded wait on phase `parity`; false after limit_ns or when the CTA aborts
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag, uint64_t limit_ns = WAIT_LIMIT_NS)
 {
+    if (mbar_try(bar, parity)) return true;  // the usual case: no clock read
     uint64_t t0 = global_ns();
     for (uint32_t i = 0;; ++i) {
         if (mbar_try(bar, parity)) return true;
         if ((i & 63) == 63) {
             if (*abort_flag) return false;
-            if (global_ns() - t0 > WAIT_LIMIT_NS) return false;
+            if (global_ns() - t0 > limit_ns) return false;
         }
     }
 }
@@ -257,6 +291,28 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// Lr[i] += fac * accumulator column i of this warp's 32 TMEM lanes, i < 16 NCH; the loads go out in
+// batches of 16-column pieces before one wait, as many as the registers left beside Lr allow
+template <int NCH>
+__device__ __forceinline__ void drain_accumulator(uint32_t taddr, float fac, float (&Lr)[NCH * 16])
+{
+    constexpr int DRAIN_BATCH = NCH * 16 + 64 <= 240 ? 4 : (NCH * 16 + 32 <= 240 ? 2 : 1);
+#pragma unroll
+    for (int c0 = 0; c0 < NCH; c0 += DRAIN_BATCH) {
+        uint32_t r[DRAIN_BATCH][16];
+#pragma unroll
+        for (int c = 0; c < DRAIN_BATCH; ++c)
+            if (c0 + c < NCH) tmem_ld16(taddr + (uint32_t)((c0 + c) * 16), r[c]);
+        tmem_wait_ld();
+#pragma unroll
+        for (int c = 0; c < DRAIN_BATCH; ++c)
+            if (c0 + c < NCH)
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    Lr[(c0 + c) * 16 + j] = fmaf(__uint_as_float(r[c][j]), fac, Lr[(c0 + c) * 16 + j]);
+    }
+}
+
 // ---- CTA pair (cluster of 2) helpers for the 2-SM MMA
 __device__ __forceinline__ uint32_t cluster_rank()
 {
@@ -279,8 +335,18 @@ __device__ __forceinline__ void cluster_sync_all()
 }
 
 // bounded wait with cluster-scope acquire (barriers that receive arrivals from the peer CTA)
-__device__ bool mbar_wait_cluster(uint32_t bar, uint32_t parity, volatile int *abort_flag)
+__device__ bool mbar_wait_cluster(uint32_t bar, uint32_t parity, volatile int *abort_flag,
+                                  uint64_t limit_ns = WAIT_LIMIT_NS)
 {
+    uint32_t ok0;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok0)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok0) return true;  // the usual case: no clock read
     uint64_t t0 = global_ns();
     for (uint32_t i = 0;; ++i) {
         uint32_t ok;
@@ -294,7 +360,7 @@ __device__ bool mbar_wait_cluster(uint32_t bar, uint32_t parity, volatile int *a
         if (ok) return true;
         if ((i & 63) == 63) {
             if (*abort_flag) return false;
-            if (global_ns() - t0 > WAIT_LIMIT_NS) return false;
+            if (global_ns() - t0 > limit_ns) return false;
         }
     }
 }
@@ -374,6 +440,46 @@ struct Products<2, 3> {
     __device__ static constexpr int b(int k) { return k == 1 ? 1 : k == 3 ? 2 : 0; }
 };
 
+// The MMAs of one K chunk: the first NP products over the chunk's nk valid K16 steps, straight-line code
+// (operand addresses are compile-time offsets from the stage bases); `first` starts a new accumulator.
+template <int NP, typename PR, int K16, int SW, bool PAIR>
+__device__ __forceinline__ void issue_chunk(uint32_t tmem_d, uint32_t a0, uint32_t b0, uint32_t stageA, uint32_t stageB,
+                                            int nk, uint32_t idesc, bool first)
+{
+#pragma unroll
+    for (int pr = 0; pr < NP; ++pr) {
+#pragma unroll
+        for (int k16 = 0; k16 < K16; ++k16) {
+            if (k16 >= nk) continue;  // zero fill beyond K
+            const uint64_t ad = sdesc<SW>(a0 + PR::a(pr) * stageA + k16 * 32);
+            const uint64_t bd = sdesc<SW>(b0 + PR::b(pr) * stageB + k16 * 32);
+            const uint32_t acc = (first && pr == 0 && k16 == 0) ? 0u : 1u;
+            if (PAIR) mma_f16_pair(tmem_d, ad, bd, idesc, acc);
+            else mma_bf16(tmem_d, ad, bd, idesc, acc);
+        }
+    }
+}
+
+// The MMAs of a merged stage: chunk kc0 + t in term place t (t = 0, 1), product x0 y0 only; nk1 valid
+// K16 steps in the second chunk.
+template <int K16, int SW, bool PAIR>
+__device__ __forceinline__ void issue_merged(uint32_t tmem_d, uint32_t a0, uint32_t b0, uint32_t stageA,
+                                             uint32_t stageB, int nk1, uint32_t idesc, bool first)
+{
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+#pragma unroll
+        for (int k16 = 0; k16 < K16; ++k16) {
+            if (t == 1 && k16 >= nk1) continue;
+            const uint64_t ad = sdesc<SW>(a0 + t * stageA + k16 * 32);
+            const uint64_t bd = sdesc<SW>(b0 + t * stageB + k16 * 32);
+            const uint32_t acc = (first && t == 0 && k16 == 0) ? 0u : 1u;
+            if (PAIR) mma_f16_pair(tmem_d, ad, bd, idesc, acc);
+            else mma_bf16(tmem_d, ad, bd, idesc, acc);
+        }
+    }
+}
+
 // One CTA sums, for 128 target rows, the products of a list of offsets:
 //   mode 0 (M2L): the 189 interaction-list offsets of parity class `cls`, A
 //     from the halo'd source planes of the level; with fused L2L (fp16 split)
@@ -399,6 +505,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     __shared__ __align__(8) uint64_t bar_tfull[2];
     __shared__ __align__(8) uint64_t bar_tempty[2];
     __shared__ __align__(8) uint64_t bar_done;
+    __shared__ __align__(8) uint64_t bar_never;  // test hook: initialised, never arrived on
     __shared__ uint32_t tmem_sh;
     __shared__ int abort_sh;
     __shared__ int produced_sh, consumed_sh;
@@ -410,7 +517,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const uint32_t stageA = TC_ROWS * SW;
     const uint32_t stageB = (uint32_t)a.npad * SW;
     const uint32_t stage_bytes = PA * stageA + PB * stageB;
-    const uint32_t tx_bytes = (uint32_t)(PA * a.rows * SW) + PB * stageB;
+    constexpr bool kGradable = PA == 2 && PB == 2;  // the degree grading applies to the 2 x 2-term products
 
     // M2L: the 8 parity classes of one brick run side by side, so CTAs resident
     // at the same time read overlapping shifted bricks, which stay in L2
@@ -420,6 +527,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int o_begin = grp * a.per_group;
     const int o_end = o_begin + a.per_group < a.n_off ? o_begin + a.per_group : a.n_off;
     const int nloc = o_end > o_begin ? o_end - o_begin : 0;
+    const bool has_l2l = a.mode == 0 && a.n_off > a.n_il && a.n_il >= o_begin && a.n_il < o_end;
+    const AccGroups groups(nloc, has_l2l, a.acc_group);
     const int x0 = (tile % a.tiles_x) * a.bx;
     const int y0 = ((tile / a.tiles_x) % a.tiles_y) * a.by;
     const int z0 = (tile / (a.tiles_x * a.tiles_y)) * a.bz;
@@ -436,6 +545,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             mbar_init(smem_u32(&bar_tempty[b]), 4);  // one arrival per epilogue warp
         }
         mbar_init(smem_u32(&bar_done), 1);
+        mbar_init(smem_u32(&bar_never), 1);
         abort_sh = 0;
         produced_sh = 0;
         consumed_sh = 0;
@@ -462,21 +572,41 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             int it = 0, s = 0;
             uint32_t round = 0;
             bool ok = true;
-            // all K chunks of one offset: A from maps `src` at (c1, c2, c3), B at `slot`
-            auto load_offset = [&](const CUtensorMap *const *src, int c1, int c2, int c3, int slot) {
-                for (int kc = 0; kc < a.kchunks && ok; ++kc) {
-                    if (it >= a.stages && !mbar_wait(smem_u32(&bar_empty[s]), (round & 1u) ^ 1u, abort_flag)) {
+            // all K chunks of one offset: A from maps `src` at (c1, c2, c3), B at operator slot `oslot`; a
+            // graded (M2L) offset copies only the terms its chunk's products read
+            auto load_offset = [&](const CUtensorMap *const *src, int c1, int c2, int c3, int oslot, bool graded) {
+                for (int kc = 0; kc < a.kchunks && ok;) {
+                    if (it >= a.stages &&
+                        !mbar_wait(smem_u32(&bar_empty[s]), (round & 1u) ^ 1u, abort_flag, a.wait_ns)) {
                         ok = false;
                         break;
                     }
                     const uint32_t full = smem_u32(&bar_full[s]);
-                    mbar_expect_tx(full, tx_bytes);
                     const uint32_t base = smem0 + (uint32_t)s * stage_bytes;
+                    const int nkc = (kGradable && graded) ? stage_chunks(a.gchunks, kc, a.kchunks) : 1;
+                    if (nkc == 2) {  // two x0 y0 chunks: A0 and B0 of chunk kc + t in term place t
+                        mbar_expect_tx(full, 2u * ((uint32_t)(a.rows * SW) + stageB));
 #pragma unroll
-                    for (int i = 0; i < PA; ++i) tma_load_4d(base + i * stageA, src[i], full, kc * KCH, c1, c2, c3);
+                        for (int t = 0; t < 2; ++t) {
+                            tma_load_4d(base + t * stageA, src[0], full, (kc + t) * KCH, c1, c2, c3);
+                            tma_load_3d(base + PA * stageA + t * stageB, mB[0], full, (kc + t) * KCH, 0, oslot);
+                        }
+                    } else {
+                        int na = PA, nb = PB;
+                        if (kGradable && graded) {
+                            const int np = chunk_products(a.gchunks, kc);
+                            na = np == 3 ? 2 : 1;
+                            nb = np >= 2 ? 2 : 1;
+                        }
+                        mbar_expect_tx(full, (uint32_t)(na * a.rows * SW) + (uint32_t)nb * stageB);
 #pragma unroll
-                    for (int j = 0; j < PB; ++j)
-                        tma_load_3d(base + PA * stageA + j * stageB, mB[j], full, kc * KCH, 0, slot);
+                        for (int i = 0; i < PA; ++i)
+                            if (i < na) tma_load_4d(base + i * stageA, src[i], full, kc * KCH, c1, c2, c3);
+#pragma unroll
+                        for (int j = 0; j < PB; ++j)
+                            if (j < nb) tma_load_3d(base + PA * stageA + j * stageB, mB[j], full, kc * KCH, 0, oslot);
+                    }
+                    kc += nkc;
                     ++it;
                     if (++s == a.stages) {
                         s = 0;
@@ -498,14 +628,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                             const int sx = cx + dx, sy = cy + dy, sz = cz + dz;
                             const int scls = (sx & 1) | ((sy & 1) << 1) | ((sz & 1) << 2);
                             load_offset(mA, x0 + (sx >> 1) + w, y0 + (sy >> 1) + w, scls * np2 + z0 + (sz >> 1) + w,
-                                        off_slot(dx, dy, dz, w));
+                                        off_slot(dx, dy, dz, w), a.gchunks != 0u);
                         }
                 // fused L2L: the parents' local expansions (natural order, no halo)
                 if (ok && a.n_off > a.n_il && a.n_il >= o_begin && a.n_il < o_end)
-                    load_offset(mL, x0, y0, z0, a.noff + 8 + cls);
+                    load_offset(mL, x0, y0, z0, a.noff + 8 + cls, false);
             } else {
                 for (int o = o_begin; o < o_end && ok; ++o)
-                    load_offset(mA, x0 + a.ws, y0 + a.ws, o * a.src_np2 + z0 + a.ws, a.noff + o);
+                    load_offset(mA, x0 + a.ws, y0 + a.ws, o * a.src_np2 + z0 + a.ws, a.noff + o, false);
             }
             produced_sh = it;
             if (!ok) {
@@ -516,42 +646,60 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         __syncwarp();
     } else if (warp == 1) {
         if (lane == 0) {
-            // ---------------- MMA issuer: one fresh accumulator per offset
+            // ---------------- MMA issuer: one fresh accumulator per group of offsets
             using PR = Products<PA, PB>;
             int it = 0, s = 0;
             uint32_t round = 0;
-            bool ok = true;
-            for (int o = 0; o < nloc && ok; ++o) {
-                const int acc = o & 1;
-                const uint32_t use = (uint32_t)(o >> 1);
-                if (o >= 2 && !mbar_wait(smem_u32(&bar_tempty[acc]), (use - 1u) & 1u, abort_flag)) {
+            // the test hook makes this thread's first wait run out (its budget), as a lost copy would
+            bool ok = !(a.inject_stall && !mbar_wait(smem_u32(&bar_never), 0, abort_flag, a.wait_ns));
+            for (int g = 0; g < groups.ng && ok; ++g) {
+                const int acc = g & 1;
+                const uint32_t use = (uint32_t)(g >> 1);
+                if (g >= 2 && !mbar_wait(smem_u32(&bar_tempty[acc]), (use - 1u) & 1u, abort_flag, a.wait_ns)) {
                     ok = false;
                     break;
                 }
                 fence_after();
                 const uint32_t tmem_d = tmem + (uint32_t)(acc * 256);
-                for (int kc = 0; kc < a.kchunks; ++kc) {
-                    if (!mbar_wait(smem_u32(&bar_full[s]), round & 1u, abort_flag)) {
-                        ok = false;
-                        break;
-                    }
-                    fence_after();
-                    const uint32_t base = smem0 + (uint32_t)s * stage_bytes;
-#pragma unroll
-                    for (int pr = 0; pr < PR::n; ++pr) {
-#pragma unroll
-                        for (int k16 = 0; k16 < K16; ++k16) {
-                            if (K16 * kc + k16 >= a.ksteps) continue;  // zero fill beyond K
-                            const uint64_t ad = sdesc<SW>(base + PR::a(pr) * stageA + k16 * 32);
-                            const uint64_t bd = sdesc<SW>(base + PA * stageA + PR::b(pr) * stageB + k16 * 32);
-                            mma_bf16(tmem_d, ad, bd, a.idesc, (kc | pr | k16) != 0 ? 1u : 0u);
+                bool first = true;  // the group's first MMA overwrites the accumulator
+                for (int o = groups.begin(g); o < groups.end(g) && ok; ++o) {
+                    const bool graded = kGradable && a.gchunks != 0u && a.mode == 0 && o_begin + o < a.n_il;
+                    for (int kc = 0; kc < a.kchunks;) {
+                        if (!mbar_wait(smem_u32(&bar_full[s]), round & 1u, abort_flag, a.wait_ns)) {
+                            ok = false;
+                            break;
                         }
-                    }
-                    mma_commit(smem_u32(&bar_empty[s]));
-                    ++it;
-                    if (++s == a.stages) {
-                        s = 0;
-                        ++round;
+                        fence_after();
+                        const uint32_t base = smem0 + (uint32_t)s * stage_bytes;
+                        const int nk = a.ksteps - K16 * kc < K16 ? a.ksteps - K16 * kc : K16;
+                        const int np = graded ? chunk_products(a.gchunks, kc) : PR::n;
+                        const int nkc = graded ? stage_chunks(a.gchunks, kc, a.kchunks) : 1;
+                        if constexpr (kGradable) {
+                            if (nkc == 2) {
+                                const int nk1 = a.ksteps - K16 * (kc + 1) < K16 ? a.ksteps - K16 * (kc + 1) : K16;
+                                issue_merged<K16, SW, false>(tmem_d, base, base + PA * stageA, stageA, stageB, nk1,
+                                                             a.idesc, first);
+                            } else if (np == 1)
+                                issue_chunk<1, PR, K16, SW, false>(tmem_d, base, base + PA * stageA, stageA, stageB, nk,
+                                                                   a.idesc, first);
+                            else if (np == 2)
+                                issue_chunk<2, PR, K16, SW, false>(tmem_d, base, base + PA * stageA, stageA, stageB, nk,
+                                                                   a.idesc, first);
+                            else
+                                issue_chunk<PR::n, PR, K16, SW, false>(tmem_d, base, base + PA * stageA, stageA, stageB,
+                                                                       nk, a.idesc, first);
+                        } else {
+                            issue_chunk<PR::n, PR, K16, SW, false>(tmem_d, base, base + PA * stageA, stageA, stageB, nk,
+                                                                   a.idesc, first);
+                        }
+                        first = false;
+                        kc += nkc;
+                        mma_commit(smem_u32(&bar_empty[s]));
+                        ++it;
+                        if (++s == a.stages) {
+                            s = 0;
+                            ++round;
+                        }
                     }
                 }
                 if (ok) mma_commit(smem_u32(&bar_tfull[acc]));
@@ -565,7 +713,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         __syncwarp();
     } else {
-        // ---------------- epilogue warps: drain each offset's accumulator into FP32 registers
+        // ---------------- epilogue warps: drain each group's accumulator into FP32 registers
         const int quad = warp & 3;
         const int row = quad * 32 + lane;
         // fused L2L offset: its A planes carry the gain gL instead of gM
@@ -575,28 +723,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
         for (int i = 0; i < NCH * 16; ++i) Lr[i] = 0.f;
         bool ok = true;
-        for (int o = 0; o < nloc; ++o) {
-            const int acc = o & 1;
-            const uint32_t use = (uint32_t)(o >> 1);
-            if (!mbar_wait(smem_u32(&bar_tfull[acc]), use & 1u, abort_flag)) {
+        for (int g = 0; g < groups.ng; ++g) {
+            const int acc = g & 1;
+            const uint32_t use = (uint32_t)(g >> 1);
+            if (!mbar_wait(smem_u32(&bar_tfull[acc]), use & 1u, abort_flag, a.wait_ns)) {
                 ok = false;
                 break;
             }
             fence_after();
-            const float fac = (a.mode == 0 && o_begin + o == a.n_il) ? l2l_fac : 1.f;
-            const uint32_t taddr = tmem + (uint32_t)(acc * 256) + ((uint32_t)(quad * 32) << 16);
-#pragma unroll
-            for (int c = 0; c < NCH; ++c) {
-                uint32_t r[16];
-                tmem_ld16(taddr + (uint32_t)(c * 16), r);
-                tmem_wait_ld();
-#pragma unroll
-                for (int j = 0; j < 16; ++j) Lr[c * 16 + j] = fmaf(__uint_as_float(r[j]), fac, Lr[c * 16 + j]);
-            }
+            const float fac = (has_l2l && g == groups.ng - 1) ? l2l_fac : 1.f;
+            drain_accumulator<NCH>(tmem + (uint32_t)(acc * 256) + ((uint32_t)(quad * 32) << 16), fac, Lr);
             fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(&bar_tempty[acc]));
         }
+        float mx = 0.f;  // largest |out_i sx(i)| of this thread's row (a.amax_out)
         if (!ok) {
             abort_sh = 1;
             if (lane == 0) atomicOr(a.err, ERRF_TIMEOUT);
@@ -622,12 +763,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const float g = pow2f(-gain_m_exp(*a.amax) - GAIN_T_EXP);
 #pragma unroll
                 for (int i = 0; i < NCH * 16; ++i)
-                    if (i < a.nc) dst[i] = Lr[i] * (__ldg(a.post + i) * g);
+                    if (i < a.nc) {
+                        const float v = Lr[i] * (__ldg(a.post + i) * g);
+                        dst[i] = v;
+                        if (a.amax_out) mx = fmaxf(mx, fabsf(v * __ldg(a.sx + i)));
+                    }
             } else {
 #pragma unroll
                 for (int i = 0; i < NCH * 16; ++i)
                     if (i < a.nc) dst[i] = Lr[i];
             }
+        }
+        if (a.amax_out) {  // the whole warp is here
+            for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            if (lane == 0 && mx > 0.f) atomicMax(a.amax_out, __float_as_uint(mx));
         }
     }
 
@@ -688,7 +837,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TC_THREADS, 1)
     const uint32_t stageA = TC_ROWS * SW;
     const uint32_t stageB = halfN * SW;
     const uint32_t stage_bytes = PA * stageA + PB * stageB;
-    const uint32_t tx_bytes = 2u * ((uint32_t)(PA * a.rows * SW) + PB * stageB);  // both CTAs' copies
 
     const int pair = blockIdx.x >> 1;
     const int grp = pair % a.groups;
@@ -697,6 +845,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TC_THREADS, 1)
     const int o_begin = grp * a.per_group;
     const int o_end = o_begin + a.per_group < a.n_off ? o_begin + a.per_group : a.n_off;
     const int nloc = o_end > o_begin ? o_end - o_begin : 0;
+    const bool has_l2l = a.n_off > a.n_il && a.n_il >= o_begin && a.n_il < o_end;
+    const AccGroups groups(nloc, has_l2l, a.acc_group);
     const int x0 = (tile % a.tiles_x) * a.bx;
     const int y0 = ((tile / a.tiles_x) % a.tiles_y) * a.by;
     const int z0 = (tile / (a.tiles_x * a.tiles_y)) * a.bz;
@@ -738,23 +888,45 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TC_THREADS, 1)
             int it = 0, s = 0;
             uint32_t round = 0;
             bool ok = true;
-            auto load_offset = [&](const CUtensorMap *const *src, int c1, int c2, int c3, int slot) {
-                for (int kc = 0; kc < a.kchunks && ok; ++kc) {
-                    if (it >= a.stages && !mbar_wait_cluster(smem_u32(&bar_empty[s]), (round & 1u) ^ 1u, abort_flag)) {
+            auto load_offset = [&](const CUtensorMap *const *src, int c1, int c2, int c3, int oslot, bool graded) {
+                for (int kc = 0; kc < a.kchunks && ok;) {
+                    if (it >= a.stages &&
+                        !mbar_wait_cluster(smem_u32(&bar_empty[s]), (round & 1u) ^ 1u, abort_flag, a.wait_ns)) {
                         ok = false;
                         break;
                     }
                     const uint32_t full_local = smem_u32(&bar_full[s]);
-                    if (leader) mbar_expect_tx(full_local, tx_bytes);
                     const uint32_t full = map_shared(full_local, 0);
                     const uint32_t base = smem0 + (uint32_t)s * stage_bytes;
+                    const int nkc = graded ? stage_chunks(a.gchunks, kc, a.kchunks) : 1;
+                    if (nkc == 2) {  // two x0 y0 chunks: A0 and B0 of chunk kc + t in term place t
+                        // the leader's barrier counts both CTAs' copies (the same boxes in each)
+                        if (leader) mbar_expect_tx(full_local, 2u * 2u * ((uint32_t)(a.rows * SW) + stageB));
 #pragma unroll
-                    for (int i = 0; i < PA; ++i)
-                        tma_load_4d_pair(base + i * stageA, src[i], full, kc * KCH, c1, c2, c3);
+                        for (int t = 0; t < 2; ++t) {
+                            tma_load_4d_pair(base + t * stageA, src[0], full, (kc + t) * KCH, c1, c2, c3);
+                            tma_load_3d_pair(base + PA * stageA + t * stageB, mB[0], full, (kc + t) * KCH,
+                                             (int)(rank * halfN), oslot);
+                        }
+                    } else {
+                        int na = PA, nb = PB;
+                        if (graded) {
+                            const int np = chunk_products(a.gchunks, kc);
+                            na = np == 3 ? 2 : 1;
+                            nb = np >= 2 ? 2 : 1;
+                        }
+                        if (leader)
+                            mbar_expect_tx(full_local, 2u * ((uint32_t)(na * a.rows * SW) + (uint32_t)nb * stageB));
 #pragma unroll
-                    for (int j = 0; j < PB; ++j)
-                        tma_load_3d_pair(base + PA * stageA + j * stageB, mB[j], full, kc * KCH,
-                                         (int)(rank * halfN), slot);
+                        for (int i = 0; i < PA; ++i)
+                            if (i < na) tma_load_4d_pair(base + i * stageA, src[i], full, kc * KCH, c1, c2, c3);
+#pragma unroll
+                        for (int j = 0; j < PB; ++j)
+                            if (j < nb)
+                                tma_load_3d_pair(base + PA * stageA + j * stageB, mB[j], full, kc * KCH,
+                                                 (int)(rank * halfN), oslot);
+                    }
+                    kc += nkc;
                     ++it;
                     if (++s == a.stages) {
                         s = 0;
@@ -773,10 +945,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TC_THREADS, 1)
                         const int sx = cx + dx, sy = cy + dy, sz = cz + dz;
                         const int scls = (sx & 1) | ((sy & 1) << 1) | ((sz & 1) << 2);
                         load_offset(mA, x0 + (sx >> 1) + w, y0 + (sy >> 1) + w, scls * np2 + z0 + (sz >> 1) + w,
-                                    off_slot(dx, dy, dz, w));
+                                    off_slot(dx, dy, dz, w), a.gchunks != 0u);
                     }
             if (ok && a.n_off > a.n_il && a.n_il >= o_begin && a.n_il < o_end)
-                load_offset(mL, x0, y0, z0, a.noff + 8 + cls);
+                load_offset(mL, x0, y0, z0, a.noff + 8 + cls, false);
             if (!ok) {
                 abort_sh = 1;
                 atomicOr(a.err, ERRF_TIMEOUT);
@@ -789,36 +961,49 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TC_THREADS, 1)
             int s = 0;
             uint32_t round = 0;
             bool ok = true;
-            for (int o = 0; o < nloc && ok; ++o) {
-                const int acc = o & 1;
-                const uint32_t use = (uint32_t)(o >> 1);
-                if (o >= 2 && !mbar_wait_cluster(smem_u32(&bar_tempty[acc]), (use - 1u) & 1u, abort_flag)) {
+            for (int g = 0; g < groups.ng && ok; ++g) {
+                const int acc = g & 1;
+                const uint32_t use = (uint32_t)(g >> 1);
+                if (g >= 2 &&
+                    !mbar_wait_cluster(smem_u32(&bar_tempty[acc]), (use - 1u) & 1u, abort_flag, a.wait_ns)) {
                     ok = false;
                     break;
                 }
                 fence_after();
                 const uint32_t tmem_d = tmem + (uint32_t)(acc * 256);
-                for (int kc = 0; kc < a.kchunks; ++kc) {
-                    if (!mbar_wait_cluster(smem_u32(&bar_full[s]), round & 1u, abort_flag)) {
-                        ok = false;
-                        break;
-                    }
-                    fence_after();
-                    const uint32_t base = smem0 + (uint32_t)s * stage_bytes;
-#pragma unroll
-                    for (int pr = 0; pr < PR::n; ++pr) {
-#pragma unroll
-                        for (int k16 = 0; k16 < K16; ++k16) {
-                            if (K16 * kc + k16 >= a.ksteps) continue;  // zero fill beyond K
-                            const uint64_t ad = sdesc<SW>(base + PR::a(pr) * stageA + k16 * 32);
-                            const uint64_t bd = sdesc<SW>(base + PA * stageA + PR::b(pr) * stageB + k16 * 32);
-                            mma_f16_pair(tmem_d, ad, bd, a.idesc, (kc | pr | k16) != 0 ? 1u : 0u);
+                bool first = true;  // the group's first MMA overwrites the accumulator
+                for (int o = groups.begin(g); o < groups.end(g) && ok; ++o) {
+                    const bool graded = a.gchunks != 0u && o_begin + o < a.n_il;
+                    for (int kc = 0; kc < a.kchunks;) {
+                        if (!mbar_wait_cluster(smem_u32(&bar_full[s]), round & 1u, abort_flag, a.wait_ns)) {
+                            ok = false;
+                            break;
                         }
-                    }
-                    mma_commit_pair(smem_u32(&bar_empty[s]));
-                    if (++s == a.stages) {
-                        s = 0;
-                        ++round;
+                        fence_after();
+                        const uint32_t base = smem0 + (uint32_t)s * stage_bytes;
+                        const int nk = a.ksteps - K16 * kc < K16 ? a.ksteps - K16 * kc : K16;
+                        const int np = graded ? chunk_products(a.gchunks, kc) : PR::n;
+                        const int nkc = graded ? stage_chunks(a.gchunks, kc, a.kchunks) : 1;
+                        if (nkc == 2) {
+                            const int nk1 = a.ksteps - K16 * (kc + 1) < K16 ? a.ksteps - K16 * (kc + 1) : K16;
+                            issue_merged<K16, SW, true>(tmem_d, base, base + PA * stageA, stageA, stageB, nk1, a.idesc,
+                                                        first);
+                        } else if (np == 1)
+                            issue_chunk<1, PR, K16, SW, true>(tmem_d, base, base + PA * stageA, stageA, stageB, nk,
+                                                              a.idesc, first);
+                        else if (np == 2)
+                            issue_chunk<2, PR, K16, SW, true>(tmem_d, base, base + PA * stageA, stageA, stageB, nk,
+                                                              a.idesc, first);
+                        else
+                            issue_chunk<PR::n, PR, K16, SW, true>(tmem_d, base, base + PA * stageA, stageA, stageB, nk,
+                                                                  a.idesc, first);
+                        first = false;
+                        kc += nkc;
+                        mma_commit_pair(smem_u32(&bar_empty[s]));
+                        if (++s == a.stages) {
+                            s = 0;
+                            ++round;
+                        }
                     }
                 }
                 if (ok) mma_commit_pair(smem_u32(&bar_tfull[acc]));
@@ -839,24 +1024,16 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
         for (int i = 0; i < NCH * 16; ++i) Lr[i] = 0.f;
         bool ok = true;
-        for (int o = 0; o < nloc; ++o) {
-            const int acc = o & 1;
-            const uint32_t use = (uint32_t)(o >> 1);
-            if (!mbar_wait_cluster(smem_u32(&bar_tfull[acc]), use & 1u, abort_flag)) {
+        for (int g = 0; g < groups.ng; ++g) {
+            const int acc = g & 1;
+            const uint32_t use = (uint32_t)(g >> 1);
+            if (!mbar_wait_cluster(smem_u32(&bar_tfull[acc]), use & 1u, abort_flag, a.wait_ns)) {
                 ok = false;
                 break;
             }
             fence_after();
-            const float fac = (o_begin + o == a.n_il) ? l2l_fac : 1.f;
-            const uint32_t taddr = tmem + (uint32_t)(acc * 256) + ((uint32_t)(quad * 32) << 16);
-#pragma unroll
-            for (int c = 0; c < NCH; ++c) {
-                uint32_t r[16];
-                tmem_ld16(taddr + (uint32_t)(c * 16), r);
-                tmem_wait_ld();
-#pragma unroll
-                for (int j = 0; j < 16; ++j) Lr[c * 16 + j] = fmaf(__uint_as_float(r[j]), fac, Lr[c * 16 + j]);
-            }
+            const float fac = (has_l2l && g == groups.ng - 1) ? l2l_fac : 1.f;
+            drain_accumulator<NCH>(tmem + (uint32_t)(acc * 256) + ((uint32_t)(quad * 32) << 16), fac, Lr);
             fence_before();
             __syncwarp();
             if (lane == 0) {
@@ -865,6 +1042,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TC_THREADS, 1)
                 else mbar_arrive_remote(map_shared(te, 0));
             }
         }
+        float mx = 0.f;  // largest |out_i sx(i)| of this thread's row (a.amax_out)
         if (!ok) {
             abort_sh = 1;
             if (lane == 0) atomicOr(a.err, ERRF_TIMEOUT);
@@ -876,7 +1054,15 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TC_THREADS, 1)
             const float g = pow2f(-gain_m_exp(*a.amax) - GAIN_T_EXP);
 #pragma unroll
             for (int i = 0; i < NCH * 16; ++i)
-                if (i < a.nc) dst[i] = Lr[i] * (__ldg(a.post + i) * g);
+                if (i < a.nc) {
+                    const float v = Lr[i] * (__ldg(a.post + i) * g);
+                    dst[i] = v;
+                    if (a.amax_out) mx = fmaxf(mx, fabsf(v * __ldg(a.sx + i)));
+                }
+        }
+        if (a.amax_out) {  // the whole warp is here
+            for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            if (lane == 0 && mx > 0.f) atomicMax(a.amax_out, __float_as_uint(mx));
         }
     }
 
@@ -1032,13 +1218,61 @@ __global__ void k_split_ops(int noff, const double *__restrict__ T, const double
     }
 }
 
-// L = sum over the offset groups, in group order
-__global__ void k_group_sum(int64_t n, int groups, const float *__restrict__ part, float *__restrict__ L)
+// L = sum over the offset groups, in group order; with amax (fp16 split) the largest |L_e sx(e mod nc)|
+// is folded into *amax
+__global__ void k_group_sum(int64_t n, int groups, const float *__restrict__ part, float *__restrict__ L, int nc,
+                            const float *__restrict__ sx, unsigned *__restrict__ amax)
 {
+    float mx = 0.f;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
         float s = 0.f;
         for (int g = 0; g < groups; ++g) s += part[(int64_t)g * n + e];
         L[e] = s;
+        if (amax) mx = fmaxf(mx, fabsf(s * __ldg(sx + (int)(e % nc))));
+    }
+    if (amax) {
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if ((threadIdx.x & 31) == 0 && mx > 0.f) atomicMax(amax, __float_as_uint(mx));
+    }
+}
+
+// fp16 split: FP32 class-layout moments -> the two balanced fp16 halo planes, 8 coefficients per thread
+// (16-byte stores per plane); rows kp wide, zero beyond nc
+__global__ void k_split_halo16(const float *__restrict__ M, int np, int hw, int nc, int kp, const float *__restrict__ s,
+                               const unsigned *__restrict__ amax, uint16_t *__restrict__ planes, size_t part_elems)
+{
+    const int np2 = np + 2 * hw;
+    const int G = kp / 8;
+    const int64_t total = 8 * (int64_t)np2 * np2 * np2 * G;
+    const float g = pow2f(gain_m_exp(*amax));
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t cell = t / G;
+        const int k0 = (int)(t - cell * G) * 8;
+        const int hx = (int)(cell % np2);
+        const int hy = (int)((cell / np2) % np2);
+        const int hzc = (int)(cell / ((int64_t)np2 * np2));
+        const int c = hzc / np2, hz = hzc % np2;
+        const int px = ((hx - hw) % np + np) % np, py = ((hy - hw) % np + np) % np, pz = ((hz - hw) % np + np) % np;
+        const float *row = M + ((int64_t)c * np * np * np + px + (int64_t)np * (py + (int64_t)np * pz)) * nc;
+        uint32_t hi[4], lo[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            uint16_t h2[2], l2[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int k = k0 + 2 * i + u;
+                const float v = k < nc ? row[k] * (__ldg(s + k) * g) : 0.f;
+                const __half t0 = __float2half_rn(v);
+                const __half t1 = __float2half_rn(v - __half2float(t0));
+                h2[u] = __half_as_ushort(t0);
+                l2[u] = __half_as_ushort(t1);
+            }
+            hi[i] = (uint32_t)h2[0] | ((uint32_t)h2[1] << 16);
+            lo[i] = (uint32_t)l2[0] | ((uint32_t)l2[1] << 16);
+        }
+        uint16_t *out = planes + cell * kp + k0;
+        *reinterpret_cast<uint4 *>(out) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+        *reinterpret_cast<uint4 *>(out + part_elems) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
     }
 }
 
@@ -1172,12 +1406,30 @@ void fill_common(const Plan &P, const TcState *S, int pa, int pb, TcArgs &a)
     a.idesc = (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(S->npad >> 3) << 17) | ((uint32_t)(TC_ROWS >> 4) << 24);
     a.Lpart = S->Lpart;
     a.err = P.d_err;
+    a.amax_out = nullptr;
+    a.sx = nullptr;
+    a.acc_group = P.acc_group;
+    a.wait_ns = P.wait_ns;
+    a.inject_stall = P.inject_stall ? 1 : 0;
     a.src_np2 = 0;
     a.out_np = 0;
     a.amaxL = nullptr;
     a.ws = P.ws;
     a.n_il = n_il(P.ws);
     a.noff = noff(P.ws);
+    // degree grading of the fp16x2 M2L (FMM_OPT_M2L_GRADE), per K chunk: chunk kc holds input
+    // coefficients KCH kc .. KCH kc + KCH - 1, whose lowest degree is floor(sqrt(KCH kc))
+    a.gchunks = 0;
+    const int d2 = P.grade & 0xFF, d1 = (P.grade >> 8) & 0xFF;
+    if (S->f16 && pa == 2 && pb == 2 && (d2 > 0 || d1 > 0)) {
+        const int kch = kchunk_of(S->sw);
+        for (int kc = 0; kc < a.kchunks && kc < 16; ++kc) {
+            int lam = 0;
+            while ((lam + 1) * (lam + 1) <= kch * kc) ++lam;
+            const int np = (d1 > 0 && lam >= d1) ? 1 : (d2 > 0 && lam >= d2) ? 2 : 3;
+            if (np < 3) a.gchunks |= (uint32_t)np << (2 * kc);
+        }
+    }
 }
 
 }  // namespace
@@ -1334,21 +1586,44 @@ fmm_status tc_prepare(Plan &P)
     return FMM_OK;
 }
 
-// fp16 split: largest |M^ s| and the balanced halo planes of M[l]
-fmm_status tc_split_moments(Plan &P, int l)
+unsigned *tc_amax(Plan &P, int l)
+{
+    TcState *S = (TcState *)P.tc;
+    return S && S->f16 && l >= 0 && l <= P.d ? S->amax + l : nullptr;
+}
+
+fmm_status tc_clear_amax(Plan &P, int l)
+{
+    unsigned *a = tc_amax(P, l);
+    if (!a) return FMM_ERR_INTERNAL;
+    FMM_CUDA_TRY(cudaMemsetAsync(a, 0, sizeof(unsigned), P.stream));
+    return FMM_OK;
+}
+
+const float *tc_scale(const Plan &P)
+{
+    const TcState *S = (const TcState *)P.tc;
+    return S && S->f16 ? S->s32 : nullptr;
+}
+
+// fp16 split: the balanced halo planes of M[l]; the level's largest |M^ s| is computed first unless the
+// kernel that wrote M[l] folded it in already
+fmm_status tc_split_moments(Plan &P, int l, bool amax_ready)
 {
     TcState *S = (TcState *)P.tc;
     if (!S || !S->f16 || l < 1 || l > P.d) return FMM_ERR_INTERNAL;
     const int np = 1 << (l - 1);
     const int64_t np2 = np + 2 * P.ws;
     const int64_t ncell = (int64_t)8 * np * np * np;
-    const int64_t nhalo = 8 * np2 * np2 * np2;
-    FMM_CUDA_TRY(cudaMemsetAsync(S->amax + l, 0, sizeof(unsigned), P.stream));
-    k_absmax<<<(unsigned)((ncell + 7) / 8 < 1216 ? (ncell + 7) / 8 : 1216), 256, 0, P.stream>>>(
-        (const float *)P.M[l], ncell, P.nc, S->s32, S->amax + l);
-    FMM_LAUNCH_CHECK(P);
-    k_split_halo<true><<<(unsigned)((nhalo + 7) / 8 < 4864 ? (nhalo + 7) / 8 : 4864), 256, 0, P.stream>>>(
-        (const float *)P.M[l], np, P.ws, P.nc, S->kp, 2, S->s32, S->amax + l, S->planes[l], S->part_elems[l]);
+    if (!amax_ready) {
+        FMM_CUDA_TRY(cudaMemsetAsync(S->amax + l, 0, sizeof(unsigned), P.stream));
+        k_absmax<<<(unsigned)((ncell + 7) / 8 < 1216 ? (ncell + 7) / 8 : 1216), 256, 0, P.stream>>>(
+            (const float *)P.M[l], ncell, P.nc, S->s32, S->amax + l);
+        FMM_LAUNCH_CHECK(P);
+    }
+    const int64_t nthr = 8 * np2 * np2 * np2 * (S->kp / 8);
+    k_split_halo16<<<(unsigned)((nthr + 255) / 256 < 8 * 1216 ? (nthr + 255) / 256 : 8 * 1216), 256, 0, P.stream>>>(
+        (const float *)P.M[l], np, P.ws, P.nc, S->kp, S->s32, S->amax + l, S->planes[l], S->part_elems[l]);
     FMM_LAUNCH_CHECK(P);
     return FMM_OK;
 }
@@ -1363,6 +1638,7 @@ fmm_status launch_m2m_tc(Plan &P, int l)
     TcArgs a;
     fill_common(P, S, S->pa, S->pb, a);
     a.mode = 1;
+    a.gchunks = 0;  // translations keep every product
     a.np = n;
     a.bx = S->bx[src];
     a.by = S->by[src];
@@ -1379,6 +1655,10 @@ fmm_status launch_m2m_tc(Plan &P, int l)
     a.L = (float *)P.M[l];
     a.post = S->s32inv;
     a.amax = S->amax + src;
+    // level l's largest |M^ s| (the gain of its planes) is folded in by whoever writes M[l]
+    FMM_CUDA_TRY(cudaMemsetAsync(S->amax + l, 0, sizeof(unsigned), P.stream));
+    a.amax_out = a.groups == 1 ? S->amax + l : nullptr;
+    a.sx = S->s32;
     TcKernel k = pick_kernel(S->pa, S->pb, S->npad / 16, S->sw);
     if (!k) return FMM_ERR_INTERNAL;
     const unsigned grid = (unsigned)a.tiles_per_class * (unsigned)a.groups;
@@ -1389,7 +1669,7 @@ fmm_status launch_m2m_tc(Plan &P, int l)
     if (a.groups > 1) {
         const int64_t cnt = (int64_t)n * n * n * P.nc;
         k_group_sum<<<(unsigned)((cnt + 255) / 256 < 2048 ? (cnt + 255) / 256 : 2048), 256, 0, P.stream>>>(
-            cnt, a.groups, S->Lpart, a.L);
+            cnt, a.groups, S->Lpart, a.L, P.nc, S->s32, S->amax + l);
         FMM_LAUNCH_CHECK(P);
     }
     return FMM_OK;
@@ -1406,15 +1686,17 @@ fmm_status launch_m2l_tc(Plan &P, int l, bool precise, bool split)
     int64_t np2 = np + 2 * P.ws;
     if (S->f16) {
         if (split) {
-            fmm_status st = tc_split_moments(P, l);
+            fmm_status st = tc_split_moments(P, l, false);
             if (st != FMM_OK) return st;
         }
-        // parent-level local expansion for the fused L2L
+        // parent-level local expansion for the fused L2L; its largest |L^ / s| was folded in by the level
+        // l - 1 launch (levels run in order), except at level 0 (the lattice operator's output)
         const int64_t ncl = (int64_t)np * np * np;
-        FMM_CUDA_TRY(cudaMemsetAsync(S->amaxL + l - 1, 0, sizeof(unsigned), P.stream));
-        k_absmax<<<(unsigned)((ncl + 7) / 8 < 1216 ? (ncl + 7) / 8 : 1216), 256, 0, P.stream>>>(
-            (const float *)P.L[l - 1], ncl, P.nc, S->s32inv, S->amaxL + l - 1);
-        FMM_LAUNCH_CHECK(P);
+        if (l == 1) {
+            FMM_CUDA_TRY(cudaMemsetAsync(S->amaxL, 0, sizeof(unsigned), P.stream));
+            k_absmax<<<1, 256, 0, P.stream>>>((const float *)P.L[0], 1, P.nc, S->s32inv, S->amaxL);
+            FMM_LAUNCH_CHECK(P);
+        }
         k_split_L<<<(unsigned)((ncl + 7) / 8 < 1216 ? (ncl + 7) / 8 : 1216), 256, 0, P.stream>>>(
             (const float *)P.L[l - 1], l - 1, P.nc, S->kp, S->s32inv, S->amaxL + l - 1, S->planesL,
             (size_t)ncl * S->kp);
@@ -1427,6 +1709,7 @@ fmm_status launch_m2l_tc(Plan &P, int l, bool precise, bool split)
     }
     TcArgs a;
     fill_common(P, S, pa, pb, a);
+    if (precise) a.gchunks = 0;  // the solute-only pass keeps every product
     a.mode = 0;
     a.np = np;
     a.bx = S->bx[l];
@@ -1443,6 +1726,11 @@ fmm_status launch_m2l_tc(Plan &P, int l, bool precise, bool split)
     a.post = S->f16 ? S->s32 : nullptr;
     a.amax = S->f16 ? S->amax + l : nullptr;
     a.amaxL = S->f16 ? S->amaxL + l - 1 : nullptr;
+    if (S->f16) {  // level l's largest |L^ / s|, for the fused L2L of level l + 1
+        FMM_CUDA_TRY(cudaMemsetAsync(S->amaxL + l, 0, sizeof(unsigned), P.stream));
+        a.amax_out = a.groups == 1 ? S->amaxL + l : nullptr;
+        a.sx = S->s32inv;
+    }
     unsigned grid = 8u * (unsigned)a.tiles_per_class * (unsigned)a.groups;
     // CTA pairs take two tiles of one class: an even number of full 128-row tiles per class
     const bool pair = S->f16 && P.tc_pair && a.rows == TC_ROWS && a.tiles_per_class % 2 == 0;
@@ -1470,7 +1758,7 @@ fmm_status launch_m2l_tc(Plan &P, int l, bool precise, bool split)
     if (a.groups > 1) {
         int64_t n = (int64_t)8 * np * np * np * P.nc;
         k_group_sum<<<(unsigned)((n + 255) / 256 < 2048 ? (n + 255) / 256 : 2048), 256, 0, P.stream>>>(
-            n, a.groups, S->Lpart, a.L);
+            n, a.groups, S->Lpart, a.L, P.nc, S->f16 ? S->s32inv : nullptr, S->f16 ? S->amaxL + l : nullptr);
         FMM_LAUNCH_CHECK(P);
     }
     return FMM_OK;

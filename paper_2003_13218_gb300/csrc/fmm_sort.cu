@@ -240,16 +240,19 @@ __global__ void k_bc_partial(int64_t N, const double *__restrict__ wpos, const d
     block_reduce_store<10>(acc, partial);
 }
 
-// energies over sorted particles: e_near, e_far, A, B, C, NF_uv
+// energies over sorted particles: e_near, e_far, A, B, C, NF_uv and (sc non-null) the soft-core near-field
+// pair sum and its lambda derivative
+constexpr int NQ_ENERGY = 8;
+
 template <typename T>
 __global__ void k_energy_partial(int64_t N, const Particle<T> *__restrict__ sp, const T *__restrict__ phi_nf,
                                  const T *__restrict__ phi_ff, const T *__restrict__ phi_u,
                                  const uint8_t *__restrict__ sol, const T *__restrict__ nfuv,
-                                 double *__restrict__ partial)
+                                 const double *__restrict__ sc, double *__restrict__ partial)
 {
-    double acc[6];
+    double acc[NQ_ENERGY];
 #pragma unroll
-    for (int k = 0; k < 6; ++k) acc[k] = 0.0;
+    for (int k = 0; k < NQ_ENERGY; ++k) acc[k] = 0.0;
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
         double qs = (double)sp[s].q;
         acc[0] += 0.5 * qs * (double)phi_nf[s];
@@ -259,12 +262,16 @@ __global__ void k_energy_partial(int64_t N, const Particle<T> *__restrict__ sp, 
                 acc[2] += qs * (double)phi_ff[s];
                 acc[3] += qs * (double)phi_u[s];
                 acc[5] += (double)nfuv[s];
+                if (sc) {
+                    acc[6] += sc[s];
+                    acc[7] += sc[N + s];
+                }
             } else {
                 acc[4] += qs * (double)phi_u[s];
             }
         }
     }
-    block_reduce_store<6>(acc, partial);
+    block_reduce_store<NQ_ENERGY>(acc, partial);
 }
 
 // block partials -> totals; blockDim.x == RED_THREADS: warp w takes the
@@ -291,16 +298,20 @@ __global__ void k_bc_final(const double *__restrict__ partial, int nb, double *_
 
 // Combine into the terms of Eq. Velecfull and Eq. FMMcalc.
 // out layout: [0..9] moments (Q, mu, S2, Qu, mu_u, S2u), [10..15] energy parts,
-// [16..21] terms (near, far, charged, quad, dipole, total), [22..28] uv terms.
+// [16..21] terms (near, far, charged, quad, dipole, total), [22..28] uv terms,
+// [29..30] soft-core near-field sum and its lambda derivative; [40..47] scratch.
 // vacuum: the boundary at infinity is vacuum (App. D): the dipole surface term
 // -(2 pi / 3V) mu.mu that gives the conducting boundary is left out, and so is
 // its solute-solvent cross term -(4 pi / 3V) mu_u.mu_v
 __global__ void k_energy_final(const double *__restrict__ partial, int nb, double *__restrict__ out, double box,
                                double kappa, int with_uv, int vacuum)
 {
-    final_sum<6>(partial, nb, out + 10);
+    final_sum<NQ_ENERGY>(partial, nb, out + 40);
     __syncthreads();
     if (threadIdx.x != 0) return;
+    for (int k = 0; k < 6; ++k) out[10 + k] = out[40 + k];
+    out[29] = out[46];
+    out[30] = out[47];
     const double PI = 3.14159265358979323846;
     double V = box * box * box;
     double Q = out[0], mx = out[1], my = out[2], mz = out[3], S2 = out[4];
@@ -444,17 +455,18 @@ fmm_status launch_bc_moments(Plan &P, const double *q, const uint8_t *sol)
 fmm_status launch_energy_reduce(Plan &P, bool with_uv)
 {
     double *part = P.red_partial + RED_BLOCKS * 10 * 2;
+    const double *sc = with_uv && P.sc_c > 0 ? P.sc_out : nullptr;
     const uint8_t *sol = with_uv ? P.sorted_sol : nullptr;
     if (P.precision == FMM_PREC_FP64) {
         const double *nfuv = (const double *)P.phi_nf + P.N;  // second half of the phi_nf buffer
         k_energy_partial<double><<<RED_BLOCKS, RED_THREADS, 0, P.stream>>>(
             P.N, (const Particle<double> *)P.sorted, (const double *)P.phi_nf, (const double *)P.phi_ff,
-            (const double *)P.phi_u, sol, nfuv, part);
+            (const double *)P.phi_u, sol, nfuv, sc, part);
     } else {
         const float *nfuv = (const float *)P.phi_nf + P.N;
         k_energy_partial<float><<<RED_BLOCKS, RED_THREADS, 0, P.stream>>>(
             P.N, (const Particle<float> *)P.sorted, (const float *)P.phi_nf, (const float *)P.phi_ff,
-            (const float *)P.phi_u, sol, nfuv, part);
+            (const float *)P.phi_u, sol, nfuv, sc, part);
     }
     FMM_LAUNCH_CHECK(P);
     double kappa = P.kappa > 0 ? P.kappa : 2.0 / P.box;
@@ -493,6 +505,6 @@ fmm_status launch_potentials_out(Plan &P, double *potentials)
     return FMM_OK;
 }
 
-size_t reduction_scratch_doubles() { return (size_t)RED_BLOCKS * 16 * 2; }
+size_t reduction_scratch_doubles() { return (size_t)RED_BLOCKS * 20 * 2; }
 
 }  // namespace fmm

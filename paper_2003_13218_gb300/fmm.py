@@ -23,6 +23,10 @@ FMM_OPT_WS, FMM_OPT_PRECISION, FMM_OPT_KAPPA, FMM_OPT_M2L_SPLIT, FMM_OPT_STREAM,
 FMM_OPT_M2L_PAIR = 7
 FMM_OPT_BOUNDARY = 8
 FMM_OPT_OVERLAP = 9
+FMM_OPT_M2L_GRADE = 10
+FMM_OPT_M2L_ACC_GROUP = 11
+FMM_OPT_SOFTCORE, FMM_OPT_SOFTCORE_LAMBDA, FMM_OPT_SOFTCORE_ALPHA = 12, 13, 14
+FMM_OPT_WAIT_BUDGET_NS, FMM_OPT_INJECT_STALL = 15, 16
 BOUNDARY = {"conducting": 0, "vacuum": 1}
 PRECISION = {"fp64": 0, "mixed": 1}
 SPLIT = {"bf16x3": 0, "bf16x2": 1, "fp32": 2, "bf16a2b3": 3, "fp16x2": 4}
@@ -45,7 +49,7 @@ class EnergyTerms(ctypes.Structure):
 
 
 class UVTerms(ctypes.Structure):
-    _fields_ = [(k, ctypes.c_double) for k in ("e_uv", "W", "A", "B", "C", "nf_uv", "bc_cross")]
+    _fields_ = [(k, ctypes.c_double) for k in ("e_uv", "W", "A", "B", "C", "nf_uv", "bc_cross", "nf_sc", "dnf_sc")]
 
     def asdict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -102,6 +106,8 @@ def load_library(path: str = LIB_PATH):
     L.fmm_batch_info.argtypes = [vp, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int), ctypes.POINTER(i64),
                                  ctypes.POINTER(i64)]
     L.fmm_batch_info.restype = c_int
+    L.fmm_batch_set_softcore.argtypes = [vp, c_int, dbl, dbl]
+    L.fmm_batch_set_softcore.restype = c_int
     L.fmm_batch_set_graph.argtypes = [vp, c_int]
     L.fmm_batch_set_graph.restype = c_int
     L.fmm_batch_destroy.argtypes = [vp]
@@ -134,7 +140,8 @@ class FMMPlan:
 
     def __init__(self, box: float, N: int, depth: int, p: int, precision: str = "fp64", kappa: float | None = None,
                  split: str = "fp16x2", timings: bool = False, m2l_pair: bool = True, boundary: str = "conducting",
-                 ws: int = 1, overlap: bool = True):
+                 ws: int = 1, overlap: bool = True, m2l_grade: tuple[int, int] | None = None,
+                 acc_group: int | None = None):
         self._lib = load_library()
         h = ctypes.c_void_p()
         _check(self._lib.fmm_plan_create(float(box), int(N), int(depth), int(p), ctypes.byref(h)), "fmm_plan_create")
@@ -156,10 +163,21 @@ class FMMPlan:
             self.set_option(FMM_OPT_BOUNDARY, BOUNDARY[boundary])
         if not overlap:
             self.set_option(FMM_OPT_OVERLAP, 0)
+        if m2l_grade is not None:  # (D2, D1): degrees from which the fp16x2 M2L drops a product / two
+            self.set_option(FMM_OPT_M2L_GRADE, int(m2l_grade[0]) | (int(m2l_grade[1]) << 8))
+        if acc_group is not None:  # offsets per TMEM accumulator drain of the tensor-core M2L
+            self.set_option(FMM_OPT_M2L_ACC_GROUP, int(acc_group))
         self.precision = precision
 
     def set_option(self, key: int, ival: int = 0, dval: float = 0.0):
         _check(self._lib.fmm_plan_set_option(self._h, int(key), int(ival), float(dval)), "fmm_plan_set_option")
+
+    def set_softcore(self, c: int, A: float = 0.0, lam: float = 0.0, alpha: float = 0.2):
+        """Soft-core solute-solvent near field (FMM_OPT_SOFTCORE): c = 0 turns it off."""
+        self.set_option(FMM_OPT_SOFTCORE, int(c), float(A))
+        if c > 0:
+            self.set_option(FMM_OPT_SOFTCORE_ALPHA, 0, float(alpha))
+            self.set_option(FMM_OPT_SOFTCORE_LAMBDA, 0, float(lam))
 
     def _bind_stream(self, *tensors):
         if any(isinstance(t, torch.Tensor) and t.is_cuda for t in tensors if t is not None):
@@ -296,6 +314,9 @@ class FMMBatch:
         _check(self._lib.fmm_batch_info(self._h, i, ctypes.byref(d), ctypes.byref(p), ctypes.byref(r),
                                         ctypes.byref(e)), "fmm_batch_info")
         return {"depth": d.value, "p": p.value, "replays": r.value, "enqueued": e.value}
+
+    def set_softcore(self, c: int, A: float = 0.0, alpha: float = 0.2):
+        _check(self._lib.fmm_batch_set_softcore(self._h, int(c), float(A), float(alpha)), "fmm_batch_set_softcore")
 
     def set_graph(self, enable: bool):
         _check(self._lib.fmm_batch_set_graph(self._h, 1 if enable else 0), "fmm_batch_set_graph")

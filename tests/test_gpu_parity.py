@@ -216,7 +216,8 @@ def test_tensor_core_m2l_matches_cuda_core_m2l(split, tol_e, tol_f):
     with the FP32 CUDA-core M2L, and both against the FP64 GPU path."""
     b = _sub_box(333333 // 64, 215.3 / 4)  # N = 15,625, d = 4
     d, p = 4, 12
-    t_tc, _, F_tc = _run(b.pos, b.q, b.L, d, p, precision="mixed", split=split)
+    # the split alone: every product, one accumulator per offset
+    t_tc, _, F_tc = _run(b.pos, b.q, b.L, d, p, precision="mixed", split=split, m2l_grade=(0, 0), acc_group=1)
     t_cc, _, F_cc = _run(b.pos, b.q, b.L, d, p, precision="mixed", split="fp32")
     t_64, _, F_64 = _run(b.pos, b.q, b.L, d, p)
     assert abs(t_tc["far"] - t_cc["far"]) <= tol_e * abs(t_64["total"])
@@ -368,3 +369,51 @@ def test_vacuum_boundary_differs_by_the_dipole_surface_term(precision):
     dF = -(4 * np.pi / (3 * V)) * b.q[:, None] * mu[None, :]
     assert np.max(np.abs((Fv - Fc) - dF)) <= 1e-9 * np.max(np.abs(Fc))
     assert abs((uvv["e_uv"] - uvc["e_uv"]) - 4 * np.pi / (3 * V) * mu_u @ (mu - mu_u)) <= 1e-12 * scale
+
+
+def test_clustered_charges_take_the_unstaged_near_field():
+    """Near field (Eq. EqNF) with charges packed into a few leaves: the row segments around the cluster
+    hold more particles than the staging capacity sized for the mean occupancy, so those blocks read
+    their neighbours from global memory; every block must still match the oracle (FP64, 1e-12)."""
+    L, N = 8.0, 2400
+    pos, q = boxes.random_charges(N, L, seed=21)
+    pos[: N // 2] = 0.7 + pos[: N // 2] / L * 1.1  # half the charges in a 1.1 A cube (about 1.5 leaves)
+    d, p = 3, 6
+    ref = oracle.fmm(pos, q, L, d, p)
+    for prec, tol_e, tol_f in (("fp64", 1e-12, 1e-10), ("mixed", 1e-6, 1e-5)):
+        terms, _, F = _run(pos, q, L, d, p, precision=prec)
+        assert abs(terms["near"] - ref["near"]) <= tol_e * (abs(ref["near"]) + abs(ref["total"])), prec
+        assert abs(terms["total"] - ref["total"]) <= tol_e * abs(ref["total"]), prec
+        assert _rms_rel(F, ref["forces"]) < tol_f, prec
+
+
+@pytest.mark.parametrize("grade,acc_group", [((0, 0), 1), ((0, 8), 1), ((0, 8), 4), ((4, 8), 8), ((0, 6), 2)])
+def test_graded_split_and_accumulation_groups_against_oracle(grade, acc_group):
+    """The degree-graded fp16x2 M2L (FMM_OPT_M2L_GRADE) and longer TMEM accumulation chains
+    (FMM_OPT_M2L_ACC_GROUP) stay within the mixed budget against the oracle (Eq. Lcoeffdef):
+    1e-6 relative energy, 1e-5 relative RMS force, at p = 12 on the 3k box (depth 3) and a
+    depth-4 box whose level-4 M2L runs on CTA pairs."""
+    b, d, _ = boxes.workload("mg_3k")
+    p = 12
+    ref = oracle.fmm(b.pos, b.q, b.L, d, p)
+    terms, _, F = _run(b.pos, b.q, b.L, d, p, precision="mixed", m2l_grade=grade, acc_group=acc_group)
+    assert abs(terms["total"] - ref["total"]) <= 1e-6 * abs(ref["total"])
+    assert _rms_rel(F, ref["forces"]) < 1e-5
+    b2 = boxes.ion_in_water(333333 // 64, "Na", seed=5, L=215.3 / 4)  # N = 15,625
+    ref2 = oracle.fmm(b2.pos, b2.q, b2.L, 4, 8)
+    t2, _, F2 = _run(b2.pos, b2.q, b2.L, 4, 8, precision="mixed", m2l_grade=grade, acc_group=acc_group)
+    assert abs(t2["total"] - ref2["total"]) <= 1e-6 * abs(ref2["total"])
+    assert _rms_rel(F2, ref2["forces"]) < 1e-5
+
+
+def test_grade_and_group_options_are_validated():
+    from paper_2003_13218_gb300.fmm import FMMError, FMM_OPT_M2L_ACC_GROUP, FMM_OPT_M2L_GRADE
+    plan = _plan(2.0, 10, 2, 4)
+    for key, bad in ((FMM_OPT_M2L_GRADE, -1), (FMM_OPT_M2L_GRADE, 21), (FMM_OPT_M2L_GRADE, 21 << 8),
+                     (FMM_OPT_M2L_GRADE, 1 << 16), (FMM_OPT_M2L_ACC_GROUP, 0), (FMM_OPT_M2L_ACC_GROUP, 65)):
+        with pytest.raises(FMMError) as e:
+            plan.set_option(key, bad)
+        assert e.value.code == 1
+    plan.set_option(FMM_OPT_M2L_GRADE, 8 | (10 << 8))
+    plan.set_option(FMM_OPT_M2L_ACC_GROUP, 64)
+    plan.close()
