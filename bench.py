@@ -67,6 +67,25 @@ def m2l_flops(d: int, p: int, levels=None, fused_l2l=False, ws: int = 1) -> floa
     return 2.0 * C * C * pairs
 
 
+GRADE_DEFAULT = (0, 8)  # the library's default M2L grading (FMM_GRADE_DEFAULT): input degrees >= 8, one product
+
+
+def mmas_per_offset(p: int, grade, products: int = 3) -> tuple[int, int]:
+    """K16 MMA steps (128-row units) per interaction-list offset of the fp16x2 tensor-core M2L and per
+    fused L2L offset: K chunks of 64 coefficients, chunk kc graded by its lowest degree floor(sqrt(64 kc))
+    (1 product from degree D1, 2 from D2, else 3)."""
+    C = (p + 1) ** 2
+    ksteps = (C + 15) // 16
+    kchunks = ((C + 63) // 64 * 64) // 64
+    d2, d1 = grade
+    m2l = 0
+    for kc in range(kchunks):
+        lam = int(math.isqrt(64 * kc))
+        np_ = 1 if (d1 > 0 and lam >= d1) else 2 if (d2 > 0 and lam >= d2) else products
+        m2l += np_ * min(4, ksteps - 4 * kc)
+    return m2l, products * ksteps
+
+
 def kernel_sha(rel):
     try:
         with open(os.path.join(ROOT, rel)) as f:
@@ -195,8 +214,10 @@ def run_ours(args):
     F = torch.empty((N, 3), dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
 
+    grade = GRADE_DEFAULT if args.m2l_grade is None else tuple(int(x) for x in args.m2l_grade.split(","))
     plan = FMMPlan(box.L, N, d, p, precision="mixed", split=args.split, timings=True, ws=args.ws,
-                   overlap=bool(args.overlap))
+                   overlap=bool(args.overlap), m2l_grade=None if args.m2l_grade is None else grade,
+                   acc_group=args.acc_group)
     for _ in range(args.warmup):
         plan.evaluate(pos, q, sol, forces=F)
     torch.cuda.synchronize()
@@ -330,7 +351,13 @@ def run_ours(args):
         C = (p + 1) ** 2
         ksteps, npad = (C + 15) // 16, (C + 15) // 16 * 16
         products = {"fp16x2": 3, "bf16x3": 6, "bf16a2b3": 4, "bf16x2": 3}.get(args.split, 0)
-        issued = 8 ** d * (n_il(args.ws) + (1 if fused else 0)) * products * ksteps * 2.0 * npad * 16
+        if args.split == "fp16x2":
+            per_m2l, per_l2l = mmas_per_offset(p, grade, products)
+        else:
+            per_m2l, per_l2l = products * ksteps, products * ksteps
+        issued = 8 ** d * (n_il(args.ws) * per_m2l + (per_l2l if fused else 0)) * 2.0 * npad * 16
+        roof["mma_steps_per_offset"] = {"m2l": per_m2l, "fused_l2l": per_l2l if fused else 0,
+                                        "ungraded": products * ksteps}
         roof["issued_flops_per_launch"] = issued
         roof["issued_tflops"] = issued / (launch_ms / 1e3) / 1e12
     roof.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
@@ -353,7 +380,9 @@ def run_ours(args):
                                "energy+forces+solute-solvent per step" % (args.workload, ION_LABEL[box.ion], box.n_waters, N,
                                                                           box.L, d, p, args.ws),
                    "l2": "flushed between timed steps (256 MB write)", "jitter_A": args.jitter, "parallelism": "replicas" if ws > 1 else "1 GPU",
-                   "m2l_split": args.split, "overlap": bool(args.overlap)},
+                   "m2l_split": args.split, "overlap": bool(args.overlap),
+                   "m2l_grade": {"d2": grade[0], "d1": grade[1], "note": "input degrees >= d1 with one fp16 product"},
+                   "acc_group": args.acc_group if args.acc_group is not None else "library default (2)"},
         "roofline": roof,
         "solute_solvent_cost": uv_cost,
         "e2e": {"value": N * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": N * (24 + 8 + 1),
@@ -591,6 +620,8 @@ def main():
                     help="1: also time the 64-box lambda-window batch and add it to the line")
     ap.add_argument("--ws", type=int, default=1, choices=[1, 2], help="well-separatedness (2: the paper's setting)")
     ap.add_argument("--p", type=int, default=None, help="expansion order (default: the workload's)")
+    ap.add_argument("--m2l-grade", default=None, help="D2,D1 of FMM_OPT_M2L_GRADE (default: the library's 0,8)")
+    ap.add_argument("--acc-group", type=int, default=None, help="FMM_OPT_M2L_ACC_GROUP (default: the library's)")
     ap.add_argument("--overlap", type=int, default=1, choices=[0, 1],
                     help="1: near field and sparse solute pass beside the far field (plan-owned streams)")
     ap.add_argument("--jitter", type=float, default=0.0,

@@ -707,9 +707,13 @@ fmm_status upward_t(Plan &P, bool solute_only)
     const Particle<T> *sp = (const Particle<T> *)(solute_only ? P.sorted_u : P.sorted);
     T inv_h = (T)((double)nside / P.box);
     const bool tc = tc_translations(P);
-    // fp16 split: the P2M at a compile-time order folds the level maximum of |Mhat s| in as it writes
+    // fp16 split: the P2M at a compile-time order folds the level maximum of |Mhat s| in as it writes.  It
+    // runs one lane per leaf, so it is used for deep trees of sparse leaves (the benchmark boxes: 262,144
+    // leaves of ~4 charges); shallow trees of dense leaves keep the thread-per-(leaf, order) kernel
     bool amax_ready = false;
-    if (std::is_same<T, float>::value && (P.p == 4 || P.p == 6 || P.p == 8 || P.p == 10 || P.p == 12)) {
+    const bool lane_per_leaf = P.nleaf >= 32768 && (double)P.N <= 12.0 * (double)P.nleaf;
+    if (std::is_same<T, float>::value && lane_per_leaf &&
+        (P.p == 4 || P.p == 6 || P.p == 8 || P.p == 10 || P.p == 12)) {
         unsigned *amax = nullptr;
         if (tc) {
             fmm_status st = tc_clear_amax(P, P.d);

@@ -255,8 +255,10 @@ __global__ void k_p2p_uv(int64_t N, int d, int ws, T h, const int *__restrict__ 
 
 namespace {
 
-// staged-tile launch: rows of BX = min(32, side) leaves; the staging capacity is twice the expected
-// particle count of a tile's rows (at least 512 records), within 96 KB of shared memory
+// staged-tile launch: rows of BX leaves, BX a power of two up to min(32, side) chosen so that a row holds
+// about 128 target charges at the mean leaf occupancy (dense leaves: short rows, more blocks); the staging
+// capacity is twice the expected particle count of a tile's rows (at least 512 records), within 96 KB of
+// shared memory
 template <typename T>
 fmm_status launch_p2p_tile(Plan &P, T h, T *phi, T *field)
 {
@@ -267,7 +269,9 @@ fmm_status launch_p2p_tile(Plan &P, T h, T *phi, T *field)
         attr = true;
     }
     const int n = 1 << P.d;
-    const int bx = n < 32 ? n : 32;
+    const double occ = (double)P.N / (double)P.nleaf;
+    int bx = 1;
+    while (bx < 32 && bx < n && (double)(2 * bx) * occ <= 128.0) bx *= 2;
     const int side = 2 * P.ws + 1, F = side * side * (bx + 2 * P.ws);
     const size_t head = ((sizeof(int) * (2 * F + 1) + 15) / 16) * 16;
     const double expect = (double)P.N / (double)P.nleaf * F;
