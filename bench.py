@@ -530,13 +530,24 @@ def measure_batch(steps: int, warmup: int, rank: int, local: int, serial: bool =
     t_graph = timed(lambda: bt.lambda_energies(pos, q, sol, lam), steps)
     clocks = sampler.stop()
     info = bt.info(0)
+    sweep = bt.sweep_info()
+    # the same graph with the sweep's levels on per-level launches instead (A/B of the persistent launch)
+    bt.set_sweep(False)
+    bt.lambda_energies(pos, q, sol, lam)
+    r_off = bt.lambda_energies(pos, q, sol, lam)
+    t_off = timed(lambda: bt.lambda_energies(pos, q, sol, lam), steps)
+    bt.set_sweep(True)
     bt.set_graph(False)
     bt.lambda_energies(pos, q, sol, lam)
     t_stream = timed(lambda: bt.lambda_energies(pos, q, sol, lam), steps)
     r_stream = bt.lambda_energies(pos, q, sol, lam)
     bt.close()
     batch = {"graph_ms": t_graph * 1e3, "stream_path_ms": t_stream * 1e3, "plan_create_s": create_s,
-             "depths": depths, "replays": info["replays"]}
+             "depths": depths, "replays": info["replays"],
+             "sweep": {"boxes": sweep["boxes"], "first_levels": sorted(set(sweep["first_level"])),
+                       "graph_ms_per_level_launches": t_off * 1e3,
+                       "bitwise_equal_to_per_level_launches": bool(
+                           all(np.array_equal(r_stream[k], r_off[k]) for k in ("e_total", "e_uv")))}}
     if serial:
         # the same boxes and depths on single plans, one after the other
         plans = [FMMPlan(b.L, b.N, d, 12, precision="mixed") for (b, _), d in zip(win, depths)]

@@ -310,6 +310,43 @@ fmm_status fmm_batch_info(fmm_batch batch, int i, int *depth, int *p, int64_t *r
  * default) allows recording. */
 fmm_status fmm_batch_set_graph(fmm_batch batch, int enable);
 
+/*
+ * Persistent sweep (mixed precision).  The M2L of Eq. Lcoeffdef with the fused
+ * L2L, on every level that runs on CTA pairs (full 128-target tiles, an even
+ * number per parity class: level 4 and deeper), is done for all boxes of the
+ * batch in ONE launch of persistent CTA pairs that pull work items from a
+ * device queue: per (box, level) the split of the parent level's local
+ * expansion, the tile pairs of the M2L, and the sum of the offset groups.  The
+ * items are queued level by level, so each depends only on earlier ones; a pair
+ * waits (bounded by FMM_BATCH_OPT_WAIT_BUDGET_NS, globaltimer) until the stage
+ * it depends on has counted all its items done.  The launch is part of the
+ * recorded graph.  Boxes whose order differs from the first box taking part,
+ * or whose tree has no such level, keep their per-level launches.  Results are
+ * bitwise those of the per-level launches (the same tile arithmetic, offset
+ * groups and summation order).  A dependency wait that runs out stops the
+ * launch: every box of the sweep then reports FMM_ERR_TIMEOUT, and the next
+ * call starts afresh.
+ */
+enum {
+    FMM_BATCH_OPT_SWEEP = 1,           /* ival 1 (default) / 0: the persistent sweep on / per-level launches */
+    FMM_BATCH_OPT_WAIT_BUDGET_NS = 2,  /* ival 1000 .. 1e10: budget of each dependency wait (default 2e9) */
+    FMM_BATCH_OPT_INJECT_STALL = 3,    /* ival 0 / 1, a test hook for the timeout path: with 1 the first
+                                          tile pair's dependency asks for one item more than its stage has,
+                                          so its wait runs out */
+    FMM_BATCH_OPT_SWEEP_PAIRS = 4      /* ival 0 .. 4096: CTA pairs of the sweep launch (0, the default: as
+                                          many as can be resident); fewer leave SMs to the boxes' near-field
+                                          and solute-pass work, which does not depend on the sweep */
+};
+
+/* Set a batch option (the keys above; dval unused).  Drops the recorded graph.
+ * Errors: FMM_ERR_INVALID_ARG for an unknown key or a value out of range. */
+fmm_status fmm_batch_set_option(fmm_batch batch, int key, int64_t ival, double dval);
+
+/* Boxes the sweep covers (0 with the sweep off or when no box takes part) and,
+ * when first_level is not NULL (int[nbox]), each box's first sweep level (0:
+ * not in the sweep). */
+fmm_status fmm_batch_sweep_info(fmm_batch batch, int *boxes, int *first_level);
+
 /* Release the batch, its plans and streams.  Accepts NULL. */
 void fmm_batch_destroy(fmm_batch batch);
 

@@ -129,7 +129,9 @@ fmm_status far_field_pass(Plan &P, bool gradient, bool solute_only, StageTimer *
     TRY(launch_lattice(P));
     if (tm) tm->mark();
     bool ev = tm && P.timings_on;
-    for (int l = 1; l <= P.d; ++l) {
+    // a batch's persistent sweep runs the levels >= sweep_from of the full pass, and its L2P after that
+    const int last = (!solute_only && P.sweep_from > 0) ? P.sweep_from - 1 : P.d;
+    for (int l = 1; l <= last; ++l) {
         if (ev) cudaEventRecord(P.ev_m2l[2 * (l - 1)], P.stream);
         // with the fp16 split the upward pass left the planes split and the L2L is fused
         const bool fused = tc_available(P, l) && tc_translations(P);
@@ -139,6 +141,7 @@ fmm_status far_field_pass(Plan &P, bool gradient, bool solute_only, StageTimer *
         if (!fused) TRY(launch_l2l(P, l));
     }
     if (tm) tm->mark();
+    if (last < P.d) return FMM_OK;
     TRY(launch_l2p(P, gradient, solute_only));
     if (tm) tm->mark();
     return FMM_OK;
@@ -385,6 +388,9 @@ fmm_status eval_enqueue_front(Plan &P, const double *dpos, const double *dq, con
     P.top_recorded = false;
     return eval_front(P, dpos, dq, dsol, true, false, nullptr);
 }
+
+// the far-field pass's L2P when the deeper levels ran in a batch's sweep (after it, on the plan's stream)
+fmm_status eval_enqueue_far_tail(Plan &P) { return P.sweep_from > 0 ? launch_l2p(P, false, false) : FMM_OK; }
 
 fmm_status eval_enqueue_back(Plan &P, const double *dq) { return eval_back(P, dq, true, nullptr, nullptr); }
 

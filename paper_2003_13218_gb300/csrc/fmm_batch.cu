@@ -108,6 +108,13 @@ struct fmm_batch_s {
     cudaEvent_t ev_start = nullptr;
     bool use_graph = true;
     int sc_c = 0;  // soft-core near field on every plan (fmm_batch_set_softcore)
+    Sweep *sweep = nullptr;          // the tensor-core levels of the boxes in one persistent launch
+    bool use_sweep = true;
+    std::vector<cudaEvent_t> ev_front;
+    cudaEvent_t ev_sweep = nullptr;
+    uint64_t wait_ns = 2000000000ull;  // budget of the sweep's dependency waits
+    bool stall = false;                // test hook: one dependency of the sweep is never met
+    int sweep_pairs = 0;               // CTA pairs of the sweep (0: as many as can be resident)
     cudaGraphExec_t graph = nullptr;
     std::vector<const void *> gptr;  // input pointers the graph was captured with
     std::vector<int> gcount;         // solute counts it was captured with
@@ -120,7 +127,11 @@ void batch_free(fmm_batch b)
 {
     if (!b) return;
     for (cudaStream_t s : b->streams) cudaStreamSynchronize(s);
+    if (b->origin) cudaStreamSynchronize(b->origin);
     if (b->graph) cudaGraphExecDestroy(b->graph);
+    sweep_destroy(b->sweep);
+    for (cudaEvent_t e : b->ev_front) cudaEventDestroy(e);
+    if (b->ev_sweep) cudaEventDestroy(b->ev_sweep);
     for (fmm_plan h : b->plans)
         if (h) fmm_plan_destroy(h);
     for (cudaEvent_t e : b->ev_done) cudaEventDestroy(e);
@@ -130,13 +141,29 @@ void batch_free(fmm_batch b)
     delete b;
 }
 
-// the whole batch once: fronts of all boxes, then backs (each back waits for
-// its box's solute count unless the plan carries a known count)
+// the whole batch once: fronts of all boxes, then (with the sweep) the deeper
+// tensor-core levels of every box in one persistent launch on the origin stream
+// and each box's L2P after it, then backs (each back waits for its box's
+// solute count unless the plan carries a known count)
 fmm_status batch_enqueue(fmm_batch b, const double *const *pos, const double *const *q, const uint8_t *const *sol)
 {
     for (int i : b->order) {
         fmm_status s = eval_enqueue_front(b->plans[i]->P, pos[i], q[i], sol[i]);
         if (s != FMM_OK) return s;
+    }
+    if (b->sweep && b->use_sweep) {
+        for (size_t k = 0; k < b->streams.size(); ++k) {
+            FMM_CUDA_TRY(cudaEventRecord(b->ev_front[k], b->streams[k]));
+            FMM_CUDA_TRY(cudaStreamWaitEvent(b->origin, b->ev_front[k], 0));
+        }
+        fmm_status s = sweep_launch(b->sweep, b->origin, b->wait_ns, b->stall, b->sweep_pairs);
+        if (s != FMM_OK) return s;
+        FMM_CUDA_TRY(cudaEventRecord(b->ev_sweep, b->origin));
+        for (cudaStream_t st : b->streams) FMM_CUDA_TRY(cudaStreamWaitEvent(st, b->ev_sweep, 0));
+        for (int i : b->order) {
+            s = eval_enqueue_far_tail(b->plans[i]->P);
+            if (s != FMM_OK) return s;
+        }
     }
     for (int i : b->order) {
         fmm_status s = eval_enqueue_back(b->plans[i]->P, q[i]);
@@ -301,6 +328,26 @@ fmm_status fmm_batch_create(int nbox, const double *box, const int64_t *N, const
         const int pi = (p && p[i] >= 0) ? p[i] : 12;
         s = make_plan(box[i], N[i], b->depth[i], pi, precision, b->streams[k % ns], &b->plans[i]);
     }
+    // one copy of the tensor-core operator tables per order: the boxes' tiles then read them from L2
+    for (int i = 0; i < nbox && s == FMM_OK; ++i)
+        for (int j = 0; j < i && s == FMM_OK; ++j)
+            if (b->plans[j]->P.p == b->plans[i]->P.p) {
+                s = tc_share_operators(b->plans[i]->P, b->plans[j]->P);
+                break;
+            }
+    // the persistent sweep over the boxes' CTA-pair levels (mixed precision)
+    if (s == FMM_OK && precision == FMM_PREC_MIXED) {
+        std::vector<Plan *> ps;
+        for (fmm_plan h : b->plans) ps.push_back(&h->P);
+        s = sweep_create(ps.data(), nbox, &b->sweep);
+        for (size_t k = 0; k < b->streams.size() && s == FMM_OK && b->sweep; ++k) {
+            cudaEvent_t ev;
+            if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) s = FMM_ERR_CUDA;
+            else b->ev_front.push_back(ev);
+        }
+        if (s == FMM_OK && b->sweep && cudaEventCreateWithFlags(&b->ev_sweep, cudaEventDisableTiming) != cudaSuccess)
+            s = FMM_ERR_CUDA;
+    }
     if (s != FMM_OK) {
         batch_free(b);
         return s;
@@ -383,6 +430,47 @@ fmm_status fmm_batch_set_softcore(fmm_batch b, int c, double A, double alpha)
         b->graph = nullptr;
         b->gptr.clear();
     }
+    return FMM_OK;
+}
+
+fmm_status fmm_batch_set_option(fmm_batch b, int key, int64_t ival, double dval)
+{
+    (void)dval;
+    if (!b) return FMM_ERR_INVALID_ARG;
+    switch (key) {
+    case FMM_BATCH_OPT_SWEEP:
+        if (ival != 0 && ival != 1) return FMM_ERR_INVALID_ARG;
+        b->use_sweep = ival != 0;
+        sweep_enable(b->sweep, b->use_sweep);
+        break;
+    case FMM_BATCH_OPT_WAIT_BUDGET_NS:
+        if (ival < 1000 || ival > 10000000000ll) return FMM_ERR_INVALID_ARG;
+        b->wait_ns = (uint64_t)ival;
+        break;
+    case FMM_BATCH_OPT_INJECT_STALL:
+        if (ival != 0 && ival != 1) return FMM_ERR_INVALID_ARG;
+        b->stall = ival != 0;
+        break;
+    case FMM_BATCH_OPT_SWEEP_PAIRS:
+        if (ival < 0 || ival > 4096) return FMM_ERR_INVALID_ARG;
+        b->sweep_pairs = (int)ival;
+        break;
+    default: return FMM_ERR_INVALID_ARG;
+    }
+    if (b->graph) {  // the recorded work changed
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+        b->gptr.clear();
+    }
+    return FMM_OK;
+}
+
+fmm_status fmm_batch_sweep_info(fmm_batch b, int *boxes, int *first_level)
+{
+    if (!b) return FMM_ERR_INVALID_ARG;
+    if (boxes) *boxes = (b->use_sweep && b->sweep) ? sweep_plans(b->sweep) : 0;
+    if (first_level)
+        for (int i = 0; i < b->nbox; ++i) first_level[i] = b->plans[i]->P.sweep_from;
     return FMM_OK;
 }
 

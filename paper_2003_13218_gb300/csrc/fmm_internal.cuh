@@ -98,6 +98,7 @@ struct Plan {
     cudaStream_t stream = 0;
     bool timings_on = false;
     bool tc_pair = true;  // CTA-pair (2-SM) tensor-core M2L where the level allows it
+    int sweep_from = 0;   // > 0: the full pass's levels >= sweep_from (and its L2P) run in a batch's sweep
     int known_count = -1; // >= 0: the solute count the caller already knows (no host wait; graph capture)
     int boundary = 0;     // FMM_BOUNDARY_CONDUCTING (Eq. Velecfull) or FMM_BOUNDARY_VACUUM (App. D)
     // FMM_OPT_SOFTCORE: soft-core solute-solvent near field (c = 0: off); lambda lives in pinned host memory
@@ -314,7 +315,23 @@ void tc_free(Plan &P);
 // P.h_out) only enqueue work, except that back waits for the host copy of the solute count unless
 // P.known_count >= 0; results are read after the plan's stream is synchronised
 fmm_status eval_enqueue_front(Plan &P, const double *dpos, const double *dq, const uint8_t *dsol);
+fmm_status eval_enqueue_far_tail(Plan &P);
 fmm_status eval_enqueue_back(Plan &P, const double *dq);
+
+// dst reads src's split operator tables when they are the same (p, ws, split); src must outlive dst
+fmm_status tc_share_operators(Plan &dst, const Plan &src);
+
+// persistent sweep of the CTA-pair tensor-core levels of many plans in one launch (fmm_m2l_tc.cu)
+struct Sweep;
+int tc_sweep_first_level(const Plan &P);  // first level a sweep can take (0: none)
+// a sweep over the plans that can take part (same expansion order); *out stays null when none can;
+// sets their sweep_from
+fmm_status sweep_create(Plan *const *plans, int n, Sweep **out);
+void sweep_enable(Sweep *sw, bool on);  // sets or clears the plans' sweep_from
+int sweep_plans(const Sweep *sw);
+// max_pairs > 0 caps the CTA pairs (the rest of the GPU stays free for the boxes' other streams)
+fmm_status sweep_launch(Sweep *sw, cudaStream_t st, uint64_t wait_ns, bool stall, int max_pairs);
+void sweep_destroy(Sweep *sw);
 fmm_status eval_results(Plan &P, fmm_energy_terms *terms, fmm_uv_terms *uv);
 
 #define FMM_CUDA_TRY(expr)                                        \

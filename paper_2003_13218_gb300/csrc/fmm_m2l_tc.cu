@@ -50,6 +50,7 @@
 #include <string.h>
 
 #include <new>
+#include <vector>
 
 #include "fmm_internal.cuh"
 
@@ -84,6 +85,7 @@ struct TcState {
     size_t part_elems[9] = {};
     uint16_t *ops = nullptr;
     size_t ops_part_elems = 0;
+    bool ops_borrowed = false;      // ops belongs to another plan's state (tc_share_operators)
     CUtensorMap mapA[9][3];
     CUtensorMap mapB[3];
     CUtensorMap mapB2[2];           // fp16: operator tiles boxed N/2 rows (one half per CTA of a pair)
@@ -310,6 +312,62 @@ __device__ __forceinline__ void drain_accumulator(uint32_t taddr, float fac, flo
 #pragma unroll
                 for (int j = 0; j < 16; ++j)
                     Lr[(c0 + c) * 16 + j] = fmaf(__uint_as_float(r[c][j]), fac, Lr[(c0 + c) * 16 + j]);
+    }
+}
+
+// Rows r0 .. r0 + 31 (those below `rows`) of the staged output tile (row stride srow in shared memory) to
+// out + idx(r) nc, idx(r) held by lane r - r0: one warp, coalesced stores, four rows in flight
+template <int NCH>
+__device__ __forceinline__ void store_rows(const float *stage, int srow, int r0, int rows, int64_t my_idx, float *out,
+                                           int nc, int lane)
+{
+#pragma unroll 1
+    for (int r = 0; r < 32; r += 4) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t di = __shfl_sync(0xffffffffu, my_idx, r + u);
+            if (r0 + r + u < rows) {
+                float *dst = out + di * nc;
+                const float *src = stage + (r0 + r + u) * srow;
+#pragma unroll
+                for (int c = 0; c < NCH * 16; c += 32)
+                    if (c + lane < nc) dst[c + lane] = src[c + lane];
+            }
+        }
+    }
+}
+
+// The warp's rows r0 .. r0 + 31 (those below `rows`), lane r - r0 holding row r in x, to out + idx(r) nc,
+// idx(r) held by lane r - r0, without shared memory: each 32 x 32 block of columns is transposed across
+// the warp by a 5-step butterfly of shuffles (step m swaps the m-wide off-diagonal blocks between lanes
+// l and l ^ m), after which lane l holds column 32 b + l of all 32 rows and every store is coalesced.
+template <int NCH>
+__device__ __forceinline__ void store_rows_shfl(float (&x)[NCH * 16], int64_t my_idx, int r0, int rows, float *out,
+                                                int nc, int lane)
+{
+    constexpr int C = NCH * 16;
+#pragma unroll
+    for (int b = 0; b < (C + 31) / 32; ++b) {
+        float v[32];
+#pragma unroll
+        for (int k = 0; k < 32; ++k) v[k] = 32 * b + k < C ? x[32 * b + k] : 0.f;
+#pragma unroll
+        for (int m = 16; m > 0; m >>= 1) {
+            const bool up = (lane & m) != 0;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                if (j & m) continue;
+                const float recv = __shfl_xor_sync(0xffffffffu, up ? v[j] : v[j | m], m);
+                if (up) v[j] = recv;
+                else v[j | m] = recv;
+            }
+        }
+        const int col = 32 * b + lane;
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+            const int64_t di = __shfl_sync(0xffffffffu, my_idx, k);
+            if (r0 + k < rows && col < nc) out[di * nc + col] = v[k];
+        }
     }
 }
 
@@ -738,41 +796,42 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             if (lane == 0) mbar_arrive(smem_u32(&bar_tempty[acc]));
         }
         float mx = 0.f;  // largest |out_i sx(i)| of this thread's row (a.amax_out)
-        if (!ok) {
+        if (!__all_sync(0xffffffffu, ok)) {
             abort_sh = 1;
             if (lane == 0) atomicOr(a.err, ERRF_TIMEOUT);
-        } else if (row < a.rows) {
-            const int tx = row % a.bx, ty = (row / a.bx) % a.by, tz = row / (a.bx * a.by);
+        } else {
+            // every MMA has completed, so the stage ring is idle: the rows go through shared memory (stride
+            // srow, odd) and leave in coalesced stores, a warp per 32 rows
+            float *stage = reinterpret_cast<float *>(smem_dyn + (smem0 - smem_u32(smem_dyn)));
+            const int srow = a.nc | 1;
+            if (row < a.rows) {
+                // with the fp16 split undo the balancing: x^ = x~ post(j) / (gM gT)
+                const float g = a.post ? pow2f(-gain_m_exp(__ldcg(a.amax)) - GAIN_T_EXP) : 1.f;
+#pragma unroll
+                for (int i = 0; i < NCH * 16; ++i)
+                    if (i < a.nc) {
+                        const float v = a.post ? Lr[i] * (__ldg(a.post + i) * g) : Lr[i];
+                        stage[row * srow + i] = v;
+                        if (a.amax_out) mx = fmaxf(mx, fabsf(v * __ldg(a.sx + i)));
+                    }
+            }
             const int64_t np = a.np;
-            int64_t idx, level_cells;
+            const int64_t level_cells = a.mode == 0 ? 8 * np * np * np : np * np * np;
+            float *out = a.groups == 1 ? a.L : a.Lpart + (int64_t)grp * level_cells * a.nc;
+            const int tx = row % a.bx, ty = (row / a.bx) % a.by, tz = row / (a.bx * a.by);
+            int64_t my_idx;
             if (a.mode == 0) {
-                idx = (int64_t)cls * np * np * np + (x0 + tx) + np * ((y0 + ty) + np * (int64_t)(z0 + tz));
-                level_cells = 8 * np * np * np;
+                my_idx = (int64_t)cls * np * np * np + (x0 + tx) + np * ((y0 + ty) + np * (int64_t)(z0 + tz));
             } else {
                 // natural coordinates of the parent level -> its class layout
                 const int px = x0 + tx, py = y0 + ty, pz = z0 + tz;
                 const int64_t on = a.out_np;
-                idx = on == 0 ? 0
-                              : (int64_t)((px & 1) | ((py & 1) << 1) | ((pz & 1) << 2)) * on * on * on + (px >> 1) +
-                                    on * ((py >> 1) + on * (int64_t)(pz >> 1));
-                level_cells = np * np * np;
+                my_idx = on == 0 ? 0
+                                 : (int64_t)((px & 1) | ((py & 1) << 1) | ((pz & 1) << 2)) * on * on * on + (px >> 1) +
+                                       on * ((py >> 1) + on * (int64_t)(pz >> 1));
             }
-            float *dst = (a.groups == 1 ? a.L : a.Lpart + (int64_t)grp * level_cells * a.nc) + idx * a.nc;
-            if (a.post) {
-                // undo the balancing: x^ = x~ post(j) / (gM gT)
-                const float g = pow2f(-gain_m_exp(*a.amax) - GAIN_T_EXP);
-#pragma unroll
-                for (int i = 0; i < NCH * 16; ++i)
-                    if (i < a.nc) {
-                        const float v = Lr[i] * (__ldg(a.post + i) * g);
-                        dst[i] = v;
-                        if (a.amax_out) mx = fmaxf(mx, fabsf(v * __ldg(a.sx + i)));
-                    }
-            } else {
-#pragma unroll
-                for (int i = 0; i < NCH * 16; ++i)
-                    if (i < a.nc) dst[i] = Lr[i];
-            }
+            __syncwarp();
+            store_rows<NCH>(stage, srow, quad * 32, a.rows, my_idx, out, a.nc, lane);
         }
         if (a.amax_out) {  // the whole warp is here
             for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -811,34 +870,57 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 // Barriers are initialised and TMEM is allocated (collectively) only after a
 // cluster barrier, and both CTAs pass a cluster barrier before the collective
 // TMEM release, so neither touches the other after it has exited.
+struct PairBars {
+    uint64_t full[TC_MAX_STAGES];
+    uint64_t empty[TC_MAX_STAGES];
+    uint64_t tfull[2];
+    uint64_t tempty[2];
+    uint64_t done;
+};
+
+// Pipeline positions of one role thread, carried from tile to tile when a pair runs several tiles (the
+// persistent sweep): stages issued, ring stage and pass, accumulator groups used.
+struct PairPipe {
+    int it = 0, s = 0;
+    uint32_t round = 0, g = 0;
+};
+
+__device__ __forceinline__ void pair_bars_init(PairBars &b, int stages)
+{
+    for (int s = 0; s < stages; ++s) {
+        mbar_init(smem_u32(&b.full[s]), 1);
+        mbar_init(smem_u32(&b.empty[s]), 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+        mbar_init(smem_u32(&b.tfull[i]), 1);
+        mbar_init(smem_u32(&b.tempty[i]), 8);  // 4 epilogue warps in each CTA
+    }
+    mbar_init(smem_u32(&b.done), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// The roles of both CTAs for pair `pair` of the launch arguments `a` (tiles 2t and 2t + 1 of one class,
+// one offset group).  The ring and accumulator phases continue from `pp`; the caller commits `done` after
+// its last tile.  A wait that runs out sets *abort_flag and records FMM_ERR_TIMEOUT.  `staged`: the caller
+// issues no copies until every thread is done with this tile, so the epilogue may stage the output rows
+// in the ring (`stage`, generic address of its start); otherwise each thread writes its row directly.
 template <int NCH>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TC_THREADS, 1)
-    k_m2l_tc_pair(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
-                  const __grid_constant__ CUtensorMap mB0, const __grid_constant__ CUtensorMap mB1,
-                  const __grid_constant__ CUtensorMap mL0, const __grid_constant__ CUtensorMap mL1, TcArgs a)
+__device__ __forceinline__ void pair_tile(const CUtensorMap *mA0, const CUtensorMap *mA1, const CUtensorMap *mB0,
+                                          const CUtensorMap *mB1, const CUtensorMap *mL0, const CUtensorMap *mL1,
+                                          const TcArgs &a, int pair, uint32_t rank, uint32_t smem0, float *stage,
+                                          bool staged, PairBars &bars, uint32_t tmem, volatile int *abort_flag,
+                                          PairPipe &pp)
 {
     constexpr int PA = 2, PB = 2, SW = 128;
     constexpr int KCH = kchunk_of(SW), K16 = SW / 32;
     using PR = Products<PA, PB>;
-    extern __shared__ uint8_t smem_dyn[];
-    __shared__ __align__(8) uint64_t bar_full[TC_MAX_STAGES];
-    __shared__ __align__(8) uint64_t bar_empty[TC_MAX_STAGES];
-    __shared__ __align__(8) uint64_t bar_tfull[2];
-    __shared__ __align__(8) uint64_t bar_tempty[2];
-    __shared__ __align__(8) uint64_t bar_done;
-    __shared__ uint32_t tmem_sh;
-    __shared__ int abort_sh;
-
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t rank = cluster_rank();
     const bool leader = rank == 0;
-    const uint32_t smem0 = (smem_u32(smem_dyn) + 1023u) & ~1023u;
     const uint32_t halfN = (uint32_t)a.npad / 2;
     const uint32_t stageA = TC_ROWS * SW;
     const uint32_t stageB = halfN * SW;
     const uint32_t stage_bytes = PA * stageA + PB * stageB;
 
-    const int pair = blockIdx.x >> 1;
     const int grp = pair % a.groups;
     const int cls = (pair / a.groups) & 7;
     const int tile = 2 * ((pair / a.groups) >> 3) + (int)rank;
@@ -853,51 +935,23 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TC_THREADS, 1)
     const int cx = cls & 1, cy = (cls >> 1) & 1, cz = (cls >> 2) & 1;
     const int np2 = a.np + 2 * a.ws;
 
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < a.stages; ++s) {
-            mbar_init(smem_u32(&bar_full[s]), 1);
-            mbar_init(smem_u32(&bar_empty[s]), 1);
-        }
-        for (int b = 0; b < 2; ++b) {
-            mbar_init(smem_u32(&bar_tfull[b]), 1);
-            mbar_init(smem_u32(&bar_tempty[b]), 8);  // 4 epilogue warps in each CTA
-        }
-        mbar_init(smem_u32(&bar_done), 1);
-        abort_sh = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    cluster_sync_all();  // the pair's barriers are initialised and both CTAs are running
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_sh)),
-                     "r"(TMEM_COLS)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
-    }
-    fence_before();
-    __syncthreads();
-    fence_after();
-    const uint32_t tmem = tmem_sh;
-    volatile int *abort_flag = &abort_sh;
-
     if (warp == 0) {
         if (lane == 0) {
             // ---------------- producer (both CTAs): own A brick, own half of B, completing on the leader's barrier
-            const CUtensorMap *mA[2] = {&mA0, &mA1};
-            const CUtensorMap *mL[2] = {&mL0, &mL1};
-            const CUtensorMap *mB[2] = {&mB0, &mB1};
-            int it = 0, s = 0;
-            uint32_t round = 0;
+            const CUtensorMap *mA[2] = {mA0, mA1};
+            const CUtensorMap *mL[2] = {mL0, mL1};
+            const CUtensorMap *mB[2] = {mB0, mB1};
             bool ok = true;
             auto load_offset = [&](const CUtensorMap *const *src, int c1, int c2, int c3, int oslot, bool graded) {
                 for (int kc = 0; kc < a.kchunks && ok;) {
-                    if (it >= a.stages &&
-                        !mbar_wait_cluster(smem_u32(&bar_empty[s]), (round & 1u) ^ 1u, abort_flag, a.wait_ns)) {
+                    if (pp.it >= a.stages && !mbar_wait_cluster(smem_u32(&bars.empty[pp.s]), (pp.round & 1u) ^ 1u,
+                                                                abort_flag, a.wait_ns)) {
                         ok = false;
                         break;
                     }
-                    const uint32_t full_local = smem_u32(&bar_full[s]);
+                    const uint32_t full_local = smem_u32(&bars.full[pp.s]);
                     const uint32_t full = map_shared(full_local, 0);
-                    const uint32_t base = smem0 + (uint32_t)s * stage_bytes;
+                    const uint32_t base = smem0 + (uint32_t)pp.s * stage_bytes;
                     const int nkc = graded ? stage_chunks(a.gchunks, kc, a.kchunks) : 1;
                     if (nkc == 2) {  // two x0 y0 chunks: A0 and B0 of chunk kc + t in term place t
                         // the leader's barrier counts both CTAs' copies (the same boxes in each)
@@ -927,10 +981,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TC_THREADS, 1)
                                                  (int)(rank * halfN), oslot);
                     }
                     kc += nkc;
-                    ++it;
-                    if (++s == a.stages) {
-                        s = 0;
-                        ++round;
+                    ++pp.it;
+                    if (++pp.s == a.stages) {
+                        pp.s = 0;
+                        ++pp.round;
                     }
                 }
             };
@@ -950,7 +1004,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TC_THREADS, 1)
             if (ok && a.n_off > a.n_il && a.n_il >= o_begin && a.n_il < o_end)
                 load_offset(mL, x0, y0, z0, a.noff + 8 + cls, false);
             if (!ok) {
-                abort_sh = 1;
+                *abort_flag = 1;
                 atomicOr(a.err, ERRF_TIMEOUT);
             }
         }
@@ -958,14 +1012,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TC_THREADS, 1)
     } else if (warp == 1) {
         if (lane == 0 && leader) {
             // ---------------- MMA issuer (even CTA): 256-row MMAs over both CTAs' operands
-            int s = 0;
-            uint32_t round = 0;
             bool ok = true;
             for (int g = 0; g < groups.ng && ok; ++g) {
-                const int acc = g & 1;
-                const uint32_t use = (uint32_t)(g >> 1);
-                if (g >= 2 &&
-                    !mbar_wait_cluster(smem_u32(&bar_tempty[acc]), (use - 1u) & 1u, abort_flag, a.wait_ns)) {
+                const uint32_t gg = pp.g + (uint32_t)g;
+                const int acc = (int)(gg & 1u);
+                const uint32_t use = gg >> 1;
+                if (gg >= 2 &&
+                    !mbar_wait_cluster(smem_u32(&bars.tempty[acc]), (use - 1u) & 1u, abort_flag, a.wait_ns)) {
                     ok = false;
                     break;
                 }
@@ -975,12 +1028,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TC_THREADS, 1)
                 for (int o = groups.begin(g); o < groups.end(g) && ok; ++o) {
                     const bool graded = a.gchunks != 0u && o_begin + o < a.n_il;
                     for (int kc = 0; kc < a.kchunks;) {
-                        if (!mbar_wait_cluster(smem_u32(&bar_full[s]), round & 1u, abort_flag, a.wait_ns)) {
+                        if (!mbar_wait_cluster(smem_u32(&bars.full[pp.s]), pp.round & 1u, abort_flag, a.wait_ns)) {
                             ok = false;
                             break;
                         }
                         fence_after();
-                        const uint32_t base = smem0 + (uint32_t)s * stage_bytes;
+                        const uint32_t base = smem0 + (uint32_t)pp.s * stage_bytes;
                         const int nk = a.ksteps - K16 * kc < K16 ? a.ksteps - K16 * kc : K16;
                         const int np = graded ? chunk_products(a.gchunks, kc) : PR::n;
                         const int nkc = graded ? stage_chunks(a.gchunks, kc, a.kchunks) : 1;
@@ -999,35 +1052,36 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TC_THREADS, 1)
                                                                   a.idesc, first);
                         first = false;
                         kc += nkc;
-                        mma_commit_pair(smem_u32(&bar_empty[s]));
-                        if (++s == a.stages) {
-                            s = 0;
-                            ++round;
+                        mma_commit_pair(smem_u32(&bars.empty[pp.s]));
+                        if (++pp.s == a.stages) {
+                            pp.s = 0;
+                            ++pp.round;
                         }
                     }
                 }
-                if (ok) mma_commit_pair(smem_u32(&bar_tfull[acc]));
+                if (ok) mma_commit_pair(smem_u32(&bars.tfull[acc]));
             }
+            pp.g += (uint32_t)groups.ng;
             if (!ok) {
-                abort_sh = 1;
+                *abort_flag = 1;
                 atomicOr(a.err, ERRF_TIMEOUT);
             }
-            mma_commit_pair(smem_u32(&bar_done));  // arrives in both CTAs once every MMA has completed
         }
         __syncwarp();
     } else {
         // ---------------- epilogue warps (both CTAs): drain this CTA's 128 rows
         const int quad = warp & 3;
         const int row = quad * 32 + lane;
-        const float l2l_fac = a.amaxL ? pow2f(gain_m_exp(*a.amax) - gain_m_exp(*a.amaxL)) : 1.f;
+        const float l2l_fac = a.amaxL ? pow2f(gain_m_exp(__ldcg(a.amax)) - gain_m_exp(__ldcg(a.amaxL))) : 1.f;
         float Lr[NCH * 16];
 #pragma unroll
         for (int i = 0; i < NCH * 16; ++i) Lr[i] = 0.f;
         bool ok = true;
         for (int g = 0; g < groups.ng; ++g) {
-            const int acc = g & 1;
-            const uint32_t use = (uint32_t)(g >> 1);
-            if (!mbar_wait_cluster(smem_u32(&bar_tfull[acc]), use & 1u, abort_flag, a.wait_ns)) {
+            const uint32_t gg = pp.g + (uint32_t)g;
+            const int acc = (int)(gg & 1u);
+            const uint32_t use = gg >> 1;
+            if (!mbar_wait_cluster(smem_u32(&bars.tfull[acc]), use & 1u, abort_flag, a.wait_ns)) {
                 ok = false;
                 break;
             }
@@ -1037,40 +1091,99 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TC_THREADS, 1)
             fence_before();
             __syncwarp();
             if (lane == 0) {
-                const uint32_t te = smem_u32(&bar_tempty[acc]);
+                const uint32_t te = smem_u32(&bars.tempty[acc]);
                 if (leader) mbar_arrive(te);
                 else mbar_arrive_remote(map_shared(te, 0));
             }
         }
+        pp.g += (uint32_t)groups.ng;
         float mx = 0.f;  // largest |out_i sx(i)| of this thread's row (a.amax_out)
-        if (!ok) {
-            abort_sh = 1;
+        if (!__all_sync(0xffffffffu, ok)) {
+            *abort_flag = 1;
             if (lane == 0) atomicOr(a.err, ERRF_TIMEOUT);
-        } else if (row < a.rows) {
-            const int tx = row % a.bx, ty = (row / a.bx) % a.by, tz = row / (a.bx * a.by);
-            const int64_t np = a.np;
-            const int64_t idx = (int64_t)cls * np * np * np + (x0 + tx) + np * ((y0 + ty) + np * (int64_t)(z0 + tz));
-            float *dst = (a.groups == 1 ? a.L : a.Lpart + (int64_t)grp * 8 * np * np * np * a.nc) + idx * a.nc;
-            const float g = pow2f(-gain_m_exp(*a.amax) - GAIN_T_EXP);
+        } else if (!staged) {
+            // the ring may already hold the next tile's copies: the rows are transposed across each warp in
+            // registers for coalesced stores
+            const float g = pow2f(-gain_m_exp(__ldcg(a.amax)) - GAIN_T_EXP);
 #pragma unroll
-            for (int i = 0; i < NCH * 16; ++i)
-                if (i < a.nc) {
-                    const float v = Lr[i] * (__ldg(a.post + i) * g);
-                    dst[i] = v;
-                    if (a.amax_out) mx = fmaxf(mx, fabsf(v * __ldg(a.sx + i)));
-                }
+            for (int i = 0; i < NCH * 16; ++i) {
+                Lr[i] = i < a.nc ? Lr[i] * (__ldg(a.post + i) * g) : 0.f;
+                if (a.amax_out && row < a.rows && i < a.nc) mx = fmaxf(mx, fabsf(Lr[i] * __ldg(a.sx + i)));
+            }
+            const int64_t np = a.np;
+            float *out = a.groups == 1 ? a.L : a.Lpart + (int64_t)grp * 8 * np * np * np * a.nc;
+            const int tx = row % a.bx, ty = (row / a.bx) % a.by, tz = row / (a.bx * a.by);
+            const int64_t my_idx = (int64_t)cls * np * np * np + (x0 + tx) + np * ((y0 + ty) + np * (int64_t)(z0 + tz));
+            store_rows_shfl<NCH>(Lr, my_idx, quad * 32, a.rows, out, a.nc, lane);
+        } else {
+            // every MMA of the tile has completed and no copy is pending, so the stage ring is idle: the rows
+            // go through shared memory (stride srow, odd) and leave in coalesced stores, a warp per 32 rows
+            const int srow = a.nc | 1;
+            const float g = pow2f(-gain_m_exp(__ldcg(a.amax)) - GAIN_T_EXP);
+            if (row < a.rows) {
+#pragma unroll
+                for (int i = 0; i < NCH * 16; ++i)
+                    if (i < a.nc) {
+                        const float v = Lr[i] * (__ldg(a.post + i) * g);
+                        stage[row * srow + i] = v;
+                        if (a.amax_out) mx = fmaxf(mx, fabsf(v * __ldg(a.sx + i)));
+                    }
+            }
+            const int64_t np = a.np;
+            float *out = a.groups == 1 ? a.L : a.Lpart + (int64_t)grp * 8 * np * np * np * a.nc;
+            const int tx = row % a.bx, ty = (row / a.bx) % a.by, tz = row / (a.bx * a.by);
+            const int64_t my_idx = (int64_t)cls * np * np * np + (x0 + tx) + np * ((y0 + ty) + np * (int64_t)(z0 + tz));
+            __syncwarp();
+            store_rows<NCH>(stage, srow, quad * 32, a.rows, my_idx, out, a.nc, lane);
         }
         if (a.amax_out) {  // the whole warp is here
             for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
             if (lane == 0 && mx > 0.f) atomicMax(a.amax_out, __float_as_uint(mx));
         }
     }
+}
+
+template <int NCH>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TC_THREADS, 1)
+    k_m2l_tc_pair(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
+                  const __grid_constant__ CUtensorMap mB0, const __grid_constant__ CUtensorMap mB1,
+                  const __grid_constant__ CUtensorMap mL0, const __grid_constant__ CUtensorMap mL1, TcArgs a)
+{
+    extern __shared__ uint8_t smem_dyn[];
+    __shared__ __align__(8) PairBars bars;
+    __shared__ uint32_t tmem_sh;
+    __shared__ int abort_sh;
+
+    const int warp = threadIdx.x >> 5;
+    const uint32_t rank = cluster_rank();
+    const uint32_t smem0 = (smem_u32(smem_dyn) + 1023u) & ~1023u;
+    if (threadIdx.x == 0) {
+        pair_bars_init(bars, a.stages);
+        abort_sh = 0;
+    }
+    cluster_sync_all();  // the pair's barriers are initialised and both CTAs are running
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_sh)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = tmem_sh;
+    PairPipe pp;
+    float *stage = reinterpret_cast<float *>(smem_dyn + (smem0 - smem_u32(smem_dyn)));
+    pair_tile<NCH>(&mA0, &mA1, &mB0, &mB1, &mL0, &mL1, a, (int)(blockIdx.x >> 1), rank, smem0, stage, true, bars,
+                   tmem, &abort_sh, pp);
+    if (warp == 1 && (threadIdx.x & 31) == 0 && rank == 0)
+        mma_commit_pair(smem_u32(&bars.done));  // arrives in both CTAs once every MMA has completed
 
     // ---------------- teardown: every MMA done (bounded wait), pair barrier, collective TMEM release
     __syncthreads();
     if (threadIdx.x == 0) {
         volatile int no_abort = 0;
-        if (!mbar_wait_cluster(smem_u32(&bar_done), 0, &no_abort)) atomicOr(a.err, ERRF_TIMEOUT);
+        if (!mbar_wait_cluster(smem_u32(&bars.done), 0, &no_abort)) atomicOr(a.err, ERRF_TIMEOUT);
     }
     fence_before();
     __syncthreads();
@@ -1151,27 +1264,35 @@ __global__ void k_split_halo(const float *__restrict__ M, int np, int hw, int nc
 
 // FP32 class-layout local expansion of level `lev` (side n = 2^lev) -> fp16
 // split planes in natural order [part][z][y][x][k], balanced L~ = L^ / s(k) gL
-// (the A operand of the fused L2L).  One warp per cell.
+// (the A operand of the fused L2L): natural cell `cell`, lanes over the coefficients.
+__device__ __forceinline__ void split_L_cell(const float *__restrict__ L, int lev, int nc, int kp,
+                                             const float *__restrict__ sinv, float g, uint16_t *__restrict__ planes,
+                                             size_t part_elems, int64_t cell, int lane)
+{
+    const int n = 1 << lev, h = n >> 1;
+    const int x = (int)(cell % n), y = (int)((cell / n) % n), z = (int)(cell / ((int64_t)n * n));
+    const int64_t src = lev == 0 ? 0
+                                 : (int64_t)((x & 1) | ((y & 1) << 1) | ((z & 1) << 2)) * h * h * h + (x >> 1) +
+                                       (int64_t)h * ((y >> 1) + (int64_t)h * (z >> 1));
+    const float *row = L + src * nc;
+    uint16_t *out = planes + cell * kp;
+    for (int k = lane; k < kp; k += 32) {
+        const float v = k < nc ? __ldcg(row + k) * (__ldg(sinv + k) * g) : 0.f;
+        split_terms<true>(v, 2, out + k, part_elems);
+    }
+}
+
+// all cells of level `lev`, one warp per cell
 __global__ void k_split_L(const float *__restrict__ L, int lev, int nc, int kp, const float *__restrict__ sinv,
                           const unsigned *__restrict__ amaxL, uint16_t *__restrict__ planes, size_t part_elems)
 {
-    const int n = 1 << lev, h = n >> 1;
+    const int n = 1 << lev;
     const int64_t ncell = (int64_t)n * n * n;
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     const float g = pow2f(gain_m_exp(*amaxL));
-    for (int64_t cell = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); cell < ncell; cell += warps) {
-        const int x = (int)(cell % n), y = (int)((cell / n) % n), z = (int)(cell / ((int64_t)n * n));
-        const int64_t src = lev == 0 ? 0
-                                     : (int64_t)((x & 1) | ((y & 1) << 1) | ((z & 1) << 2)) * h * h * h + (x >> 1) +
-                                           (int64_t)h * ((y >> 1) + (int64_t)h * (z >> 1));
-        const float *row = L + src * nc;
-        uint16_t *out = planes + cell * kp;
-        for (int k = lane; k < kp; k += 32) {
-            const float v = k < nc ? row[k] * (__ldg(sinv + k) * g) : 0.f;
-            split_terms<true>(v, 2, out + k, part_elems);
-        }
-    }
+    for (int64_t cell = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); cell < ncell; cell += warps)
+        split_L_cell(L, lev, nc, kp, sinv, g, planes, part_elems, cell, lane);
 }
 
 // FP64 operators -> split B tables [part][slot][j][k] (K-major, rows kp wide):
@@ -1219,17 +1340,58 @@ __global__ void k_split_ops(int noff, const double *__restrict__ T, const double
 }
 
 // L = sum over the offset groups, in group order; with amax (fp16 split) the largest |L_e sx(e mod nc)|
-// is folded into *amax
+// is folded into *amax.  Elements [e0, e1) by threads t = 0 .. nt - 1, four at a time (16-byte loads and
+// stores) when n is a multiple of 4 (the partial arrays then stay 16-byte aligned); each element is the
+// same ordered sum either way.  Returns this thread's share of the maximum.
+__device__ __forceinline__ float group_sum_range(int64_t n, int groups, const float *__restrict__ part,
+                                                 float *__restrict__ L, int nc, const float *__restrict__ sx,
+                                                 bool fold, int64_t e0, int64_t e1, int64_t t, int64_t nt)
+{
+    float mx = 0.f;
+    if ((n & 3) == 0 && (e0 & 3) == 0) {
+        for (int64_t e = e0 + 4 * t; e < e1; e += 4 * nt) {
+            if (e + 4 > e1) {  // a ragged end of the range
+                for (int64_t k = e; k < e1; ++k) {
+                    float s = 0.f;
+                    for (int g = 0; g < groups; ++g) s += __ldcg(part + (int64_t)g * n + k);
+                    L[k] = s;
+                    if (fold) mx = fmaxf(mx, fabsf(s * __ldg(sx + (int)(k % nc))));
+                }
+                break;
+            }
+            float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int g = 0; g < groups; ++g) {
+                const float4 v = __ldcg(reinterpret_cast<const float4 *>(part + (int64_t)g * n + e));
+                s.x += v.x;
+                s.y += v.y;
+                s.z += v.z;
+                s.w += v.w;
+            }
+            *reinterpret_cast<float4 *>(L + e) = s;
+            if (fold) {
+                const int c = (int)(e % nc);
+                mx = fmaxf(mx, fabsf(s.x * __ldg(sx + c)));
+                mx = fmaxf(mx, fabsf(s.y * __ldg(sx + (c + 1 < nc ? c + 1 : c + 1 - nc))));
+                mx = fmaxf(mx, fabsf(s.z * __ldg(sx + (c + 2 < nc ? c + 2 : c + 2 - nc))));
+                mx = fmaxf(mx, fabsf(s.w * __ldg(sx + (c + 3 < nc ? c + 3 : c + 3 - nc))));
+            }
+        }
+    } else {
+        for (int64_t e = e0 + t; e < e1; e += nt) {
+            float s = 0.f;
+            for (int g = 0; g < groups; ++g) s += __ldcg(part + (int64_t)g * n + e);
+            L[e] = s;
+            if (fold) mx = fmaxf(mx, fabsf(s * __ldg(sx + (int)(e % nc))));
+        }
+    }
+    return mx;
+}
+
 __global__ void k_group_sum(int64_t n, int groups, const float *__restrict__ part, float *__restrict__ L, int nc,
                             const float *__restrict__ sx, unsigned *__restrict__ amax)
 {
-    float mx = 0.f;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-        float s = 0.f;
-        for (int g = 0; g < groups; ++g) s += part[(int64_t)g * n + e];
-        L[e] = s;
-        if (amax) mx = fmaxf(mx, fabsf(s * __ldg(sx + (int)(e % nc))));
-    }
+    float mx = group_sum_range(n, groups, part, L, nc, sx, amax != nullptr, 0, n,
+                               blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
     if (amax) {
         for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         if ((threadIdx.x & 31) == 0 && mx > 0.f) atomicMax(amax, __float_as_uint(mx));
@@ -1274,6 +1436,218 @@ __global__ void k_split_halo16(const float *__restrict__ M, int np, int hw, int 
         *reinterpret_cast<uint4 *>(out) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
         *reinterpret_cast<uint4 *>(out + part_elems) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
     }
+}
+
+// ------------------------------------------------------------------ persistent sweep of a batch
+// The tensor-core levels of many boxes (the lambda windows or frames of a batch) in one launch of
+// persistent CTA pairs.  Per (box, level) three stages, each a run of work items:
+//   P  the parent level's local expansion split into the fused L2L's fp16 planes (k_split_L), and the
+//      reset of the level's largest |L^ / s|;
+//   M  the tile pairs of the level's M2L + fused L2L (the k_m2l_tc_pair work, same offset groups, one item
+//      per tile pair running its groups in turn);
+//   G  with offset groups > 1, the group sum into L (k_group_sum), folding the level's maximum.
+// The items of all boxes sit in one device queue in level order, and P, M, G within a level, so every
+// item depends only on items before it.  A pair claims the next item with an atomic add, waits (bounded,
+// globaltimer) until the stage it depends on has counted all its items done, runs it, and adds one to
+// its own stage's counter (release after the pair's writes).  Because items are claimed in queue order
+// and the oldest unfinished item is always held by a running pair with its inputs complete, the sweep
+// makes progress whatever number of pairs is resident.  A wait that runs out sets the queue's abort
+// word: every pair stops claiming and the launch ends with FMM_ERR_TIMEOUT recorded.
+constexpr int SWEEP_P_CELLS = 512;         // parent cells per P item
+constexpr int64_t SWEEP_G_ELEMS = 1 << 16;  // L elements per G item
+
+struct SweepLevel {
+    CUtensorMap mA[2], mB[2], mL[2];  // the level's pair-kernel tensor maps
+    TcArgs a;                         // the level's pair-kernel arguments
+    const float *Lprev;               // P: L of level l - 1 (class layout)
+    const float *sinv;                // P: 1 / s(k)
+    const unsigned *amaxL_prev;       // P: largest |L^ / s| of level l - 1 (final when P runs)
+    uint16_t *planesL;                // P: the fused L2L planes
+    size_t partL;                     // P: elements per term of planesL
+    unsigned *amaxL;                  // this level's largest |L^ / s|, reset by P, folded by M or G
+    int64_t gs_n;                     // G: elements of the level's L
+    int lev, nc, kp;
+    int n_items[3];                   // items of stages P, M, G (G: 0 with one offset group)
+    int prev;                         // the same box's previous sweep level (-1: done before the launch)
+};
+
+__device__ __forceinline__ int ld_acquire(const int *p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int ld_relaxed(const int *p)
+{
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// counter of stage `st` of level entry `e`: q[2 + 3 e + st]; q[0] is the queue head, q[1] the abort word
+__device__ __forceinline__ int *sweep_counter(int *q, int e, int st) { return q + 2 + 3 * e + st; }
+
+// bounded wait for the dependency of item `it` (stage, level entry, index); false after limit_ns or abort
+__device__ bool sweep_wait(const SweepLevel *__restrict__ lv, int4 it, int *q, uint64_t limit_ns, int stall)
+{
+    const int *c;
+    int target;
+    if (it.x == 0) {
+        const int pe = lv[it.y].prev;
+        if (pe < 0) return true;
+        const int st = lv[pe].n_items[2] > 0 ? 2 : 1;
+        c = sweep_counter(q, pe, st);
+        target = lv[pe].n_items[st];
+    } else {
+        c = sweep_counter(q, it.y, it.x - 1);
+        target = lv[it.y].n_items[it.x - 1];
+    }
+    target += stall;  // test hook: a count that is never reached
+    if (ld_acquire(c) >= target) return true;
+    const uint64_t t0 = global_ns();
+    for (uint32_t i = 0;; ++i) {
+        __nanosleep(100);
+        if (ld_acquire(c) >= target) return true;
+        if ((i & 15) == 15) {
+            if (ld_relaxed(q + 1)) return false;
+            if (global_ns() - t0 > limit_ns) return false;
+        }
+    }
+}
+
+template <int NCH>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TC_THREADS, 1)
+    k_m2l_sweep(const SweepLevel *__restrict__ lv, const int4 *__restrict__ items, int n_items, int stages,
+                int *__restrict__ q, uint64_t wait_ns, int stall_item)
+{
+    extern __shared__ uint8_t smem_dyn[];
+    __shared__ __align__(8) PairBars bars;
+    __shared__ uint32_t tmem_sh;
+    __shared__ int abort_sh;
+    __shared__ int item_sh;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = cluster_rank();
+    const bool leader = rank == 0;
+    const uint32_t smem0 = (smem_u32(smem_dyn) + 1023u) & ~1023u;
+    if (threadIdx.x == 0) {
+        pair_bars_init(bars, stages);
+        abort_sh = 0;
+        item_sh = n_items;
+    }
+    cluster_sync_all();
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_sh)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = tmem_sh;
+    float *stage = reinterpret_cast<float *>(smem_dyn + (smem0 - smem_u32(smem_dyn)));
+    PairPipe pp;
+    int done_entry = -1, done_stage = 0;  // the item the pair finished last (leader thread 0)
+    for (;;) {
+        // ---- the leader's thread 0 publishes the finished item, claims the next and waits for its inputs
+        if (leader && threadIdx.x == 0) {
+            if (done_entry >= 0) {
+                __threadfence();
+                atomicAdd(sweep_counter(q, done_entry, done_stage), 1);
+            }
+            int j = n_items;
+            if (!ld_relaxed(q + 1)) {
+                j = atomicAdd(q, 1);
+                if (j < n_items && !sweep_wait(lv, items[j], q, wait_ns, j == stall_item ? 1 : 0)) {
+                    atomicOr(lv[items[j].y].a.err, ERRF_TIMEOUT);
+                    atomicExch(q + 1, 1);
+                    j = n_items;
+                }
+                if (j > n_items) j = n_items;
+            }
+            item_sh = j;
+            asm volatile("st.shared::cluster.s32 [%0], %1;" ::"r"(map_shared(smem_u32(&item_sh), 1)), "r"(j)
+                         : "memory");
+        }
+        __syncwarp();
+        cluster_sync_all();
+        const int j = item_sh;
+        if (j >= n_items) break;
+        const int4 it = items[j];
+        const SweepLevel &e = lv[it.y];
+        if (it.x == 1) {
+            // stage M: one tile pair; the maps live in global memory, and the planes it copies were written
+            // by other pairs through the generic proxy
+            if (warp == 0 && lane == 0) {
+#pragma unroll
+                for (int m = 0; m < 2; ++m) {
+                    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&e.mA[m]) : "memory");
+                    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&e.mB[m]) : "memory");
+                    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&e.mL[m]) : "memory");
+                }
+                asm volatile("fence.proxy.async.global;" ::: "memory");
+            }
+            __syncwarp();
+            // every offset group of the tile pair in turn (the ring runs on from group to group); only the
+            // last group's epilogue stages its rows in the ring
+            for (int g = 0; g < e.a.groups; ++g) {
+                if (*(volatile int *)&abort_sh) break;  // a wait ran out: the remaining groups are skipped
+                pair_tile<NCH>(&e.mA[0], &e.mA[1], &e.mB[0], &e.mB[1], &e.mL[0], &e.mL[1], e.a, it.z * e.a.groups + g,
+                               rank, smem0, stage, g == e.a.groups - 1, bars, tmem, &abort_sh, pp);
+            }
+        } else if (it.x == 0) {
+            // stage P: parent cells [SWEEP_P_CELLS it.z, ...) of level l - 1, one warp per cell over the pair
+            const int64_t ncell = (int64_t)1 << (3 * (e.lev - 1));
+            const int64_t c0 = (int64_t)it.z * SWEEP_P_CELLS;
+            const int64_t c1 = c0 + SWEEP_P_CELLS < ncell ? c0 + SWEEP_P_CELLS : ncell;
+            const float g = pow2f(gain_m_exp(__ldcg(e.amaxL_prev)));
+            const int gw = (int)rank * (TC_THREADS / 32) + warp;
+            for (int64_t cell = c0 + gw; cell < c1; cell += 2 * (TC_THREADS / 32))
+                split_L_cell(e.Lprev, e.lev - 1, e.nc, e.kp, e.sinv, g, e.planesL, e.partL, cell, lane);
+            if (it.z == 0 && leader && threadIdx.x == 0) atomicExch(e.amaxL, 0u);
+            asm volatile("fence.proxy.async.global;" ::: "memory");  // the planes are read by TMA next
+        } else {
+            // stage G: L elements [SWEEP_G_ELEMS it.z, ...), thread per element over the pair
+            const int64_t e0 = (int64_t)it.z * SWEEP_G_ELEMS;
+            const int64_t e1 = e0 + SWEEP_G_ELEMS < e.gs_n ? e0 + SWEEP_G_ELEMS : e.gs_n;
+            float mx = group_sum_range(e.gs_n, e.a.groups, e.a.Lpart, e.a.L, e.nc, e.sinv, true, e0, e1,
+                                       (int64_t)rank * TC_THREADS + threadIdx.x, 2 * TC_THREADS);
+            for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            if (lane == 0 && mx > 0.f) atomicMax(e.amaxL, __float_as_uint(mx));
+        }
+        __syncthreads();
+        if (threadIdx.x == 0 && abort_sh) atomicExch(q + 1, 1);
+        __syncwarp();
+        cluster_sync_all();  // both CTAs are done with the item
+        if (leader && threadIdx.x == 0) {
+            done_entry = it.y;
+            done_stage = it.x;
+        }
+    }
+
+    // ---------------- teardown: every MMA done (bounded wait), pair barrier, collective TMEM release
+    if (warp == 1 && lane == 0 && leader) mma_commit_pair(smem_u32(&bars.done));
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile int no_abort = 0;
+        if (!mbar_wait_cluster(smem_u32(&bars.done), 0, &no_abort)) atomicExch(q + 1, 1);
+    }
+    fence_before();
+    __syncthreads();
+    cluster_sync_all();
+    fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    cluster_sync_all();
+}
+
+// every box of the sweep reports a launch that stopped early
+__global__ void k_sweep_status(const int *__restrict__ q, int *const *__restrict__ errs, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && q[1]) atomicOr(errs[i], ERRF_TIMEOUT);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
@@ -1335,6 +1709,20 @@ TcPairKernel pick_pair_kernel(int nch)
         FMM_TC_CASE(1) FMM_TC_CASE(2) FMM_TC_CASE(3) FMM_TC_CASE(4) FMM_TC_CASE(6) FMM_TC_CASE(7) FMM_TC_CASE(8)
         FMM_TC_CASE(9) FMM_TC_CASE(11) FMM_TC_CASE(13) FMM_TC_CASE(15) FMM_TC_CASE(16)
 #undef FMM_TC_CASE
+    default: return nullptr;
+    }
+}
+
+typedef void (*SweepKernel)(const SweepLevel *, const int4 *, int, int, int *, uint64_t, int);
+
+// the sweep is built for the orders p = 6, 8, 10 and 12 (NCH 4, 6, 8, 11)
+SweepKernel pick_sweep_kernel(int nch)
+{
+    switch (nch) {
+    case 4: return k_m2l_sweep<4>;
+    case 6: return k_m2l_sweep<6>;
+    case 8: return k_m2l_sweep<8>;
+    case 11: return k_m2l_sweep<11>;
     default: return nullptr;
     }
 }
@@ -1675,6 +2063,41 @@ fmm_status launch_m2m_tc(Plan &P, int l)
     return FMM_OK;
 }
 
+// Arguments of the level-l M2L (+ fused L2L with the fp16 split); returns whether the level runs on CTA
+// pairs (an even number of full 128-row tiles per class), whose stage ring and M = 256 descriptor it sets
+static bool m2l_args(const Plan &P, const TcState *S, int l, bool precise, int pa, int pb, TcArgs &a)
+{
+    const int np = 1 << (l - 1);
+    fill_common(P, S, pa, pb, a);
+    if (precise) a.gchunks = 0;  // the solute-only pass keeps every product
+    a.mode = 0;
+    a.np = np;
+    a.bx = S->bx[l];
+    a.by = S->by[l];
+    a.bz = S->bz[l];
+    a.rows = a.bx * a.by * a.bz;
+    a.tiles_x = np / a.bx;
+    a.tiles_y = np / a.by;
+    a.tiles_per_class = a.tiles_x * a.tiles_y * (np / a.bz);
+    a.groups = S->groups[l];
+    a.per_group = S->per_group[l];
+    a.n_off = a.n_il + (S->f16 ? 1 : 0);
+    a.L = (float *)P.L[l];
+    a.post = S->f16 ? S->s32 : nullptr;
+    a.amax = S->f16 ? S->amax + l : nullptr;
+    a.amaxL = S->f16 ? S->amaxL + l - 1 : nullptr;
+    if (S->f16) {
+        a.amax_out = a.groups == 1 ? S->amaxL + l : nullptr;
+        a.sx = S->s32inv;
+    }
+    const bool pair = S->f16 && P.tc_pair && a.rows == TC_ROWS && a.tiles_per_class % 2 == 0;
+    if (pair) {
+        a.stages = tc_pair_stages(S->npad);
+        a.idesc = (1u << 4) | ((uint32_t)(S->npad >> 3) << 17) | ((uint32_t)((2 * TC_ROWS) >> 4) << 24);  // M = 256
+    }
+    return pair;
+}
+
 fmm_status launch_m2l_tc(Plan &P, int l, bool precise, bool split)
 {
     TcState *S = (TcState *)P.tc;
@@ -1707,40 +2130,16 @@ fmm_status launch_m2l_tc(Plan &P, int l, bool precise, bool split)
             (const float *)P.M[l], np, P.ws, P.nc, S->kp, pa, nullptr, nullptr, S->planes[l], S->part_elems[l]);
         FMM_LAUNCH_CHECK(P);
     }
-    TcArgs a;
-    fill_common(P, S, pa, pb, a);
-    if (precise) a.gchunks = 0;  // the solute-only pass keeps every product
-    a.mode = 0;
-    a.np = np;
-    a.bx = S->bx[l];
-    a.by = S->by[l];
-    a.bz = S->bz[l];
-    a.rows = a.bx * a.by * a.bz;
-    a.tiles_x = np / a.bx;
-    a.tiles_y = np / a.by;
-    a.tiles_per_class = a.tiles_x * a.tiles_y * (np / a.bz);
-    a.groups = S->groups[l];
-    a.per_group = S->per_group[l];
-    a.n_off = a.n_il + (S->f16 ? 1 : 0);
-    a.L = (float *)P.L[l];
-    a.post = S->f16 ? S->s32 : nullptr;
-    a.amax = S->f16 ? S->amax + l : nullptr;
-    a.amaxL = S->f16 ? S->amaxL + l - 1 : nullptr;
-    if (S->f16) {  // level l's largest |L^ / s|, for the fused L2L of level l + 1
+    if (S->f16)  // level l's largest |L^ / s|, for the fused L2L of level l + 1
         FMM_CUDA_TRY(cudaMemsetAsync(S->amaxL + l, 0, sizeof(unsigned), P.stream));
-        a.amax_out = a.groups == 1 ? S->amaxL + l : nullptr;
-        a.sx = S->s32inv;
-    }
+    TcArgs a;
+    const bool pair = m2l_args(P, S, l, precise, pa, pb, a);
     unsigned grid = 8u * (unsigned)a.tiles_per_class * (unsigned)a.groups;
-    // CTA pairs take two tiles of one class: an even number of full 128-row tiles per class
-    const bool pair = S->f16 && P.tc_pair && a.rows == TC_ROWS && a.tiles_per_class % 2 == 0;
     const bool time_it = P.timings_on && l == P.d && P.ev_top[0] && !precise;
     if (time_it) cudaEventRecord(P.ev_top[0], P.stream);
     if (pair) {
         TcPairKernel k2 = pick_pair_kernel(S->npad / 16);
         if (!k2) return FMM_ERR_INTERNAL;
-        a.stages = tc_pair_stages(S->npad);
-        a.idesc = (1u << 4) | ((uint32_t)(S->npad >> 3) << 17) | ((uint32_t)((2 * TC_ROWS) >> 4) << 24);  // M = 256
         k2<<<grid, TC_THREADS, tc_pair_smem_bytes(S->npad), P.stream>>>(S->mapA[l][0], S->mapA[l][1], S->mapB2[0],
                                                                          S->mapB2[1], S->mapL[l][0], S->mapL[l][1], a);
     } else {
@@ -1764,12 +2163,210 @@ fmm_status launch_m2l_tc(Plan &P, int l, bool precise, bool split)
     return FMM_OK;
 }
 
+// ------------------------------------------------------------------ persistent sweep (host)
+int tc_sweep_first_level(const Plan &P)
+{
+    const TcState *S = (const TcState *)P.tc;
+    if (!S || !S->f16 || !P.tc_pair || P.precision != FMM_PREC_MIXED) return 0;
+    for (int l = 2; l <= P.d; ++l) {  // level 1 reads the lattice's L[0]: it stays on its own launches
+        const int np = 1 << (l - 1);
+        const int tpc = (np / S->bx[l]) * (np / S->by[l]) * (np / S->bz[l]);
+        if (S->bx[l] * S->by[l] * S->bz[l] == TC_ROWS && tpc % 2 == 0) return l;  // and every deeper level
+    }
+    return 0;
+}
+
+struct Sweep {
+    std::vector<Plan *> plans;  // the plans taking part
+    std::vector<int> first;     // their first sweep level
+    int nch = 0, stages = 0, pairs = 0, n_items = 0, n_lv = 0, stall_item = -1;
+    size_t smem = 0;
+    SweepLevel *d_lv = nullptr;
+    int4 *d_items = nullptr;
+    int *d_q = nullptr;
+    int **d_errs = nullptr;
+};
+
+void sweep_destroy(Sweep *sw)
+{
+    if (!sw) return;
+    for (Plan *P : sw->plans) P->sweep_from = 0;
+    cudaFree(sw->d_lv);
+    cudaFree(sw->d_items);
+    cudaFree(sw->d_q);
+    cudaFree(sw->d_errs);
+    delete sw;
+}
+
+void sweep_enable(Sweep *sw, bool on)
+{
+    if (!sw) return;
+    for (size_t k = 0; k < sw->plans.size(); ++k) sw->plans[k]->sweep_from = on ? sw->first[k] : 0;
+}
+
+int sweep_plans(const Sweep *sw) { return sw ? (int)sw->plans.size() : 0; }
+
+fmm_status sweep_create(Plan *const *plans, int n, Sweep **out)
+{
+    *out = nullptr;
+    Sweep *sw = new (std::nothrow) Sweep();
+    if (!sw) return FMM_ERR_OOM;
+    for (int i = 0; i < n; ++i) {
+        Plan &P = *plans[i];
+        const int l0 = tc_sweep_first_level(P);
+        if (l0 <= 0) continue;
+        const int c = ((const TcState *)P.tc)->npad / 16;
+        if (!pick_sweep_kernel(c) || (sw->nch && c != sw->nch)) continue;  // stays on its per-level launches
+        sw->nch = c;
+        sw->plans.push_back(&P);
+        sw->first.push_back(l0);
+    }
+    if (sw->plans.empty()) {
+        delete sw;
+        return FMM_OK;
+    }
+    // one entry per (plan, level), each pointing at the same plan's previous level
+    std::vector<SweepLevel> lv;
+    int lmin = 1 << 30, lmax = 0;
+    for (size_t k = 0; k < sw->plans.size(); ++k) {
+        Plan &P = *sw->plans[k];
+        const TcState *S = (const TcState *)P.tc;
+        int prev = -1;
+        for (int l = sw->first[k]; l <= P.d; ++l) {
+            SweepLevel e;
+            memset((void *)&e, 0, sizeof(e));
+            if (!m2l_args(P, S, l, false, S->pa, S->pb, e.a) || (sw->stages && e.a.stages != sw->stages)) {
+                sweep_destroy(sw);
+                return FMM_ERR_INTERNAL;
+            }
+            sw->stages = e.a.stages;
+            e.mA[0] = S->mapA[l][0];
+            e.mA[1] = S->mapA[l][1];
+            e.mB[0] = S->mapB2[0];
+            e.mB[1] = S->mapB2[1];
+            e.mL[0] = S->mapL[l][0];
+            e.mL[1] = S->mapL[l][1];
+            const int64_t ncl = (int64_t)1 << (3 * (l - 1));  // cells of level l - 1
+            e.Lprev = (const float *)P.L[l - 1];
+            e.sinv = S->s32inv;
+            e.amaxL_prev = S->amaxL + l - 1;
+            e.planesL = S->planesL;
+            e.partL = (size_t)ncl * S->kp;
+            e.amaxL = S->amaxL + l;
+            e.gs_n = 8 * ncl * P.nc;
+            e.lev = l;
+            e.nc = P.nc;
+            e.kp = S->kp;
+            e.n_items[0] = (int)((ncl + SWEEP_P_CELLS - 1) / SWEEP_P_CELLS);
+            e.n_items[1] = 4 * e.a.tiles_per_class;  // tile pairs: 8 classes x tiles / 2, all groups in one item
+            e.n_items[2] = e.a.groups > 1 ? (int)((e.gs_n + SWEEP_G_ELEMS - 1) / SWEEP_G_ELEMS) : 0;
+            e.prev = prev;
+            prev = (int)lv.size();
+            lv.push_back(e);
+            lmin = l < lmin ? l : lmin;
+            lmax = l > lmax ? l : lmax;
+        }
+    }
+    // the queue: level by level, within a level stage P of every entry, then M, then G
+    std::vector<int4> items;
+    int m_items = 0;
+    for (int l = lmin; l <= lmax; ++l)
+        for (int st = 0; st < 3; ++st)
+            for (size_t e = 0; e < lv.size(); ++e) {
+                if (lv[e].lev != l) continue;
+                for (int i = 0; i < lv[e].n_items[st]; ++i) {
+                    if (st == 1 && sw->stall_item < 0) sw->stall_item = (int)items.size();
+                    if (st == 1) ++m_items;
+                    items.push_back(make_int4(st, (int)e, i, 0));
+                }
+            }
+    sw->n_lv = (int)lv.size();
+    sw->n_items = (int)items.size();
+    std::vector<int *> errs;
+    for (Plan *P : sw->plans) errs.push_back(P->d_err);
+    fmm_status s = FMM_OK;
+    if (cudaMalloc(&sw->d_lv, sizeof(SweepLevel) * lv.size()) != cudaSuccess ||
+        cudaMalloc(&sw->d_items, sizeof(int4) * items.size()) != cudaSuccess ||
+        cudaMalloc(&sw->d_q, sizeof(int) * (2 + 3 * lv.size())) != cudaSuccess ||
+        cudaMalloc(&sw->d_errs, sizeof(int *) * errs.size()) != cudaSuccess)
+        s = FMM_ERR_OOM;
+    if (s == FMM_OK &&
+        (cudaMemcpy(sw->d_lv, lv.data(), sizeof(SweepLevel) * lv.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+         cudaMemcpy(sw->d_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+         cudaMemcpy(sw->d_errs, errs.data(), sizeof(int *) * errs.size(), cudaMemcpyHostToDevice) != cudaSuccess))
+        s = FMM_ERR_CUDA;
+    // as many pairs as can be resident (one CTA per SM), at most one per tile pair of the queue
+    const int npad = 16 * sw->nch;
+    sw->smem = tc_pair_smem_bytes(npad);
+    SweepKernel k = pick_sweep_kernel(sw->nch);
+    if (s == FMM_OK && cudaFuncSetAttribute((const void *)k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)sw->smem) != cudaSuccess)
+        s = FMM_ERR_CUDA;
+    if (s == FMM_OK) {
+        int dev = 0, sms = 0, clusters = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(sms > 0 ? sms : 2));
+        cfg.blockDim = dim3(TC_THREADS);
+        cfg.dynamicSmemBytes = sw->smem;
+        if (cudaOccupancyMaxActiveClusters(&clusters, (const void *)k, &cfg) != cudaSuccess || clusters < 1)
+            clusters = sms / 2;
+        cudaGetLastError();
+        sw->pairs = clusters < m_items ? clusters : m_items;
+        if (sw->pairs < 1) sw->pairs = 1;
+    }
+    if (s != FMM_OK) {
+        sweep_destroy(sw);
+        return s;
+    }
+    sweep_enable(sw, true);
+    *out = sw;
+    return FMM_OK;
+}
+
+fmm_status sweep_launch(Sweep *sw, cudaStream_t st, uint64_t wait_ns, bool stall, int max_pairs)
+{
+    if (!sw) return FMM_OK;
+    FMM_CUDA_TRY(cudaMemsetAsync(sw->d_q, 0, sizeof(int) * (2 + 3 * (size_t)sw->n_lv), st));
+    SweepKernel k = pick_sweep_kernel(sw->nch);
+    const int pairs = max_pairs > 0 && max_pairs < sw->pairs ? max_pairs : sw->pairs;
+    k<<<2u * (unsigned)pairs, TC_THREADS, sw->smem, st>>>(sw->d_lv, sw->d_items, sw->n_items, sw->stages, sw->d_q,
+                                                              wait_ns, stall ? sw->stall_item : -1);
+    FMM_CUDA_TRY(cudaGetLastError());
+    const int n = (int)sw->plans.size();
+    k_sweep_status<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(sw->d_q, sw->d_errs, n);
+    FMM_CUDA_TRY(cudaGetLastError());
+    return FMM_OK;
+}
+
+// The split operator tables depend only on p, ws and the split (the M2L, M2M and L2L operators are
+// built for unit cells), so plans that agree on those can read one copy: dst drops its own and reads
+// src's, which must outlive it.  A plan with another table is left alone.
+fmm_status tc_share_operators(Plan &dst, const Plan &src)
+{
+    TcState *D = (TcState *)dst.tc;
+    const TcState *S = (const TcState *)src.tc;
+    if (!D || !S || D == S || D->ops == S->ops) return FMM_OK;
+    if (dst.p != src.p || dst.ws != src.ws || D->f16 != S->f16 || D->pa != S->pa || D->pb != S->pb ||
+        D->parts != S->parts || D->npad != S->npad || D->kp != S->kp || D->noff != S->noff || D->sw != S->sw ||
+        D->ops_part_elems != S->ops_part_elems)
+        return FMM_OK;
+    FMM_CUDA_TRY(cudaDeviceSynchronize());  // nothing of dst's may still read its own table
+    if (!D->ops_borrowed) cudaFree(D->ops);
+    D->ops = S->ops;
+    D->ops_borrowed = true;
+    memcpy((void *)D->mapB, (const void *)S->mapB, sizeof(D->mapB));
+    memcpy((void *)D->mapB2, (const void *)S->mapB2, sizeof(D->mapB2));
+    return FMM_OK;
+}
+
 void tc_free(Plan &P)
 {
     TcState *S = (TcState *)P.tc;
     if (!S) return;
     for (int l = 0; l < 9; ++l) cudaFree(S->planes[l]);
-    cudaFree(S->ops);
+    if (!S->ops_borrowed) cudaFree(S->ops);
     cudaFree(S->Lpart);
     cudaFree(S->s32);
     cudaFree(S->s32inv);

@@ -27,6 +27,7 @@ FMM_OPT_M2L_GRADE = 10
 FMM_OPT_M2L_ACC_GROUP = 11
 FMM_OPT_SOFTCORE, FMM_OPT_SOFTCORE_LAMBDA, FMM_OPT_SOFTCORE_ALPHA = 12, 13, 14
 FMM_OPT_WAIT_BUDGET_NS, FMM_OPT_INJECT_STALL = 15, 16
+FMM_BATCH_OPT_SWEEP, FMM_BATCH_OPT_WAIT_BUDGET_NS, FMM_BATCH_OPT_INJECT_STALL, FMM_BATCH_OPT_SWEEP_PAIRS = 1, 2, 3, 4
 BOUNDARY = {"conducting": 0, "vacuum": 1}
 PRECISION = {"fp64": 0, "mixed": 1}
 SPLIT = {"bf16x3": 0, "bf16x2": 1, "fp32": 2, "bf16a2b3": 3, "fp16x2": 4}
@@ -110,6 +111,10 @@ def load_library(path: str = LIB_PATH):
     L.fmm_batch_set_softcore.restype = c_int
     L.fmm_batch_set_graph.argtypes = [vp, c_int]
     L.fmm_batch_set_graph.restype = c_int
+    L.fmm_batch_set_option.argtypes = [vp, c_int, i64, dbl]
+    L.fmm_batch_set_option.restype = c_int
+    L.fmm_batch_sweep_info.argtypes = [vp, ctypes.POINTER(c_int), vp]
+    L.fmm_batch_sweep_info.restype = c_int
     L.fmm_batch_destroy.argtypes = [vp]
     L.fmm_batch_destroy.restype = None
     L.fmm_status_string.argtypes = [c_int]
@@ -320,6 +325,19 @@ class FMMBatch:
 
     def set_graph(self, enable: bool):
         _check(self._lib.fmm_batch_set_graph(self._h, 1 if enable else 0), "fmm_batch_set_graph")
+
+    def set_option(self, key: int, ival: int, dval: float = 0.0):
+        _check(self._lib.fmm_batch_set_option(self._h, int(key), int(ival), float(dval)), "fmm_batch_set_option")
+
+    def set_sweep(self, enable: bool):
+        self.set_option(FMM_BATCH_OPT_SWEEP, 1 if enable else 0)
+
+    def sweep_info(self):
+        """Boxes in the persistent sweep and each box's first sweep level (0: not in it)."""
+        nb = ctypes.c_int()
+        first = np.zeros(self.n, np.int32)
+        _check(self._lib.fmm_batch_sweep_info(self._h, ctypes.byref(nb), first.ctypes.data), "fmm_batch_sweep_info")
+        return {"boxes": nb.value, "first_level": first.tolist()}
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

@@ -50,6 +50,12 @@ def test_status_strings_and_null_handling(lib):
     assert lib.fmm_plan_create(-1.0, 10, 3, 4, ctypes.byref(h)) == 1
     assert lib.fmm_plan_create(1.0, 10, 3, 99, ctypes.byref(h)) == 1
     assert lib.fmm_plan_create(1.0, 10, 3, 4, None) == 1
+    lib.fmm_batch_set_option.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double]
+    lib.fmm_batch_set_option.restype = ctypes.c_int
+    assert lib.fmm_batch_set_option(None, 1, 1, 0.0) == 1
+    lib.fmm_batch_sweep_info.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    lib.fmm_batch_sweep_info.restype = ctypes.c_int
+    assert lib.fmm_batch_sweep_info(None, None, None) == 1
 
 
 def test_product_path_does_not_touch_the_oracle():

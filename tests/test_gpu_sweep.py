@@ -1,0 +1,112 @@
+"""The persistent sweep of a batch (fmm_batch_*, FMM_BATCH_OPT_SWEEP): the CTA-pair
+tensor-core levels (M2L of Eq. Lcoeffdef with the fused L2L) of all boxes in one
+launch of persistent CTA pairs pulling (box, level, stage, tile) items from a device
+queue.  It must give bitwise the results of the per-level launches, on the stream
+path and in the recorded graph, cover exactly the boxes it can (order p of the first
+box taking part, a level with full tile pairs), agree with single plans, and stop
+cleanly with FMM_ERR_TIMEOUT when a dependency wait runs out."""
+import numpy as np
+import pytest
+
+from paper_2003_13218_gb300 import boxes
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def _windows(sizes, seed=7):
+    out = []
+    for b, n_w in enumerate(sizes):
+        ion = ("Mg", "Na", "Cl")[b % 3]
+        lam = (b % 4) / 3.0
+        box = boxes.ion_in_water(n_w, ion, seed=seed * 100 + b, ion_charge=lam * boxes.ION_CHARGE[ion])
+        out.append((box, lam))
+    return out
+
+
+def _dev(ws):
+    pos = [torch.from_numpy(b.pos).to(DEV) for b, _ in ws]
+    q = [torch.from_numpy(b.q).to(DEV) for b, _ in ws]
+    sol = [torch.from_numpy(b.is_solute).to(DEV) for b, _ in ws]
+    return pos, q, sol
+
+
+# depths 3 (no pair level), 4 (sweep level 4), 5 (levels 4, 5) and 6 (levels 4..6); one box at p = 10
+SIZES = [900, 5000, 11000, 16000, 21000, 34000]
+DEPTHS = [3, 4, 4, 5, 5, 6]
+PS = [12, 12, 10, 12, 12, 12]
+
+
+def test_sweep_covers_the_pair_levels_and_is_bitwise_the_per_level_path():
+    from paper_2003_13218_gb300.fmm import FMMBatch
+    ws = _windows(SIZES)
+    lam = np.array([l for _, l in ws])
+    pos, q, sol = _dev(ws)
+    bt = FMMBatch([b.L for b, _ in ws], [b.N for b, _ in ws], DEPTHS, PS)
+    info = bt.sweep_info()
+    # depth 3: no level with full tile pairs; p = 10: another order than the first box taking part
+    assert info["first_level"] == [0, 4, 0, 4, 4, 4] and info["boxes"] == 4
+    bt.set_graph(False)
+    r_on = bt.lambda_energies(pos, q, sol, lam)
+    r_on2 = bt.lambda_energies(pos, q, sol, lam)
+    bt.set_sweep(False)
+    assert bt.sweep_info() == {"boxes": 0, "first_level": [0] * 6}
+    r_off = bt.lambda_energies(pos, q, sol, lam)
+    for k in ("e_total", "e_uv", "v_lambda", "dv_dlambda"):
+        assert np.array_equal(r_on[k], r_off[k]), k
+        assert np.array_equal(r_on[k], r_on2[k]), k
+    bt.close()
+
+
+def test_sweep_in_the_recorded_graph_and_against_single_plans():
+    from paper_2003_13218_gb300.fmm import FMMBatch, FMMPlan
+    ws = _windows(SIZES[1:], seed=8)
+    d, p = DEPTHS[1:], [12] * 5
+    pos, q, sol = _dev(ws)
+    bt = FMMBatch([b.L for b, _ in ws], [b.N for b, _ in ws], d, p)
+    assert bt.sweep_info()["boxes"] == 5
+    r1 = bt.lambda_energies(pos, q, sol)  # stream path, then recorded
+    r2 = bt.lambda_energies(pos, q, sol)  # replay
+    r3 = bt.lambda_energies(pos, q, sol)
+    assert bt.info(0)["replays"] == 2
+    for k in ("e_total", "e_uv"):
+        assert np.array_equal(r1[k], r2[k]) and np.array_equal(r1[k], r3[k])
+    # coordinates moved in place: the replayed sweep sees them
+    g = torch.Generator(device="cpu").manual_seed(3)
+    for i in range(len(ws)):
+        pos[i].add_((torch.rand(pos[i].shape, generator=g, dtype=torch.float64) - 0.5).to(DEV) * 0.02)
+    r4 = bt.lambda_energies(pos, q, sol)
+    assert bt.info(0)["replays"] == 3
+    for i, (b, _) in enumerate(ws):
+        plan = FMMPlan(b.L, b.N, d[i], 12, precision="mixed")
+        t, uv = plan.evaluate(pos[i], q[i], sol[i], forces=None)
+        plan.close()
+        assert abs(r4["e_total"][i] - t["total"]) <= 1e-12 * abs(t["total"])
+        assert abs(r4["e_uv"][i] - uv["e_uv"]) <= 1e-12 * abs(t["total"])
+    bt.close()
+
+
+def test_sweep_dependency_wait_runs_out_and_the_batch_recovers():
+    from paper_2003_13218_gb300.fmm import (FMM_BATCH_OPT_INJECT_STALL, FMM_BATCH_OPT_WAIT_BUDGET_NS, FMMBatch,
+                                            FMMError)
+    ws = _windows([5000, 16000, 21000], seed=9)
+    pos, q, sol = _dev(ws)
+    bt = FMMBatch([b.L for b, _ in ws], [b.N for b, _ in ws], [4, 5, 5], [12] * 3)
+    ref = bt.lambda_energies(pos, q, sol)
+    bt.set_option(FMM_BATCH_OPT_WAIT_BUDGET_NS, 1_000_000)  # 1 ms
+    bt.set_option(FMM_BATCH_OPT_INJECT_STALL, 1)
+    for _ in range(2):  # the stream path, then the graph recorded with the stall
+        with pytest.raises(FMMError) as e:
+            bt.lambda_energies(pos, q, sol)
+        assert e.value.code == 5  # FMM_ERR_TIMEOUT
+    bt.set_option(FMM_BATCH_OPT_INJECT_STALL, 0)
+    again = bt.lambda_energies(pos, q, sol)
+    again2 = bt.lambda_energies(pos, q, sol)
+    for k in ("e_total", "e_uv"):
+        assert np.array_equal(again[k], ref[k]) and np.array_equal(again2[k], ref[k])
+    for key, bad in ((FMM_BATCH_OPT_WAIT_BUDGET_NS, 999), (FMM_BATCH_OPT_INJECT_STALL, 2), (99, 0)):
+        with pytest.raises(FMMError) as e:
+            bt.set_option(key, bad)
+        assert e.value.code == 1
+    bt.close()
