@@ -424,6 +424,8 @@ def oracle_step(b, d, p):
     oracle.solute_solvent(b.pos, b.q, b.is_solute, b.L, d, p)
 
 
+BATCH_TOL = 1e-6  # relative energy error budget of the batch tuner's order choice (the metric's 1e-6)
+
 SAMPLE_SHRINK = 8  # the oracle's bounded sample: a 1/512 sub-box (both the cpu_baseline leg and --impl reference)
 
 
@@ -511,9 +513,13 @@ def measure_batch(steps: int, warmup: int, rank: int, local: int, serial: bool =
     q = [torch.from_numpy(b.q).to(dev) for b, _ in win]
     sol = [torch.from_numpy(b.is_solute).to(dev) for b, _ in win]
     t0 = time.perf_counter()
-    bt = FMMBatch([b.L for b, _ in win], [b.N for b, _ in win], None, [12] * len(win), precision="mixed")
+    # depth, order (within BATCH_TOL relative energy error) and launch form chosen by the batch tuner
+    bt = FMMBatch([b.L for b, _ in win], [b.N for b, _ in win], None, [-1] * len(win), precision="mixed",
+                  energy_rel_tol=BATCH_TOL, sweep="auto")
     create_s = time.perf_counter() - t0
     depths = [bt.info(i)["depth"] for i in range(len(win))]
+    orders = [bt.info(i)["p"] for i in range(len(win))]
+    tune = bt.tune_info()
 
     def timed(fn, k):
         torch.cuda.synchronize()
@@ -530,13 +536,17 @@ def measure_batch(steps: int, warmup: int, rank: int, local: int, serial: bool =
     t_graph = timed(lambda: bt.lambda_energies(pos, q, sol, lam), steps)
     clocks = sampler.stop()
     info = bt.info(0)
-    sweep = bt.sweep_info()
-    # the same graph with the sweep's levels on per-level launches instead (A/B of the persistent launch)
-    bt.set_sweep(False)
+    r_graph = bt.lambda_energies(pos, q, sol, lam)
+    # the same graph with the other launch form (A/B of the persistent sweep)
+    sweep_was = tune["sweep_on"]
+    bt.set_sweep(not sweep_was)
+    sweep = bt.sweep_info() if not sweep_was else None
     bt.lambda_energies(pos, q, sol, lam)
-    r_off = bt.lambda_energies(pos, q, sol, lam)
-    t_off = timed(lambda: bt.lambda_energies(pos, q, sol, lam), steps)
-    bt.set_sweep(True)
+    r_other = bt.lambda_energies(pos, q, sol, lam)
+    t_other = timed(lambda: bt.lambda_energies(pos, q, sol, lam), steps)
+    bt.set_sweep(sweep_was)
+    if sweep is None:
+        sweep = bt.sweep_info()
     bt.set_graph(False)
     bt.lambda_energies(pos, q, sol, lam)
     t_stream = timed(lambda: bt.lambda_energies(pos, q, sol, lam), steps)
@@ -544,13 +554,20 @@ def measure_batch(steps: int, warmup: int, rank: int, local: int, serial: bool =
     bt.close()
     batch = {"graph_ms": t_graph * 1e3, "stream_path_ms": t_stream * 1e3, "plan_create_s": create_s,
              "depths": depths, "replays": info["replays"],
+             "orders": sorted(set(orders)),
+             "tuner": {"energy_rel_tol": BATCH_TOL, "p_err_vs_p15_on_water_test_box": {str(k): v for k, v in
+                                                                                   tune["p_err"].items()},
+                       "p_chosen": tune["p_chosen"], "graph_ms_sweep_off": tune["ms_sweep_off"],
+                       "graph_ms_sweep_on": tune["ms_sweep_on"], "sweep_chosen": tune["sweep_on"],
+                       "note": "timed on uniform test charges at batch creation"},
              "sweep": {"boxes": sweep["boxes"], "first_levels": sorted(set(sweep["first_level"])),
-                       "graph_ms_per_level_launches": t_off * 1e3,
-                       "bitwise_equal_to_per_level_launches": bool(
-                           all(np.array_equal(r_stream[k], r_off[k]) for k in ("e_total", "e_uv")))}}
+                       "in_use": sweep_was,
+                       ("graph_ms_per_level_launches" if sweep_was else "graph_ms_with_sweep"): t_other * 1e3,
+                       "bitwise_equal_to_the_other_form": bool(
+                           all(np.array_equal(r_graph[k], r_other[k]) for k in ("e_total", "e_uv")))}}
     if serial:
         # the same boxes and depths on single plans, one after the other
-        plans = [FMMPlan(b.L, b.N, d, 12, precision="mixed") for (b, _), d in zip(win, depths)]
+        plans = [FMMPlan(b.L, b.N, d, pi, precision="mixed") for (b, _), d, pi in zip(win, depths, orders)]
         def serial_run():
             for pl, x, y, z in zip(plans, pos, q, sol):
                 pl.evaluate(x, y, z, forces=None)
@@ -560,10 +577,24 @@ def measure_batch(steps: int, warmup: int, rank: int, local: int, serial: bool =
         for pl in plans:
             pl.close()
         batch["single_plans_serial_ms"] = t_serial * 1e3
+        # the tuned order on the actual boxes: the smallest and the largest box against FP64 at the same
+        # order (the metric's arithmetic error) and against FP64 at p = 15 (the change the order makes)
+        acc = {}
+        for i in (int(np.argmin([b.N for b, _ in win])), int(np.argmax([b.N for b, _ in win]))):
+            b = win[i][0]
+            row = {}
+            for pr, key in ((orders[i], "vs_fp64_same_p"), (15, "vs_fp64_p15")):
+                ref = FMMPlan(b.L, b.N, depths[i], pr, precision="fp64")
+                e64 = ref.evaluate(pos[i], q[i], sol[i], forces=None)[0]["total"]
+                ref.close()
+                row[key] = abs(r_stream["e_total"][i] - e64) / abs(e64)
+            acc["box%d_N%d" % (i, b.N)] = row
+        batch["rel_err_e_total"] = acc
         batch["max_rel_diff_e_uv_vs_single_plans"] = float(np.max(np.abs(r_stream["e_uv"] - e_single) /
                                                                   np.maximum(np.abs(e_single), 1e-30)))
     workload = ("lambda64: 64 boxes, %d charges in all (%d..%d per box), species Mg/Na/Cl, lambda = (b mod 16)/15, "
-                "p 12, depth chosen by timing" % (Ntot, min(b.N for b, _ in win), max(b.N for b, _ in win)))
+                "order p and depth chosen by the batch tuner" % (Ntot, min(b.N for b, _ in win),
+                                                                  max(b.N for b, _ in win)))
     out = {"Ntot": Ntot, "t_graph": t_graph, "batch": batch, "clocks": clocks, "workload": workload}
     if shard_world > 1:
         from paper_2003_13218_gb300 import shard

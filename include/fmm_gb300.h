@@ -274,6 +274,39 @@ fmm_status fmm_batch_create(int nbox, const double *box, const int64_t *N, const
                             int precision, fmm_batch *out);
 
 /*
+ * What the batch tuner chooses beyond the depth (fmm_batch_create_tuned).
+ *   energy_rel_tol  > 0: boxes with p[i] < 0 take the smallest order in {6, 8, 10, 12} whose mixed-precision
+ *                   total energy (Eq. Velecfull) stays within this relative error of an FP64 order-15
+ *                   evaluation on a water-like test box of every depth group (the depths are tuned first,
+ *                   at p = 12): the group's smallest size (fewest charges per leaf, the largest truncation
+ *                   error) and its cell: a +2 e ion at the centre (where the cells of every level meet)
+ *                   and floor((N - 1) / 3) rigid 3-site waters (O -0.834
+ *                   e, H +0.417 e, O-H 0.9572 A, H-O-H 104.52 deg) on a jittered cubic lattice in random
+ *                   orientations, at the group's depth.  12 when none does; 0: they take 12.  The budget
+ *                   bounds the change against order 15, not the error against the exact energy: at ws = 1
+ *                   the expansion converges slowly, and on sparse leaves order 15 itself can differ from the
+ *                   Ewald energy by a few 1e-6.
+ *   sweep           -1: the persistent sweep (FMM_BATCH_OPT_SWEEP) on or off, whichever replays the recorded
+ *                   graph of the whole batch faster on uniform test charges; 0: off; 1: on.
+ */
+typedef struct {
+    double energy_rel_tol;
+    int sweep;
+} fmm_tune_policy;
+
+/* fmm_batch_create with a tuning policy (fmm_batch_create is this with {0, 1}).  Errors as fmm_batch_create,
+ * plus FMM_ERR_INVALID_ARG for a NULL policy, a negative or NaN tolerance or sweep outside -1..1. */
+fmm_status fmm_batch_create_tuned(int nbox, const double *box, const int64_t *N, const int *depth, const int *p,
+                                  int precision, const fmm_tune_policy *policy, fmm_batch *out);
+
+/* What the tuner measured (each nullable): p_err double[4], the largest relative energy error over the depth
+ * groups' test boxes of p = 6, 8, 10, 12 against FP64 p = 15 (-1: not measured); p_chosen the order it chose (0: none); the graph replay
+ * times (ms) of the batch on test charges with the sweep off and on (-1: not timed); sweep_on whether the
+ * sweep is in use. */
+fmm_status fmm_batch_tune_info(fmm_batch batch, double *p_err, int *p_chosen, double *ms_sweep_off, double *ms_sweep_on,
+                               int *sweep_on);
+
+/*
  * One evaluation of every box.  pos[i] (double[N_i][3]), q[i] (double[N_i]),
  * is_solute[i] (uint8_t[N_i]): DEVICE pointers, which must stay valid and
  * unchanged in place between calls that reuse them.  lambda_c: host double[nbox]

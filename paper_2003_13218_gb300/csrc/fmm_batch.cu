@@ -23,6 +23,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <utility>
 #include <new>
 #include <vector>
 
@@ -115,6 +116,11 @@ struct fmm_batch_s {
     uint64_t wait_ns = 2000000000ull;  // budget of the sweep's dependency waits
     bool stall = false;                // test hook: one dependency of the sweep is never met
     int sweep_pairs = 0;               // CTA pairs of the sweep (0: as many as can be resident)
+    // what the tuner measured: relative energy error of p = 6, 8, 10, 12 against p = 15 on its water box
+    // (-1: not measured), the order it chose (0: none), graph replay times with the sweep off and on (ms)
+    double p_err[4] = {-1.0, -1.0, -1.0, -1.0};
+    int p_tuned = 0;
+    double ms_sweep[2] = {-1.0, -1.0};
     cudaGraphExec_t graph = nullptr;
     std::vector<const void *> gptr;  // input pointers the graph was captured with
     std::vector<int> gcount;         // solute counts it was captured with
@@ -227,6 +233,176 @@ bool graph_matches(fmm_batch b, const double *const *pos, const double *const *q
     return true;
 }
 
+// SplitMix64 (Steele, Lea and Flood 2014): the tuner's own stream of test coordinates
+struct SplitMix {
+    uint64_t x;
+    uint64_t next()
+    {
+        uint64_t z = (x += 0x9E3779B97F4A7C15ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    }
+    double uniform() { return (double)(next() >> 11) * (1.0 / 9007199254740992.0); }
+};
+
+// A water-like test box for the order tuner: a +2 e ion at the box centre (the corner that cells of every
+// level share: the slowest-converging place for a charge) and floor((N - 1) / 3) rigid 3-site waters
+// (O -0.834 e, H +0.417 e, O-H 0.9572 A, H-O-H 104.52 deg) with O on the other sites of an n^3 lattice
+// of side L, site i at (i + (n mod 2) / 2) L / n (taken in a random order, jittered by U(-0.3, 0.3) A),
+// each molecule turned by a uniformly random rotation (a uniform unit quaternion, Shoemake 1992); the
+// remaining (N - 1) mod 3 sites carry no charge.  Coordinates wrapped into [0, L).  For even n the
+// molecules sit on the faces of the cells of the levels below the lattice spacing and straddle them:
+// the harder case for the truncated expansions, so the order found is the safer one.
+void water_test_box(int64_t N, double L, uint64_t seed, std::vector<double> &pos, std::vector<double> &q)
+{
+    SplitMix rng{seed};
+    const int64_t nw = (N - 1) / 3, extra = (N - 1) % 3;
+    int64_t n = 1;
+    while (n * n * n < nw + extra + 1) ++n;
+    const double a = L / (double)n;
+    std::vector<int64_t> site((size_t)(n * n * n));
+    for (int64_t i = 0; i < (int64_t)site.size(); ++i) site[i] = i;
+    for (int64_t i = (int64_t)site.size() - 1; i > 0; --i) std::swap(site[i], site[rng.next() % (uint64_t)(i + 1)]);
+    const double half = 0.5 * 104.52 * M_PI / 180.0, b = 0.9572;
+    const double hx = b * sin(half), hy = b * cos(half);
+    pos.assign(3 * (size_t)N, 0.0);
+    q.assign((size_t)N, 0.0);
+    auto wrap = [&](double x) {
+        x = fmod(x, L);
+        return x < 0.0 ? x + L : (x >= L ? 0.0 : x);
+    };
+    // the ion takes the lattice site nearest the centre; the molecules the others
+    const int64_t ci = n / 2, centre = ci + n * (ci + n * ci);
+    for (int64_t i = 0; i < (int64_t)site.size(); ++i)
+        if (site[i] == centre) {
+            std::swap(site[i], site.back());
+            break;
+        }
+    int64_t k = 0;
+    for (int d = 0; d < 3; ++d) pos[d] = 0.5 * L;
+    q[k++] = 2.0;
+    for (int64_t m = 0; m < nw + extra; ++m) {
+        const int64_t c = site[m];
+        const double off = 0.5 * (double)(n % 2);  // site n / 2 at L / 2; for even n the sites lie on cell faces
+        double o[3] = {((double)(c % n) + off) * a, ((double)((c / n) % n) + off) * a, ((double)(c / (n * n)) + off) * a};
+        for (int d = 0; d < 3; ++d) o[d] += 0.6 * rng.uniform() - 0.3;
+        if (m >= nw) {  // an uncharged site
+            for (int d = 0; d < 3; ++d) pos[3 * k + d] = wrap(o[d]);
+            ++k;
+            continue;
+        }
+        const double u1 = rng.uniform(), u2 = rng.uniform(), u3 = rng.uniform();
+        const double qw = sqrt(1.0 - u1) * sin(2.0 * M_PI * u2), qx = sqrt(1.0 - u1) * cos(2.0 * M_PI * u2);
+        const double qy = sqrt(u1) * sin(2.0 * M_PI * u3), qz = sqrt(u1) * cos(2.0 * M_PI * u3);
+        const double R[3][3] = {{1 - 2 * (qy * qy + qz * qz), 2 * (qx * qy - qz * qw), 2 * (qx * qz + qy * qw)},
+                                {2 * (qx * qy + qz * qw), 1 - 2 * (qx * qx + qz * qz), 2 * (qy * qz - qx * qw)},
+                                {2 * (qx * qz - qy * qw), 2 * (qy * qz + qx * qw), 1 - 2 * (qx * qx + qy * qy)}};
+        const double h[2][3] = {{hx, hy, 0.0}, {-hx, hy, 0.0}};
+        for (int d = 0; d < 3; ++d) pos[3 * k + d] = wrap(o[d]);
+        q[k++] = -0.834;
+        for (int t = 0; t < 2; ++t) {
+            for (int d = 0; d < 3; ++d)
+                pos[3 * k + d] = wrap(o[d] + R[d][0] * h[t][0] + R[d][1] * h[t][1] + R[d][2] * h[t][2]);
+            q[k++] = 0.417;
+        }
+    }
+}
+
+// Relative energy errors, against an FP64 order-15 evaluation, of mixed-precision evaluations at
+// p = 6, 8, 10, 12 on a water test box of N charges in a cell of side L at depth d: err[4].
+fmm_status order_errors(int64_t N, double L, int d, cudaStream_t st, double err[4])
+{
+    std::vector<double> hpos, hq;
+    water_test_box(N, L, 0x5EEDull + (uint64_t)N, hpos, hq);
+    double *dpos = nullptr, *dq = nullptr;
+    fmm_status s = FMM_OK;
+    if (cudaMalloc(&dpos, sizeof(double) * hpos.size()) != cudaSuccess ||
+        cudaMalloc(&dq, sizeof(double) * hq.size()) != cudaSuccess)
+        s = FMM_ERR_OOM;
+    if (s == FMM_OK && (cudaMemcpy(dpos, hpos.data(), sizeof(double) * hpos.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+                        cudaMemcpy(dq, hq.data(), sizeof(double) * hq.size(), cudaMemcpyHostToDevice) != cudaSuccess))
+        s = FMM_ERR_CUDA;
+    const int cand[5] = {6, 8, 10, 12, 15};
+    double e[5] = {0, 0, 0, 0, 0};
+    for (int c = 0; c < 5 && s == FMM_OK; ++c) {
+        fmm_plan h = nullptr;
+        s = make_plan(L, N, d, cand[c], c < 4 ? FMM_PREC_MIXED : FMM_PREC_FP64, st, &h);
+        if (s == FMM_OK) s = fmm_energy(h, dpos, dq, &e[c], nullptr);
+        if (h) fmm_plan_destroy(h);
+    }
+    cudaFree(dpos);
+    cudaFree(dq);
+    if (s != FMM_OK) return s;
+    for (int c = 0; c < 4; ++c) err[c] = fabs(e[c] - e[4]) / fmax(fabs(e[4]), 1e-300);
+    return FMM_OK;
+}
+
+// Sweep on or off, whichever replays the recorded graph of the whole batch faster on uniform test charges
+// (one solute per box): per mode one run on the streams, a recording, two warm replays and three timed.
+fmm_status tune_sweep(fmm_batch b, const int64_t *N, const double *box)
+{
+    std::vector<double *> tp(b->nbox, nullptr), tq(b->nbox, nullptr);
+    std::vector<uint8_t *> ts(b->nbox, nullptr);
+    fmm_status s = FMM_OK;
+    for (int i = 0; i < b->nbox && s == FMM_OK; ++i) {
+        if (cudaMalloc(&tp[i], sizeof(double) * 3 * N[i]) != cudaSuccess ||
+            cudaMalloc(&tq[i], sizeof(double) * N[i]) != cudaSuccess || cudaMalloc(&ts[i], N[i]) != cudaSuccess)
+            s = FMM_ERR_OOM;
+        else k_tune_fill<<<1216, 256, 0, b->origin>>>(N[i], box[i], tp[i], tq[i], ts[i]);
+    }
+    if (s == FMM_OK && cudaStreamSynchronize(b->origin) != cudaSuccess) s = FMM_ERR_CUDA;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (s == FMM_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) s = FMM_ERR_CUDA;
+    const bool graph = b->use_graph;
+    for (int mode = 0; mode < 2 && s == FMM_OK; ++mode) {
+        b->use_sweep = mode == 1;
+        sweep_enable(b->sweep, b->use_sweep);
+        s = batch_enqueue(b, tp.data(), tq.data(), (const uint8_t *const *)ts.data());
+        if (s == FMM_OK) s = batch_sync(b);
+        if (s != FMM_OK) break;
+        b->use_graph = true;
+        batch_capture(b, tp.data(), tq.data(), (const uint8_t *const *)ts.data());
+        if (!b->graph) {  // no graph: time the stream path instead
+            for (int it = 0; it < 5 && s == FMM_OK; ++it) {
+                if (it == 2) cudaEventRecord(e0, b->origin);
+                s = batch_enqueue(b, tp.data(), tq.data(), (const uint8_t *const *)ts.data());
+                for (size_t k = 0; k < b->streams.size() && s == FMM_OK; ++k) {
+                    cudaEventRecord(b->ev_done[k], b->streams[k]);
+                    cudaStreamWaitEvent(b->origin, b->ev_done[k], 0);
+                }
+            }
+        } else {
+            for (int it = 0; it < 5; ++it) {
+                if (it == 2) cudaEventRecord(e0, b->origin);
+                cudaGraphLaunch(b->graph, b->origin);
+            }
+        }
+        cudaEventRecord(e1, b->origin);
+        if (s == FMM_OK && cudaEventSynchronize(e1) != cudaSuccess) s = FMM_ERR_CUDA;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        b->ms_sweep[mode] = ms / 3.0;
+        if (b->graph) {
+            cudaGraphExecDestroy(b->graph);
+            b->graph = nullptr;
+        }
+        b->use_graph = graph;
+    }
+    b->gptr.clear();
+    b->gcount.clear();
+    b->use_sweep = s == FMM_OK && b->ms_sweep[1] < b->ms_sweep[0];
+    sweep_enable(b->sweep, b->use_sweep);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    for (int i = 0; i < b->nbox; ++i) {
+        cudaFree(tp[i]);
+        cudaFree(tq[i]);
+        cudaFree(ts[i]);
+    }
+    return s;
+}
+
 }  // namespace
 
 extern "C" {
@@ -234,7 +410,17 @@ extern "C" {
 fmm_status fmm_batch_create(int nbox, const double *box, const int64_t *N, const int *depth, const int *p,
                             int precision, fmm_batch *out)
 {
+    fmm_tune_policy pol;
+    pol.energy_rel_tol = 0.0;  // p < 0: 12
+    pol.sweep = 1;
+    return fmm_batch_create_tuned(nbox, box, N, depth, p, precision, &pol, out);
+}
+
+fmm_status fmm_batch_create_tuned(int nbox, const double *box, const int64_t *N, const int *depth, const int *p,
+                                  int precision, const fmm_tune_policy *policy, fmm_batch *out)
+{
     if (!out) return FMM_ERR_INVALID_ARG;
+    if (!policy || !(policy->energy_rel_tol >= 0.0) || policy->sweep < -1 || policy->sweep > 1) return FMM_ERR_INVALID_ARG;
     *out = nullptr;
     if (nbox < 1 || !box || !N || (precision != FMM_PREC_MIXED && precision != FMM_PREC_FP64))
         return FMM_ERR_INVALID_ARG;
@@ -269,6 +455,13 @@ fmm_status fmm_batch_create(int nbox, const double *box, const int64_t *N, const
     for (int i = 0; i < nbox; ++i) b->order[i] = i;
     std::stable_sort(b->order.begin(), b->order.end(), [&](int x, int y) { return N[x] > N[y]; });
 
+    // order: given, or (p[i] < 0) 12, or tuned after the depths (below)
+    std::vector<int> porder(nbox, 12);
+    std::vector<int> free_p;
+    for (int i = 0; i < nbox; ++i) {
+        if (p && p[i] >= 0) porder[i] = p[i];
+        else free_p.push_back(i);
+    }
     // depth: given, or tuned per group of boxes with the same starting guess
     std::vector<int> offset(9, 0);
     std::vector<bool> tuned(9, false);
@@ -287,7 +480,7 @@ fmm_status fmm_batch_create(int nbox, const double *box, const int64_t *N, const
                 if (!(depth && depth[j] > 0) && depth_guess(N[j]) == d0) grp.push_back(j);
             std::sort(grp.begin(), grp.end(), [&](int x, int y) { return N[x] < N[y]; });
             const int r = grp[grp.size() / 2];
-            const int pr = (p && p[r] >= 0) ? p[r] : 12;
+            const int pr = porder[r];
             cudaFree(tpos);
             cudaFree(tq);
             cudaFree(tsol);
@@ -322,11 +515,39 @@ fmm_status fmm_batch_create(int nbox, const double *box, const int64_t *N, const
     cudaFree(tpos);
     cudaFree(tq);
     cudaFree(tsol);
+    // tuned order: for each group of boxes with the same depth, a water test box of the group's smallest
+    // size and its cell at that depth (the fewest charges per leaf: cells cut through more molecules, the
+    // largest truncation error of the group); the batch takes the smallest order that keeps every group's
+    // error within the budget (one order: one operator table and one sweep), 12 when none does
+    if (s == FMM_OK && !free_p.empty() && policy->energy_rel_tol > 0.0) {
+        for (int c = 0; c < 4; ++c) b->p_err[c] = 0.0;
+        std::vector<bool> done(9, false);
+        for (int i : free_p) {
+            const int d = b->depth[i];
+            if (done[d] || s != FMM_OK) continue;
+            done[d] = true;
+            std::vector<int> grp;
+            for (int j : free_p)
+                if (b->depth[j] == d) grp.push_back(j);
+            std::sort(grp.begin(), grp.end(), [&](int x, int y) { return N[x] < N[y]; });
+            const int r = grp[0];
+            double err[4];
+            s = order_errors(N[r], box[r], d, b->streams[0], err);
+            for (int c = 0; c < 4 && s == FMM_OK; ++c) b->p_err[c] = fmax(b->p_err[c], err[c]);
+        }
+        const int cand[4] = {6, 8, 10, 12};
+        b->p_tuned = 12;
+        for (int c = 0; c < 4; ++c)
+            if (b->p_err[c] <= policy->energy_rel_tol) {
+                b->p_tuned = cand[c];
+                break;
+            }
+        for (int i : free_p) porder[i] = b->p_tuned;
+    }
     // the plans, on the streams round robin in size order
     for (int k = 0; k < nbox && s == FMM_OK; ++k) {
         const int i = b->order[k];
-        const int pi = (p && p[i] >= 0) ? p[i] : 12;
-        s = make_plan(box[i], N[i], b->depth[i], pi, precision, b->streams[k % ns], &b->plans[i]);
+        s = make_plan(box[i], N[i], b->depth[i], porder[i], precision, b->streams[k % ns], &b->plans[i]);
     }
     // one copy of the tensor-core operator tables per order: the boxes' tiles then read them from L2
     for (int i = 0; i < nbox && s == FMM_OK; ++i)
@@ -347,6 +568,13 @@ fmm_status fmm_batch_create(int nbox, const double *box, const int64_t *N, const
         }
         if (s == FMM_OK && b->sweep && cudaEventCreateWithFlags(&b->ev_sweep, cudaEventDisableTiming) != cudaSuccess)
             s = FMM_ERR_CUDA;
+        if (s == FMM_OK && b->sweep) {
+            if (policy->sweep == -1) s = tune_sweep(b, N, box);
+            else {
+                b->use_sweep = policy->sweep == 1;
+                sweep_enable(b->sweep, b->use_sweep);
+            }
+        }
     }
     if (s != FMM_OK) {
         batch_free(b);
@@ -471,6 +699,19 @@ fmm_status fmm_batch_sweep_info(fmm_batch b, int *boxes, int *first_level)
     if (boxes) *boxes = (b->use_sweep && b->sweep) ? sweep_plans(b->sweep) : 0;
     if (first_level)
         for (int i = 0; i < b->nbox; ++i) first_level[i] = b->plans[i]->P.sweep_from;
+    return FMM_OK;
+}
+
+fmm_status fmm_batch_tune_info(fmm_batch b, double *p_err, int *p_chosen, double *ms_sweep_off, double *ms_sweep_on,
+                               int *sweep_on)
+{
+    if (!b) return FMM_ERR_INVALID_ARG;
+    if (p_err)
+        for (int c = 0; c < 4; ++c) p_err[c] = b->p_err[c];
+    if (p_chosen) *p_chosen = b->p_tuned;
+    if (ms_sweep_off) *ms_sweep_off = b->ms_sweep[0];
+    if (ms_sweep_on) *ms_sweep_on = b->ms_sweep[1];
+    if (sweep_on) *sweep_on = (b->sweep && b->use_sweep) ? 1 : 0;
     return FMM_OK;
 }
 

@@ -56,6 +56,10 @@ class UVTerms(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class TunePolicy(ctypes.Structure):
+    _fields_ = [("energy_rel_tol", ctypes.c_double), ("sweep", ctypes.c_int)]
+
+
 class Timings(ctypes.Structure):
     _fields_ = [(k, ctypes.c_float) for k in ("sort", "upward", "lattice", "m2l_l2l", "l2p", "p2p", "solute_pass",
                                               "reduce", "total", "m2l_kernels", "m2l_top")]
@@ -102,6 +106,11 @@ def load_library(path: str = LIB_PATH):
     pp = ctypes.POINTER(vp)
     L.fmm_batch_create.argtypes = [c_int, vp, vp, vp, vp, c_int, ctypes.POINTER(vp)]
     L.fmm_batch_create.restype = c_int
+    L.fmm_batch_create_tuned.argtypes = [c_int, vp, vp, vp, vp, c_int, ctypes.POINTER(TunePolicy), ctypes.POINTER(vp)]
+    L.fmm_batch_create_tuned.restype = c_int
+    L.fmm_batch_tune_info.argtypes = [vp, vp, ctypes.POINTER(c_int), ctypes.POINTER(dbl), ctypes.POINTER(dbl),
+                                      ctypes.POINTER(c_int)]
+    L.fmm_batch_tune_info.restype = c_int
     L.fmm_batch_lambda_energies.argtypes = [vp, pp, pp, pp, vp, vp, vp, vp, vp]
     L.fmm_batch_lambda_energies.restype = c_int
     L.fmm_batch_info.argtypes = [vp, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int), ctypes.POINTER(i64),
@@ -284,7 +293,10 @@ class FMMBatch:
     Inputs are lists of CUDA tensors; keep the same tensors (updated in place) between
     calls so that the batch can replay its recorded CUDA graph."""
 
-    def __init__(self, boxes, Ns, depths=None, ps=None, precision: str = "mixed"):
+    def __init__(self, boxes, Ns, depths=None, ps=None, precision: str = "mixed", energy_rel_tol: float | None = None,
+                 sweep: str | None = None):
+        """energy_rel_tol / sweep given: fmm_batch_create_tuned with that policy (sweep "auto", "on" or "off";
+        boxes with ps[i] < 0 or ps None then take the tuned order); otherwise fmm_batch_create."""
         self._lib = load_library()
         n = len(boxes)
         self.n = n
@@ -293,10 +305,13 @@ class FMMBatch:
         self._d = None if depths is None else np.ascontiguousarray(depths, np.int32)
         self._p = None if ps is None else np.ascontiguousarray(ps, np.int32)
         h = ctypes.c_void_p()
-        _check(self._lib.fmm_batch_create(n, self._box.ctypes.data, self._N.ctypes.data,
-                                          None if self._d is None else self._d.ctypes.data,
-                                          None if self._p is None else self._p.ctypes.data,
-                                          PRECISION[precision], ctypes.byref(h)), "fmm_batch_create")
+        args = (n, self._box.ctypes.data, self._N.ctypes.data, None if self._d is None else self._d.ctypes.data,
+                None if self._p is None else self._p.ctypes.data, PRECISION[precision])
+        if energy_rel_tol is None and sweep is None:
+            _check(self._lib.fmm_batch_create(*args, ctypes.byref(h)), "fmm_batch_create")
+        else:
+            pol = TunePolicy(float(energy_rel_tol or 0.0), {"auto": -1, "off": 0, "on": 1}[sweep or "on"])
+            _check(self._lib.fmm_batch_create_tuned(*args, ctypes.byref(pol), ctypes.byref(h)), "fmm_batch_create_tuned")
         self._h = h
 
     def lambda_energies(self, pos, q, is_solute, lambda_c=None):
@@ -319,6 +334,17 @@ class FMMBatch:
         _check(self._lib.fmm_batch_info(self._h, i, ctypes.byref(d), ctypes.byref(p), ctypes.byref(r),
                                         ctypes.byref(e)), "fmm_batch_info")
         return {"depth": d.value, "p": p.value, "replays": r.value, "enqueued": e.value}
+
+    def tune_info(self):
+        """What the tuner measured: energy errors of p = 6, 8, 10, 12 against p = 15, the order chosen, the graph
+        replay times with the sweep off / on, and whether the sweep is in use."""
+        err = np.zeros(4)
+        pc, on = ctypes.c_int(), ctypes.c_int()
+        t0, t1 = ctypes.c_double(), ctypes.c_double()
+        _check(self._lib.fmm_batch_tune_info(self._h, err.ctypes.data, ctypes.byref(pc), ctypes.byref(t0),
+                                             ctypes.byref(t1), ctypes.byref(on)), "fmm_batch_tune_info")
+        return {"p_err": {6: err[0], 8: err[1], 10: err[2], 12: err[3]}, "p_chosen": pc.value,
+                "ms_sweep_off": t0.value, "ms_sweep_on": t1.value, "sweep_on": bool(on.value)}
 
     def set_softcore(self, c: int, A: float = 0.0, alpha: float = 0.2):
         _check(self._lib.fmm_batch_set_softcore(self._h, int(c), float(A), float(alpha)), "fmm_batch_set_softcore")

@@ -110,3 +110,44 @@ def test_sweep_dependency_wait_runs_out_and_the_batch_recovers():
             bt.set_option(key, bad)
         assert e.value.code == 1
     bt.close()
+
+
+def test_tuned_batch_picks_order_within_the_error_budget_and_the_faster_launch_form():
+    """fmm_batch_create_tuned: boxes that leave p to the tuner take the smallest order whose energy error
+    against FP64 p = 15 on the water test box of every depth group is within the budget (and the error it
+    measured shrinks with the order); boxes with a given p keep it; the sweep is in use exactly when it
+    replayed faster; the results are those of an untuned batch with the same depths and orders; and each
+    box's mixed-precision energy at the tuned order is within 1e-6 of FP64 at the same order.  (The
+    criterion is agreement with order 15 on the test boxes: at ws = 1 the FMM itself is not converged to
+    1e-6 of the Ewald energy even at p = 15 on some boxes, so no per-box promise against the exact energy
+    is made.)"""
+    from paper_2003_13218_gb300.fmm import FMMBatch
+    ws = _windows([4000, 9000, 16000, 21000], seed=12)
+    pos, q, sol = _dev(ws)
+    tol = 1e-6
+    bt = FMMBatch([b.L for b, _ in ws], [b.N for b, _ in ws], [4, 4, 5, 5], [-1, -1, -1, 12], energy_rel_tol=tol,
+                  sweep="auto")
+    info = bt.tune_info()
+    err = info["p_err"]
+    assert all(err[p] >= 0.0 for p in (6, 8, 10, 12))
+    assert err[6] > err[10] and err[8] > err[12]
+    expect = next((p for p in (6, 8, 10, 12) if err[p] <= tol), 12)
+    assert info["p_chosen"] == expect
+    assert [bt.info(i)["p"] for i in range(4)] == [expect, expect, expect, 12]
+    assert info["ms_sweep_off"] > 0.0 and info["ms_sweep_on"] > 0.0
+    assert info["sweep_on"] == (info["ms_sweep_on"] < info["ms_sweep_off"])
+    assert (bt.sweep_info()["boxes"] > 0) == info["sweep_on"]
+    r = bt.lambda_energies(pos, q, sol)
+    ref = FMMBatch([b.L for b, _ in ws], [b.N for b, _ in ws], [4, 4, 5, 5], [expect, expect, expect, 12])
+    r_ref = ref.lambda_energies(pos, q, sol)
+    for k in ("e_total", "e_uv"):
+        assert np.array_equal(r[k], r_ref[k])
+    ref.close()
+    from paper_2003_13218_gb300.fmm import FMMPlan
+    for i in range(3):
+        b = ws[i][0]
+        pl = FMMPlan(b.L, b.N, [4, 4, 5, 5][i], expect, precision="fp64")
+        e64, _ = pl.energy(pos[i], q[i])
+        pl.close()
+        assert abs(r["e_total"][i] - e64) <= 1e-6 * abs(e64)
+    bt.close()
