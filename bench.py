@@ -515,11 +515,12 @@ def measure_batch(steps: int, warmup: int, rank: int, local: int, serial: bool =
     t0 = time.perf_counter()
     # depth, order (within BATCH_TOL relative energy error) and launch form chosen by the batch tuner
     bt = FMMBatch([b.L for b, _ in win], [b.N for b, _ in win], None, [-1] * len(win), precision="mixed",
-                  energy_rel_tol=BATCH_TOL, sweep="auto")
+                  energy_rel_tol=BATCH_TOL, sweep="auto", tiles=True)
     create_s = time.perf_counter() - t0
     depths = [bt.info(i)["depth"] for i in range(len(win))]
     orders = [bt.info(i)["p"] for i in range(len(win))]
     tune = bt.tune_info()
+    bricks = sorted({"d%d: %dx%dx%d" % (l, *bk) for l, bk in (bt.brick(i) for i in range(len(win)))})
 
     def timed(fn, k):
         torch.cuda.synchronize()
@@ -557,7 +558,8 @@ def measure_batch(steps: int, warmup: int, rank: int, local: int, serial: bool =
              "orders": sorted(set(orders)),
              "tuner": {"energy_rel_tol": BATCH_TOL, "p_err_vs_p15_on_water_test_box": {str(k): v for k, v in
                                                                                    tune["p_err"].items()},
-                       "p_chosen": tune["p_chosen"], "graph_ms_sweep_off": tune["ms_sweep_off"],
+                       "p_chosen": tune["p_chosen"], "tile_bricks": bricks,
+                       "graph_ms_sweep_off": tune["ms_sweep_off"],
                        "graph_ms_sweep_on": tune["ms_sweep_on"], "sweep_chosen": tune["sweep_on"],
                        "note": "timed on uniform test charges at batch creation"},
              "sweep": {"boxes": sweep["boxes"], "first_levels": sorted(set(sweep["first_level"])),
@@ -593,7 +595,7 @@ def measure_batch(steps: int, warmup: int, rank: int, local: int, serial: bool =
         batch["max_rel_diff_e_uv_vs_single_plans"] = float(np.max(np.abs(r_stream["e_uv"] - e_single) /
                                                                   np.maximum(np.abs(e_single), 1e-30)))
     workload = ("lambda64: 64 boxes, %d charges in all (%d..%d per box), species Mg/Na/Cl, lambda = (b mod 16)/15, "
-                "order p and depth chosen by the batch tuner" % (Ntot, min(b.N for b, _ in win),
+                "order p, depth, tile bricks and launch form chosen by the batch tuner" % (Ntot, min(b.N for b, _ in win),
                                                                   max(b.N for b, _ in win)))
     out = {"Ntot": Ntot, "t_graph": t_graph, "batch": batch, "clocks": clocks, "workload": workload}
     if shard_world > 1:

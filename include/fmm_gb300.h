@@ -150,10 +150,16 @@ enum {
                               kernels (default 2 s); a wait that runs out makes the call return FMM_ERR_TIMEOUT
                               after the kernel has waited, with its own 2 s limit, for its copies and MMAs in
                               flight; the plan stays usable */
-    FMM_OPT_INJECT_STALL = 16     /* ival 0 / 1, a test hook for the timeout path: with 1 the single-CTA
+    FMM_OPT_INJECT_STALL = 16,    /* ival 0 / 1, a test hook for the timeout path: with 1 the single-CTA
                               tensor-core kernels first wait on a barrier that nothing arrives on, so every
                               evaluation returns FMM_ERR_TIMEOUT after the wait budget (use with
                               FMM_OPT_M2L_PAIR = 0 and a short budget) */
+    FMM_OPT_M2L_BRICK = 17        /* ival = l | bx << 8 | by << 16 | bz << 24: the tiles of the tensor-core M2L of
+                              level l (2..depth; and the M2M from it) are bricks of bx x by x bz cells of one
+                              parity class, bx by bz = 128, each dividing 2^(l-1), an even number per class.
+                              Only the grouping of targets into tiles changes: results are bitwise the same.
+                              FMM_ERR_UNSUPPORTED without the tensor-core path (FP64 plans); a WS, PRECISION
+                              or M2L_SPLIT change restores the default bricks */
 };
 #define FMM_GRADE_DEFAULT (8 << 8)  /* D2 = 0, D1 = 8: input degrees >= 8 with one product */
 #define FMM_ACC_GROUP_DEFAULT 2
@@ -288,13 +294,17 @@ fmm_status fmm_batch_create(int nbox, const double *box, const int64_t *N, const
  *                   Ewald energy by a few 1e-6.
  *   sweep           -1: the persistent sweep (FMM_BATCH_OPT_SWEEP) on or off, whichever replays the recorded
  *                   graph of the whole batch faster on uniform test charges; 0: off; 1: on.
+ *   tiles           1: for every depth group with a tensor-core pair level, the tile brick of its deepest
+ *                   level (FMM_OPT_M2L_BRICK) is the fastest of the power-of-two bricks bx >= by >= bz of 128
+ *                   cells, timed on the group's median box with uniform test charges; 0: the default brick.
  */
 typedef struct {
     double energy_rel_tol;
     int sweep;
+    int tiles;
 } fmm_tune_policy;
 
-/* fmm_batch_create with a tuning policy (fmm_batch_create is this with {0, 1}).  Errors as fmm_batch_create,
+/* fmm_batch_create with a tuning policy (fmm_batch_create is this with {0, 1, 0}).  Errors as fmm_batch_create,
  * plus FMM_ERR_INVALID_ARG for a NULL policy, a negative or NaN tolerance or sweep outside -1..1. */
 fmm_status fmm_batch_create_tuned(int nbox, const double *box, const int64_t *N, const int *depth, const int *p,
                                   int precision, const fmm_tune_policy *policy, fmm_batch *out);
@@ -305,6 +315,9 @@ fmm_status fmm_batch_create_tuned(int nbox, const double *box, const int64_t *N,
  * sweep is in use. */
 fmm_status fmm_batch_tune_info(fmm_batch batch, double *p_err, int *p_chosen, double *ms_sweep_off, double *ms_sweep_on,
                                int *sweep_on);
+
+/* The deepest level of box i and the tile brick of its tensor-core M2L (0s without the tensor-core path). */
+fmm_status fmm_batch_brick_info(fmm_batch batch, int i, int *level, int *bx, int *by, int *bz);
 
 /*
  * One evaluation of every box.  pos[i] (double[N_i][3]), q[i] (double[N_i]),

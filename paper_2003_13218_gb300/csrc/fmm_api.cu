@@ -516,6 +516,10 @@ fmm_status fmm_plan_set_option(fmm_plan plan, int key, int64_t ival, double dval
         if (ival != 0 && ival != 1) return FMM_ERR_INVALID_ARG;
         P.inject_stall = ival != 0;
         return FMM_OK;
+    case FMM_OPT_M2L_BRICK:
+        if (ival < 0 || ival > 0xFFFFFFFFll) return FMM_ERR_INVALID_ARG;
+        return tc_set_brick(P, (int)(ival & 0xFF), (int)((ival >> 8) & 0xFF), (int)((ival >> 16) & 0xFF),
+                            (int)((ival >> 24) & 0xFF));
     case FMM_OPT_OVERLAP:
         if (ival != 0 && ival != 1) return FMM_ERR_INVALID_ARG;
         P.overlap = ival != 0;

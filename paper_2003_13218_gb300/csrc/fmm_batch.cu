@@ -338,6 +338,64 @@ fmm_status order_errors(int64_t N, double L, int d, cudaStream_t st, double err[
     return FMM_OK;
 }
 
+// The deepest level's tile brick per depth group: the group's median box, uniform test charges, each
+// power-of-two brick bx >= by >= bz of 128 cells that fits the level (an even number of tiles per class)
+// timed on the box's own plan (time_plan: a warm-up and the best of two), the fastest set on every plan
+// of the group.
+fmm_status tune_bricks(fmm_batch b, const int64_t *N, const double *box)
+{
+    fmm_status s = FMM_OK;
+    std::vector<bool> done(9, false);
+    for (int i = 0; i < b->nbox && s == FMM_OK; ++i) {
+        Plan &P = b->plans[i]->P;
+        const int d = P.d;
+        if (done[d] || d < 2 || tc_sweep_first_level(P) == 0) continue;
+        done[d] = true;
+        std::vector<int> grp;
+        for (int j = 0; j < b->nbox; ++j)
+            if (b->plans[j]->P.d == d && b->plans[j]->P.p == P.p) grp.push_back(j);
+        std::sort(grp.begin(), grp.end(), [&](int x, int y) { return N[x] < N[y]; });
+        const int r = grp[grp.size() / 2];
+        Plan &R = b->plans[r]->P;
+        double *tp = nullptr, *tq = nullptr;
+        uint8_t *ts = nullptr;
+        if (cudaMalloc(&tp, sizeof(double) * 3 * N[r]) != cudaSuccess ||
+            cudaMalloc(&tq, sizeof(double) * N[r]) != cudaSuccess || cudaMalloc(&ts, N[r]) != cudaSuccess) {
+            cudaFree(tp);
+            cudaFree(tq);
+            cudaFree(ts);
+            return FMM_ERR_OOM;
+        }
+        k_tune_fill<<<1216, 256, 0, R.stream>>>(N[r], box[r], tp, tq, ts);
+        const int np = 1 << (d - 1);
+        int bx0, by0, bz0;
+        tc_get_brick(R, d, &bx0, &by0, &bz0);
+        float best = 1e30f;
+        int bb[3] = {bx0, by0, bz0};
+        for (int bx = 128; bx >= 1 && s == FMM_OK; bx >>= 1)
+            for (int by = bx; by >= 1 && s == FMM_OK; by >>= 1) {
+                const int bz = 128 / (bx * by);
+                if (bz < 1 || bz > by || bx * by * bz != 128 || bx > np || by > np || bz > np) continue;
+                if (((np / bx) * (np / by) * (np / bz)) % 2) continue;
+                if (tc_set_brick(R, d, bx, by, bz) != FMM_OK) continue;
+                float ms = 0.f;
+                s = time_plan(b->plans[r], tp, tq, ts, &ms);
+                if (s == FMM_OK && ms < best) {
+                    best = ms;
+                    bb[0] = bx;
+                    bb[1] = by;
+                    bb[2] = bz;
+                }
+            }
+        cudaFree(tp);
+        cudaFree(tq);
+        cudaFree(ts);
+        for (int j : grp)
+            if (s == FMM_OK) s = tc_set_brick(b->plans[j]->P, d, bb[0], bb[1], bb[2]);
+    }
+    return s;
+}
+
 // Sweep on or off, whichever replays the recorded graph of the whole batch faster on uniform test charges
 // (one solute per box): per mode one run on the streams, a recording, two warm replays and three timed.
 fmm_status tune_sweep(fmm_batch b, const int64_t *N, const double *box)
@@ -413,6 +471,7 @@ fmm_status fmm_batch_create(int nbox, const double *box, const int64_t *N, const
     fmm_tune_policy pol;
     pol.energy_rel_tol = 0.0;  // p < 0: 12
     pol.sweep = 1;
+    pol.tiles = 0;
     return fmm_batch_create_tuned(nbox, box, N, depth, p, precision, &pol, out);
 }
 
@@ -420,7 +479,9 @@ fmm_status fmm_batch_create_tuned(int nbox, const double *box, const int64_t *N,
                                   int precision, const fmm_tune_policy *policy, fmm_batch *out)
 {
     if (!out) return FMM_ERR_INVALID_ARG;
-    if (!policy || !(policy->energy_rel_tol >= 0.0) || policy->sweep < -1 || policy->sweep > 1) return FMM_ERR_INVALID_ARG;
+    if (!policy || !(policy->energy_rel_tol >= 0.0) || policy->sweep < -1 || policy->sweep > 1 || policy->tiles < 0 ||
+        policy->tiles > 1)
+        return FMM_ERR_INVALID_ARG;
     *out = nullptr;
     if (nbox < 1 || !box || !N || (precision != FMM_PREC_MIXED && precision != FMM_PREC_FP64))
         return FMM_ERR_INVALID_ARG;
@@ -549,6 +610,8 @@ fmm_status fmm_batch_create_tuned(int nbox, const double *box, const int64_t *N,
         const int i = b->order[k];
         s = make_plan(box[i], N[i], b->depth[i], porder[i], precision, b->streams[k % ns], &b->plans[i]);
     }
+    // tile bricks of the deepest level, per depth group, by timing (before anything is recorded)
+    if (s == FMM_OK && policy->tiles == 1 && precision == FMM_PREC_MIXED) s = tune_bricks(b, N, box);
     // one copy of the tensor-core operator tables per order: the boxes' tiles then read them from L2
     for (int i = 0; i < nbox && s == FMM_OK; ++i)
         for (int j = 0; j < i && s == FMM_OK; ++j)
@@ -712,6 +775,14 @@ fmm_status fmm_batch_tune_info(fmm_batch b, double *p_err, int *p_chosen, double
     if (ms_sweep_off) *ms_sweep_off = b->ms_sweep[0];
     if (ms_sweep_on) *ms_sweep_on = b->ms_sweep[1];
     if (sweep_on) *sweep_on = (b->sweep && b->use_sweep) ? 1 : 0;
+    return FMM_OK;
+}
+
+fmm_status fmm_batch_brick_info(fmm_batch b, int i, int *level, int *bx, int *by, int *bz)
+{
+    if (!b || i < 0 || i >= b->nbox || !level || !bx || !by || !bz) return FMM_ERR_INVALID_ARG;
+    *level = b->plans[i]->P.d;
+    tc_get_brick(b->plans[i]->P, *level, bx, by, bz);
     return FMM_OK;
 }
 

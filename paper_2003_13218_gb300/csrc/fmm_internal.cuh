@@ -318,6 +318,10 @@ fmm_status eval_enqueue_front(Plan &P, const double *dpos, const double *dq, con
 fmm_status eval_enqueue_far_tail(Plan &P);
 fmm_status eval_enqueue_back(Plan &P, const double *dq);
 
+// the level-l tile brick of the tensor-core M2L (and of the M2M from level l); see FMM_OPT_M2L_BRICK
+fmm_status tc_set_brick(Plan &P, int l, int bx, int by, int bz);
+void tc_get_brick(const Plan &P, int l, int *bx, int *by, int *bz);
+
 // dst reads src's split operator tables when they are the same (p, ws, split); src must outlive dst
 fmm_status tc_share_operators(Plan &dst, const Plan &src);
 

@@ -2340,6 +2340,50 @@ fmm_status sweep_launch(Sweep *sw, cudaStream_t st, uint64_t wait_ns, bool stall
     return FMM_OK;
 }
 
+// Brick of the level-l tiles: bx x by x bz target cells of one parity class (the MMA's 128 rows), each
+// dividing the class side 2^(l-1), an even number of tiles per class (CTA pairs); the level's plane maps
+// are encoded for it.  Which targets share a tile changes, no target's arithmetic does.
+fmm_status tc_set_brick(Plan &P, int l, int bx, int by, int bz)
+{
+    TcState *S = (TcState *)P.tc;
+    if (!S) return FMM_ERR_UNSUPPORTED;
+    if (l < 2 || l > P.d) return FMM_ERR_INVALID_ARG;
+    const int np = 1 << (l - 1);
+    if (bx < 1 || by < 1 || bz < 1 || bx * by * bz != TC_ROWS || np % bx || np % by || np % bz ||
+        ((np / bx) * (np / by) * (np / bz)) % 2)
+        return FMM_ERR_INVALID_ARG;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+    if (!enc) return FMM_ERR_INTERNAL;
+    const CUtensorMapDataType dt = S->f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    const int64_t np2 = np + 2 * P.ws;
+    CUtensorMap a[3], lm[2];
+    for (int i = 0; i < S->parts; ++i)
+        TRY_TC(encode_planes(enc, &a[i], dt, S->planes[l] + i * S->part_elems[l], S->kp, np2, np2, 8 * np2, bx, by,
+                             bz, S->sw));
+    for (int i = S->parts; i < 3; ++i) a[i] = a[0];
+    if (S->f16)
+        for (int i = 0; i < 2; ++i)
+            TRY_TC(encode_planes(enc, &lm[i], dt, S->planesL + (size_t)i * np * np * np * S->kp, S->kp, np, np, np,
+                                 bx, by, bz, S->sw));
+    else
+        lm[0] = lm[1] = a[0];
+    for (int i = 0; i < 3; ++i) S->mapA[l][i] = a[i];
+    S->mapL[l][0] = lm[0];
+    S->mapL[l][1] = lm[1];
+    S->bx[l] = bx;
+    S->by[l] = by;
+    S->bz[l] = bz;
+    return FMM_OK;
+}
+
+void tc_get_brick(const Plan &P, int l, int *bx, int *by, int *bz)
+{
+    const TcState *S = (const TcState *)P.tc;
+    *bx = S && l >= 1 && l <= P.d ? S->bx[l] : 0;
+    *by = S && l >= 1 && l <= P.d ? S->by[l] : 0;
+    *bz = S && l >= 1 && l <= P.d ? S->bz[l] : 0;
+}
+
 // The split operator tables depend only on p, ws and the split (the M2L, M2M and L2L operators are
 // built for unit cells), so plans that agree on those can read one copy: dst drops its own and reads
 // src's, which must outlive it.  A plan with another table is left alone.

@@ -27,6 +27,7 @@ FMM_OPT_M2L_GRADE = 10
 FMM_OPT_M2L_ACC_GROUP = 11
 FMM_OPT_SOFTCORE, FMM_OPT_SOFTCORE_LAMBDA, FMM_OPT_SOFTCORE_ALPHA = 12, 13, 14
 FMM_OPT_WAIT_BUDGET_NS, FMM_OPT_INJECT_STALL = 15, 16
+FMM_OPT_M2L_BRICK = 17
 FMM_BATCH_OPT_SWEEP, FMM_BATCH_OPT_WAIT_BUDGET_NS, FMM_BATCH_OPT_INJECT_STALL, FMM_BATCH_OPT_SWEEP_PAIRS = 1, 2, 3, 4
 BOUNDARY = {"conducting": 0, "vacuum": 1}
 PRECISION = {"fp64": 0, "mixed": 1}
@@ -57,7 +58,7 @@ class UVTerms(ctypes.Structure):
 
 
 class TunePolicy(ctypes.Structure):
-    _fields_ = [("energy_rel_tol", ctypes.c_double), ("sweep", ctypes.c_int)]
+    _fields_ = [("energy_rel_tol", ctypes.c_double), ("sweep", ctypes.c_int), ("tiles", ctypes.c_int)]
 
 
 class Timings(ctypes.Structure):
@@ -111,6 +112,9 @@ def load_library(path: str = LIB_PATH):
     L.fmm_batch_tune_info.argtypes = [vp, vp, ctypes.POINTER(c_int), ctypes.POINTER(dbl), ctypes.POINTER(dbl),
                                       ctypes.POINTER(c_int)]
     L.fmm_batch_tune_info.restype = c_int
+    L.fmm_batch_brick_info.argtypes = [vp, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int), ctypes.POINTER(c_int),
+                                       ctypes.POINTER(c_int)]
+    L.fmm_batch_brick_info.restype = c_int
     L.fmm_batch_lambda_energies.argtypes = [vp, pp, pp, pp, vp, vp, vp, vp, vp]
     L.fmm_batch_lambda_energies.restype = c_int
     L.fmm_batch_info.argtypes = [vp, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int), ctypes.POINTER(i64),
@@ -185,6 +189,10 @@ class FMMPlan:
 
     def set_option(self, key: int, ival: int = 0, dval: float = 0.0):
         _check(self._lib.fmm_plan_set_option(self._h, int(key), int(ival), float(dval)), "fmm_plan_set_option")
+
+    def set_brick(self, level: int, bx: int, by: int, bz: int):
+        """Tile brick of the tensor-core M2L of a level (FMM_OPT_M2L_BRICK)."""
+        self.set_option(FMM_OPT_M2L_BRICK, int(level) | (int(bx) << 8) | (int(by) << 16) | (int(bz) << 24))
 
     def set_softcore(self, c: int, A: float = 0.0, lam: float = 0.0, alpha: float = 0.2):
         """Soft-core solute-solvent near field (FMM_OPT_SOFTCORE): c = 0 turns it off."""
@@ -294,9 +302,10 @@ class FMMBatch:
     calls so that the batch can replay its recorded CUDA graph."""
 
     def __init__(self, boxes, Ns, depths=None, ps=None, precision: str = "mixed", energy_rel_tol: float | None = None,
-                 sweep: str | None = None):
-        """energy_rel_tol / sweep given: fmm_batch_create_tuned with that policy (sweep "auto", "on" or "off";
-        boxes with ps[i] < 0 or ps None then take the tuned order); otherwise fmm_batch_create."""
+                 sweep: str | None = None, tiles: bool = False):
+        """energy_rel_tol / sweep / tiles given: fmm_batch_create_tuned with that policy (sweep "auto", "on" or
+        "off"; boxes with ps[i] < 0 or ps None then take the tuned order; tiles: time the deepest level's tile
+        bricks); otherwise fmm_batch_create."""
         self._lib = load_library()
         n = len(boxes)
         self.n = n
@@ -307,10 +316,11 @@ class FMMBatch:
         h = ctypes.c_void_p()
         args = (n, self._box.ctypes.data, self._N.ctypes.data, None if self._d is None else self._d.ctypes.data,
                 None if self._p is None else self._p.ctypes.data, PRECISION[precision])
-        if energy_rel_tol is None and sweep is None:
+        if energy_rel_tol is None and sweep is None and not tiles:
             _check(self._lib.fmm_batch_create(*args, ctypes.byref(h)), "fmm_batch_create")
         else:
-            pol = TunePolicy(float(energy_rel_tol or 0.0), {"auto": -1, "off": 0, "on": 1}[sweep or "on"])
+            pol = TunePolicy(float(energy_rel_tol or 0.0), {"auto": -1, "off": 0, "on": 1}[sweep or "on"],
+                             1 if tiles else 0)
             _check(self._lib.fmm_batch_create_tuned(*args, ctypes.byref(pol), ctypes.byref(h)), "fmm_batch_create_tuned")
         self._h = h
 
@@ -345,6 +355,13 @@ class FMMBatch:
                                              ctypes.byref(t1), ctypes.byref(on)), "fmm_batch_tune_info")
         return {"p_err": {6: err[0], 8: err[1], 10: err[2], 12: err[3]}, "p_chosen": pc.value,
                 "ms_sweep_off": t0.value, "ms_sweep_on": t1.value, "sweep_on": bool(on.value)}
+
+    def brick(self, i: int):
+        """The deepest level of box i and its tile brick (bx, by, bz)."""
+        l, x, y, z = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(self._lib.fmm_batch_brick_info(self._h, i, ctypes.byref(l), ctypes.byref(x), ctypes.byref(y),
+                                              ctypes.byref(z)), "fmm_batch_brick_info")
+        return l.value, (x.value, y.value, z.value)
 
     def set_softcore(self, c: int, A: float = 0.0, alpha: float = 0.2):
         _check(self._lib.fmm_batch_set_softcore(self._h, int(c), float(A), float(alpha)), "fmm_batch_set_softcore")

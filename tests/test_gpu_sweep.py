@@ -151,3 +151,64 @@ def test_tuned_batch_picks_order_within_the_error_budget_and_the_faster_launch_f
         pl.close()
         assert abs(r["e_total"][i] - e64) <= 1e-6 * abs(e64)
     bt.close()
+
+
+def test_m2l_brick_option_changes_no_result():
+    """FMM_OPT_M2L_BRICK regroups the targets of a level into tiles; every target's sum is the same, so
+    energies, forces and E_uv are bitwise those of the default bricks, and bad bricks are refused."""
+    from paper_2003_13218_gb300.fmm import FMM_OPT_M2L_BRICK, FMMError, FMMPlan
+    b = boxes.ion_in_water(12000, "Cl", seed=5)
+    pos = torch.from_numpy(b.pos).to(DEV)
+    q = torch.from_numpy(b.q).to(DEV)
+    sol = torch.from_numpy(b.is_solute).to(DEV)
+    out = []
+    for bricks in ([], [(5, 8, 4, 4), (4, 8, 4, 4)], [(5, 16, 4, 2)]):
+        plan = FMMPlan(b.L, b.N, 5, 12, precision="mixed")
+        for l, x, y, z in bricks:
+            plan.set_brick(l, x, y, z)
+        F = torch.empty((b.N, 3), dtype=torch.float64, device=DEV)
+        t, uv = plan.evaluate(pos, q, sol, forces=F)
+        out.append((t["total"], uv["e_uv"], F.cpu().numpy()))
+        plan.close()
+    for t, u, F in out[1:]:
+        assert t == out[0][0] and u == out[0][1] and np.array_equal(F, out[0][2])
+    plan = FMMPlan(b.L, b.N, 5, 12, precision="mixed")
+    plan.set_brick(5, 16, 8, 1)  # the default brick of level 5 is accepted
+    for l, x, y, z in ((5, 8, 8, 8),    # 512 cells
+                       (6, 8, 4, 4),    # a level beyond the depth
+                       (4, 3, 8, 4),    # does not divide the class side
+                       (4, 8, 8, 2),    # fine at level 4 ...
+                       (3, 4, 4, 8)):   # ... but level 3 (side 4) has one tile per class: no pairs
+        if (l, x, y, z) == (4, 8, 8, 2):
+            plan.set_brick(l, x, y, z)
+            continue
+        with pytest.raises(FMMError) as e:
+            plan.set_brick(l, x, y, z)
+        assert e.value.code == 1
+    plan.close()
+    p64 = FMMPlan(b.L, b.N, 5, 12, precision="fp64")
+    with pytest.raises(FMMError) as e:
+        p64.set_brick(5, 8, 4, 4)
+    assert e.value.code == 7  # FMM_ERR_UNSUPPORTED: no tensor-core path
+    p64.close()
+
+
+def test_tuned_bricks_are_shared_by_a_depth_group_and_change_no_result():
+    from paper_2003_13218_gb300.fmm import FMMBatch
+    ws = _windows([9000, 11000, 16000, 21000], seed=13)
+    pos, q, sol = _dev(ws)
+    d, p = [4, 4, 5, 5], [12] * 4
+    bt = FMMBatch([b.L for b, _ in ws], [b.N for b, _ in ws], d, p, tiles=True)
+    br = [bt.brick(i) for i in range(4)]
+    assert [l for l, _ in br] == d
+    assert br[0][1] == br[1][1] and br[2][1] == br[3][1]
+    for _, (x, y, z) in br:
+        assert x * y * z == 128 and x >= y >= z
+    r = bt.lambda_energies(pos, q, sol)
+    ref = FMMBatch([b.L for b, _ in ws], [b.N for b, _ in ws], d, p)
+    assert [ref.brick(i)[1] for i in range(4)] == [(8, 8, 2), (8, 8, 2), (16, 8, 1), (16, 8, 1)]
+    r_ref = ref.lambda_energies(pos, q, sol)
+    for k in ("e_total", "e_uv"):
+        assert np.array_equal(r[k], r_ref[k])
+    ref.close()
+    bt.close()
