@@ -67,13 +67,14 @@ def m2l_flops(d: int, p: int, levels=None, fused_l2l=False, ws: int = 1) -> floa
     return 2.0 * C * C * pairs
 
 
-GRADE_DEFAULT = (0, 8)  # the library's default M2L grading (FMM_GRADE_DEFAULT): input degrees >= 8, one product
+GRADE_DEFAULT = (4, 8)  # the library's default M2L grading (FMM_GRADE_DEFAULT): degrees 4..7 two products, >= 8 one
 
 
 def mmas_per_offset(p: int, grade, products: int = 3) -> tuple[int, int]:
     """K16 MMA steps (128-row units) per interaction-list offset of the fp16x2 tensor-core M2L and per
     fused L2L offset: K chunks of 64 coefficients, chunk kc graded by its lowest degree floor(sqrt(64 kc))
-    (1 product from degree D1, 2 from D2, else 3)."""
+    (1 product from degree D1, 2 from D2, else 3); in a 3-product chunk the K16 steps whose lowest degree
+    floor(sqrt(64 kc + 16 s)) reaches D2 take 2."""
     C = (p + 1) ** 2
     ksteps = (C + 15) // 16
     kchunks = ((C + 63) // 64 * 64) // 64
@@ -82,7 +83,11 @@ def mmas_per_offset(p: int, grade, products: int = 3) -> tuple[int, int]:
     for kc in range(kchunks):
         lam = int(math.isqrt(64 * kc))
         np_ = 1 if (d1 > 0 and lam >= d1) else 2 if (d2 > 0 and lam >= d2) else products
-        m2l += np_ * min(4, ksteps - 4 * kc)
+        for st in range(min(4, ksteps - 4 * kc)):
+            if np_ == 3 and d2 > 0 and int(math.isqrt(64 * kc + 16 * st)) >= d2:
+                m2l += 2
+            else:
+                m2l += np_
     return m2l, products * ksteps
 
 
@@ -381,7 +386,7 @@ def run_ours(args):
                                                                           box.L, d, p, args.ws),
                    "l2": "flushed between timed steps (256 MB write)", "jitter_A": args.jitter, "parallelism": "replicas" if ws > 1 else "1 GPU",
                    "m2l_split": args.split, "overlap": bool(args.overlap),
-                   "m2l_grade": {"d2": grade[0], "d1": grade[1], "note": "input degrees >= d1 with one fp16 product"},
+                   "m2l_grade": {"d2": grade[0], "d1": grade[1], "note": "K16 steps of input degree >= d2 with two fp16 products, K chunks of degree >= d1 with one"},
                    "acc_group": args.acc_group if args.acc_group is not None else "library default (2)"},
         "roofline": roof,
         "solute_solvent_cost": uv_cost,
@@ -664,7 +669,7 @@ def main():
                     help="1: also time the 64-box lambda-window batch and add it to the line")
     ap.add_argument("--ws", type=int, default=1, choices=[1, 2], help="well-separatedness (2: the paper's setting)")
     ap.add_argument("--p", type=int, default=None, help="expansion order (default: the workload's)")
-    ap.add_argument("--m2l-grade", default=None, help="D2,D1 of FMM_OPT_M2L_GRADE (default: the library's 0,8)")
+    ap.add_argument("--m2l-grade", default=None, help="D2,D1 of FMM_OPT_M2L_GRADE (default: the library's 4,8)")
     ap.add_argument("--acc-group", type=int, default=None, help="FMM_OPT_M2L_ACC_GROUP (default: the library's)")
     ap.add_argument("--overlap", type=int, default=1, choices=[0, 1],
                     help="1: near field and sparse solute pass beside the far field (plan-owned streams)")

@@ -125,10 +125,11 @@ enum {
                               solute pass of Eq. FMMcalc beside the L2P; 0 runs every stage in order on the
                               plan's stream (the per-stage times then add up) */,
     FMM_OPT_M2L_GRADE = 10 /* ival = D2 | (D1 << 8), fp16x2 tensor-core M2L only: per K chunk of input coefficients
-                              (64 per chunk), by the chunk's lowest degree lambda: lambda >= D2 drops the moments'
-                              second fp16 term (2 products: ~2^-12 relative on those terms), lambda >= D1 drops
-                              the operators' second term as well (1 product, ~2^-11), and two consecutive
-                              1-product chunks share one pipeline stage; 0 = never.  Contributions of high input
+                              (64 per chunk), by the chunk's lowest degree lambda: lambda >= D1 keeps one product
+                              (both operands' first fp16 terms, ~2^-11 relative on those terms) and two
+                              consecutive 1-product chunks share one pipeline stage; otherwise each K16 step of
+                              the chunk whose lowest degree reaches D2 drops the moments' second fp16 term (2
+                              products: ~2^-12 relative on those terms), the other steps keep all 3; 0 = never.  Contributions of high input
                               degrees to a well-separated cell's local expansion are small, so the error stays far
                               below the first-term precision of the low degrees.  D2, D1 in 0..20; default
                               FMM_GRADE_DEFAULT.  M2M, the fused L2L and the solute-only pass always use 3
@@ -161,7 +162,7 @@ enum {
                               FMM_ERR_UNSUPPORTED without the tensor-core path (FP64 plans); a WS, PRECISION
                               or M2L_SPLIT change restores the default bricks */
 };
-#define FMM_GRADE_DEFAULT (8 << 8)  /* D2 = 0, D1 = 8: input degrees >= 8 with one product */
+#define FMM_GRADE_DEFAULT (4 | (8 << 8))  /* D2 = 4, D1 = 8: degrees 4..7 with two products, >= 8 with one */
 #define FMM_ACC_GROUP_DEFAULT 2
 enum { FMM_BOUNDARY_CONDUCTING = 0, FMM_BOUNDARY_VACUUM = 1 };
 enum { FMM_PREC_FP64 = 0, FMM_PREC_MIXED = 1 };

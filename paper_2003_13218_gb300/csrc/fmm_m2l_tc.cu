@@ -114,6 +114,8 @@ struct TcArgs {
     int out_np;             // M2M: class-layout side of the parent level (0 at level 0)
     uint32_t idesc;
     uint32_t gchunks;       // fp16x2 M2L offsets: products per K chunk, 2 bits per chunk (0 = all 3), FMM_OPT_M2L_GRADE
+    uint32_t gsteps;        // in a 3-product chunk, the first K16 step from which x1 y0 is dropped, 3 bits per chunk
+                            // (0: none)
     int acc_group;          // offsets summed in one TMEM accumulator before it is drained (>= 1)
     uint64_t wait_ns;       // budget of every pipeline wait (FMM_OPT_WAIT_BUDGET_NS); the teardown keeps its own
     int inject_stall;       // test hook (single-CTA kernel): the MMA issuer first waits on a barrier nothing arrives on
@@ -156,6 +158,10 @@ __device__ __forceinline__ int chunk_products(uint32_t g, int kc)
     const int c = (int)((g >> (2 * kc)) & 3u);
     return c == 0 ? 3 : c;
 }
+
+// First K16 step of chunk kc (a 3-product chunk) whose lowest input degree reaches D2: from there on the
+// chunk drops x1 y0 (0: no such step).
+__device__ __forceinline__ int step_split(uint32_t gs, int kc) { return (int)((gs >> (3 * kc)) & 7u); }
 
 // A graded offset's stages: two consecutive chunks of one product each (x0 y0 only) share one stage, their
 // A0 / B0 boxes in the places of the two terms; returns how many chunks the stage starting at kc covers.
@@ -498,9 +504,10 @@ struct Products<2, 3> {
     __device__ static constexpr int b(int k) { return k == 1 ? 1 : k == 3 ? 2 : 0; }
 };
 
-// The MMAs of one K chunk: the first NP products over the chunk's nk valid K16 steps, straight-line code
-// (operand addresses are compile-time offsets from the stage bases); `first` starts a new accumulator.
-template <int NP, typename PR, int K16, int SW, bool PAIR>
+// The MMAs of one K chunk: the first NP products over the chunk's nk valid K16 steps (the third, x1 y0, only
+// on steps below S2), straight-line code (operand addresses are compile-time offsets from the stage bases);
+// `first` starts a new accumulator.
+template <int NP, typename PR, int K16, int SW, bool PAIR, int S2 = K16>
 __device__ __forceinline__ void issue_chunk(uint32_t tmem_d, uint32_t a0, uint32_t b0, uint32_t stageA, uint32_t stageB,
                                             int nk, uint32_t idesc, bool first)
 {
@@ -508,7 +515,8 @@ __device__ __forceinline__ void issue_chunk(uint32_t tmem_d, uint32_t a0, uint32
     for (int pr = 0; pr < NP; ++pr) {
 #pragma unroll
         for (int k16 = 0; k16 < K16; ++k16) {
-            if (k16 >= nk) continue;  // zero fill beyond K
+            if (k16 >= nk) continue;         // zero fill beyond K
+            if (pr == 2 && k16 >= S2) continue;  // steps of degree >= D2: x0 y0 + x0 y1 only
             const uint64_t ad = sdesc<SW>(a0 + PR::a(pr) * stageA + k16 * 32);
             const uint64_t bd = sdesc<SW>(b0 + PR::b(pr) * stageB + k16 * 32);
             const uint32_t acc = (first && pr == 0 && k16 == 0) ? 0u : 1u;
@@ -536,6 +544,20 @@ __device__ __forceinline__ void issue_merged(uint32_t tmem_d, uint32_t a0, uint3
             else mma_bf16(tmem_d, ad, bd, idesc, acc);
         }
     }
+}
+
+// A chunk with all of the split's products, x1 y0 dropped from step s2 on (s2 = 0: on no step): one
+// compile-time variant per split point
+template <typename PR, int K16, int SW, bool PAIR>
+__device__ __forceinline__ void issue_full_chunk(int s2, uint32_t tmem_d, uint32_t a0, uint32_t b0, uint32_t stageA,
+                                                 uint32_t stageB, int nk, uint32_t idesc, bool first)
+{
+    if constexpr (PR::n == 3 && K16 == 4) {
+        if (s2 == 1) return issue_chunk<3, PR, K16, SW, PAIR, 1>(tmem_d, a0, b0, stageA, stageB, nk, idesc, first);
+        if (s2 == 2) return issue_chunk<3, PR, K16, SW, PAIR, 2>(tmem_d, a0, b0, stageA, stageB, nk, idesc, first);
+        if (s2 == 3) return issue_chunk<3, PR, K16, SW, PAIR, 3>(tmem_d, a0, b0, stageA, stageB, nk, idesc, first);
+    }
+    issue_chunk<PR::n, PR, K16, SW, PAIR>(tmem_d, a0, b0, stageA, stageB, nk, idesc, first);
 }
 
 // One CTA sums, for 128 target rows, the products of a list of offsets:
@@ -721,7 +743,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const uint32_t tmem_d = tmem + (uint32_t)(acc * 256);
                 bool first = true;  // the group's first MMA overwrites the accumulator
                 for (int o = groups.begin(g); o < groups.end(g) && ok; ++o) {
-                    const bool graded = kGradable && a.gchunks != 0u && a.mode == 0 && o_begin + o < a.n_il;
+                    const bool graded =
+                        kGradable && (a.gchunks | a.gsteps) != 0u && a.mode == 0 && o_begin + o < a.n_il;
                     for (int kc = 0; kc < a.kchunks;) {
                         if (!mbar_wait(smem_u32(&bar_full[s]), round & 1u, abort_flag, a.wait_ns)) {
                             ok = false;
@@ -744,8 +767,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                                 issue_chunk<2, PR, K16, SW, false>(tmem_d, base, base + PA * stageA, stageA, stageB, nk,
                                                                    a.idesc, first);
                             else
-                                issue_chunk<PR::n, PR, K16, SW, false>(tmem_d, base, base + PA * stageA, stageA, stageB,
-                                                                       nk, a.idesc, first);
+                                issue_full_chunk<PR, K16, SW, false>(graded ? step_split(a.gsteps, kc) : 0, tmem_d, base,
+                                                                     base + PA * stageA, stageA, stageB, nk, a.idesc,
+                                                                     first);
                         } else {
                             issue_chunk<PR::n, PR, K16, SW, false>(tmem_d, base, base + PA * stageA, stageA, stageB, nk,
                                                                    a.idesc, first);
@@ -1026,7 +1050,7 @@ __device__ __forceinline__ void pair_tile(const CUtensorMap *mA0, const CUtensor
                 const uint32_t tmem_d = tmem + (uint32_t)(acc * 256);
                 bool first = true;  // the group's first MMA overwrites the accumulator
                 for (int o = groups.begin(g); o < groups.end(g) && ok; ++o) {
-                    const bool graded = a.gchunks != 0u && o_begin + o < a.n_il;
+                    const bool graded = (a.gchunks | a.gsteps) != 0u && o_begin + o < a.n_il;
                     for (int kc = 0; kc < a.kchunks;) {
                         if (!mbar_wait_cluster(smem_u32(&bars.full[pp.s]), pp.round & 1u, abort_flag, a.wait_ns)) {
                             ok = false;
@@ -1048,8 +1072,8 @@ __device__ __forceinline__ void pair_tile(const CUtensorMap *mA0, const CUtensor
                             issue_chunk<2, PR, K16, SW, true>(tmem_d, base, base + PA * stageA, stageA, stageB, nk,
                                                               a.idesc, first);
                         else
-                            issue_chunk<PR::n, PR, K16, SW, true>(tmem_d, base, base + PA * stageA, stageA, stageB, nk,
-                                                                  a.idesc, first);
+                            issue_full_chunk<PR, K16, SW, true>(graded ? step_split(a.gsteps, kc) : 0, tmem_d, base,
+                                                                base + PA * stageA, stageA, stageB, nk, a.idesc, first);
                         first = false;
                         kc += nkc;
                         mma_commit_pair(smem_u32(&bars.empty[pp.s]));
@@ -1808,14 +1832,26 @@ void fill_common(const Plan &P, const TcState *S, int pa, int pb, TcArgs &a)
     // degree grading of the fp16x2 M2L (FMM_OPT_M2L_GRADE), per K chunk: chunk kc holds input
     // coefficients KCH kc .. KCH kc + KCH - 1, whose lowest degree is floor(sqrt(KCH kc))
     a.gchunks = 0;
+    a.gsteps = 0;
     const int d2 = P.grade & 0xFF, d1 = (P.grade >> 8) & 0xFF;
+    auto lowest_degree = [](int k) {  // of input coefficient k: floor(sqrt(k))
+        int lam = 0;
+        while ((lam + 1) * (lam + 1) <= k) ++lam;
+        return lam;
+    };
     if (S->f16 && pa == 2 && pb == 2 && (d2 > 0 || d1 > 0)) {
         const int kch = kchunk_of(S->sw);
-        for (int kc = 0; kc < a.kchunks && kc < 16; ++kc) {
-            int lam = 0;
-            while ((lam + 1) * (lam + 1) <= kch * kc) ++lam;
+        for (int kc = 0; kc < a.kchunks && kc < 10; ++kc) {
+            const int lam = lowest_degree(kch * kc);
             const int np = (d1 > 0 && lam >= d1) ? 1 : (d2 > 0 && lam >= d2) ? 2 : 3;
             if (np < 3) a.gchunks |= (uint32_t)np << (2 * kc);
+            // a 3-product chunk whose later K16 steps reach D2 drops x1 y0 there
+            if (np == 3 && d2 > 0)
+                for (int st = 1; st * 16 < kch; ++st)
+                    if (lowest_degree(kch * kc + 16 * st) >= d2) {
+                        a.gsteps |= (uint32_t)st << (3 * kc);
+                        break;
+                    }
         }
     }
 }
@@ -2026,7 +2062,7 @@ fmm_status launch_m2m_tc(Plan &P, int l)
     TcArgs a;
     fill_common(P, S, S->pa, S->pb, a);
     a.mode = 1;
-    a.gchunks = 0;  // translations keep every product
+    a.gchunks = a.gsteps = 0;  // translations keep every product
     a.np = n;
     a.bx = S->bx[src];
     a.by = S->by[src];
@@ -2069,7 +2105,7 @@ static bool m2l_args(const Plan &P, const TcState *S, int l, bool precise, int p
 {
     const int np = 1 << (l - 1);
     fill_common(P, S, pa, pb, a);
-    if (precise) a.gchunks = 0;  // the solute-only pass keeps every product
+    if (precise) a.gchunks = a.gsteps = 0;  // the solute-only pass keeps every product
     a.mode = 0;
     a.np = np;
     a.bx = S->bx[l];

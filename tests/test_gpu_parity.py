@@ -387,7 +387,7 @@ def test_clustered_charges_take_the_unstaged_near_field():
         assert _rms_rel(F, ref["forces"]) < tol_f, prec
 
 
-@pytest.mark.parametrize("grade,acc_group", [((0, 0), 1), ((0, 8), 1), ((0, 8), 4), ((4, 8), 8), ((0, 6), 2)])
+@pytest.mark.parametrize("grade,acc_group", [((0, 0), 1), ((0, 8), 1), ((4, 8), 2), ((0, 8), 4), ((4, 8), 8), ((0, 6), 2)])
 def test_graded_split_and_accumulation_groups_against_oracle(grade, acc_group):
     """The degree-graded fp16x2 M2L (FMM_OPT_M2L_GRADE) and longer TMEM accumulation chains
     (FMM_OPT_M2L_ACC_GROUP) stay within the mixed budget against the oracle (Eq. Lcoeffdef):
