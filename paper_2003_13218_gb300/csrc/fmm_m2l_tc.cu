@@ -1467,8 +1467,8 @@ __global__ void k_split_halo16(const float *__restrict__ M, int np, int hw, int 
 // persistent CTA pairs.  Per (box, level) three stages, each a run of work items:
 //   P  the parent level's local expansion split into the fused L2L's fp16 planes (k_split_L), and the
 //      reset of the level's largest |L^ / s|;
-//   M  the tile pairs of the level's M2L + fused L2L (the k_m2l_tc_pair work, same offset groups, one item
-//      per tile pair running its groups in turn);
+//   M  the tile pairs of the level's M2L + fused L2L (the k_m2l_tc_pair work, same offset groups): one
+//      item per tile pair running its groups in turn, or per offset group where the level is small;
 //   G  with offset groups > 1, the group sum into L (k_group_sum), folding the level's maximum.
 // The items of all boxes sit in one device queue in level order, and P, M, G within a level, so every
 // item depends only on items before it.  A pair claims the next item with an atomic add, waits (bounded,
@@ -1491,6 +1491,7 @@ struct SweepLevel {
     unsigned *amaxL;                  // this level's largest |L^ / s|, reset by P, folded by M or G
     int64_t gs_n;                     // G: elements of the level's L
     int lev, nc, kp;
+    int gpi;                          // M: offset groups per item (all of a tile pair's, or one)
     int n_items[3];                   // items of stages P, M, G (G: 0 with one offset group)
     int prev;                         // the same box's previous sweep level (-1: done before the launch)
 };
@@ -1614,12 +1615,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TC_THREADS, 1)
                 asm volatile("fence.proxy.async.global;" ::: "memory");
             }
             __syncwarp();
-            // every offset group of the tile pair in turn (the ring runs on from group to group); only the
-            // last group's epilogue stages its rows in the ring
-            for (int g = 0; g < e.a.groups; ++g) {
+            // the item's offset groups of one tile pair in turn (the ring runs on from group to group); only
+            // the last group's epilogue stages its rows in the ring
+            for (int g = 0; g < e.gpi; ++g) {
                 if (*(volatile int *)&abort_sh) break;  // a wait ran out: the remaining groups are skipped
-                pair_tile<NCH>(&e.mA[0], &e.mA[1], &e.mB[0], &e.mB[1], &e.mL[0], &e.mL[1], e.a, it.z * e.a.groups + g,
-                               rank, smem0, stage, g == e.a.groups - 1, bars, tmem, &abort_sh, pp);
+                pair_tile<NCH>(&e.mA[0], &e.mA[1], &e.mB[0], &e.mB[1], &e.mL[0], &e.mL[1], e.a, it.z * e.gpi + g,
+                               rank, smem0, stage, g == e.gpi - 1, bars, tmem, &abort_sh, pp);
             }
         } else if (it.x == 0) {
             // stage P: parent cells [SWEEP_P_CELLS it.z, ...) of level l - 1, one warp per cell over the pair
@@ -2294,13 +2295,32 @@ fmm_status sweep_create(Plan *const *plans, int n, Sweep **out)
             e.nc = P.nc;
             e.kp = S->kp;
             e.n_items[0] = (int)((ncl + SWEEP_P_CELLS - 1) / SWEEP_P_CELLS);
-            e.n_items[1] = 4 * e.a.tiles_per_class;  // tile pairs: 8 classes x tiles / 2, all groups in one item
+            e.gpi = e.a.groups;  // set per level below
+            e.n_items[1] = 4 * e.a.tiles_per_class;  // tile pairs: 8 classes x tiles / 2
             e.n_items[2] = e.a.groups > 1 ? (int)((e.gs_n + SWEEP_G_ELEMS - 1) / SWEEP_G_ELEMS) : 0;
             e.prev = prev;
             prev = (int)lv.size();
             lv.push_back(e);
             lmin = l < lmin ? l : lmin;
             lmax = l > lmax ? l : lmax;
+        }
+    }
+    // item grain per level: whole tile pairs (all their offset groups in turn: one ramp and one exposed
+    // epilogue per tile pair) when the level's tile pairs over all entries fill the resident pairs twice;
+    // otherwise one offset group per item, so that a lone deep box's small levels spread over the GPU
+    {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        for (int l = lmin; l <= lmax; ++l) {
+            long long tp = 0;
+            for (const SweepLevel &e : lv)
+                if (e.lev == l) tp += e.n_items[1];
+            for (SweepLevel &e : lv)
+                if (e.lev == l && tp < (long long)sms) {  // 2 x (sms / 2) pairs
+                    e.gpi = 1;
+                    e.n_items[1] *= e.a.groups;
+                }
         }
     }
     // the queue: level by level, within a level stage P of every entry, then M, then G
