@@ -511,14 +511,19 @@ template <int NP, typename PR, int K16, int SW, bool PAIR, int S2 = K16>
 __device__ __forceinline__ void issue_chunk(uint32_t tmem_d, uint32_t a0, uint32_t b0, uint32_t stageA, uint32_t stageB,
                                             int nk, uint32_t idesc, bool first)
 {
+    // descriptors of the stage bases once; an operand at byte offset o from a base is the base's descriptor
+    // plus o / 16 in the address field (14 bits of 16-byte units: shared-memory addresses stay below 2^18,
+    // so the sum never carries out of the field)
+    const uint64_t ad0 = sdesc<SW>(a0), bd0 = sdesc<SW>(b0);
+    const uint64_t sa = stageA >> 4, sb = stageB >> 4;
 #pragma unroll
     for (int pr = 0; pr < NP; ++pr) {
 #pragma unroll
         for (int k16 = 0; k16 < K16; ++k16) {
             if (k16 >= nk) continue;         // zero fill beyond K
             if (pr == 2 && k16 >= S2) continue;  // steps of degree >= D2: x0 y0 + x0 y1 only
-            const uint64_t ad = sdesc<SW>(a0 + PR::a(pr) * stageA + k16 * 32);
-            const uint64_t bd = sdesc<SW>(b0 + PR::b(pr) * stageB + k16 * 32);
+            const uint64_t ad = ad0 + (uint64_t)PR::a(pr) * sa + (uint64_t)(k16 * 2);
+            const uint64_t bd = bd0 + (uint64_t)PR::b(pr) * sb + (uint64_t)(k16 * 2);
             const uint32_t acc = (first && pr == 0 && k16 == 0) ? 0u : 1u;
             if (PAIR) mma_f16_pair(tmem_d, ad, bd, idesc, acc);
             else mma_bf16(tmem_d, ad, bd, idesc, acc);
@@ -532,13 +537,15 @@ template <int K16, int SW, bool PAIR>
 __device__ __forceinline__ void issue_merged(uint32_t tmem_d, uint32_t a0, uint32_t b0, uint32_t stageA,
                                              uint32_t stageB, int nk1, uint32_t idesc, bool first)
 {
+    const uint64_t ad0 = sdesc<SW>(a0), bd0 = sdesc<SW>(b0);  // stepped as in issue_chunk
+    const uint64_t sa = stageA >> 4, sb = stageB >> 4;
 #pragma unroll
     for (int t = 0; t < 2; ++t) {
 #pragma unroll
         for (int k16 = 0; k16 < K16; ++k16) {
             if (t == 1 && k16 >= nk1) continue;
-            const uint64_t ad = sdesc<SW>(a0 + t * stageA + k16 * 32);
-            const uint64_t bd = sdesc<SW>(b0 + t * stageB + k16 * 32);
+            const uint64_t ad = ad0 + (uint64_t)t * sa + (uint64_t)(k16 * 2);
+            const uint64_t bd = bd0 + (uint64_t)t * sb + (uint64_t)(k16 * 2);
             const uint32_t acc = (first && t == 0 && k16 == 0) ? 0u : 1u;
             if (PAIR) mma_f16_pair(tmem_d, ad, bd, idesc, acc);
             else mma_bf16(tmem_d, ad, bd, idesc, acc);
