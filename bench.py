@@ -212,6 +212,8 @@ def run_ours(args):
     box, d, p = boxes.workload(args.workload, seed=rank)
     if args.p is not None:
         p = args.p
+    if args.depth is not None:
+        d = args.depth
     N = box.N
     pos = torch.from_numpy(box.pos).to(dev)
     q = torch.from_numpy(box.q).to(dev)
@@ -669,6 +671,7 @@ def main():
                     help="1: also time the 64-box lambda-window batch and add it to the line")
     ap.add_argument("--ws", type=int, default=1, choices=[1, 2], help="well-separatedness (2: the paper's setting)")
     ap.add_argument("--p", type=int, default=None, help="expansion order (default: the workload's)")
+    ap.add_argument("--depth", type=int, default=None, help="tree depth (default: the workload's)")
     ap.add_argument("--m2l-grade", default=None, help="D2,D1 of FMM_OPT_M2L_GRADE (default: the library's 4,8)")
     ap.add_argument("--acc-group", type=int, default=None, help="FMM_OPT_M2L_ACC_GROUP (default: the library's)")
     ap.add_argument("--overlap", type=int, default=1, choices=[0, 1],

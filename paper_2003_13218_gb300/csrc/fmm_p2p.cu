@@ -23,6 +23,23 @@ __device__ inline float inv_sqrt<float>(float x) { return rsqrtf(x); }
 template <>
 __device__ inline double inv_sqrt<double>(double x) { return 1.0 / sqrt(x); }
 
+// One source of the near field: adds q_j / r and q_j r / r^3 for r = (ox, oy, oz) - x_j.  A source at r = 0
+// (the target itself: the same stored coordinates) adds nothing; the near field never holds a charge's own
+// periodic image (2^depth > 2 ws + 1).
+template <typename T>
+__device__ __forceinline__ void p2p_pair(const Particle<T> &pj, T ox, T oy, T oz, T &acc, T &ex, T &ey, T &ez)
+{
+    const T rx = ox - pj.x, ry = oy - pj.y, rz = oz - pj.z;
+    const T r2 = rx * rx + ry * ry + rz * rz;
+    const T ir = r2 > T(0) ? inv_sqrt<T>(r2) : T(0);
+    const T qir = pj.q * ir;
+    acc += qir;
+    const T qir3 = qir * ir * ir;
+    ex += qir3 * rx;
+    ey += qir3 * ry;
+    ez += qir3 * rz;
+}
+
 // One thread per sorted charge i: phi_i = sum q_j / r_ij, e_i = sum q_j r_ij / r_ij^3.
 template <typename T>
 __global__ void k_p2p(int64_t N, int d, int ws, T h, const int *__restrict__ start, const int *__restrict__ sleaf,
@@ -175,44 +192,46 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p_tile(int d, int ws, int bx,
         const int it = lo - rc * W;  // index of the target leaf within its row
         const int s = gst[lo] + (st - pre[lo]);  // sorted index of the target
         const Particle<T> pi = staged ? stg[st] : sp[s];
-        T acc = 0, ex = 0, ey = 0, ez = 0;
+        // four independent partial sums (sources j, j + 1, j + 2, j + 3 of each leaf), so that the loads and
+        // the dependent additions of consecutive pairs overlap; added in a fixed order at the end
+        T a[4] = {0, 0, 0, 0}, fx[4] = {0, 0, 0, 0}, fy[4] = {0, 0, 0, 0}, fz[4] = {0, 0, 0, 0};
         for (int dz = -ws; dz <= ws; ++dz)
             for (int dy = -ws; dy <= ws; ++dy)
                 for (int dx = -ws; dx <= ws; ++dx) {
                     const int f = ((dz + ws) * side + dy + ws) * W + it + dx;
                     const T ox = pi.x - T(dx) * h, oy = pi.y - T(dy) * h, oz = pi.z - T(dz) * h;
-                    int jb, je, self;
+                    int jb, je;
                     const Particle<T> *src;
                     if (staged) {
                         jb = pre[f];
                         je = pre[f + 1];
                         src = stg;
-                        self = st;
                     } else {  // the leaf's records in the sorted array
                         jb = gst[f];
                         je = jb + (pre[f + 1] - pre[f]);
                         src = sp;
-                        self = s;
                     }
-                    for (int j = jb; j < je; ++j) {
-                        if (j == self) continue;
-                        const Particle<T> pj = src[j];
-                        const T rx = ox - pj.x, ry = oy - pj.y, rz = oz - pj.z;
-                        const T r2 = rx * rx + ry * ry + rz * rz;
-                        const T ir = inv_sqrt<T>(r2);
-                        const T qir = pj.q * ir;
-                        acc += qir;
-                        const T qir3 = qir * ir * ir;
-                        ex += qir3 * rx;
-                        ey += qir3 * ry;
-                        ez += qir3 * rz;
+                    int j = jb;
+                    for (; j + 4 <= je; j += 4) {
+                        Particle<T> q4[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) q4[u] = src[j + u];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) p2p_pair<T>(q4[u], ox, oy, oz, a[u], fx[u], fy[u], fz[u]);
+                    }
+                    if (j < je) {
+                        p2p_pair<T>(src[j], ox, oy, oz, a[0], fx[0], fy[0], fz[0]);
+                        if (j + 1 < je) {
+                            p2p_pair<T>(src[j + 1], ox, oy, oz, a[1], fx[1], fy[1], fz[1]);
+                            if (j + 2 < je) p2p_pair<T>(src[j + 2], ox, oy, oz, a[2], fx[2], fy[2], fz[2]);
+                        }
                     }
                 }
-        phi[s] = acc;
+        phi[s] = (a[0] + a[1]) + (a[2] + a[3]);
         if (field) {
-            field[3 * s] = ex;
-            field[3 * s + 1] = ey;
-            field[3 * s + 2] = ez;
+            field[3 * s] = (fx[0] + fx[1]) + (fx[2] + fx[3]);
+            field[3 * s + 1] = (fy[0] + fy[1]) + (fy[2] + fy[3]);
+            field[3 * s + 2] = (fz[0] + fz[1]) + (fz[2] + fz[3]);
         }
     }
 }
