@@ -1788,13 +1788,28 @@ TcKernel pick_kernel(int pa, int pb, int nch, int sw)
         if (st_ != FMM_OK) return st_;     \
     } while (0)
 
-// offsets split over `want` CTAs per tile: per_group offsets each
-void split_offsets(int n_off, int tiles, int max_groups, int &groups, int &per_group)
+// Offsets split over `groups` CTAs per tile, per_group offsets each.  With one CTA per SM a launch of
+// tiles x g CTAs takes ceil(tiles g / sms) waves of ceil(n_off / g) offsets plus a fixed cost per CTA
+// (pipeline fill and the exposed epilogue: about SPLIT_FIXED offsets' worth); g is the smallest that
+// minimises that product.
+constexpr int SPLIT_FIXED = 10;
+
+void split_offsets(int n_off, int tiles, int max_groups, int sms, int &groups, int &per_group)
 {
-    int want = (2 * 152 + tiles - 1) / tiles;  // enough CTAs to fill the GPU twice
-    if (want < 1) want = 1;
-    if (want > max_groups) want = max_groups;
-    per_group = (n_off + want - 1) / want;
+    long long best = -1;
+    int g_best = 1;
+    for (int g = 1; g <= max_groups && g <= n_off; ++g) {
+        const int per = (n_off + g - 1) / g;
+        const int used = (n_off + per - 1) / per;  // groups that actually hold offsets
+        if (used != g) continue;
+        const long long waves = ((long long)tiles * g + sms - 1) / sms;
+        const long long cost = waves * (per + SPLIT_FIXED);
+        if (best < 0 || cost < best) {
+            best = cost;
+            g_best = g;
+        }
+    }
+    per_group = (n_off + g_best - 1) / g_best;
     groups = (n_off + per_group - 1) / per_group;
 }
 
@@ -1968,6 +1983,10 @@ fmm_status tc_prepare(Plan &P)
     }
     // source planes per level
     size_t lpart_elems = 0;
+    int sms = 0, dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                 cudaSuccess || sms < 1)
+        sms = 152;
     for (int l = 1; l <= P.d; ++l) {
         int np = 1 << (l - 1);
         int64_t np2 = np + 2 * P.ws;  // periodic halo of ws cells
@@ -1990,14 +2009,14 @@ fmm_status tc_prepare(Plan &P)
             S->mapL[l][0] = S->mapL[l][1] = S->mapA[l][0];  // unused kernel parameters
         }
         const int tiles = 8 * (np / S->bx[l]) * (np / S->by[l]) * (np / S->bz[l]);
-        split_offsets(n_il(P.ws) + (S->f16 ? 1 : 0), tiles, 27, S->groups[l], S->per_group[l]);
+        split_offsets(n_il(P.ws) + (S->f16 ? 1 : 0), tiles, 27, sms, S->groups[l], S->per_group[l]);
         if (S->groups[l] > 1) {
             size_t need = (size_t)S->groups[l] * 8 * np * np * np * P.nc;
             if (need > lpart_elems) lpart_elems = need;
         }
         // M2M into level l - 1 (natural side np, bricks of the level-l planes)
         const int mtiles = (np / S->bx[l]) * (np / S->by[l]) * (np / S->bz[l]);
-        split_offsets(8, mtiles, 8, S->mgroups[l - 1], S->mper_group[l - 1]);
+        split_offsets(8, mtiles, 8, sms, S->mgroups[l - 1], S->mper_group[l - 1]);
         if (S->f16 && S->mgroups[l - 1] > 1) {
             size_t need = (size_t)S->mgroups[l - 1] * np * np * np * P.nc;
             if (need > lpart_elems) lpart_elems = need;
