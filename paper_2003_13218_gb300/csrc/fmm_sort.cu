@@ -3,6 +3,8 @@
 // FP64 compensated energy reductions of Eq. Velecfull and Eq. FMMcalc.
 #include <math.h>
 
+#include <type_traits>
+
 #include "fmm_internal.cuh"
 
 namespace fmm {
@@ -188,32 +190,28 @@ __device__ inline KSum warp_merge(KSum k)
     return k;
 }
 
-// block-level reduction of NQ per-thread sums -> partial[block][NQ][2]: warps
-// first, then the first warp over the warps' results
+// block-level reduction of NQ per-thread sums -> partial[block][NQ][2]: the 32 lanes of a warp are added
+// plainly in a fixed xor tree (deterministic; GB300's FP64 pipe is slow, and a compensated merge per lane
+// and round cost most of the reduction), the block's warp sums compensated (lane q of warp 0, quantity q),
+// and the blocks again compensated by final_sum
 template <int NQ>
 __device__ void block_reduce_store(const double (&acc)[NQ], double *__restrict__ partial)
 {
-    __shared__ double sh[RED_THREADS / 32][NQ][2];
+    static_assert(NQ <= 32, "one lane per quantity");
+    __shared__ double sh[RED_THREADS / 32][NQ];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
-        KSum k = warp_merge(KSum{acc[q], 0.0});
-        if (lane == 0) {
-            sh[w][q][0] = k.s;
-            sh[w][q][1] = k.c;
-        }
+        double v = acc[q];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) sh[w][q] = v;
     }
     __syncthreads();
-    if (w == 0) {
-        for (int q = 0; q < NQ; ++q) {
-            KSum k{0.0, 0.0};
-            if (lane < RED_THREADS / 32) k = KSum{sh[lane][q][0], sh[lane][q][1]};
-            k = warp_merge(k);
-            if (lane == 0) {
-                partial[(blockIdx.x * NQ + q) * 2] = k.s;
-                partial[(blockIdx.x * NQ + q) * 2 + 1] = k.c;
-            }
-        }
+    if (w == 0 && lane < NQ) {
+        KSum k{0.0, 0.0};
+        for (int i = 0; i < RED_THREADS / 32; ++i) k.add(sh[i][lane]);
+        partial[(blockIdx.x * NQ + lane) * 2] = k.s;
+        partial[(blockIdx.x * NQ + lane) * 2 + 1] = k.c;
     }
 }
 
@@ -221,8 +219,8 @@ __device__ void block_reduce_store(const double (&acc)[NQ], double *__restrict__
 __global__ void k_bc_partial(int64_t N, const double *__restrict__ wpos, const double *__restrict__ q,
                              const uint8_t *__restrict__ sol, double *__restrict__ partial)
 {
-    // a thread's own elements (N / 77,824, about 13 at N = 1M) are summed plainly; the
-    // compensated sums start at the warp level
+    // a thread's own elements (N / 77,824, about 13 at N = 1M) and a warp's lanes are summed
+    // plainly; the compensated sums start at the block level
     double acc[10];
 #pragma unroll
     for (int k = 0; k < 10; ++k) acc[k] = 0.0;
@@ -372,10 +370,13 @@ __global__ void k_forces_out(int64_t N, const int *__restrict__ perm, const Part
     int i = perm[s];
     double qi = q[i];
     if (!isfinite(qi)) qi = 0.0;
-    double Q = mom[0];
+    const double Q = mom[0], cq = c * qi;
     for (int a = 0; a < 3; ++a) {
-        double f = qi * ((double)f_nf[3 * s + a] - (double)g_ff[3 * s + a]);
-        f -= c * qi * (Q * wpos[3 * (int64_t)i + a] - (vacuum ? 0.0 : mom[1 + a]));
+        // the mixed path's field (FP32 near and far parts) is formed in FP32 and converted once
+        const double fld = std::is_same<T, float>::value ? (double)(f_nf[3 * s + a] - g_ff[3 * s + a])
+                                                         : (double)f_nf[3 * s + a] - (double)g_ff[3 * s + a];
+        double f = qi * fld;
+        f -= cq * (Q * wpos[3 * (int64_t)i + a] - (vacuum ? 0.0 : mom[1 + a]));
         forces[3 * (int64_t)i + a] = f;
     }
 }
