@@ -419,8 +419,8 @@ void fmm_batch_destroy(fmm_batch batch);
  * The only scratch is a file-scope device array of 80 KiB that every GPU
  * loading the library keeps until the process exits; it bounds N to
  * 4,194,304 charges (larger N: FMM_ERR_INVALID_ARG, nothing launched).  The
- * first call on each device looks up that array's device address, so make the
- * first call on a device before capturing any stream on it.  All calls share
+ * first call on each device looks up that array's device address (a
+ * runtime query); later calls reuse it.  All calls share
  * the array: calls that overlap on the GPU (other streams, other host threads)
  * race, so serialise them.  Other errors: FMM_ERR_INVALID_ARG for null
  * pointers, N < 1 or a non-finite or non-positive box; FMM_ERR_CUDA if the
