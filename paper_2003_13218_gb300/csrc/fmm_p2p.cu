@@ -40,57 +40,14 @@ __device__ __forceinline__ void p2p_pair(const Particle<T> &pj, T ox, T oy, T oz
     ez += qir3 * rz;
 }
 
-// One thread per sorted charge i: phi_i = sum q_j / r_ij, e_i = sum q_j r_ij / r_ij^3.
-template <typename T>
-__global__ void k_p2p(int64_t N, int d, int ws, T h, const int *__restrict__ start, const int *__restrict__ sleaf,
-                      const Particle<T> *__restrict__ sp, T *__restrict__ phi, T *__restrict__ field)
-{
-    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (s >= N) return;
-    int nside = 1 << d;
-    int leaf = sleaf[s];
-    int x = leaf % nside, y = (leaf / nside) % nside, z = leaf / (nside * nside);
-    Particle<T> pi = sp[s];
-    T acc = 0, ex = 0, ey = 0, ez = 0;
-    for (int dz = -ws; dz <= ws; ++dz) {
-        int zz = (z + dz + nside) & (nside - 1);
-        for (int dy = -ws; dy <= ws; ++dy) {
-            int yy = (y + dy + nside) & (nside - 1);
-            for (int dx = -ws; dx <= ws; ++dx) {
-                int xx = (x + dx + nside) & (nside - 1);
-                int c = xx + nside * (yy + nside * zz);
-                T ox = pi.x - T(dx) * h, oy = pi.y - T(dy) * h, oz = pi.z - T(dz) * h;
-                for (int j = start[c]; j < start[c + 1]; ++j) {
-                    if (j == s) continue;
-                    Particle<T> pj = sp[j];
-                    T rx = ox - pj.x, ry = oy - pj.y, rz = oz - pj.z;
-                    T r2 = rx * rx + ry * ry + rz * rz;
-                    T ir = inv_sqrt<T>(r2);
-                    T qir = pj.q * ir;
-                    acc += qir;
-                    T qir3 = qir * ir * ir;
-                    ex += qir3 * rx;
-                    ey += qir3 * ry;
-                    ez += qir3 * rz;
-                }
-            }
-        }
-    }
-    phi[s] = acc;
-    if (field) {
-        field[3 * s] = ex;
-        field[3 * s + 1] = ey;
-        field[3 * s + 2] = ez;
-    }
-}
-
-// The same near field with the neighbour particles staged in shared memory.  A block takes a row segment
-// of BX consecutive leaves along x at (y, z) -- their charges are contiguous in the sorted order -- and
-// copies the particles of the (2 ws + 1)^2 rows around it, each BX + 2 ws leaves long (x wrapped
-// periodically, a leaf may appear twice when BX + 2 ws exceeds the side), into shared memory with
-// 16-byte cp.async copies.  Then each thread takes one target charge of the segment and sums over its
-// (2 ws + 1)^3 neighbour leaves in the same order and with the same arithmetic as k_p2p (so the results
-// are identical); a block whose rows hold more than `cap` particles reads them from global memory.
+// The near field with the neighbour particles staged in shared memory: phi_i = sum q_j / r_ij and
+// e_i = sum q_j r_ij / r_ij^3 per sorted charge i.  A block takes a row segment of BX consecutive leaves
+// along x at (y, z) -- their charges are contiguous in the sorted order -- and copies the particles of the
+// (2 ws + 1)^2 rows around it, each BX + 2 ws leaves long (x wrapped periodically, a leaf may appear twice
+// when BX + 2 ws exceeds the side), into shared memory with 16-byte cp.async copies.  Then each thread
+// takes one target charge of the segment and sums over its (2 ws + 1)^3 neighbour leaves in a fixed
+// order; a block whose rows hold more than `cap` particles reads them from global memory with the same
+// arithmetic in the same order, so the staged and unstaged blocks give identical results.
 //   shared memory: pre[R W + 1] (staged start of leaf f = r W + i, row r = (dz + ws)(2 ws + 1) + dy + ws,
 //   i = x - x0 + ws), gst[R W] (the leaf's first sorted index), then the staged records.
 constexpr int P2P_THREADS = 128;
