@@ -248,6 +248,25 @@ def test_ewald_wigner_single_charge(where):
     assert rel(e, C["wigner_sc"] * q[0] ** 2 / (2 * b)) < 1e-11
 
 
+def _wigner_crystal(kind, b, q, shift):
+    """Charges q on a cubic cell of side b: 2 (body-centred) or 4 (face-centred) per cell."""
+    basis = {"bcc": [(0, 0, 0), (0.5, 0.5, 0.5)],
+             "fcc": [(0, 0, 0), (0.5, 0.5, 0), (0.5, 0, 0.5), (0, 0.5, 0.5)]}[kind]
+    pos = (np.array(basis) + np.array(shift)) * b
+    n = len(basis)
+    r_s = (3 * b ** 3 / (4 * PI * n)) ** (1 / 3)
+    return pos, np.full(n, q), -n * C["wigner_" + kind] * q * q / r_s
+
+
+@pytest.mark.parametrize("kind,shift", [("bcc", (0.13, 0.13, 0.13)), ("bcc", (0.71, 0.05, 0.4)),
+                                        ("fcc", (0.21, 0.07, 0.33))])
+def test_ewald_wigner_crystals(kind, shift):
+    """Several equal charges per cell with the background (Q = 2, 4): the total net charge enters
+    the charged term squared, and the energy is the published Wigner-crystal constant."""
+    pos, q, target = _wigner_crystal(kind, 1.3, 0.7, shift)
+    assert rel(oracle.ewald(pos, q, 1.3)["energy"], target) < 1e-11
+
+
 def test_ewald_kappa_independent_for_charged_box():
     pos, q = boxes.random_charges(30, 3.0, seed=5)
     e = [oracle.ewald(pos, q, 3.0, kappa=k / 1.5)["energy"] for k in (5.0, 6.0, 7.5)]
@@ -296,6 +315,16 @@ def test_fmm_wigner_charge_on_a_cell_corner():
             for p in (8, 16, 24)]
     assert errs[0] > errs[1] > errs[2]
     assert errs[2] < 2e-5
+
+
+@pytest.mark.parametrize("kind,shift", [("bcc", (0.13, 0.13, 0.13)), ("fcc", (0.21, 0.07, 0.33))])
+def test_fmm_wigner_crystals(kind, shift):
+    """P2 with several charges per cell: the charged term (Eq. 6) with Q = 2 and 4, and the
+    quadrupole and dipole surface terms (Eq. surfchargedend, App. D), which no longer cancel
+    term by term, give the published Wigner-crystal energy; the error falls with p."""
+    pos, q, target = _wigner_crystal(kind, 1.3, 0.7, shift)
+    errs = [rel(oracle.fmm(pos, q, 1.3, 2, p, forces=False)["total"], target) for p in (12, 20)]
+    assert errs[1] < 1e-9 and errs[1] < errs[0]
 
 
 def test_fmm_nacl_madelung():
