@@ -6,7 +6,12 @@ calls fail loudly -- there is no CPU fallback.
 
 Inputs may be CUDA tensors (float64 positions [N, 3], float64 charges [N],
 uint8 solute flags [N]) or host NumPy arrays / CPU tensors; host inputs go
-through the library's own host<->device copies.
+through the library's own host<->device copies.  The binding checks what the
+C ABI cannot: an input with fewer elements than the call reads is refused, one
+of another element type or layout is converted; an output (forces, potentials)
+is written in place and must be contiguous, of the right type and long enough.
+A batch keeps the addresses of its per-box tensors in its recorded CUDA graph,
+so those must already be contiguous CUDA tensors of the right type.
 """
 from __future__ import annotations
 
@@ -141,16 +146,53 @@ def _check(code, where):
         raise FMMError(code, where)
 
 
-def _ptr(x):
-    """(pointer, keepalive) for a CUDA/CPU tensor or NumPy array; None stays None."""
+_KIND = {"f8": (torch.float64, np.dtype(np.float64)), "u1": (torch.uint8, np.dtype(np.uint8))}
+
+
+def _ptr(x, count=None, kind="f8", name="array", out=False):
+    """(pointer, keepalive) for a tensor (CUDA or CPU) or NumPy array; None stays None.
+
+    The C ABI takes plain pointers and cannot check what they point to, so the checks are made here:
+    `count` is the number of elements the call reads or writes (fewer is a ValueError), `kind` the
+    element type ("f8" double, "u1" uint8).  An input of another element type or layout is converted
+    (a copy that lives until the call returns); an output is written in place, so it must already be
+    contiguous and of the right type."""
     if x is None:
         return None, None
+    tdt, ndt = _KIND[kind]
     if isinstance(x, torch.Tensor):
+        if out and (x.dtype != tdt or not x.is_contiguous()):
+            raise ValueError(f"{name}: an output must be a contiguous {tdt} tensor (got {x.dtype}, "
+                             f"contiguous={x.is_contiguous()})")
+        if x.dtype != tdt:
+            x = x.to(tdt)
         if not x.is_contiguous():
             x = x.contiguous()
-        return ctypes.c_void_p(x.data_ptr()), x
-    a = np.ascontiguousarray(x)
-    return ctypes.c_void_p(a.ctypes.data), a
+        n, ptr = x.numel(), x.data_ptr()
+    else:
+        if out and not (isinstance(x, np.ndarray) and x.dtype == ndt and x.flags.c_contiguous and x.flags.writeable):
+            raise ValueError(f"{name}: an output must be a writeable C-contiguous {ndt} array")
+        x = np.ascontiguousarray(x, dtype=ndt)
+        n, ptr = x.size, x.ctypes.data
+    if count is not None and n < count:
+        raise ValueError(f"{name}: {n} elements, the call {'writes' if out else 'reads'} {count}")
+    return ctypes.c_void_p(ptr), x
+
+
+def _batch_ptrs(xs, counts, kind, name):
+    """Array of per-box device pointers for fmm_batch_lambda_energies.  The batch replays a recorded
+    CUDA graph that holds these addresses, so nothing is converted: every entry must already be a
+    contiguous CUDA tensor of the element type with at least counts[i] elements."""
+    xs = list(xs)
+    if len(xs) != len(counts):
+        raise ValueError(f"{name}: {len(xs)} tensors for {len(counts)} boxes")
+    tdt = _KIND[kind][0]
+    for i, (x, c) in enumerate(zip(xs, counts)):
+        if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == tdt and x.is_contiguous()):
+            raise ValueError(f"{name}[{i}]: must be a contiguous CUDA {tdt} tensor")
+        if x.numel() < c:
+            raise ValueError(f"{name}[{i}]: {x.numel()} elements, the box has {c}")
+    return (ctypes.c_void_p * len(xs))(*[ctypes.c_void_p(x.data_ptr()) for x in xs]), xs
 
 
 class FMMPlan:
@@ -209,10 +251,11 @@ class FMMPlan:
     def evaluate(self, pos, q, is_solute=None, forces=None, want_terms=True):
         """fmm_evaluate: returns (terms dict or None, uv dict or None); fills ``forces`` if given."""
         self._bind_stream(pos, q, is_solute, forces)
-        pp, kp = _ptr(pos)
-        pq, kq = _ptr(q)
-        ps, ks = _ptr(is_solute)
-        pf, kf = _ptr(forces)
+        N = self.N
+        pp, kp = _ptr(pos, 3 * N, "f8", "pos")
+        pq, kq = _ptr(q, N, "f8", "q")
+        ps, ks = _ptr(is_solute, N, "u1", "is_solute")
+        pf, kf = _ptr(forces, 3 * N, "f8", "forces", out=True)
         t = EnergyTerms()
         u = UVTerms()
         _check(self._lib.fmm_evaluate(self._h, pp, pq, ps, pf, ctypes.byref(t) if want_terms else None,
@@ -221,8 +264,8 @@ class FMMPlan:
 
     def energy(self, pos, q):
         self._bind_stream(pos, q)
-        pp, kp = _ptr(pos)
-        pq, kq = _ptr(q)
+        pp, kp = _ptr(pos, 3 * self.N, "f8", "pos")
+        pq, kq = _ptr(q, self.N, "f8", "q")
         e = ctypes.c_double()
         t = EnergyTerms()
         _check(self._lib.fmm_energy(self._h, pp, pq, ctypes.byref(e), ctypes.byref(t)), "fmm_energy")
@@ -235,9 +278,9 @@ class FMMPlan:
             else:
                 out = np.empty((self.N, 3), dtype=np.float64)
         self._bind_stream(pos, q, out)
-        pp, kp = _ptr(pos)
-        pq, kq = _ptr(q)
-        pf, kf = _ptr(out)
+        pp, kp = _ptr(pos, 3 * self.N, "f8", "pos")
+        pq, kq = _ptr(q, self.N, "f8", "q")
+        pf, kf = _ptr(out, 3 * self.N, "f8", "out", out=True)
         e = ctypes.c_double()
         _check(self._lib.fmm_forces(self._h, pp, pq, pf, ctypes.byref(e) if with_energy else None), "fmm_forces")
         return out, (e.value if with_energy else None)
@@ -250,10 +293,10 @@ class FMMPlan:
             else:
                 out = np.empty((self.N,), dtype=np.float64)
         self._bind_stream(pos, q, out, forces)
-        pp, kp = _ptr(pos)
-        pq, kq = _ptr(q)
-        po, ko = _ptr(out)
-        pf, kf = _ptr(forces)
+        pp, kp = _ptr(pos, 3 * self.N, "f8", "pos")
+        pq, kq = _ptr(q, self.N, "f8", "q")
+        po, ko = _ptr(out, self.N, "f8", "out", out=True)
+        pf, kf = _ptr(forces, 3 * self.N, "f8", "forces", out=True)
         e = ctypes.c_double()
         _check(self._lib.fmm_potentials(self._h, pp, pq, po, pf, ctypes.byref(e) if with_energy else None),
                "fmm_potentials")
@@ -261,9 +304,9 @@ class FMMPlan:
 
     def solute_solvent_energy(self, pos, q, is_solute):
         self._bind_stream(pos, q, is_solute)
-        pp, kp = _ptr(pos)
-        pq, kq = _ptr(q)
-        ps, ks = _ptr(is_solute)
+        pp, kp = _ptr(pos, 3 * self.N, "f8", "pos")
+        pq, kq = _ptr(q, self.N, "f8", "q")
+        ps, ks = _ptr(is_solute, self.N, "u1", "is_solute")
         e = ctypes.c_double()
         u = UVTerms()
         _check(self._lib.fmm_solute_solvent_energy(self._h, pp, pq, ps, ctypes.byref(e), ctypes.byref(u)),
@@ -326,16 +369,18 @@ class FMMBatch:
 
     def lambda_energies(self, pos, q, is_solute, lambda_c=None):
         n = self.n
-        keep = list(pos) + list(q) + list(is_solute)
-        arr = lambda xs: (ctypes.c_void_p * n)(*[ctypes.c_void_p(x.data_ptr()) for x in xs])
-        P, Q, S = arr(pos), arr(q), arr(is_solute)
+        Ns = [int(v) for v in self._N]
+        P, kp = _batch_ptrs(pos, [3 * v for v in Ns], "f8", "pos")
+        Q, kq = _batch_ptrs(q, Ns, "f8", "q")
+        S, ks = _batch_ptrs(is_solute, Ns, "u1", "is_solute")
         lam = None if lambda_c is None else np.ascontiguousarray(lambda_c, np.float64)
+        if lam is not None and lam.size < n:
+            raise ValueError(f"lambda_c: {lam.size} values for {n} boxes")
         out = {k: np.zeros(n) for k in ("e_total", "e_uv", "v_lambda", "dv_dlambda")}
         _check(self._lib.fmm_batch_lambda_energies(self._h, P, Q, S, None if lam is None else lam.ctypes.data,
                                                    out["e_total"].ctypes.data, out["e_uv"].ctypes.data,
                                                    out["v_lambda"].ctypes.data, out["dv_dlambda"].ctypes.data),
                "fmm_batch_lambda_energies")
-        del keep
         return out
 
     def info(self, i: int):
