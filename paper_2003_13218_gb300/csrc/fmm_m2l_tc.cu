@@ -30,11 +30,20 @@
 // stages still fit twice in shared memory and move in half as many requests),
 // but the MMAs stop at K = (p+1)^2 padded to 16.
 //
+// Degree grading (fp16 split, FMM_OPT_M2L_GRADE = D2 | D1 << 8).  The smaller
+// product terms matter less for the higher input degrees: a K chunk whose
+// lowest degree is >= D1 takes the one product x0 y0 (two such chunks share a
+// pipeline stage), and in a 3-product chunk the K16 steps whose lowest degree
+// reaches D2 drop x1 y0 (one compile-time MMA sequence per split point).  The
+// defaults D2 = 4, D1 = 8 give 16 K16 MMA steps per offset at p = 12 instead
+// of 33.
+//
 // Accumulation.  The tensor core's FP32 accumulation rounds with a bias, which
 // over thousands of MMAs into one accumulator shows up at the 1e-5 level.  So
-// each offset's products go into a fresh TMEM accumulator (two, alternating),
-// and the epilogue warps drain it and add it to the row held in FP32 registers
-// (round to nearest) while the tensor core works on the next offset.
+// the products of a short run of offsets (FMM_OPT_M2L_ACC_GROUP, default 2) go
+// into a fresh TMEM accumulator (two, alternating), and the epilogue warps
+// drain it and add it to the row held in FP32 registers (round to nearest)
+// while the tensor core works on the next run.
 //
 // Roles (6 warps): warp 0 lane 0 issues TMA loads into a 2..6-stage ring, warp 1
 // lane 0 issues tcgen05.mma, warps 2..5 drain TMEM (warp w reads TMEM lanes
