@@ -188,7 +188,7 @@ fmm_status fmm_plan_create(double box, int64_t N, int depth, int p, fmm_plan *ou
 
 /* Set an option (see FMM_OPT_*).  Changing WS, PRECISION, KAPPA or M2L_SPLIT
  * rebuilds the plan's tables.  FMM_ERR_INVALID_ARG for unknown keys or bad
- * values, FMM_ERR_UNSUPPORTED for values this build does not provide. */
+ * values, FMM_ERR_UNSUPPORTED for values this library does not provide. */
 fmm_status fmm_plan_set_option(fmm_plan plan, int key, int64_t ival, double dval);
 
 /*

@@ -630,7 +630,7 @@ const char *fmm_status_string(fmm_status s)
     case FMM_ERR_OOM: return "out of memory";
     case FMM_ERR_TIMEOUT: return "device wait timed out";
     case FMM_ERR_INTERNAL: return "internal consistency check failed";
-    case FMM_ERR_UNSUPPORTED: return "option value not supported by this build";
+    case FMM_ERR_UNSUPPORTED: return "option value not supported by this library";
     default: return "unknown status";
     }
 }
